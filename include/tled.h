@@ -1,0 +1,251 @@
+/*
+ * libtled -- coupled thermo-visco-hyperelastic total Lagrangian explicit
+ * dynamics (TLED) for soft tissue under thermal ablation, on one NVIDIA B300
+ * (sm_103a).  The method is that of Zhang, Lay, Roberts and Chauhan,
+ * arXiv 2009.10400: bioheat transfer (Pennes, Eq. 1) computed on the deformed
+ * configuration (Eqs. 5-6), thermal expansion through the multiplicative
+ * split F = F_elas F_ther (Eqs. 7-11), a transversely isotropic
+ * visco-hyperelastic law (Table 5, Prony recurrence of Section 4.3), explicit
+ * Euler for temperature (Eq. 20) and central differences for displacement
+ * (Eq. 27), on one-point hexahedra (H8, Eqs. 18, 25) or linear tetrahedra
+ * (T4, Eqs. 19, 26), plus an Arrhenius damage integral (Section 7).
+ *
+ * Conventions
+ *  - Every call returns an int status: TLED_OK (0) or a negative TLED_E_*
+ *    code.  Nothing throws across this boundary.  tled_last_error() gives a
+ *    one-line detail (offending element / node ids are 0-based, in the
+ *    caller's numbering).
+ *  - SI units; temperatures in degrees C; indices int32; floating inputs are
+ *    float64 and are copied at call time (the library keeps no caller
+ *    pointer).  The device computes in FP32 with compensated (float-float)
+ *    accumulation of nodal displacement and temperature.
+ *  - Device memory: the library never allocates device memory.  After the
+ *    set-up calls, tled_workspace_size() reports how many bytes it needs; the
+ *    caller passes a device buffer of at least that size (256-byte aligned)
+ *    to tled_init() and keeps it alive until tled_destroy().
+ *  - Streams: all device work is enqueued on the stream given to
+ *    tled_create() (NULL = the legacy default stream).  Calls that return
+ *    host data synchronise that stream.
+ *  - A context is not thread-safe; distinct contexts are independent.
+ *
+ * Call order:  create -> set_mesh -> set_material -> [set_bcs] ->
+ *   [set_heat_sources] -> [set_params] -> workspace_size -> init ->
+ *   { step, sync, get_*, set_state, set_heat_sources, save/load } -> destroy.
+ */
+#ifndef TLED_H
+#define TLED_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TLED_VERSION 1
+
+/* status codes */
+#define TLED_OK 0
+#define TLED_E_ARG (-1)      /* bad argument: NULL pointer, size or value out of range */
+#define TLED_E_MESH (-2)     /* connectivity index out of range, or det J0 <= 0 */
+#define TLED_E_STATE (-3)    /* call out of order (e.g. step before init) */
+#define TLED_E_CUDA (-4)     /* a CUDA runtime call failed */
+#define TLED_E_UNSTABLE (-5) /* NaN/Inf in the nodal state (time step too large?) */
+#define TLED_E_INVERTED (-6) /* an element reached J <= 0 */
+#define TLED_E_TIMEOUT (-7)  /* a bounded device wait ran out */
+#define TLED_E_NOMEM (-8)    /* workspace smaller than tled_workspace_size() */
+#define TLED_E_FORMAT (-9)   /* checkpoint blob malformed (magic, size, checksum) */
+
+/* element types */
+#define TLED_T4 4 /* 4-node linear tetrahedron, corners 0..3, positive volume */
+#define TLED_H8 8 /* 8-node hexahedron, VTK corner order, one-point centroid rule */
+
+/* where a read-back goes */
+#define TLED_HOST 0
+#define TLED_DEVICE 1
+
+/* tled_params.flags */
+#define TLED_EXPANSION (1u << 0)   /* thermal expansion split, Eqs. (7)-(11) */
+#define TLED_TEMP_DEP (1u << 1)    /* c(T), k(T) linear in T (Table 5) */
+#define TLED_COMPENSATED (1u << 2) /* float-float accumulation of u and T */
+
+/* boundary mask bits (per node) */
+#define TLED_FIX_X 1u
+#define TLED_FIX_Y 2u
+#define TLED_FIX_Z 4u
+#define TLED_FIX_T 8u
+
+/* Uniform material of the tissue.  Mechanics: Table 5's transversely
+ * isotropic neo-Hookean law Psi = mu/2 (I1b - 3) + kappa/2 (J - 1)^2 +
+ * k1/(2 k2) [exp(k2 (I4b - 1)^2) - 1] (k2 = 0: the quadratic term
+ * k1/2 (I4b - 1)^2 of Table 5, eta_a = k1); Prony series of the generalised
+ * Maxwell model (Section 2.2).  Heat: Pennes, Eq. (1). */
+typedef struct tled_material {
+    double rho;           /* density, kg/m^3 */
+    double mu, kappa;     /* shear and bulk modulus, Pa */
+    double k1, k2;        /* fibre stiffness Pa, fibre exponent (dimensionless) */
+    double a0[3];         /* unit fibre direction in the reference configuration */
+    int32_t n_prony;      /* number of Prony terms, 0..4 */
+    int32_t pad;
+    double prony_g[4];    /* phi_i, relative moduli */
+    double prony_tau[4];  /* tau_i, s */
+    double alpha;         /* isotropic thermal expansion, 1/K (Eq. 11) */
+    double k;             /* thermal conductivity at T_ref, W/(m K) */
+    double c;             /* specific heat at T_ref, J/(kg K) */
+    double beta_k;        /* relative slope of k(T), 1/K (used with TLED_TEMP_DEP) */
+    double beta_c;        /* relative slope of c(T), 1/K (used with TLED_TEMP_DEP) */
+    double T_ref;         /* temperature at which k and c are given, C */
+    double wb_cb;         /* perfusion w_b c_b, W/(m^3 K) */
+    double Qm;            /* metabolic heat, W/m^3 */
+    double T0;            /* initial and stress-free temperature, C */
+    double Ta;            /* arterial blood temperature, C */
+    double lnA;           /* natural log of the Arrhenius frequency factor, ln(1/s) */
+    double Ea;            /* Arrhenius activation energy, J/mol */
+} tled_material;
+
+/* A Gaussian volumetric heat source Q(x, t) = power exp(-|x - c(t)|^2 / (2 sigma^2))
+ * with c(t) = c0 + vel t, active for t_on <= t < t_off; x is the current
+ * nodal position X + u(t). */
+typedef struct tled_source {
+    double c0[3], vel[3];
+    double sigma;  /* m */
+    double power;  /* peak density, W/m^3 */
+    double t_on, t_off;
+} tled_source;
+
+typedef struct tled_params {
+    double dt;          /* time step, s; 0 = dt_safety * stable step */
+    double dt_safety;   /* fraction of the stable step used when dt = 0 (default 0.8) */
+    double gamma;       /* mass-proportional damping D = gamma M, 1/s (Eq. 21) */
+    double mass_scale;  /* mechanical mass multiplier >= 1 (1 = none) */
+    double kappa_hg;    /* H8 hourglass coefficient (default 0.1) */
+    double kappa_hgT;   /* H8 thermal hourglass coefficient (default 0.1) */
+    uint32_t flags;     /* TLED_EXPANSION | TLED_TEMP_DEP | TLED_COMPENSATED */
+    int32_t tile_elems; /* elements per tile, 0 = default (H8 512, T4 1024) */
+} tled_params;
+
+typedef struct tled_stats {
+    int64_t step;           /* steps taken since t = 0 or the last set_state */
+    double t, dt;           /* current time and time step, s */
+    double T_max, T_min;    /* nodal temperature extrema, C */
+    double u_max;           /* max nodal |u|, m */
+    double damage_volume;   /* sum of lumped volumes with Omega >= 1, m^3 */
+    double heat_content;    /* sum_i C_i (T_i - T0), J (thermal mass at T_ref) */
+    double kinetic_energy;  /* sum_i 1/2 m_i |v_i|^2, J (mechanical, mass-scaled) */
+    uint32_t status;        /* device status bits (0 = healthy) */
+    int32_t pad;
+} tled_stats;
+
+typedef struct tled_ctx tled_ctx;
+
+/* Library version (TLED_VERSION). */
+int tled_version(void);
+/* Static text for a status code. */
+const char *tled_status_string(int code);
+
+/* Create a context on CUDA device `device`; all work goes to `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  *out receives the context.
+ * device = -1 makes a host-only context: set-up, validation, planning and
+ * tled_workspace_size() work without a GPU; tled_init() then fails with
+ * E_STATE.  Errors: E_ARG (out NULL), E_CUDA (device not usable). */
+int tled_create(tled_ctx **out, int device, void *cuda_stream);
+/* Destroy a context (and its CUDA graphs).  Does not free the workspace. */
+int tled_destroy(tled_ctx *ctx);
+/* Last error detail of the context (never NULL; "" if none). */
+const char *tled_last_error(const tled_ctx *ctx);
+
+/* Mesh (total Lagrangian reference configuration, Section 4.1).
+ * elem_type: TLED_T4 or TLED_H8.  X0: [n_nodes][3] host float64.  conn:
+ * [n_elems][elem_type] host int32, 0-based.  Errors: E_ARG, E_MESH (index out
+ * of range or det J0 <= 0 -- the detail names the element). */
+int tled_set_mesh(tled_ctx *ctx, int elem_type, int64_t n_nodes, const double *X0, int64_t n_elems,
+                  const int32_t *conn);
+
+/* Material.  m: uniform values.  per_elem: optional host float64
+ * [n_elems][6] = (mu, kappa, k1, k2, k, alpha) per element, overriding the
+ * uniform ones.  fibre: optional host float64 [n_elems][3] unit fibre
+ * directions.  Errors: E_ARG (NaN/negative moduli, n_prony > 4), E_STATE
+ * (no mesh). */
+int tled_set_material(tled_ctx *ctx, const tled_material *m, const double *per_elem, const double *fibre);
+
+/* Boundary conditions.  mask: host uint8 [n_nodes] of TLED_FIX_* bits (a
+ * fixed displacement component follows ubar; TLED_FIX_T holds the node's
+ * temperature).  ubar: optional host float64 [n_nodes][3], the prescribed
+ * displacement reached after ramp_time (linear ramp; 0 = at once); NULL
+ * means zero.  The exterior is otherwise adiabatic and traction-free. */
+int tled_set_bcs(tled_ctx *ctx, const uint8_t *mask, const double *ubar, double ramp_time);
+
+/* Heat sources (n <= 16).  May be called again after init to change the
+ * sources (enqueued on the stream; takes effect at the next step). */
+int tled_set_heat_sources(tled_ctx *ctx, int32_t n, const tled_source *s);
+
+/* Solver parameters.  p NULL = defaults (auto dt at 0.8, no damping, no mass
+ * scaling, hourglass 0.1/0.1, expansion + compensation on). */
+int tled_set_params(tled_ctx *ctx, const tled_params *p);
+
+/* Bytes of device workspace tled_init() needs for the current set-up. */
+int tled_workspace_size(tled_ctx *ctx, int64_t *bytes);
+
+/* Precompute (shape-function derivatives, volumes, lumped masses, stable
+ * step, tiling) and upload into the caller's device buffer; zero state at
+ * T = T0.  Synchronises the stream.  Errors: E_NOMEM, E_STATE, E_CUDA. */
+int tled_init(tled_ctx *ctx, void *dev_workspace, int64_t bytes);
+
+/* The time step in use (after init) and the two stable-step bounds
+ * (mechanical CFL and thermal Gershgorin, before the safety factor). */
+int tled_get_dt(tled_ctx *ctx, double *dt, double *dt_mech, double *dt_thermal);
+
+/* Enqueue n explicit coupled steps (element pass, deterministic node gather,
+ * nodal updates of u, T and damage).  Asynchronous: device faults such as
+ * NaN or inversion are reported by the next tled_sync(). */
+int tled_step(tled_ctx *ctx, int64_t n);
+
+/* Wait for the stream; return TLED_OK, or E_UNSTABLE / E_INVERTED if the
+ * device flagged the state (the detail names the first node / element). */
+int tled_sync(tled_ctx *ctx);
+
+/* Read-back in the caller's node order.  where = TLED_HOST: out is host
+ * memory and the call synchronises; TLED_DEVICE: out is device memory and
+ * the copy is only enqueued.
+ *   displacement: [n_nodes][3] float64, m
+ *   temperature:  [n_nodes]    float64, C
+ *   damage:       [n_nodes]    float64, fraction 1 - exp(-Omega) */
+int tled_get_displacement(tled_ctx *ctx, double *out, int where);
+int tled_get_temperature(tled_ctx *ctx, double *out, int where);
+int tled_get_damage(tled_ctx *ctx, double *out, int where);
+
+/* Overwrite the full state from host float64 arrays (caller order):
+ * u [n][3], v [n][3] (velocity at t - dt/2), T [n], Omega [n], and visc
+ * [n_elems][n_prony][6] (xx,yy,zz,xy,yz,xz; NULL = zero), at time t after
+ * `step` steps.  Synchronises. */
+int tled_set_state(tled_ctx *ctx, const double *u, const double *v, const double *T, const double *Omega,
+                   const double *visc, double t, int64_t step);
+/* Read the full state into host float64 arrays (any pointer may be NULL). */
+int tled_get_state(tled_ctx *ctx, double *u, double *v, double *T, double *Omega, double *visc, double *t,
+                   int64_t *step);
+
+/* Diagnostic timing: enqueue n steps with the kernels launched one by one (no
+ * graph) and CUDA events around each launch on the context stream; ms[0]
+ * receives the summed device time of the tile kernel (element pass,
+ * in-tile gather, interior-node update), ms[1] that of the shared-node
+ * kernel.  The steps are real (the state advances).  Synchronises. */
+int tled_step_timed(tled_ctx *ctx, int64_t n, double *ms);
+
+/* Plan summary after tled_workspace_size(): info[0] tiles, [1] interior
+ * nodes, [2] shared nodes, [3] partial slots, [4] workspace bytes, [5]
+ * element type. */
+int tled_plan_info(tled_ctx *ctx, int64_t *info);
+
+/* Scalar diagnostics, reduced on the device in FP64 in a fixed order
+ * (deterministic).  Synchronises. */
+int tled_get_stats(tled_ctx *ctx, tled_stats *s);
+
+/* Checkpoint: serialise the exact device state (bitwise) with a header and
+ * checksum.  Call with buf NULL to get *bytes; then with a buffer of that
+ * size.  load verifies magic, sizes, a hash of the set-up and the checksum
+ * (E_FORMAT otherwise). */
+int tled_save_state(tled_ctx *ctx, void *buf, int64_t *bytes);
+int tled_load_state(tled_ctx *ctx, const void *buf, int64_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

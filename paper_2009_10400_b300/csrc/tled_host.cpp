@@ -1,0 +1,344 @@
+// Host-side set-up of libtled: reference geometry, lumped masses, the stable
+// time step, and the tiling/renumbering plan that lets one CTA gather element
+// contributions into nodes in a fixed order without float atomics.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "tled_internal.h"
+
+namespace tled {
+
+// Natural-coordinate derivatives of the shape functions at the single
+// integration point.  H8 (VTK order): dN_a/dxi = s_a / 8 at the centroid with
+// corner signs s_a (Eqs. 18, 25: one-point rule).  T4: N = (1-xi-eta-zeta,
+// xi, eta, zeta), constant derivatives (Eqs. 19, 26).
+static const double kH8Sign[8][3] = {{-1, -1, -1}, {1, -1, -1}, {1, 1, -1}, {-1, 1, -1},
+                                     {-1, -1, 1},  {1, -1, 1},  {1, 1, 1},  {-1, 1, 1}};
+static const double kT4Deriv[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+static inline double nat_deriv(int npe, int a, int k) {
+    return npe == 8 ? kH8Sign[a][k] * 0.125 : kT4Deriv[a][k];
+}
+
+// Reference Jacobian J0 = sum_a X_a (x) dN_a/dxi, its inverse, and the element
+// volume (8 det J0 for H8, det J0 / 6 for T4).  Returns false if det J0 <= 0.
+bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V) {
+    double J[9] = {0};
+    for (int a = 0; a < npe; a++)
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) J[3 * i + j] += X[3 * (int64_t)cn[a] + i] * nat_deriv(npe, a, j);
+    double c00 = J[4] * J[8] - J[5] * J[7];
+    double c01 = J[5] * J[6] - J[3] * J[8];
+    double c02 = J[3] * J[7] - J[4] * J[6];
+    double det = J[0] * c00 + J[1] * c01 + J[2] * c02;
+    if (!(det > 0.0)) return false;
+    double id = 1.0 / det;
+    Jinv[0] = c00 * id;
+    Jinv[1] = (J[2] * J[7] - J[1] * J[8]) * id;
+    Jinv[2] = (J[1] * J[5] - J[2] * J[4]) * id;
+    Jinv[3] = c01 * id;
+    Jinv[4] = (J[0] * J[8] - J[2] * J[6]) * id;
+    Jinv[5] = (J[2] * J[3] - J[0] * J[5]) * id;
+    Jinv[6] = c02 * id;
+    Jinv[7] = (J[1] * J[6] - J[0] * J[7]) * id;
+    Jinv[8] = (J[0] * J[4] - J[1] * J[3]) * id;
+    *V = npe == 8 ? 8.0 * det : det / 6.0;
+    return true;
+}
+
+// dh_a/dX_j = sum_k dN_a/dxi_k (J0^-1)_kj
+static void shape_gradients(int npe, const double Jinv[9], double B[8][3]) {
+    for (int a = 0; a < npe; a++)
+        for (int j = 0; j < 3; j++) {
+            double s = 0;
+            for (int k = 0; k < 3; k++) s += nat_deriv(npe, a, k) * Jinv[3 * k + j];
+            B[a][j] = s;
+        }
+}
+
+// H8 hourglass base vectors at the corners: xi eta, eta zeta, xi zeta, xi eta zeta
+static inline double hg_h(int a, int al) {
+    const double *s = kH8Sign[a];
+    return al == 0 ? s[0] * s[1] : al == 1 ? s[1] * s[2] : al == 2 ? s[0] * s[2] : s[0] * s[1] * s[2];
+}
+
+static double cross_norm_half(const double *d1, const double *d2) {
+    double c0 = d1[1] * d2[2] - d1[2] * d2[1];
+    double c1 = d1[2] * d2[0] - d1[0] * d2[2];
+    double c2 = d1[0] * d2[1] - d1[1] * d2[0];
+    return 0.5 * std::sqrt(c0 * c0 + c1 * c1 + c2 * c2);
+}
+
+// Stable-step reading: dt_mech = min_e L_e / c_d with L_e = V / A_max (H8) or
+// the minimum altitude 3 V / A_max (T4), c_d = sqrt((kappa + 4 mu / 3 + 4 k1) /
+// (rho * mass_scale)); dt_th = min_i 2 C_i / (sum over incident elements of
+// the absolute row sums of the element conduction matrix at k_max, plus the
+// perfusion conductance).  Per-element moduli come from `mat6` ([ne][6], caller
+// order) when given.
+void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const tled_material &m,
+               const double *mat6, const tled_params &p, double *dt_mech, double *dt_th) {
+    static const int HF[6][4] = {{0, 1, 2, 3}, {4, 5, 6, 7}, {0, 1, 5, 4}, {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}};
+    static const int TF[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+    const bool td = (p.flags & TLED_TEMP_DEP) != 0;
+    const double kfac = td ? std::max(1.0, 1.0 + m.beta_k * (90.0 - m.T_ref)) : 1.0;
+    const double cfac = td ? std::min(1.0, 1.0 + m.beta_c * (90.0 - m.T_ref)) : 1.0;
+    std::vector<double> row(nn, 0.0), Vn(nn, 0.0);
+    double dtm = INFINITY;
+    for (int64_t e = 0; e < ne; e++) {
+        const int32_t *cn = conn + e * npe;
+        double Jinv[9], V;
+        element_geometry(npe, X, cn, Jinv, &V);
+        double B[8][3];
+        shape_gradients(npe, Jinv, B);
+        const double *P[8];
+        for (int a = 0; a < npe; a++) P[a] = X + 3 * (int64_t)cn[a];
+        double Amax = 0;
+        if (npe == 8) {
+            for (auto &f : HF) {
+                double d1[3], d2[3];
+                for (int j = 0; j < 3; j++) {
+                    d1[j] = P[f[2]][j] - P[f[0]][j];
+                    d2[j] = P[f[3]][j] - P[f[1]][j];
+                }
+                Amax = std::max(Amax, cross_norm_half(d1, d2));
+            }
+        } else {
+            for (auto &f : TF) {
+                double d1[3], d2[3];
+                for (int j = 0; j < 3; j++) {
+                    d1[j] = P[f[1]][j] - P[f[0]][j];
+                    d2[j] = P[f[2]][j] - P[f[0]][j];
+                }
+                Amax = std::max(Amax, cross_norm_half(d1, d2));
+            }
+        }
+        const double mu = mat6 ? mat6[6 * e + 0] : m.mu;
+        const double kap = mat6 ? mat6[6 * e + 1] : m.kappa;
+        const double k1 = mat6 ? mat6[6 * e + 2] : m.k1;
+        const double kc = mat6 ? mat6[6 * e + 4] : m.k;
+        const double L = (npe == 8 ? 1.0 : 3.0) * V / Amax;
+        const double cd = std::sqrt((kap + 4.0 * mu / 3.0 + 4.0 * k1) / (m.rho * p.mass_scale));
+        dtm = std::min(dtm, L / cd);
+        // element conduction matrix at F = I, k_max, plus the thermal hourglass term
+        const double kmax = kc * kfac;
+        double G[8][4] = {{0}};
+        double BB = 0;
+        if (npe == 8) {
+            for (int a = 0; a < 8; a++)
+                for (int j = 0; j < 3; j++) BB += B[a][j] * B[a][j];
+            for (int al = 0; al < 4; al++) {
+                double c[3] = {0, 0, 0};
+                for (int b = 0; b < 8; b++)
+                    for (int j = 0; j < 3; j++) c[j] += hg_h(b, al) * P[b][j];
+                for (int a = 0; a < 8; a++) G[a][al] = hg_h(a, al) - (c[0] * B[a][0] + c[1] * B[a][1] + c[2] * B[a][2]);
+            }
+        }
+        const double khgT = p.kappa_hgT * V * BB / 8.0;
+        for (int a = 0; a < npe; a++) {
+            double rs = 0;
+            for (int b = 0; b < npe; b++) {
+                double K = V * kmax * (B[a][0] * B[b][0] + B[a][1] * B[b][1] + B[a][2] * B[b][2]);
+                if (npe == 8)
+                    K += kmax * khgT * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2] + G[a][3] * G[b][3]);
+                rs += std::fabs(K);
+            }
+            row[cn[a]] += rs;
+            Vn[cn[a]] += V / npe;
+        }
+    }
+    double dtt = INFINITY;
+    for (int64_t i = 0; i < nn; i++) {
+        const double r = row[i] + m.wb_cb * Vn[i];
+        const double C = m.rho * m.c * Vn[i] * cfac;
+        if (r > 0) dtt = std::min(dtt, 2.0 * C / r);
+    }
+    *dt_mech = dtm;
+    *dt_th = dtt;
+}
+
+// ---------------------------------------------------------------------------
+// tiling plan
+// ---------------------------------------------------------------------------
+static inline uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+
+int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, int tile_elems, Plan &p,
+               std::string &err) {
+    p = Plan();
+    p.npe = npe;
+    p.nn = nn;
+    p.ne = ne;
+    if (tile_elems <= 0) tile_elems = npe == 8 ? 512 : 1024;
+    tile_elems = std::min(tile_elems, kMaxSlots / npe);
+    // --- Morton order of element centroids
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < nn; i++)
+        for (int j = 0; j < 3; j++) {
+            lo[j] = std::min(lo[j], X[3 * i + j]);
+            hi[j] = std::max(hi[j], X[3 * i + j]);
+        }
+    double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+    std::vector<uint64_t> key(ne);
+    for (int64_t e = 0; e < ne; e++) {
+        double c[3] = {0, 0, 0};
+        for (int a = 0; a < npe; a++)
+            for (int j = 0; j < 3; j++) c[j] += X[3 * (int64_t)conn[e * npe + a] + j];
+        uint64_t k = 0;
+        for (int j = 0; j < 3; j++) {
+            double q = (c[j] / npe - lo[j]) / ext;
+            uint64_t iq = (uint64_t)std::min(std::max(q, 0.0) * 2097151.0, 2097151.0);
+            k |= spread3(iq) << j;
+        }
+        key[e] = k;
+    }
+    p.elem_old.resize(ne);
+    std::iota(p.elem_old.begin(), p.elem_old.end(), 0);
+    std::stable_sort(p.elem_old.begin(), p.elem_old.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+
+    // --- cut tiles: at most tile_elems elements and kMaxLocal distinct nodes
+    std::vector<int32_t> mark(nn, -1);
+    std::vector<int32_t> tile_begin;
+    int n_local = 0, n_in = 0, t = -1;
+    for (int64_t i = 0; i < ne; i++) {
+        const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
+        int fresh = 0;
+        if (t >= 0)
+            for (int a = 0; a < npe; a++) fresh += (mark[cn[a]] != t);
+        if (t < 0 || n_in == tile_elems || n_local + fresh > kMaxLocal) {
+            t++;
+            tile_begin.push_back((int32_t)i);
+            n_local = 0;
+            n_in = 0;
+        }
+        for (int a = 0; a < npe; a++)
+            if (mark[cn[a]] != t) {
+                mark[cn[a]] = t;
+                n_local++;
+            }
+        n_in++;
+    }
+    p.n_tiles = (int)tile_begin.size();
+    tile_begin.push_back((int32_t)ne);
+
+    // --- how many tiles touch each node
+    std::vector<int32_t> ntouch(nn, 0), last(nn, -1);
+    for (int tt = 0; tt < p.n_tiles; tt++)
+        for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
+            const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
+            for (int a = 0; a < npe; a++)
+                if (last[cn[a]] != tt) {
+                    last[cn[a]] = tt;
+                    ntouch[cn[a]]++;
+                }
+        }
+    for (int64_t i = 0; i < nn; i++)
+        if (ntouch[i] == 0) {
+            err = "node " + std::to_string(i) + " belongs to no element";
+            return TLED_E_MESH;
+        }
+
+    // --- numbering: interior nodes tile by tile, then shared nodes by first tile
+    p.node_new.assign(nn, -1);
+    p.tile_info.assign((size_t)p.n_tiles * kTileInfo, 0);
+    int32_t next = 0;
+    for (int tt = 0; tt < p.n_tiles; tt++) {
+        int32_t *ti = &p.tile_info[(size_t)tt * kTileInfo];
+        ti[0] = tile_begin[tt];
+        ti[1] = tile_begin[tt + 1] - tile_begin[tt];
+        ti[2] = next;
+        for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
+            const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
+            for (int a = 0; a < npe; a++)
+                if (ntouch[cn[a]] == 1 && p.node_new[cn[a]] < 0) p.node_new[cn[a]] = next++;
+        }
+        ti[3] = next - ti[2];
+    }
+    p.n_interior = next;
+    for (int tt = 0; tt < p.n_tiles; tt++)
+        for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
+            const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
+            for (int a = 0; a < npe; a++)
+                if (p.node_new[cn[a]] < 0) p.node_new[cn[a]] = next++;
+        }
+    p.n_shared = next - p.n_interior;
+    p.node_old.assign(nn, 0);
+    for (int64_t i = 0; i < nn; i++) p.node_old[p.node_new[i]] = (int32_t)i;
+
+    // --- per tile: local node lists, local connectivity, gather CSR, partial slots
+    p.conn_local.assign((size_t)ne * npe, 0);
+    p.slots.assign((size_t)ne * npe, 0);
+    std::vector<int32_t> local(nn, -1);
+    std::vector<std::vector<int32_t>> sh_slots(p.n_shared);
+    int64_t part = 0;
+    for (int tt = 0; tt < p.n_tiles; tt++) {
+        int32_t *ti = &p.tile_info[(size_t)tt * kTileInfo];
+        const int32_t e0 = ti[0], ne_t = ti[1], int_begin = ti[2], n_int = ti[3];
+        std::vector<int32_t> shared;
+        for (int64_t i = e0; i < e0 + ne_t; i++) {
+            const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
+            for (int a = 0; a < npe; a++) {
+                int32_t g = p.node_new[cn[a]];
+                if (g >= p.n_interior && local[g] != -2 - tt) {
+                    local[g] = -2 - tt;  // seen in this tile
+                    shared.push_back(g);
+                }
+            }
+        }
+        std::sort(shared.begin(), shared.end());
+        const int nl = n_int + (int)shared.size();
+        if (nl > kMaxLocal) {
+            err = "internal: tile exceeds the local node limit";
+            return TLED_E_MESH;
+        }
+        ti[4] = nl;
+        ti[5] = (int32_t)p.tile_shared.size();
+        ti[6] = (int32_t)p.rowptr.size();
+        ti[7] = (int32_t)part;
+        for (size_t j = 0; j < shared.size(); j++) {
+            p.tile_shared.push_back(shared[j]);
+            sh_slots[shared[j] - p.n_interior].push_back((int32_t)(part + (int64_t)j));
+        }
+        part += (int64_t)shared.size();
+        // local index of every node of the tile
+        std::vector<uint16_t> cnt(nl + 1, 0);
+        for (int64_t i = e0; i < e0 + ne_t; i++) {
+            const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
+            for (int a = 0; a < npe; a++) {
+                int32_t g = p.node_new[cn[a]];
+                int l;
+                if (g < p.n_interior) {
+                    l = g - int_begin;
+                } else {
+                    l = n_int + (int)(std::lower_bound(shared.begin(), shared.end(), g) - shared.begin());
+                }
+                p.conn_local[(size_t)i * npe + a] = (uint16_t)l;
+                cnt[l + 1]++;
+            }
+        }
+        for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
+        for (int l = 0; l <= nl; l++) p.rowptr.push_back(cnt[l]);
+        std::vector<uint16_t> cur(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = e0; i < e0 + ne_t; i++)
+            for (int a = 0; a < npe; a++) {
+                int l = p.conn_local[(size_t)i * npe + a];
+                p.slots[(size_t)e0 * npe + cur[l]++] = (uint16_t)((i - e0) * npe + a);
+            }
+    }
+    p.n_partials = part;
+    p.sh_rowptr.assign(p.n_shared + 1, 0);
+    for (int64_t s = 0; s < p.n_shared; s++) p.sh_rowptr[s + 1] = p.sh_rowptr[s] + (int32_t)sh_slots[s].size();
+    p.sh_list.reserve(part);
+    for (int64_t s = 0; s < p.n_shared; s++) p.sh_list.insert(p.sh_list.end(), sh_slots[s].begin(), sh_slots[s].end());
+    return TLED_OK;
+}
+
+}  // namespace tled

@@ -1,0 +1,118 @@
+// Internal declarations of libtled: device data layout, kernel arguments,
+// host-side plan.  Not part of the public C ABI (include/tled.h).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/tled.h"
+
+namespace tled {
+
+constexpr int kBlock = 256;        // threads per CTA of the tile kernel
+constexpr int kMaxLocal = 1024;    // max nodes touched by one tile (shared memory)
+constexpr int kMaxTileElems = 1024;
+constexpr int kMaxSlots = 4096;   // max element corners per tile (shared memory)
+constexpr int kMaxSources = 16;
+constexpr int kTileInfo = 8;       // ints per tile record
+
+// device status word bits
+constexpr uint32_t kStatusInverted = 1u;
+constexpr uint32_t kStatusNaN = 2u;
+constexpr uint32_t kStatusTimeout = 4u;
+
+// Host-side plan: element/node renumbering and tiling.  Elements are sorted
+// along a Morton curve and cut into tiles; a node touched by exactly one tile
+// is "interior" (updated by that tile's CTA), otherwise "shared" (its partial
+// sums go through a fixed-order second pass).
+struct Plan {
+    int npe = 0;
+    int64_t nn = 0, ne = 0;
+    std::vector<int32_t> elem_old;      // new element -> caller element
+    std::vector<int32_t> node_new;      // caller node -> new node
+    std::vector<int32_t> node_old;      // new node -> caller node
+    int64_t n_interior = 0, n_shared = 0;
+    int n_tiles = 0;
+    std::vector<int32_t> tile_info;     // [n_tiles][8]: e0, ne, int_begin, n_int, n_local, sh_off, row_off, part_off
+    std::vector<int32_t> tile_shared;   // per tile: new ids of its shared nodes (ascending)
+    std::vector<uint16_t> conn_local;   // [ne][npe] tile-local node index
+    std::vector<uint16_t> rowptr;       // per tile: n_local + 1 offsets into the tile's slots
+    std::vector<uint16_t> slots;        // [ne*npe] (local element * npe + corner), grouped by local node
+    std::vector<int32_t> sh_rowptr;     // [n_shared + 1]
+    std::vector<int32_t> sh_list;       // partial-slot indices, ascending tile order
+    int64_t n_partials = 0;
+};
+
+// Arguments of the step kernels (passed by value).
+struct StepArgs {
+    // node arrays (new numbering)
+    float4 *xu;            // u_hi.xyz, theta_hi
+    float4 *lo;            // u_lo.xyz, theta_lo
+    float4 *vel;           // v.xyz, Omega
+    const float4 *X0;      // X.xyz, lumped volume V_i
+    const float4 *nodec;   // m_i, Cth_i, mask bits (as float bits), 0
+    const float4 *ubar;    // prescribed displacement or nullptr
+    // element arrays (new numbering, SoA with stride ne)
+    const uint16_t *conn_local;
+    const float *jinv;     // [9][ne] inverse reference Jacobian at the integration point
+    const float *V0;       // [ne]
+    const float *mat;      // [6][ne] mu, kappa, k1, k2, k, alpha  or nullptr (uniform)
+    const float *fib;      // [3][ne] or nullptr (uniform)
+    float *visc;           // [n_prony*6][ne]
+    int64_t ne;
+    // tiles
+    const int *tile_info;
+    const int *tile_shared;
+    const uint16_t *rowptr;
+    const uint16_t *slots;
+    float4 *partials;
+    const int *sh_rowptr;
+    const int *sh_list;
+    int64_t n_interior, n_shared;
+    // sources and time
+    const double *src;     // [kMaxSources][10]
+    const int *n_src;      // device scalar (sources may change between chunks)
+    const double *time_base;
+    const int64_t *step_base;
+    unsigned int *status;  // [4]: bits, first bad element (new id), first bad node (new id), spare
+    // scalars
+    double dt;
+    float dtf;
+    float damp_a, damp_b;  // v+ = damp_a v + damp_b (-f/m) with damp_a = (1-g dt/2)/(1+g dt/2), damp_b = dt/(1+g dt/2)
+    float mu, kappa, k1, k2, kc, alpha;   // uniform material
+    float a0x, a0y, a0z;
+    int n_prony;
+    float pr_a[4], pr_b[4];               // Prony coefficients dt phi/(dt+tau), tau/(dt+tau)
+    unsigned int flags;
+    float beta_c, beta_k, Tref_m_T0;      // T_ref - T0
+    float theta_a;                        // Ta - T0
+    float wbcb, Qm;
+    float lnA, Ea_R, T0_K;                // T0 + 273.15
+    float khg, khgT;                      // kappa_hg, kappa_hgT
+    double ramp_time;
+};
+
+// kernel launchers (tled_kernels.cu)
+cudaError_t launch_tile_step(const StepArgs &a, int n_tiles, int npe, int k, cudaStream_t s);
+cudaError_t launch_shared_step(const StepArgs &a, int npe, int k, cudaStream_t s);
+cudaError_t launch_bump(double *time_base, int64_t *step_base, int K, double dt, cudaStream_t s);
+// read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction
+cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,
+                            cudaStream_t s);
+size_t tile_smem_bytes(int npe);
+cudaError_t tile_kernel_setup(int npe);
+// FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
+// damaged volume; deterministic two-stage reduction through `partials` [kStatBlocks][8].
+constexpr int kStatBlocks = 296;
+cudaError_t launch_stats(const StepArgs &a, int64_t nn, double *partials, double *out, cudaStream_t s);
+
+// host geometry and planning (tled_host.cpp)
+bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V);
+void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const tled_material &m,
+               const double *mat6, const tled_params &p, double *dt_mech, double *dt_th);
+int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, int tile_elems, Plan &p,
+               std::string &err);
+
+}  // namespace tled

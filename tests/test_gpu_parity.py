@@ -1,0 +1,186 @@
+"""Parity of the CUDA library against the FP64 oracle, element by element, on
+the same seeded inputs (relative L2 of u and theta <= 1e-4, damage fraction
+within 1e-3 absolute)."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import TOL_DAMAGE, TOL_E, compare, rel_l2, run_oracle
+from paper_2009_10400_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _tled():
+    from paper_2009_10400_b300 import tled
+    return tled
+
+
+def _gpu_run(prob, n_steps, dt, every=None, tile_elems=0):
+    tled = _tled()
+    s = tled.Solver.from_problem(prob, dt=dt, tile_elems=tile_elems)
+    snaps = []
+    every = every or n_steps
+    done = 0
+    while done < n_steps:
+        k = min(every, n_steps - done)
+        s.step(k)
+        s.sync()
+        done += k
+        snaps.append((done, s.displacement(), s.temperature(), s.damage()))
+    return s, snaps
+
+
+def _check_trajectory(prob, n_steps, every, tile_elems=0, tol_e=TOL_E):
+    m, _, ref = run_oracle(prob, n_steps, every)
+    _, got = _gpu_run(prob, n_steps, m.dt, every, tile_elems)
+    worst = {}
+    for (k, u_r, T_r, O_r), (k2, u, T, d) in zip(ref, got):
+        assert k == k2
+        c = compare(u, T, d, u_r, T_r, O_r, prob.T0)
+        for key, v in c.items():
+            worst[key] = max(worst.get(key, 0.0), v)
+        assert c["e_u"] <= tol_e, (k, c)
+        assert c["e_theta"] <= tol_e, (k, c)
+        assert c["d_abs"] <= TOL_DAMAGE, (k, c)
+    return worst
+
+
+def test_cube_h8_2000_steps_matches_oracle():
+    """5 cm cube of 8^3 H8, 2000 steps at the stable step, oracle every 500."""
+    prob = W.cube_h8(n=8)
+    w = _check_trajectory(prob, 2000, 500)
+    print("cube_h8", w)
+
+
+def test_cube_t4_ragged_tiles_matches_oracle():
+    """Kuhn-split jittered tet cube (1296 tets: two tiles, the second ragged),
+    per-element material noise and vMF fibres, moving source."""
+    prob = W.cube_t4(n=6)
+    w = _check_trajectory(prob, 600, 200)
+    print("cube_t4", w)
+
+
+def test_block_h8_noise_many_tiles_matches_oracle():
+    """16^3 H8 block (8 tiles, interior and shared nodes) with +-10% material noise."""
+    prob = W.block_h8(n=16, h=3e-3)
+    w = _check_trajectory(prob, 400, 200)
+    print("block_h8_16", w)
+
+
+def test_small_tiles_exercise_shared_nodes():
+    """Tiny tiles (37 elements) make most nodes shared between tiles: the
+    second-pass gather must give the same answer."""
+    prob = W.cube_h8(n=6, jitter=0.2)
+    w = _check_trajectory(prob, 300, 100, tile_elems=37)
+    print("small tiles", w)
+
+
+def test_ellipsoid_t4_matches_oracle():
+    """Coarse seeded Delaunay ellipsoid 'liver' with vMF fibres and a moving source."""
+    prob = W.ellipsoid_t4(spacing=9e-3)
+    w = _check_trajectory(prob, 300, 100)
+    print("ellipsoid", prob.ne, w)
+
+
+def test_auto_dt_matches_oracle():
+    tled = _tled()
+    for prob in (W.cube_h8(n=8), W.cube_t4(n=4), W.ellipsoid_t4(spacing=1.2e-2)):
+        m = oracle.OracleModel(prob)
+        s = tled.Solver.from_problem(prob)
+        dt, dtm, dtt = s.get_dt()
+        np.testing.assert_allclose(dt, m.dt, rtol=1e-12)
+        np.testing.assert_allclose(dtm, m.dt_mech, rtol=1e-12)
+        np.testing.assert_allclose(dtt, m.dt_th, rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["h8", "t4"])
+def test_single_step_from_random_state(kind):
+    """One step from a seeded mid-run state (large u, theta, Prony state):
+    every node's new u, T and Omega against the oracle."""
+    tled = _tled()
+    prob = W.block_h8(n=10, h=4e-3) if kind == "h8" else W.cube_t4(n=5)
+    st = W.random_state(prob, 17)
+    m = oracle.OracleModel(prob)
+    s = tled.Solver.from_problem(prob, dt=m.dt, tile_elems=100)
+    s.set_state(st["u"], st["v"], st["T"], st["Omega"], st["visc"], t=0.01, step=5)
+    s.step(1)
+    s.sync()
+    os_ = m.state_from(**st, t=0.01, step=5)
+    m.step(os_, 1)
+    u, T, d = s.displacement(), s.temperature(), s.damage()
+    np.testing.assert_allclose(u, os_.u, rtol=0, atol=2e-6 * np.abs(os_.u).max())
+    np.testing.assert_allclose(T, os_.T, rtol=0, atol=2e-6 * np.abs(os_.T - 37).max())
+    np.testing.assert_allclose(d, oracle.damage_fraction(os_.Omega), rtol=0, atol=1e-6)
+    g = s.get_state()
+    np.testing.assert_allclose(g["visc"], os_.visc, rtol=0, atol=1e-5 * np.abs(os_.visc).max())
+
+
+def test_deterministic_bitwise():
+    tled = _tled()
+    prob = W.block_h8(n=12, h=4e-3)
+    outs = []
+    for _ in range(2):
+        s = tled.Solver.from_problem(prob, tile_elems=64)
+        s.step(200)
+        s.sync()
+        outs.append((s.displacement(), s.temperature(), s.damage()))
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_checkpoint_resume_bitwise():
+    tled = _tled()
+    prob = W.cube_t4(n=5)
+    a = tled.Solver.from_problem(prob)
+    a.step(300)
+    a.sync()
+    ref = (a.displacement(), a.temperature(), a.damage())
+    b = tled.Solver.from_problem(prob)
+    b.step(150)
+    blob = b.save_state()
+    c = tled.Solver.from_problem(prob)
+    c.load_state(blob)
+    c.step(150)
+    c.sync()
+    got = (c.displacement(), c.temperature(), c.damage())
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    bad = bytearray(blob)
+    bad[-1] ^= 0xFF
+    with pytest.raises(tled.TledError) as ei:
+        c.load_state(bytes(bad))
+    assert ei.value.code == tled.E_FORMAT
+
+
+def test_stats_match_state():
+    tled = _tled()
+    prob = W.cube_h8(n=8)
+    s = tled.Solver.from_problem(prob)
+    s.step(500)
+    st = s.stats()
+    T = s.temperature()
+    u = s.displacement()
+    assert st["status"] == 0
+    np.testing.assert_allclose(st["T_max"], T.max(), rtol=1e-12)
+    np.testing.assert_allclose(st["T_min"], T.min(), rtol=1e-12)
+    np.testing.assert_allclose(st["u_max"], np.linalg.norm(u, axis=1).max(), rtol=1e-6)
+    m = oracle.OracleModel(prob)
+    np.testing.assert_allclose(st["heat_content"], (m.Cth * (T - 37.0)).sum(), rtol=1e-6)
+
+
+def test_inversion_is_reported():
+    """A huge prescribed compression of a single element inverts it; the device
+    flags the element and tled_sync reports E_INVERTED (no device trap)."""
+    tled = _tled()
+    X, conn = W.hex_grid((1, 1, 1), (0.01, 0.01, 0.01))
+    mat = W._material(1)
+    ubar = np.zeros((8, 3))
+    ubar[X[:, 2] > 0.005, 2] = -0.02  # top face pushed 2 cm below the bottom
+    mask = np.full(8, W.MASK_U, np.uint8)
+    prob = W.Problem(name="inv", npe=8, X=X, conn=conn, **mat, mask=mask, ubar=ubar, ramp_time=0.0)
+    s = tled.Solver.from_problem(prob, dt=1e-5)
+    s.step(3)
+    with pytest.raises(tled.TledError) as ei:
+        s.sync()
+    assert ei.value.code == tled.E_INVERTED

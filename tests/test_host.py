@@ -1,0 +1,130 @@
+"""CPU-only tests of the library boundary: the shared object loads and exports
+every symbol include/tled.h declares, and the host-side validation and
+planning (host-only context, device -1) behave."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2009_10400_b300 import tled
+from paper_2009_10400_b300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char \*|int64_t)\s*(tled_\w+)\s*\(", txt, re.M))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    L = tled.lib()
+    names = _declared()
+    assert len(names) >= 24
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(tled.exported_symbols()) | {"tled_version"}
+    assert L.tled_version() == 1
+
+
+def _planner(prob, **kw):
+    p = tled.HostPlanner()
+    p.set_mesh(prob.npe, prob.X, prob.conn)
+    per = np.stack([prob.mu, prob.kappa, prob.k1, prob.k2, prob.kc, prob.alpha], 1) if prob.per_element else None
+    p.set_material(tled.material_from_problem(prob), per, prob.a0 if prob.per_element else None)
+    p.set_bcs(prob.mask)
+    p.set_heat_sources(prob.sources)
+    p.set_params(**kw)
+    return p
+
+
+def test_plan_counts_structured_block():
+    prob = W.block_h8(n=16, h=3e-3)
+    p = _planner(prob)
+    info = p.plan_info()
+    # Morton order cuts 16^3 into eight 8^3 tiles of 512 elements
+    assert info["n_tiles"] == 8
+    assert info["n_interior"] + info["n_shared"] == prob.nn
+    # shared nodes are exactly those on the three internal planes i, j or k = 8
+    assert info["n_shared"] == 17 ** 3 - 16 ** 3
+    assert info["workspace"] > 0
+
+
+def test_plan_single_tile_has_no_shared_nodes():
+    prob = W.cube_h8(n=8)
+    info = _planner(prob).plan_info()
+    assert info["n_tiles"] == 1 and info["n_shared"] == 0 and info["n_interior"] == 729
+
+
+def test_plan_tile_size_parameter():
+    prob = W.cube_t4(n=4)
+    info = _planner(prob, tile_elems=50).plan_info()
+    assert info["n_tiles"] == -(-prob.ne // 50)
+
+
+def test_rejects_bad_mesh():
+    X, conn = W.hex_grid((1, 1, 1), (0.01, 0.01, 0.01))
+    p = tled.HostPlanner()
+    bad = conn.copy()
+    bad[0, 3] = 99
+    with pytest.raises(tled.TledError) as e:
+        p.set_mesh(8, X, bad)
+    assert e.value.code == tled.E_MESH
+    inv = conn[:, [4, 5, 6, 7, 0, 1, 2, 3]]  # mirrored: det J0 < 0
+    with pytest.raises(tled.TledError) as e:
+        p.set_mesh(8, X, inv)
+    assert e.value.code == tled.E_MESH and "element 0" in str(e.value)
+    with pytest.raises(tled.TledError) as e:
+        p.set_mesh(5, X, conn)
+    assert e.value.code == tled.E_ARG
+
+
+def test_rejects_unreferenced_node():
+    X, conn = W.hex_grid((1, 1, 1), (0.01, 0.01, 0.01))
+    X2 = np.vstack([X, [[1.0, 1.0, 1.0]]])
+    prob = W.cube_h8(n=1)
+    p = tled.HostPlanner()
+    p.set_mesh(8, X2, conn)
+    p.set_material(tled.material_from_problem(prob))
+    with pytest.raises(tled.TledError) as e:
+        p.workspace_size()
+    assert e.value.code == tled.E_MESH
+
+
+def test_rejects_bad_material_and_params():
+    prob = W.cube_h8(n=2)
+    p = tled.HostPlanner()
+    p.set_mesh(8, prob.X, prob.conn)
+    m = tled.material_from_problem(prob)
+    m.rho = float("nan")
+    with pytest.raises(tled.TledError) as e:
+        p.set_material(m)
+    assert e.value.code == tled.E_ARG
+    m = tled.material_from_problem(prob)
+    m.n_prony, m.prony_g[0] = 1, 1.5
+    with pytest.raises(tled.TledError):
+        p.set_material(m)
+    with pytest.raises(tled.TledError):
+        p.set_params(mass_scale=0.5)
+    with pytest.raises(tled.TledError):
+        p.set_heat_sources(np.zeros((17, 10)) + 1)
+    fib = np.tile([1.0, 1.0, 0.0], (prob.ne, 1))
+    with pytest.raises(tled.TledError):
+        p.set_material(tled.material_from_problem(prob), None, fib)
+
+
+def test_call_order_errors():
+    p = tled.HostPlanner()
+    with pytest.raises(tled.TledError) as e:
+        p.workspace_size()
+    assert e.value.code == tled.E_STATE
+    prob = W.cube_h8(n=2)
+    p2 = _planner(prob)
+    with pytest.raises(tled.TledError) as e:
+        p2.init()
+    assert e.value.code == tled.E_STATE
