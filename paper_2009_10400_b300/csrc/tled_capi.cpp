@@ -60,6 +60,7 @@ struct tled_ctx {
     double t = 0;
     uint64_t setup_hash = 0;
     std::map<int, cudaGraphExec_t> graphs;
+    int tile_ctas = 1;  // persistent grid of the tile kernel
 };
 
 namespace {
@@ -112,7 +113,7 @@ Layout make_layout(const tled_ctx *c) {
         off = align256(off + std::max<size_t>(bytes, 1));
         return o;
     };
-    const size_t nn = (size_t)c->nn, ne = (size_t)c->ne;
+    const size_t nn = (size_t)c->nn, ne = (size_t)p.ne_pad;
     L.xu = take(16 * nn);
     L.lo = take(16 * nn);
     L.vel = take(16 * nn);
@@ -192,7 +193,7 @@ inline void split_ff(double x, float &hi, float &lo) {
 
 int write_state(tled_ctx *c, const double *u, const double *v, const double *T, const double *Om, const double *visc) {
     const Plan &p = c->plan;
-    const int64_t nn = c->nn, ne = c->ne;
+    const int64_t nn = c->nn;
     std::vector<float4> xu(nn), lo(nn), vel(nn);
     for (int64_t g = 0; g < nn; g++) {
         const int64_t i = p.node_old[g];
@@ -208,11 +209,13 @@ int write_state(tled_ctx *c, const double *u, const double *v, const double *T, 
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.lo, lo.data(), 16 * nn, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.vel, vel.data(), 16 * nn, cudaMemcpyHostToDevice, c->stream));
     const int np = n_prony(c);
-    std::vector<float> vs((size_t)np * 6 * ne, 0.f);
+    const int64_t nep = p.ne_pad;
+    std::vector<float> vs((size_t)np * 6 * nep, 0.f);
     if (visc)
-        for (int64_t e = 0; e < ne; e++) {
+        for (int64_t e = 0; e < nep; e++) {
             const int64_t eo = p.elem_old[e];
-            for (int q = 0; q < np * 6; q++) vs[(size_t)q * ne + e] = (float)visc[eo * np * 6 + q];
+            if (eo < 0) continue;
+            for (int q = 0; q < np * 6; q++) vs[(size_t)q * nep + e] = (float)visc[eo * np * 6 + q];
         }
     if (np) CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.visc, vs.data(), vs.size() * 4, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -235,7 +238,7 @@ int check_status(tled_ctx *c) {
     CUDA_TRY(c, cudaMemcpyAsync(st, c->ws + c->L.status, 16, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (st[0] & tled::kStatusInverted) {
-        int64_t e = st[1] < (unsigned)c->ne ? c->plan.elem_old[st[1]] : -1;
+        int64_t e = st[1] < (unsigned)c->plan.ne_pad ? c->plan.elem_old[st[1]] : -1;
         return fail(c, TLED_E_INVERTED, "element " + std::to_string(e) + " inverted (J <= 0)");
     }
     if (st[0] & tled::kStatusNaN) {
@@ -437,13 +440,15 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     const int64_t nn = c->nn, ne = c->ne;
     const tled_material &m = c->mat;
     // --- element geometry (new order), lumped masses
-    std::vector<float> jinv(9 * ne), V0(ne);
+    const int64_t nep = p.ne_pad;
+    std::vector<float> jinv(9 * nep, 0.f), V0(nep, 0.f);
     std::vector<double> Mn(nn, 0.0), Cn(nn, 0.0), Vn(nn, 0.0);
-    for (int64_t e = 0; e < ne; e++) {
+    for (int64_t e = 0; e < nep; e++) {
         const int64_t eo = p.elem_old[e];
+        if (eo < 0) continue;  // padding slot
         double Ji[9], V;
         tled::element_geometry(npe, c->X.data(), c->conn.data() + eo * npe, Ji, &V);
-        for (int q = 0; q < 9; q++) jinv[(size_t)q * ne + e] = (float)Ji[q];
+        for (int q = 0; q < 9; q++) jinv[(size_t)q * nep + e] = (float)Ji[q];
         V0[e] = (float)V;
         for (int a = 0; a < npe; a++) {
             const int64_t i = c->conn[eo * npe + a];
@@ -460,17 +465,18 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         unsigned mk = c->mask[i] & 15u;
         float mkf;
         std::memcpy(&mkf, &mk, 4);
-        nodec[g] = make_float4((float)Mn[i], (float)Cn[i], mkf, 0.f);
+        nodec[g] = make_float4((float)(1.0 / Mn[i]), (float)(1.0 / Cn[i]), mkf, 0.f);
         if (!c->ubar.empty())
             ub[g] = make_float4((float)c->ubar[3 * i], (float)c->ubar[3 * i + 1], (float)c->ubar[3 * i + 2], 0.f);
     }
-    std::vector<float> mat(c->mat6.empty() ? 0 : 6 * ne), fib(c->fib.empty() ? 0 : 3 * ne);
-    for (int64_t e = 0; e < ne; e++) {
+    std::vector<float> mat(c->mat6.empty() ? 0 : 6 * nep, 0.f), fib(c->fib.empty() ? 0 : 3 * nep, 0.f);
+    for (int64_t e = 0; e < nep; e++) {
         const int64_t eo = p.elem_old[e];
+        if (eo < 0) continue;
         if (!mat.empty())
-            for (int q = 0; q < 6; q++) mat[(size_t)q * ne + e] = (float)c->mat6[6 * eo + q];
+            for (int q = 0; q < 6; q++) mat[(size_t)q * nep + e] = (float)c->mat6[6 * eo + q];
         if (!fib.empty())
-            for (int q = 0; q < 3; q++) fib[(size_t)q * ne + e] = (float)c->fib[3 * eo + q];
+            for (int q = 0; q < 3; q++) fib[(size_t)q * nep + e] = (float)c->fib[3 * eo + q];
     }
     // --- time step
     tled::stable_dt(npe, nn, c->X.data(), ne, c->conn.data(), m, c->mat6.empty() ? nullptr : c->mat6.data(), c->prm,
@@ -505,7 +511,6 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     if (r2) return r2;
     r2 = set_clock(c, 0.0, 0);
     if (r2) return r2;
-    CUDA_TRY(c, tled::tile_kernel_setup(npe));
     // --- kernel arguments
     StepArgs &A = c->A;
     A = StepArgs{};
@@ -521,7 +526,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.mat = c->mat6.empty() ? nullptr : dptr<float>(c, L.mat);
     A.fib = c->fib.empty() ? nullptr : dptr<float>(c, L.fib);
     A.visc = dptr<float>(c, L.visc);
-    A.ne = ne;
+    A.ne = nep;
     A.tile_info = dptr<int>(c, L.tile_info);
     A.tile_shared = dptr<int>(c, L.tile_shared);
     A.rowptr = dptr<uint16_t>(c, L.rowptr);
@@ -539,6 +544,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     const double dt = c->dt, g = c->prm.gamma;
     A.dt = dt;
     A.dtf = (float)dt;
+    A.inv_dt = (float)(1.0 / dt);
     A.damp_a = (float)((1.0 - 0.5 * g * dt) / (1.0 + 0.5 * g * dt));
     A.damp_b = (float)(dt / (1.0 + 0.5 * g * dt));
     A.mu = (float)m.mu; A.kappa = (float)m.kappa; A.k1 = (float)m.k1; A.k2 = (float)m.k2;
@@ -566,6 +572,12 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.khg = (float)c->prm.kappa_hg;
     A.khgT = (float)c->prm.kappa_hgT;
     A.ramp_time = c->ramp;
+    A.n_tiles = p.n_tiles;
+    tled::tile_smem_layout(A, npe);
+    CUDA_TRY(c, tled::tile_kernel_setup(A, npe));
+    int n_sm = 0;
+    CUDA_TRY(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    c->tile_ctas = tled::tile_grid(A, npe, n_sm);
     // set-up hash for checkpoints
     uint64_t h = fnv1a(c->X.data(), 8 * c->X.size());
     h = fnv1a(c->conn.data(), 4 * c->conn.size(), h);
@@ -594,7 +606,7 @@ static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     CUDA_TRY(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < K && e == cudaSuccess; k++) {
-        e = tled::launch_tile_step(c->A, c->plan.n_tiles, c->npe, k, c->cap);
+        e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
         if (e == cudaSuccess) e = tled::launch_shared_step(c->A, c->npe, k, c->cap);
     }
     if (e == cudaSuccess)
@@ -685,7 +697,8 @@ int tled_get_state(tled_ctx *c, double *u, double *v, double *T, double *Omega, 
     CUDA_TRY(c, cudaMemcpyAsync(lo.data(), c->ws + c->L.lo, 16 * nn, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(vel.data(), c->ws + c->L.vel, 16 * nn, cudaMemcpyDeviceToHost, c->stream));
     const int np = n_prony(c);
-    std::vector<float> vs((size_t)np * 6 * ne);
+    const int64_t nep = p.ne_pad;
+    std::vector<float> vs((size_t)np * 6 * nep);
     if (np && visc)
         CUDA_TRY(c, cudaMemcpyAsync(vs.data(), c->ws + c->L.visc, 4 * vs.size(), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -705,9 +718,10 @@ int tled_get_state(tled_ctx *c, double *u, double *v, double *T, double *Omega, 
         if (Omega) Omega[i] = vel[g].w;
     }
     if (visc && np)
-        for (int64_t e = 0; e < ne; e++) {
+        for (int64_t e = 0; e < nep; e++) {
             const int64_t eo = p.elem_old[e];
-            for (int q = 0; q < np * 6; q++) visc[eo * np * 6 + q] = vs[(size_t)q * ne + e];
+            if (eo < 0) continue;
+            for (int q = 0; q < np * 6; q++) visc[eo * np * 6 + q] = vs[(size_t)q * nep + e];
         }
     if (t) *t = c->t;
     if (step) *step = c->step;
@@ -724,7 +738,7 @@ int tled_step_timed(tled_ctx *c, int64_t n, double *ms) {
     cudaError_t err = cudaSuccess;
     for (int64_t i = 0; i < n && err == cudaSuccess; i++) {
         cudaEventRecord(ev[3 * i], c->stream);
-        err = tled::launch_tile_step(c->A, c->plan.n_tiles, c->npe, 0, c->stream);
+        err = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
         cudaEventRecord(ev[3 * i + 1], c->stream);
         if (err == cudaSuccess) err = tled::launch_shared_step(c->A, c->npe, 0, c->stream);
         cudaEventRecord(ev[3 * i + 2], c->stream);
@@ -807,7 +821,7 @@ struct CkptHeader {
 int tled_save_state(tled_ctx *c, void *buf, int64_t *bytes) {
     if (!c || !bytes) return fail(c, TLED_E_ARG, "NULL size pointer");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
-    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->ne;
+    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->plan.ne_pad;
     const int64_t payload = (int64_t)(3 * 16 * nn + 4 * nv);
     const int64_t need = (int64_t)sizeof(CkptHeader) + payload;
     if (!buf) {
@@ -846,7 +860,7 @@ int tled_load_state(tled_ctx *c, const void *buf, int64_t bytes) {
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
     if (std::memcmp(h.magic, "TLEDCKP1", 8) != 0) return fail(c, TLED_E_FORMAT, "bad checkpoint magic");
-    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->ne;
+    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->plan.ne_pad;
     const int64_t payload = (int64_t)(3 * 16 * nn + 4 * nv);
     if (h.version != TLED_VERSION || h.npe != (uint32_t)c->npe || h.nn != c->nn || h.ne != c->ne ||
         h.n_prony != n_prony(c) || h.payload != payload || bytes < (int64_t)sizeof(h) + payload)

@@ -177,8 +177,8 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     p.npe = npe;
     p.nn = nn;
     p.ne = ne;
-    if (tile_elems <= 0) tile_elems = npe == 8 ? 512 : 1024;
-    tile_elems = std::min(tile_elems, kMaxSlots / npe);
+    if (tile_elems <= 0) tile_elems = kMaxTileElems;
+    tile_elems = std::min(tile_elems, kMaxTileElems);
     // --- Morton order of element centroids
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = 0; i < nn; i++)
@@ -246,13 +246,22 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
             return TLED_E_MESH;
         }
 
-    // --- numbering: interior nodes tile by tile, then shared nodes by first tile
+    // --- numbering: interior nodes tile by tile, then shared nodes by first tile.
+    // Element slots are padded so that every tile starts at a multiple of 4
+    // (16-byte aligned bulk copies of the per-element streams).
     p.node_new.assign(nn, -1);
     p.tile_info.assign((size_t)p.n_tiles * kTileInfo, 0);
+    std::vector<int64_t> tile_pad(p.n_tiles + 1, 0);
+    for (int tt = 0; tt < p.n_tiles; tt++) tile_pad[tt + 1] = tile_pad[tt] + ((tile_begin[tt + 1] - tile_begin[tt] + 3) & ~3);
+    p.ne_pad = tile_pad[p.n_tiles];
+    if (p.ne_pad > 0x7fffffff) {
+        err = "mesh too large";
+        return TLED_E_MESH;
+    }
     int32_t next = 0;
     for (int tt = 0; tt < p.n_tiles; tt++) {
         int32_t *ti = &p.tile_info[(size_t)tt * kTileInfo];
-        ti[0] = tile_begin[tt];
+        ti[0] = (int32_t)tile_pad[tt];
         ti[1] = tile_begin[tt + 1] - tile_begin[tt];
         ti[2] = next;
         for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
@@ -274,8 +283,12 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     for (int64_t i = 0; i < nn; i++) p.node_old[p.node_new[i]] = (int32_t)i;
 
     // --- per tile: local node lists, local connectivity, gather CSR, partial slots
-    p.conn_local.assign((size_t)ne * npe, 0);
-    p.slots.assign((size_t)ne * npe, 0);
+    std::vector<int32_t> sorted_old(p.elem_old);
+    p.elem_old.assign(p.ne_pad, -1);
+    for (int tt = 0; tt < p.n_tiles; tt++)
+        for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) p.elem_old[tile_pad[tt] + (i - tile_begin[tt])] = sorted_old[i];
+    p.conn_local.assign((size_t)p.ne_pad * npe, 0);
+    p.slots.assign((size_t)p.ne_pad * npe, 0);
     std::vector<int32_t> local(nn, -1);
     std::vector<std::vector<int32_t>> sh_slots(p.n_shared);
     int64_t part = 0;
@@ -301,6 +314,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         }
         ti[4] = nl;
         ti[5] = (int32_t)p.tile_shared.size();
+        while (p.rowptr.size() % 8) p.rowptr.push_back(0);
         ti[6] = (int32_t)p.rowptr.size();
         ti[7] = (int32_t)part;
         for (size_t j = 0; j < shared.size(); j++) {
@@ -309,7 +323,6 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         }
         part += (int64_t)shared.size();
         // local index of every node of the tile
-        std::vector<uint16_t> cnt(nl + 1, 0);
         for (int64_t i = e0; i < e0 + ne_t; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
             for (int a = 0; a < npe; a++) {
@@ -321,18 +334,31 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
                     l = n_int + (int)(std::lower_bound(shared.begin(), shared.end(), g) - shared.begin());
                 }
                 p.conn_local[(size_t)i * npe + a] = (uint16_t)l;
-                cnt[l + 1]++;
             }
         }
-        for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
-        for (int l = 0; l <= nl; l++) p.rowptr.push_back(cnt[l]);
-        std::vector<uint16_t> cur(cnt.begin(), cnt.end() - 1);
-        for (int64_t i = e0; i < e0 + ne_t; i++)
-            for (int a = 0; a < npe; a++) {
-                int l = p.conn_local[(size_t)i * npe + a];
-                p.slots[(size_t)e0 * npe + cur[l]++] = (uint16_t)((i - e0) * npe + a);
-            }
+        // gather lists, one segment per chunk of kChunk elements: for every local
+        // node the slot offsets (corner * kChunk + element-in-chunk) of its
+        // incident corners, ascending element then corner; segment 1 follows
+        // segment 0 in the tile's code list.
+        int w = 0;
+        for (int ch = 0; ch < 2; ch++) {
+            const int64_t c0 = e0 + (int64_t)ch * kChunk, c1 = std::min<int64_t>(e0 + ne_t, c0 + kChunk);
+            std::vector<int32_t> cnt(nl + 1, 0);
+            for (int64_t i = c0; i < c1; i++)
+                for (int a = 0; a < npe; a++) cnt[p.conn_local[(size_t)i * npe + a] + 1]++;
+            cnt[0] = w;
+            for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
+            for (int l = 0; l <= nl; l++) p.rowptr.push_back((uint16_t)cnt[l]);
+            std::vector<int32_t> cur(cnt.begin(), cnt.end() - 1);
+            for (int64_t i = c0; i < c1; i++)
+                for (int a = 0; a < npe; a++) {
+                    int l = p.conn_local[(size_t)i * npe + a];
+                    p.slots[(size_t)e0 * npe + cur[l]++] = (uint16_t)(a * kChunk + (int)(i - c0));
+                }
+            w = cnt[nl];
+        }
     }
+    while (p.rowptr.size() % 8) p.rowptr.push_back(0);
     p.n_partials = part;
     p.sh_rowptr.assign(p.n_shared + 1, 0);
     for (int64_t s = 0; s < p.n_shared; s++) p.sh_rowptr[s + 1] = p.sh_rowptr[s] + (int32_t)sh_slots[s].size();

@@ -11,10 +11,10 @@
 
 namespace tled {
 
-constexpr int kBlock = 256;        // threads per CTA of the tile kernel
-constexpr int kMaxLocal = 1024;    // max nodes touched by one tile (shared memory)
-constexpr int kMaxTileElems = 1024;
-constexpr int kMaxSlots = 4096;   // max element corners per tile (shared memory)
+constexpr int kBlock = 256;        // threads per CTA of the tile kernel = elements per chunk
+constexpr int kChunk = 256;        // a tile is processed in chunks of kChunk elements (one per thread)
+constexpr int kMaxTileElems = 512; // at most two chunks per tile
+constexpr int kMaxLocal = 768;     // max nodes touched by one tile (shared memory)
 constexpr int kMaxSources = 16;
 constexpr int kTileInfo = 8;       // ints per tile record
 
@@ -30,16 +30,19 @@ constexpr uint32_t kStatusTimeout = 4u;
 struct Plan {
     int npe = 0;
     int64_t nn = 0, ne = 0;
-    std::vector<int32_t> elem_old;      // new element -> caller element
+    int64_t ne_pad = 0;                 // padded element count: every tile starts at a multiple of 4
+    std::vector<int32_t> elem_old;      // padded element slot -> caller element (-1 = padding)
     std::vector<int32_t> node_new;      // caller node -> new node
     std::vector<int32_t> node_old;      // new node -> caller node
     int64_t n_interior = 0, n_shared = 0;
     int n_tiles = 0;
-    std::vector<int32_t> tile_info;     // [n_tiles][8]: e0, ne, int_begin, n_int, n_local, sh_off, row_off, part_off
+    std::vector<int32_t> tile_info;     // [n_tiles][8]: e0 (padded slot, multiple of 4), ne, int_begin, n_int,
+                                        //   n_local, sh_off, row_off (multiple of 8), part_off
     std::vector<int32_t> tile_shared;   // per tile: new ids of its shared nodes (ascending)
-    std::vector<uint16_t> conn_local;   // [ne][npe] tile-local node index
-    std::vector<uint16_t> rowptr;       // per tile: n_local + 1 offsets into the tile's slots
-    std::vector<uint16_t> slots;        // [ne*npe] (local element * npe + corner), grouped by local node
+    std::vector<uint16_t> conn_local;   // [ne_pad][npe] tile-local node index
+    std::vector<uint16_t> rowptr;       // per tile: 2 x (n_local + 1) offsets (one segment per chunk), padded to 8
+    std::vector<uint16_t> slots;        // [ne_pad*npe] slot offsets corner * kChunk + element-in-chunk, grouped
+                                        //   by chunk, then local node, ascending element within a node
     std::vector<int32_t> sh_rowptr;     // [n_shared + 1]
     std::vector<int32_t> sh_list;       // partial-slot indices, ascending tile order
     int64_t n_partials = 0;
@@ -76,10 +79,17 @@ struct StepArgs {
     const int *n_src;      // device scalar (sources may change between chunks)
     const double *time_base;
     const int64_t *step_base;
-    unsigned int *status;  // [4]: bits, first bad element (new id), first bad node (new id), spare
+    unsigned int *status;  // [4]: bits, first bad element (padded slot), first bad node (new id), spare
+    // dynamic shared-memory layout of the tile kernel (bytes)
+    int sm_chunk_in;       // bytes of one chunk's staged element inputs
+    int sm_ch_stride;      // max(sm_chunk_in, slot buffer bytes), 128-aligned
+    int sm_codes, sm_rowptr, sm_xu, sm_X, sm_acc, sm_bar, sm_total;
+    int n_tiles;
+    int n_comp;            // staged float components per element (J0^-1 9, V0, [mat 6], [fibre 3], Prony 6 n)
     // scalars
     double dt;
     float dtf;
+    float inv_dt;
     float damp_a, damp_b;  // v+ = damp_a v + damp_b (-f/m) with damp_a = (1-g dt/2)/(1+g dt/2), damp_b = dt/(1+g dt/2)
     float mu, kappa, k1, k2, kc, alpha;   // uniform material
     float a0x, a0y, a0z;
@@ -95,14 +105,15 @@ struct StepArgs {
 };
 
 // kernel launchers (tled_kernels.cu)
-cudaError_t launch_tile_step(const StepArgs &a, int n_tiles, int npe, int k, cudaStream_t s);
+cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s);
+int tile_grid(const StepArgs &a, int npe, int n_sm);  // persistent grid size
 cudaError_t launch_shared_step(const StepArgs &a, int npe, int k, cudaStream_t s);
 cudaError_t launch_bump(double *time_base, int64_t *step_base, int K, double dt, cudaStream_t s);
 // read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction
 cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,
                             cudaStream_t s);
-size_t tile_smem_bytes(int npe);
-cudaError_t tile_kernel_setup(int npe);
+void tile_smem_layout(StepArgs &a, int npe);  // fills the sm_* fields
+cudaError_t tile_kernel_setup(const StepArgs &a, int npe);
 // FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
 // damaged volume; deterministic two-stage reduction through `partials` [kStatBlocks][8].
 constexpr int kStatBlocks = 296;

@@ -20,6 +20,7 @@
 // Floating point: FP32 throughout; kinematics are written in H = du/dX so
 // that J - 1, E and I4b - 1 never cancel; nodal u and theta accumulate in
 // float-float (TwoSum) pairs; theta is stored relative to T0.
+#include <algorithm>
 #include <cstdint>
 
 #include "tled_internal.h"
@@ -81,13 +82,53 @@ __device__ __forceinline__ void prepare_sources(const StepArgs &A, int k, SrcSme
 }
 
 // ---------------------------------------------------------------------------
+// TMA bulk copies and mbarriers (inline PTX, sm_90+ / sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait (about 2^31 SM cycles, i.e. around a second): on time-out the
+// caller flags the device status instead of hanging.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // nodal update: Eq. (27) in velocity form, Eq. (20), Arrhenius
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4 f, float4 xu, float4 X,
-                                            const SrcSmem &S) {
-    const float4 lo = A.lo[g];
-    const float4 vo = A.vel[g];
-    const float4 nc = __ldg(&A.nodec[g]);
+// xu: (u_hi, theta_hi); X: (X0, V_i); lo: (u_lo, theta_lo); vo: (v, Omega);
+// nc: (1/m_i, 1/C_i, mask bits, 0); f: (internal force, thermal load).
+__device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4 f, float4 xu, float4 X, float4 lo,
+                                            float4 vo, float4 nc, const SrcSmem &S) {
     const unsigned mask = __float_as_uint(nc.z);
     const bool comp = (A.flags & TLED_COMPENSATED) != 0;
     const float dt = A.dtf;
@@ -96,7 +137,7 @@ __device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4
 
     float u[3] = {xu.x, xu.y, xu.z}, ul[3] = {lo.x, lo.y, lo.z}, v[3] = {vo.x, vo.y, vo.z};
     const float fv[3] = {f.x, f.y, f.z};
-    const float im = 1.f / nc.x;
+    const float im = nc.x;
 #pragma unroll
     for (int d = 0; d < 3; d++) {
         if (mask & (1u << d)) {
@@ -108,7 +149,7 @@ __device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4
                 const float4 ub = __ldg(&A.ubar[g]);
                 target = (float)((d == 0 ? ub.x : d == 1 ? ub.y : ub.z) * r);
             }
-            v[d] = (target - u[d] - ul[d]) / dt;
+            v[d] = (target - u[d] - ul[d]) * A.inv_dt;
             u[d] = target;
             ul[d] = 0.f;
         } else {
@@ -123,22 +164,22 @@ __device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4
     // Eq. (20), physical conduction sign: C dtheta/dt = -fT - wbcb V (theta - theta_a) + V (Qm + Qr)
     float th = xu.w, tl = lo.w;
     const float theta = th + tl;
-    float C = nc.y;
-    if (A.flags & TLED_TEMP_DEP) C *= 1.f + A.beta_c * (theta - A.Tref_m_T0);
+    float iC = nc.y;
+    if (A.flags & TLED_TEMP_DEP) iC = __fdividef(iC, 1.f + A.beta_c * (theta - A.Tref_m_T0));
     float Q = A.Qm;
     for (int s = 0; s < S.n; s++) {
         const float dx = px - S.cx[s], dy = py - S.cy[s], dz = pz - S.cz[s];
         Q += S.P[s] * __expf(-(dx * dx + dy * dy + dz * dz) * S.inv2s2[s]);
     }
     if (!(mask & TLED_FIX_T)) {
-        const float dth = dt / C * (-f.w + X.w * (Q - A.wbcb * (theta - A.theta_a)));
+        const float dth = dt * iC * (-f.w + X.w * (Q - A.wbcb * (theta - A.theta_a)));
         if (comp)
             add_ff(th, tl, dth);
         else
             th += dth;
     }
     // Arrhenius damage integral, explicit in T(t); exp(ln A - Ea/(R T)) avoids A > FLT_MAX
-    const float Om = vo.w + dt * expf(A.lnA - A.Ea_R / (theta + A.T0_K));
+    const float Om = vo.w + dt * expf(A.lnA - __fdividef(A.Ea_R, theta + A.T0_K));
     if (!(isfinite(th) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) {
         atomicOr(A.status, kStatusNaN);
         atomicMin(A.status + 2, (unsigned)g);
@@ -151,72 +192,122 @@ __device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4
 // ---------------------------------------------------------------------------
 // element pass
 // ---------------------------------------------------------------------------
+// In-place unnormalised Walsh-Hadamard transform of 8 values:
+// X_k = sum_i x_i (-1)^popcount(i & k).  With hexahedron corners ordered by
+// i = [xi > 0] + 2 [eta > 0] + 4 [zeta > 0], the coefficients are the corner
+// sums against the sign vectors: xi -> -X1, eta -> -X2, zeta -> -X4,
+// xi eta -> X3, eta zeta -> X6, xi zeta -> X5, xi eta zeta -> -X7; the
+// transform is its own inverse up to a factor 8.
+__device__ __forceinline__ void wht8(float *x) {
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+            if ((i & h) == 0) {
+                const float a = x[i], b = x[i + h];
+                x[i] = a + b;
+                x[i + h] = a - b;
+            }
+}
+// WHT index -> VTK corner (an involution)
+__device__ __forceinline__ constexpr int wht_corner(int i) { return i == 2 ? 3 : i == 3 ? 2 : i == 6 ? 7 : i == 7 ? 6 : i; }
+
+struct ElemIn {
+    float Ji[9];
+    float V;
+    float mu, kap, k1, k2, kc, al;
+    float ax, ay, az;
+    float vs[4][6];
+};
+
+// Element inputs staged in shared memory for one chunk: connectivity, then
+// float components [q][kChunk]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz], Prony state.
 template <int NPE>
-__device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int el, const float4 *__restrict__ s_xu,
-                                             const float4 *__restrict__ s_X, float4 *__restrict__ s_slot) {
-    const int64_t ne = A.ne;
-    // ---- loads: connectivity, reference geometry, material, Prony state
-    int cl[NPE];
+__device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, int ec, int *cl, ElemIn &E) {
     if constexpr (NPE == 8) {
-        const uint4 c = __ldg(reinterpret_cast<const uint4 *>(A.conn_local) + e);
+        const uint4 c = reinterpret_cast<const uint4 *>(base)[ec];
         cl[0] = c.x & 0xffff; cl[1] = c.x >> 16; cl[2] = c.y & 0xffff; cl[3] = c.y >> 16;
         cl[4] = c.z & 0xffff; cl[5] = c.z >> 16; cl[6] = c.w & 0xffff; cl[7] = c.w >> 16;
     } else {
-        const uint2 c = __ldg(reinterpret_cast<const uint2 *>(A.conn_local) + e);
+        const uint2 c = reinterpret_cast<const uint2 *>(base)[ec];
         cl[0] = c.x & 0xffff; cl[1] = c.x >> 16; cl[2] = c.y & 0xffff; cl[3] = c.y >> 16;
     }
-    float Ji[9];
+    const float *cp = reinterpret_cast<const float *>(base + kChunk * NPE * 2) + ec;
+    int q = 0;
 #pragma unroll
-    for (int q = 0; q < 9; q++) Ji[q] = __ldg(A.jinv + q * ne + e);
-    const float V = __ldg(A.V0 + e);
-    float mu = A.mu, kap = A.kappa, k1 = A.k1, k2 = A.k2, kc = A.kc, al = A.alpha;
+    for (int k = 0; k < 9; k++) E.Ji[k] = cp[(q++) * kChunk];
+    E.V = cp[(q++) * kChunk];
     if (A.mat) {
-        mu = __ldg(A.mat + e);
-        kap = __ldg(A.mat + ne + e);
-        k1 = __ldg(A.mat + 2 * ne + e);
-        k2 = __ldg(A.mat + 3 * ne + e);
-        kc = __ldg(A.mat + 4 * ne + e);
-        al = __ldg(A.mat + 5 * ne + e);
+        E.mu = cp[(q++) * kChunk]; E.kap = cp[(q++) * kChunk]; E.k1 = cp[(q++) * kChunk];
+        E.k2 = cp[(q++) * kChunk]; E.kc = cp[(q++) * kChunk]; E.al = cp[(q++) * kChunk];
+    } else {
+        E.mu = A.mu; E.kap = A.kappa; E.k1 = A.k1; E.k2 = A.k2; E.kc = A.kc; E.al = A.alpha;
     }
-    float ax = A.a0x, ay = A.a0y, az = A.a0z;
     if (A.fib) {
-        ax = __ldg(A.fib + e);
-        ay = __ldg(A.fib + ne + e);
-        az = __ldg(A.fib + 2 * ne + e);
+        E.ax = cp[(q++) * kChunk]; E.ay = cp[(q++) * kChunk]; E.az = cp[(q++) * kChunk];
+    } else {
+        E.ax = A.a0x; E.ay = A.a0y; E.az = A.a0z;
     }
-    float vs[4][6];
 #pragma unroll
     for (int p = 0; p < 4; p++)
 #pragma unroll
-        for (int s = 0; s < 6; s++) vs[p][s] = (p < A.n_prony) ? A.visc[(int64_t)(p * 6 + s) * ne + e] : 0.f;
+        for (int s = 0; s < 6; s++) E.vs[p][s] = (p < A.n_prony) ? cp[(q + p * 6 + s) * kChunk] : 0.f;
+}
 
-    // ---- gather nodal displacement and temperature rise from shared memory
-    float ux[NPE], uy[NPE], uz[NPE], th[NPE];
-#pragma unroll
-    for (int a = 0; a < NPE; a++) {
-        const float4 q = s_xu[cl[a]];
-        ux[a] = q.x; uy[a] = q.y; uz[a] = q.z; th[a] = q.w;
-    }
-    // ---- Eq. (17) without forming I + H: H = sum_a u_a (x) dh_a/dX with
-    //      dh/dX = s * Xi * J0^-1 (Xi: corner signs for H8 with s = 1/8; T4 derivative table)
-    float G[3][3], gt[3];
+// One element: deformation gradient, thermal split, stress, Prony, nodal
+// forces + hourglass, thermal loads.  Corner contributions are written to the
+// chunk's slot buffer at [corner][ec] (conflict-free).
+template <int NPE>
+__device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int ec, const int *cl, ElemIn &E,
+                                             const float4 *__restrict__ s_xu, const float4 *__restrict__ s_X,
+                                             float4 *__restrict__ slot) {
+    const int64_t ne = A.ne;
+    const float *Ji = E.Ji;
+    const float V = E.V, mu = E.mu, kap = E.kap, k1 = E.k1, k2 = E.k2, kc = E.kc, al = E.al;
+    const float ax = E.ax, ay = E.ay, az = E.az;
+
+    // ---- corner values and the sums against the shape-function sign vectors
+    float G[3][3], gt[3], the;
+    float hu[4][3], ht[4], cX[4][3];  // H8 hourglass projections
     if constexpr (NPE == 8) {
+        float wx[8], wy[8], wz[8], wt[8], px[8], py[8], pz[8];
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            float gx = 0.f, gy = 0.f, gz = 0.f, gT = 0.f;
-#pragma unroll
-            for (int a = 0; a < 8; a++) {
-                gx += sgn(a, j) * ux[a]; gy += sgn(a, j) * uy[a]; gz += sgn(a, j) * uz[a]; gT += sgn(a, j) * th[a];
-            }
-            G[0][j] = gx; G[1][j] = gy; G[2][j] = gz; gt[j] = gT;
+        for (int i = 0; i < 8; i++) {
+            const int a = cl[wht_corner(i)];
+            const float4 q = s_xu[a];
+            const float4 x = s_X[a];
+            wx[i] = q.x; wy[i] = q.y; wz[i] = q.z; wt[i] = q.w;
+            px[i] = x.x; py[i] = x.y; pz[i] = x.z;
         }
+        wht8(wx); wht8(wy); wht8(wz); wht8(wt); wht8(px); wht8(py); wht8(pz);
+        G[0][0] = -wx[1]; G[0][1] = -wx[2]; G[0][2] = -wx[4];
+        G[1][0] = -wy[1]; G[1][1] = -wy[2]; G[1][2] = -wy[4];
+        G[2][0] = -wz[1]; G[2][1] = -wz[2]; G[2][2] = -wz[4];
+        gt[0] = -wt[1]; gt[1] = -wt[2]; gt[2] = -wt[4];
+        the = 0.125f * wt[0];
+        // hourglass vectors xi eta, eta zeta, xi zeta, xi eta zeta
+        hu[0][0] = wx[3]; hu[1][0] = wx[6]; hu[2][0] = wx[5]; hu[3][0] = -wx[7];
+        hu[0][1] = wy[3]; hu[1][1] = wy[6]; hu[2][1] = wy[5]; hu[3][1] = -wy[7];
+        hu[0][2] = wz[3]; hu[1][2] = wz[6]; hu[2][2] = wz[5]; hu[3][2] = -wz[7];
+        ht[0] = wt[3]; ht[1] = wt[6]; ht[2] = wt[5]; ht[3] = -wt[7];
+        cX[0][0] = px[3]; cX[1][0] = px[6]; cX[2][0] = px[5]; cX[3][0] = -px[7];
+        cX[0][1] = py[3]; cX[1][1] = py[6]; cX[2][1] = py[5]; cX[3][1] = -py[7];
+        cX[0][2] = pz[3]; cX[1][2] = pz[6]; cX[2][2] = pz[5]; cX[3][2] = -pz[7];
     } else {
+        float ux[4], uy[4], uz[4], th[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+            const float4 q = s_xu[cl[a]];
+            ux[a] = q.x; uy[a] = q.y; uz[a] = q.z; th[a] = q.w;
+        }
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             G[0][j] = ux[j + 1] - ux[0]; G[1][j] = uy[j + 1] - uy[0]; G[2][j] = uz[j + 1] - uz[0];
             gt[j] = th[j + 1] - th[0];
         }
+        the = 0.25f * ((th[0] + th[1]) + (th[2] + th[3]));
     }
+    // ---- Eq. (17) without forming I + H: H = s G J0^-1 (s = 1/8 for H8)
     constexpr float sc = NPE == 8 ? 0.125f : 1.f;
     float H[3][3], gth[3];
 #pragma unroll
@@ -225,14 +316,12 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
         for (int i = 0; i < 3; i++) H[i][j] = sc * (G[i][0] * Ji[j] + G[i][1] * Ji[3 + j] + G[i][2] * Ji[6 + j]);
         gth[j] = sc * (gt[0] * Ji[j] + gt[1] * Ji[3 + j] + gt[2] * Ji[6 + j]);
     }
-    float the = 0.f;
-#pragma unroll
-    for (int a = 0; a < NPE; a++) the += th[a];
-    the *= 1.f / NPE;
 
     // ---- thermal split (Eqs. 7-11, isotropic): lambda = 1 + delta, delta = alpha theta_e
     const float dl = (A.flags & TLED_EXPANSION) ? al * the : 0.f;
     const float lam = 1.f + dl;
+    const float il = __frcp_rn(lam);
+    const float il2 = il * il;
     // J - 1 = tr H + [(tr H)^2 - tr(H^2)]/2 + det H
     const float trH = H[0][0] + H[1][1] + H[2][2];
     const float trH2 = H[0][0] * H[0][0] + H[1][1] * H[1][1] + H[2][2] * H[2][2] +
@@ -242,29 +331,28 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
                        H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
     const float Jm1 = trH + 0.5f * (trH * trH - trH2) + detH;
     // Green-Lagrange E = (H + H^T + H^T H)/2, then E_el = (E - (delta + delta^2/2) I) / lambda^2
-    float E[6];  // xx yy zz xy yz xz
-    E[0] = H[0][0] + 0.5f * (H[0][0] * H[0][0] + H[1][0] * H[1][0] + H[2][0] * H[2][0]);
-    E[1] = H[1][1] + 0.5f * (H[0][1] * H[0][1] + H[1][1] * H[1][1] + H[2][1] * H[2][1]);
-    E[2] = H[2][2] + 0.5f * (H[0][2] * H[0][2] + H[1][2] * H[1][2] + H[2][2] * H[2][2]);
-    E[3] = 0.5f * (H[0][1] + H[1][0] + H[0][0] * H[0][1] + H[1][0] * H[1][1] + H[2][0] * H[2][1]);
-    E[4] = 0.5f * (H[1][2] + H[2][1] + H[0][1] * H[0][2] + H[1][1] * H[1][2] + H[2][1] * H[2][2]);
-    E[5] = 0.5f * (H[0][2] + H[2][0] + H[0][0] * H[0][2] + H[1][0] * H[1][2] + H[2][0] * H[2][2]);
-    const float il2 = 1.f / (lam * lam);
+    float Ee[6];  // xx yy zz xy yz xz
+    Ee[0] = H[0][0] + 0.5f * (H[0][0] * H[0][0] + H[1][0] * H[1][0] + H[2][0] * H[2][0]);
+    Ee[1] = H[1][1] + 0.5f * (H[0][1] * H[0][1] + H[1][1] * H[1][1] + H[2][1] * H[2][1]);
+    Ee[2] = H[2][2] + 0.5f * (H[0][2] * H[0][2] + H[1][2] * H[1][2] + H[2][2] * H[2][2]);
+    Ee[3] = 0.5f * (H[0][1] + H[1][0] + H[0][0] * H[0][1] + H[1][0] * H[1][1] + H[2][0] * H[2][1]);
+    Ee[4] = 0.5f * (H[1][2] + H[2][1] + H[0][1] * H[0][2] + H[1][1] * H[1][2] + H[2][1] * H[2][2]);
+    Ee[5] = 0.5f * (H[0][2] + H[2][0] + H[0][0] * H[0][2] + H[1][0] * H[1][2] + H[2][0] * H[2][2]);
     const float d1 = dl + 0.5f * dl * dl;
-    E[0] = (E[0] - d1) * il2; E[1] = (E[1] - d1) * il2; E[2] = (E[2] - d1) * il2;
-    E[3] *= il2; E[4] *= il2; E[5] *= il2;
+    Ee[0] = (Ee[0] - d1) * il2; Ee[1] = (Ee[1] - d1) * il2; Ee[2] = (Ee[2] - d1) * il2;
+    Ee[3] *= il2; Ee[4] *= il2; Ee[5] *= il2;
     // J_el - 1 = ((J - 1) - (lambda^3 - 1)) / lambda^3
     const float l3m1 = dl * (3.f + dl * (3.f + dl));
-    const float jel = (Jm1 - l3m1) / (lam * lam * lam);
+    const float jel = (Jm1 - l3m1) * (il2 * il);
     const float Jel = 1.f + jel;
     if (!(Jel > 0.f)) {
         atomicOr(A.status, kStatusInverted);
         atomicMin(A.status + 1, (unsigned)e);
     }
     // C_el = I + 2 E_el and its inverse adj(C_el) / J_el^2
-    const float c00 = 1.f + 2.f * E[0], c11 = 1.f + 2.f * E[1], c22 = 1.f + 2.f * E[2];
-    const float c01 = 2.f * E[3], c12 = 2.f * E[4], c02 = 2.f * E[5];
-    const float iJ2 = 1.f / (Jel * Jel);
+    const float c00 = 1.f + 2.f * Ee[0], c11 = 1.f + 2.f * Ee[1], c22 = 1.f + 2.f * Ee[2];
+    const float c01 = 2.f * Ee[3], c12 = 2.f * Ee[4], c02 = 2.f * Ee[5];
+    const float iJ2 = __frcp_rn(Jel * Jel);
     float Ci[6];
     Ci[0] = (c11 * c22 - c12 * c12) * iJ2;
     Ci[1] = (c00 * c22 - c02 * c02) * iJ2;
@@ -272,15 +360,20 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
     Ci[3] = (c02 * c12 - c01 * c22) * iJ2;
     Ci[4] = (c01 * c02 - c00 * c12) * iJ2;
     Ci[5] = (c01 * c12 - c02 * c11) * iJ2;
-    // J_el^(-2/3) and J_el^(-2/3) - 1 without cancellation
-    const float lg = log1pf(jel);
-    const float Jm23 = expf(-(2.f / 3.f) * lg);
-    const float Jm23m1 = expm1f(-(2.f / 3.f) * lg);
+    // J_el^(-2/3) - 1 without cancellation: binomial series of (1 + j)^(-2/3) for
+    // |j| < 0.1 (terms to j^8, truncation below 4e-9 relative), else expm1(-2/3 log1p(j))
+    float Jm23m1;
+    if (fabsf(jel) < 0.1f) {
+        Jm23m1 = jel * (-0.66666667f + jel * (0.55555556f + jel * (-0.49382716f + jel * (0.45267490f +
+                 jel * (-0.42249657f + jel * (0.39902454f + jel * (-0.38002337f + jel * 0.36418906f)))))));
+    } else {
+        Jm23m1 = expm1f(-(2.f / 3.f) * log1pf(jel));
+    }
+    const float Jm23 = 1.f + Jm23m1;
     // isochoric part: mu J^-2/3 (I - I1/3 C^-1) = 2 mu J^-2/3 C^-1 dev(E_el)
-    const float tr3 = (E[0] + E[1] + E[2]) * (1.f / 3.f);
-    const float D[6] = {E[0] - tr3, E[1] - tr3, E[2] - tr3, E[3], E[4], E[5]};
-    // symmetric product M = Ci * D (both symmetric and commuting)
-    float M[6];
+    const float tr3 = (Ee[0] + Ee[1] + Ee[2]) * (1.f / 3.f);
+    const float D[6] = {Ee[0] - tr3, Ee[1] - tr3, Ee[2] - tr3, Ee[3], Ee[4], Ee[5]};
+    float M[6];  // C^-1 dev(E), symmetric (the two commute)
     M[0] = Ci[0] * D[0] + Ci[3] * D[3] + Ci[5] * D[5];
     M[1] = Ci[3] * D[3] + Ci[1] * D[1] + Ci[4] * D[4];
     M[2] = Ci[5] * D[5] + Ci[4] * D[4] + Ci[2] * D[2];
@@ -288,7 +381,8 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
     M[4] = Ci[3] * D[5] + Ci[1] * D[4] + Ci[4] * D[2];
     M[5] = Ci[0] * D[5] + Ci[3] * D[4] + Ci[5] * D[2];
     // fibre term: I4b - 1 = (J^-2/3 - 1) + 2 J^-2/3 a.E_el.a
-    const float aEa = ax * ax * E[0] + ay * ay * E[1] + az * az * E[2] + 2.f * (ax * ay * E[3] + ay * az * E[4] + ax * az * E[5]);
+    const float aEa = ax * ax * Ee[0] + ay * ay * Ee[1] + az * az * Ee[2] +
+                      2.f * (ax * ay * Ee[3] + ay * az * Ee[4] + ax * az * Ee[5]);
     const float I4 = 1.f + 2.f * aEa;
     const float x4 = Jm23m1 + 2.f * Jm23 * aEa;
     const float psi4 = k1 * x4 * expf(k2 * x4 * x4);
@@ -310,7 +404,7 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
             if (p < A.n_prony) {
 #pragma unroll
                 for (int s = 0; s < 6; s++) {
-                    const float tp = A.pr_a[p] * S0[s] + A.pr_b[p] * vs[p][s];
+                    const float tp = A.pr_a[p] * S0[s] + A.pr_b[p] * E.vs[p][s];
                     A.visc[(int64_t)(p * 6 + s) * ne + e] = tp;
                     St[s] -= tp;
                 }
@@ -346,16 +440,7 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
 
     if constexpr (NPE == 8) {
         // hourglass control: gamma_a,al = h_a,al - c_al . dh_a/dX with c_al = sum_b h_b,al X_b;
-        // f_a += k_hg sum_al gamma_a,al q_al with q_al = sum_b h_b,al u_b - H c_al
-        float Xr[8][3];
-        {
-            const float4 x0 = s_X[cl[0]];
-#pragma unroll
-            for (int a = 0; a < 8; a++) {
-                const float4 xa = s_X[cl[a]];
-                Xr[a][0] = xa.x - x0.x; Xr[a][1] = xa.y - x0.y; Xr[a][2] = xa.z - x0.z;
-            }
-        }
+        // f_a += k_hg sum_al gamma_a,al q_al with q_al = sum_b h_b,al u_b - H c_al (thermal alike)
         float jn2 = 0.f;
 #pragma unroll
         for (int q = 0; q < 9; q++) jn2 += Ji[q] * Ji[q];
@@ -366,89 +451,235 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
         float wT[3] = {0.f, 0.f, 0.f};
 #pragma unroll
         for (int l = 0; l < 4; l++) {
-            float c[3] = {0.f, 0.f, 0.f}, hu[3] = {0.f, 0.f, 0.f}, ht = 0.f;
-#pragma unroll
-            for (int b = 0; b < 8; b++) {
-                c[0] += hgv(b, l) * Xr[b][0]; c[1] += hgv(b, l) * Xr[b][1]; c[2] += hgv(b, l) * Xr[b][2];
-                hu[0] += hgv(b, l) * ux[b]; hu[1] += hgv(b, l) * uy[b]; hu[2] += hgv(b, l) * uz[b];
-                ht += hgv(b, l) * th[b];
-            }
 #pragma unroll
             for (int i = 0; i < 3; i++) {
-                qa[l][i] = hu[i] - (H[i][0] * c[0] + H[i][1] * c[1] + H[i][2] * c[2]);
+                qa[l][i] = hu[l][i] - (H[i][0] * cX[l][0] + H[i][1] * cX[l][1] + H[i][2] * cX[l][2]);
 #pragma unroll
-                for (int j = 0; j < 3; j++) Wm[i][j] += qa[l][i] * c[j];
+                for (int j = 0; j < 3; j++) Wm[i][j] += qa[l][i] * cX[l][j];
             }
-            qT[l] = ht - (c[0] * gth[0] + c[1] * gth[1] + c[2] * gth[2]);
-            wT[0] += qT[l] * c[0]; wT[1] += qT[l] * c[1]; wT[2] += qT[l] * c[2];
+            qT[l] = ht[l] - (cX[l][0] * gth[0] + cX[l][1] * gth[1] + cX[l][2] * gth[2]);
+            wT[0] += qT[l] * cX[l][0]; wT[1] += qT[l] * cX[l][1]; wT[2] += qT[l] * cX[l][2];
         }
         // fold the -k_hg W dh_a/dX part into Q and r
-        const float hs = 0.125f;
+        const float kh8 = 0.125f * khg, kT8 = 0.125f * khgT;
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int k = 0; k < 3; k++)
-                Qm[i][k] -= khg * hs * (Wm[i][0] * Ji[3 * k] + Wm[i][1] * Ji[3 * k + 1] + Wm[i][2] * Ji[3 * k + 2]);
+                Qm[i][k] -= kh8 * (Wm[i][0] * Ji[3 * k] + Wm[i][1] * Ji[3 * k + 1] + Wm[i][2] * Ji[3 * k + 2]);
 #pragma unroll
-        for (int k = 0; k < 3; k++) r[k] -= khgT * hs * (Ji[3 * k] * wT[0] + Ji[3 * k + 1] * wT[1] + Ji[3 * k + 2] * wT[2]);
+        for (int k = 0; k < 3; k++) r[k] -= kT8 * (Ji[3 * k] * wT[0] + Ji[3 * k + 1] * wT[1] + Ji[3 * k + 2] * wT[2]);
+        // corner values by the inverse transform of the sign-vector coefficients
+        float fx[8], fy[8], fz[8], ft[8];
+        fx[0] = 0.f; fx[1] = -Qm[0][0]; fx[2] = -Qm[0][1]; fx[4] = -Qm[0][2];
+        fx[3] = khg * qa[0][0]; fx[6] = khg * qa[1][0]; fx[5] = khg * qa[2][0]; fx[7] = -khg * qa[3][0];
+        fy[0] = 0.f; fy[1] = -Qm[1][0]; fy[2] = -Qm[1][1]; fy[4] = -Qm[1][2];
+        fy[3] = khg * qa[0][1]; fy[6] = khg * qa[1][1]; fy[5] = khg * qa[2][1]; fy[7] = -khg * qa[3][1];
+        fz[0] = 0.f; fz[1] = -Qm[2][0]; fz[2] = -Qm[2][1]; fz[4] = -Qm[2][2];
+        fz[3] = khg * qa[0][2]; fz[6] = khg * qa[1][2]; fz[5] = khg * qa[2][2]; fz[7] = -khg * qa[3][2];
+        ft[0] = 0.f; ft[1] = -r[0]; ft[2] = -r[1]; ft[4] = -r[2];
+        ft[3] = khgT * qT[0]; ft[6] = khgT * qT[1]; ft[5] = khgT * qT[2]; ft[7] = -khgT * qT[3];
+        wht8(fx); wht8(fy); wht8(fz); wht8(ft);
 #pragma unroll
-        for (int a = 0; a < 8; a++) {
-            float f[3], fT;
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-                f[i] = sgn(a, 0) * Qm[i][0] + sgn(a, 1) * Qm[i][1] + sgn(a, 2) * Qm[i][2] +
-                       khg * (hgv(a, 0) * qa[0][i] + hgv(a, 1) * qa[1][i] + hgv(a, 2) * qa[2][i] + hgv(a, 3) * qa[3][i]);
-            fT = sgn(a, 0) * r[0] + sgn(a, 1) * r[1] + sgn(a, 2) * r[2] +
-                 khgT * (hgv(a, 0) * qT[0] + hgv(a, 1) * qT[1] + hgv(a, 2) * qT[2] + hgv(a, 3) * qT[3]);
-            s_slot[el * 8 + a] = make_float4(f[0], f[1], f[2], fT);
-        }
+        for (int i = 0; i < 8; i++) slot[wht_corner(i) * kChunk + ec] = make_float4(fx[i], fy[i], fz[i], ft[i]);
     } else {
         // T4: dh_0 = -(dh_1 + dh_2 + dh_3), dh_{j+1} = row j of J0^-1
-        s_slot[el * 4 + 0] = make_float4(-(Qm[0][0] + Qm[0][1] + Qm[0][2]), -(Qm[1][0] + Qm[1][1] + Qm[1][2]),
-                                         -(Qm[2][0] + Qm[2][1] + Qm[2][2]), -(r[0] + r[1] + r[2]));
+        slot[ec] = make_float4(-(Qm[0][0] + Qm[0][1] + Qm[0][2]), -(Qm[1][0] + Qm[1][1] + Qm[1][2]),
+                               -(Qm[2][0] + Qm[2][1] + Qm[2][2]), -(r[0] + r[1] + r[2]));
 #pragma unroll
-        for (int j = 0; j < 3; j++) s_slot[el * 4 + 1 + j] = make_float4(Qm[0][j], Qm[1][j], Qm[2][j], r[j]);
+        for (int j = 0; j < 3; j++) slot[(1 + j) * kChunk + ec] = make_float4(Qm[0][j], Qm[1][j], Qm[2][j], r[j]);
     }
 }
 
 // ---------------------------------------------------------------------------
-// kernels
+// tile kernel (persistent: CTA b handles tiles b, b + gridDim.x, ...)
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+struct TileInfo {
+    int e0, ne_t, ib, n_int, nl, sh_off, row_off, part_off;
+};
+__device__ __forceinline__ TileInfo tile_info(const StepArgs &A, int t) {
+    const int4 a = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t);
+    const int4 b = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t + 1);
+    return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+__device__ __forceinline__ uint32_t rowptr_bytes(int nl) { return (uint32_t)(((2 * (nl + 1)) + 7) & ~7) * 2; }
+
+// Warm L2 with a tile's streams (issued one tile ahead, so the bulk copies of
+// the next tile hit L2 while this one computes).
+template <int NPE>
+__device__ void prefetch_tile(const StepArgs &A, const TileInfo &T) {
+    const int64_t ne = A.ne;
+    const uint32_t n4 = (uint32_t)((T.ne_t + 3) & ~3);
+    prefetch_l2(A.conn_local + (int64_t)T.e0 * NPE, n4 * NPE * 2);
+    for (int j = 0; j < 9; j++) prefetch_l2(A.jinv + j * ne + T.e0, n4 * 4);
+    prefetch_l2(A.V0 + T.e0, n4 * 4);
+    if (A.mat)
+        for (int j = 0; j < 6; j++) prefetch_l2(A.mat + j * ne + T.e0, n4 * 4);
+    if (A.fib)
+        for (int j = 0; j < 3; j++) prefetch_l2(A.fib + j * ne + T.e0, n4 * 4);
+    for (int j = 0; j < 6 * A.n_prony; j++) prefetch_l2(A.visc + j * ne + T.e0, n4 * 4);
+    prefetch_l2(A.slots + (int64_t)T.e0 * NPE, n4 * NPE * 2);
+    prefetch_l2(A.rowptr + T.row_off, rowptr_bytes(T.nl));
+    if (T.n_int > 0) {
+        const uint32_t nb = 16u * T.n_int;
+        prefetch_l2(A.xu + T.ib, nb);
+        prefetch_l2(A.X0 + T.ib, nb);
+        prefetch_l2(A.lo + T.ib, nb);
+        prefetch_l2(A.vel + T.ib, nb);
+        prefetch_l2(A.nodec + T.ib, nb);
+    }
+}
+
+template <int NPE>
+__device__ void stage_tile(const StepArgs &A, const TileInfo &T, char *smem, uint64_t *bar) {
+    const int64_t ne = A.ne;
+    const int nch = (T.ne_t + kChunk - 1) / kChunk;
+    const int cin = kChunk * NPE * 2;
+    uint32_t tx = 0;
+    for (int c = 0; c < nch; c++) {
+        const int n4 = ((min(kChunk, T.ne_t - c * kChunk)) + 3) & ~3;
+        tx += n4 * NPE * 2 + A.n_comp * n4 * 4;
+    }
+    tx += (((T.ne_t + 3) & ~3) * NPE * 2) + rowptr_bytes(T.nl) + 32u * T.n_int;
+    mbar_expect_tx(bar, tx);
+    for (int c = 0; c < nch; c++) {
+        const int64_t eb = (int64_t)T.e0 + c * kChunk;
+        const int n4 = ((min(kChunk, T.ne_t - c * kChunk)) + 3) & ~3;
+        char *base = smem + c * A.sm_ch_stride;
+        bulk_g2s(base, A.conn_local + eb * NPE, n4 * NPE * 2, bar);
+        char *cp = base + cin;
+        int q = 0;
+        for (int j = 0; j < 9; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.jinv + j * ne + eb, n4 * 4, bar);
+        bulk_g2s(cp + (q++) * kChunk * 4, A.V0 + eb, n4 * 4, bar);
+        if (A.mat)
+            for (int j = 0; j < 6; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.mat + j * ne + eb, n4 * 4, bar);
+        if (A.fib)
+            for (int j = 0; j < 3; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.fib + j * ne + eb, n4 * 4, bar);
+        for (int j = 0; j < 6 * A.n_prony; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.visc + j * ne + eb, n4 * 4, bar);
+    }
+    bulk_g2s(smem + A.sm_codes, A.slots + (int64_t)T.e0 * NPE, ((T.ne_t + 3) & ~3) * NPE * 2, bar);
+    bulk_g2s(smem + A.sm_rowptr, A.rowptr + T.row_off, rowptr_bytes(T.nl), bar);
+    if (T.n_int > 0) {
+        bulk_g2s(smem + A.sm_xu, A.xu + T.ib, 16u * T.n_int, bar);
+        bulk_g2s(smem + A.sm_X, A.X0 + T.ib, 16u * T.n_int, bar);
+    }
+}
+
 template <int NPE>
 __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, const int k) {
-    extern __shared__ float4 smem[];
-    float4 *s_xu = smem;
-    float4 *s_X = smem + kMaxLocal;
-    float4 *s_slot = smem + 2 * kMaxLocal;
+    extern __shared__ __align__(128) char smem[];
     __shared__ SrcSmem S;
-    const int *ti = A.tile_info + (size_t)blockIdx.x * kTileInfo;
-    const int e0 = ti[0], ne_t = ti[1], ib = ti[2], n_int = ti[3], nl = ti[4], sh_off = ti[5], row_off = ti[6],
-              part_off = ti[7];
-    // 1. gather the tile's nodes
-    for (int l = threadIdx.x; l < nl; l += kBlock) {
-        const int64_t g = l < n_int ? (int64_t)ib + l : (int64_t)__ldg(A.tile_shared + sh_off + l - n_int);
-        s_xu[l] = A.xu[g];
-        s_X[l] = __ldg(&A.X0[g]);
+    __shared__ int s_abort;
+    char *R = smem;  // chunk inputs at c * ch_stride; slot buffer at 0
+    const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_codes);
+    const uint16_t *s_row = reinterpret_cast<const uint16_t *>(smem + A.sm_rowptr);
+    float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
+    float4 *s_X = reinterpret_cast<float4 *>(smem + A.sm_X);
+    float4 *s_acc = reinterpret_cast<float4 *>(smem + A.sm_acc);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);
+    float4 *slot = reinterpret_cast<float4 *>(R);
+    float4 *ns = reinterpret_cast<float4 *>(R + A.sm_ch_stride);
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_barrier_init();
+        s_abort = 0;
     }
-    prepare_sources(A, k, S);  // contains __syncthreads
-    __syncthreads();
-    // 2. element pass
-    for (int el = threadIdx.x; el < ne_t; el += kBlock) element_step<NPE>(A, (int64_t)e0 + el, el, s_xu, s_X, s_slot);
-    __syncthreads();
-    // 3. node-centric gather in a fixed order, then nodal update or partial store
-    const uint16_t *rp = A.rowptr + row_off;
-    const uint16_t *sl = A.slots + (size_t)e0 * NPE;
-    for (int l = threadIdx.x; l < nl; l += kBlock) {
-        const int r0 = __ldg(rp + l), r1 = __ldg(rp + l + 1);
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int r = r0; r < r1; r++) {
-            const float4 c = s_slot[__ldg(sl + r)];
-            acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
+    prepare_sources(A, k, S);  // __syncthreads inside: barrier init visible to all
+    uint32_t ph0 = 0, ph1 = 0;
+    for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
+        const TileInfo T = tile_info(A, t);
+        const int nch = (T.ne_t + kChunk - 1) / kChunk;
+        // node state of interior nodes goes to the second chunk's input area once that is consumed
+        const bool ns_smem = T.n_int > 0 && 48 * T.n_int <= A.sm_chunk_in;
+        // ---- 1. one thread stages the tile with bulk copies and warms L2 for the next one
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            stage_tile<NPE>(A, T, smem, &bar[0]);
+            if (t + (int)gridDim.x < A.n_tiles) prefetch_tile<NPE>(A, tile_info(A, t + gridDim.x));
         }
-        if (l < n_int)
-            node_update(A, (int64_t)ib + l, acc, s_xu[l], s_X[l], S);
-        else
-            A.partials[part_off + l - n_int] = acc;
+        // ---- 2. meanwhile: the tile's shared nodes with ordinary loads (mostly L2 hits)
+        for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
+            const int64_t g = __ldg(A.tile_shared + T.sh_off + l - T.n_int);
+            s_xu[l] = A.xu[g];
+            s_X[l] = __ldg(&A.X0[g]);
+        }
+        if (!mbar_wait(&bar[0], ph0)) {
+            atomicOr(A.status, kStatusTimeout);
+            s_abort = 1;
+            mbar_wait(&bar[0], ph0);
+        }
+        ph0 ^= 1;
+        __syncthreads();
+        if (s_abort) return;
+        // ---- 3. element chunks: inputs -> registers, slots, fixed-order accumulation
+        for (int c = 0; c < nch; c++) {
+            const int ec = threadIdx.x;
+            const int el = c * kChunk + ec;
+            const bool active = el < T.ne_t;
+            int cl[NPE];
+            ElemIn E;
+            if (active) load_elem<NPE>(A, R + c * A.sm_ch_stride, ec, cl, E);
+            __syncthreads();  // chunk inputs consumed: the slot buffer may overwrite them
+            if (c == nch - 1 && ns_smem && threadIdx.x == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&bar[1], 48u * T.n_int);
+                bulk_g2s(ns, A.lo + T.ib, 16u * T.n_int, &bar[1]);
+                bulk_g2s(ns + T.n_int, A.vel + T.ib, 16u * T.n_int, &bar[1]);
+                bulk_g2s(ns + 2 * T.n_int, A.nodec + T.ib, 16u * T.n_int, &bar[1]);
+            }
+            if (active) element_step<NPE>(A, (int64_t)T.e0 + el, ec, cl, E, s_xu, s_X, slot);
+            __syncthreads();
+            const uint16_t *rp = s_row + c * (T.nl + 1);
+            for (int l = threadIdx.x; l < T.nl; l += kBlock) {
+                int r = rp[l];
+                const int r1 = rp[l + 1];
+                float4 a0 = c == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : s_acc[l];
+                float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (; r + 1 < r1; r += 2) {
+                    const float4 v0 = slot[s_code[r]];
+                    const float4 v1 = slot[s_code[r + 1]];
+                    a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
+                    a1.x += v1.x; a1.y += v1.y; a1.z += v1.z; a1.w += v1.w;
+                }
+                if (r < r1) {
+                    const float4 v0 = slot[s_code[r]];
+                    a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
+                }
+                s_acc[l] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+            }
+            __syncthreads();
+        }
+        // ---- 4. nodal update of interior nodes; partial sums of shared nodes
+        if (ns_smem) {
+            if (!mbar_wait(&bar[1], ph1)) {
+                atomicOr(A.status, kStatusTimeout);
+                mbar_wait(&bar[1], ph1);
+                return;
+            }
+            ph1 ^= 1;
+        }
+        for (int l = threadIdx.x; l < T.nl; l += kBlock) {
+            const float4 acc = s_acc[l];
+            if (l < T.n_int) {
+                const int64_t g = (int64_t)T.ib + l;
+                float4 lo, vo, nc;
+                if (ns_smem) {
+                    lo = ns[l]; vo = ns[T.n_int + l]; nc = ns[2 * T.n_int + l];
+                } else {
+                    lo = A.lo[g]; vo = A.vel[g]; nc = __ldg(&A.nodec[g]);
+                }
+                node_update(A, g, acc, s_xu[l], s_X[l], lo, vo, nc, S);
+            } else {
+                A.partials[T.part_off + l - T.n_int] = acc;
+            }
+        }
+        __syncthreads();  // all shared-memory reads of this tile done before the next staging
     }
 }
 
@@ -465,7 +696,7 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
         const float4 c = A.partials[__ldg(A.sh_list + r)];
         acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
     }
-    node_update(A, g, acc, A.xu[g], __ldg(&A.X0[g]), S);
+    node_update(A, g, acc, A.xu[g], __ldg(&A.X0[g]), A.lo[g], A.vel[g], __ldg(&A.nodec[g]), S);
 }
 
 __global__ void bump_kernel(double *time_base, int64_t *step_base, int K, double dt) {
@@ -498,8 +729,8 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(const StepArgs A, in
         const float4 h = A.xu[g], l = A.lo[g], v = A.vel[g], nc = A.nodec[g], X = A.X0[g];
         const double ux = (double)h.x + l.x, uy = (double)h.y + l.y, uz = (double)h.z + l.z;
         const double th = (double)h.w + l.w;
-        ke += 0.5 * (double)nc.x * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
-        heat += (double)nc.y * th;
+        ke += 0.5 / (double)nc.x * ((double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z);
+        heat += th / (double)nc.y;
         tmax = fmax(tmax, th);
         tmin = fmin(tmin, th);
         umax = fmax(umax, ux * ux + uy * uy + uz * uz);
@@ -538,21 +769,49 @@ __global__ void stats_final_kernel(const double *partials, int nb, double *out) 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-size_t tile_smem_bytes(int npe) { return (size_t)(2 * kMaxLocal + kMaxSlots) * sizeof(float4); }
+static int align128(int x) { return (x + 127) & ~127; }
 
-cudaError_t tile_kernel_setup(int npe) {
-    const int bytes = (int)tile_smem_bytes(npe);
-    if (npe == 8) return cudaFuncSetAttribute(tile_step_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    return cudaFuncSetAttribute(tile_step_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+void tile_smem_layout(StepArgs &a, int npe) {
+    a.n_comp = 10 + (a.mat ? 6 : 0) + (a.fib ? 3 : 0) + 6 * a.n_prony;
+    a.sm_chunk_in = align128(kChunk * npe * 2 + a.n_comp * kChunk * 4);
+    a.sm_ch_stride = std::max(a.sm_chunk_in, kChunk * npe * 16);
+    int off = a.sm_ch_stride + a.sm_chunk_in;  // two chunks (the second also hosts the interior node state)
+    a.sm_codes = off;
+    off = align128(off + kMaxTileElems * npe * 2);
+    a.sm_rowptr = off;
+    off = align128(off + (2 * (kMaxLocal + 1) + 8) * 2);
+    a.sm_xu = off;
+    off = align128(off + kMaxLocal * 16);
+    a.sm_X = off;
+    off = align128(off + kMaxLocal * 16);
+    a.sm_acc = off;
+    off = align128(off + kMaxLocal * 16);
+    a.sm_bar = off;
+    off = align128(off + 16);
+    a.sm_total = off;
 }
 
-cudaError_t launch_tile_step(const StepArgs &a, int n_tiles, int npe, int k, cudaStream_t s) {
-    if (n_tiles <= 0) return cudaSuccess;
-    const size_t sm = tile_smem_bytes(npe);
+cudaError_t tile_kernel_setup(const StepArgs &a, int npe) {
     if (npe == 8)
-        tile_step_kernel<8><<<n_tiles, kBlock, sm, s>>>(a, k);
+        return cudaFuncSetAttribute(tile_step_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.sm_total);
+    return cudaFuncSetAttribute(tile_step_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.sm_total);
+}
+
+int tile_grid(const StepArgs &a, int npe, int n_sm) {
+    int per_sm = 0;
+    cudaError_t e = npe == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<8>, kBlock, a.sm_total)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<4>, kBlock, a.sm_total);
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    return std::max(1, std::min(a.n_tiles, per_sm * n_sm));
+}
+
+cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s) {
+    if (a.n_tiles <= 0) return cudaSuccess;
+    const size_t sm = (size_t)a.sm_total;
+    if (npe == 8)
+        tile_step_kernel<8><<<n_ctas, kBlock, sm, s>>>(a, k);
     else
-        tile_step_kernel<4><<<n_tiles, kBlock, sm, s>>>(a, k);
+        tile_step_kernel<4><<<n_ctas, kBlock, sm, s>>>(a, k);
     return cudaGetLastError();
 }
 
