@@ -20,8 +20,8 @@ namespace {
 constexpr int kGraphChunk = 32;  // steps per captured graph
 
 struct Layout {
-    size_t xu, lo, vel, X0, nodec, ubar, conn, jinv, V0, mat, fib, visc;
-    size_t tile_info, tile_shared, rowptr, slots, partials, sh_rowptr, sh_list;
+    size_t xu, lo, vel, X0, nodec, ubar, elem_rec, visc;
+    size_t tile_info, tile_shared, part_pos, csr, partials, sh_rowptr;
     size_t src, nsrc, time_base, step_base, status, node_new, stat_part, stat_out, staging;
     size_t total;
 };
@@ -104,6 +104,16 @@ tled_params default_params() {
 
 int n_prony(const tled_ctx *c) { return c->mat.n_prony; }
 
+// bytes of one tile's element record: local connectivity then the constant float components
+size_t rec_bytes(const tled_ctx *c) {
+    const int ncomp = 10 + (c->mat6.empty() ? 0 : 6) + (c->fib.empty() ? 0 : 3);
+    return (size_t)tled::kTile * c->npe * 2 + (size_t)ncomp * tled::kTile * 4;
+}
+// Prony state index of element slot e, component q (tile-blocked [t][6 n_prony][kTile])
+inline size_t visc_index(int np, int64_t e, int q) {
+    return (size_t)(e / tled::kTile) * np * 6 * tled::kTile + (size_t)q * tled::kTile + (size_t)(e % tled::kTile);
+}
+
 Layout make_layout(const tled_ctx *c) {
     const Plan &p = c->plan;
     Layout L{};
@@ -120,19 +130,14 @@ Layout make_layout(const tled_ctx *c) {
     L.X0 = take(16 * nn);
     L.nodec = take(16 * nn);
     L.ubar = take(c->ubar.empty() ? 0 : 16 * nn);
-    L.conn = take(2 * ne * c->npe);
-    L.jinv = take(4 * 9 * ne);
-    L.V0 = take(4 * ne);
-    L.mat = take(c->mat6.empty() ? 0 : 4 * 6 * ne);
-    L.fib = take(c->fib.empty() ? 0 : 4 * 3 * ne);
+    L.elem_rec = take((size_t)p.n_tiles * rec_bytes(c));
     L.visc = take(4 * 6 * (size_t)std::max(n_prony(c), 0) * ne);
     L.tile_info = take(4 * p.tile_info.size());
     L.tile_shared = take(4 * p.tile_shared.size());
-    L.rowptr = take(2 * p.rowptr.size());
-    L.slots = take(2 * p.slots.size());
+    L.csr = take(2 * p.csr.size());
     L.partials = take(16 * (size_t)p.n_partials);
     L.sh_rowptr = take(4 * p.sh_rowptr.size());
-    L.sh_list = take(4 * p.sh_list.size());
+    L.part_pos = take(4 * p.part_pos.size());
     L.src = take(8 * 10 * tled::kMaxSources);
     L.nsrc = take(4);
     L.time_base = take(8);
@@ -215,7 +220,7 @@ int write_state(tled_ctx *c, const double *u, const double *v, const double *T, 
         for (int64_t e = 0; e < nep; e++) {
             const int64_t eo = p.elem_old[e];
             if (eo < 0) continue;
-            for (int q = 0; q < np * 6; q++) vs[(size_t)q * nep + e] = (float)visc[eo * np * 6 + q];
+            for (int q = 0; q < np * 6; q++) vs[visc_index(np, e, q)] = (float)visc[eo * np * 6 + q];
         }
     if (np) CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.visc, vs.data(), vs.size() * 4, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -441,15 +446,26 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     const tled_material &m = c->mat;
     // --- element geometry (new order), lumped masses
     const int64_t nep = p.ne_pad;
-    std::vector<float> jinv(9 * nep, 0.f), V0(nep, 0.f);
+    const size_t rb = rec_bytes(c);
+    const int kT = tled::kTile;
+    std::vector<char> rec((size_t)p.n_tiles * rb, 0);
     std::vector<double> Mn(nn, 0.0), Cn(nn, 0.0), Vn(nn, 0.0);
     for (int64_t e = 0; e < nep; e++) {
         const int64_t eo = p.elem_old[e];
         if (eo < 0) continue;  // padding slot
         double Ji[9], V;
         tled::element_geometry(npe, c->X.data(), c->conn.data() + eo * npe, Ji, &V);
-        for (int q = 0; q < 9; q++) jinv[(size_t)q * nep + e] = (float)Ji[q];
-        V0[e] = (float)V;
+        char *r = rec.data() + (size_t)(e / kT) * rb;
+        const int ei = (int)(e % kT);
+        std::memcpy(r + (size_t)ei * npe * 2, &p.conn_local[(size_t)e * npe], (size_t)npe * 2);
+        float *cf = reinterpret_cast<float *>(r + (size_t)kT * npe * 2) + ei;
+        int q = 0;
+        for (int j = 0; j < 9; j++) cf[(q++) * kT] = (float)Ji[j];
+        cf[(q++) * kT] = (float)V;
+        if (!c->mat6.empty())
+            for (int j = 0; j < 6; j++) cf[(q++) * kT] = (float)c->mat6[6 * eo + j];
+        if (!c->fib.empty())
+            for (int j = 0; j < 3; j++) cf[(q++) * kT] = (float)c->fib[3 * eo + j];
         for (int a = 0; a < npe; a++) {
             const int64_t i = c->conn[eo * npe + a];
             Mn[i] += c->prm.mass_scale * m.rho * V / npe;
@@ -469,15 +485,6 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         if (!c->ubar.empty())
             ub[g] = make_float4((float)c->ubar[3 * i], (float)c->ubar[3 * i + 1], (float)c->ubar[3 * i + 2], 0.f);
     }
-    std::vector<float> mat(c->mat6.empty() ? 0 : 6 * nep, 0.f), fib(c->fib.empty() ? 0 : 3 * nep, 0.f);
-    for (int64_t e = 0; e < nep; e++) {
-        const int64_t eo = p.elem_old[e];
-        if (eo < 0) continue;
-        if (!mat.empty())
-            for (int q = 0; q < 6; q++) mat[(size_t)q * nep + e] = (float)c->mat6[6 * eo + q];
-        if (!fib.empty())
-            for (int q = 0; q < 3; q++) fib[(size_t)q * nep + e] = (float)c->fib[3 * eo + q];
-    }
     // --- time step
     tled::stable_dt(npe, nn, c->X.data(), ne, c->conn.data(), m, c->mat6.empty() ? nullptr : c->mat6.data(), c->prm,
                     &c->dt_mech, &c->dt_th);
@@ -491,17 +498,12 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     CUDA_TRY(c, up(L.X0, X0.data(), 16 * nn));
     CUDA_TRY(c, up(L.nodec, nodec.data(), 16 * nn));
     CUDA_TRY(c, up(L.ubar, ub.data(), 16 * ub.size()));
-    CUDA_TRY(c, up(L.conn, p.conn_local.data(), 2 * p.conn_local.size()));
-    CUDA_TRY(c, up(L.jinv, jinv.data(), 4 * jinv.size()));
-    CUDA_TRY(c, up(L.V0, V0.data(), 4 * V0.size()));
-    CUDA_TRY(c, up(L.mat, mat.data(), 4 * mat.size()));
-    CUDA_TRY(c, up(L.fib, fib.data(), 4 * fib.size()));
+    CUDA_TRY(c, up(L.elem_rec, rec.data(), rec.size()));
     CUDA_TRY(c, up(L.tile_info, p.tile_info.data(), 4 * p.tile_info.size()));
     CUDA_TRY(c, up(L.tile_shared, p.tile_shared.data(), 4 * p.tile_shared.size()));
-    CUDA_TRY(c, up(L.rowptr, p.rowptr.data(), 2 * p.rowptr.size()));
-    CUDA_TRY(c, up(L.slots, p.slots.data(), 2 * p.slots.size()));
+    CUDA_TRY(c, up(L.csr, p.csr.data(), 2 * p.csr.size()));
     CUDA_TRY(c, up(L.sh_rowptr, p.sh_rowptr.data(), 4 * p.sh_rowptr.size()));
-    CUDA_TRY(c, up(L.sh_list, p.sh_list.data(), 4 * p.sh_list.size()));
+    CUDA_TRY(c, up(L.part_pos, p.part_pos.data(), 4 * p.part_pos.size()));
     CUDA_TRY(c, up(L.node_new, node_new.data(), 4 * nn));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     c->inited = true;  // buffers placed; the rest uses the regular paths
@@ -520,20 +522,18 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.X0 = dptr<float4>(c, L.X0);
     A.nodec = dptr<float4>(c, L.nodec);
     A.ubar = c->ubar.empty() ? nullptr : dptr<float4>(c, L.ubar);
-    A.conn_local = dptr<uint16_t>(c, L.conn);
-    A.jinv = dptr<float>(c, L.jinv);
-    A.V0 = dptr<float>(c, L.V0);
-    A.mat = c->mat6.empty() ? nullptr : dptr<float>(c, L.mat);
-    A.fib = c->fib.empty() ? nullptr : dptr<float>(c, L.fib);
+    A.elem_rec = dptr<char>(c, L.elem_rec);
+    A.rec_bytes = (int64_t)rb;
+    A.has_mat = !c->mat6.empty();
+    A.has_fib = !c->fib.empty();
     A.visc = dptr<float>(c, L.visc);
     A.ne = nep;
     A.tile_info = dptr<int>(c, L.tile_info);
     A.tile_shared = dptr<int>(c, L.tile_shared);
-    A.rowptr = dptr<uint16_t>(c, L.rowptr);
-    A.slots = dptr<uint16_t>(c, L.slots);
+    A.csr = dptr<uint16_t>(c, L.csr);
     A.partials = dptr<float4>(c, L.partials);
+    A.part_pos = dptr<int>(c, L.part_pos);
     A.sh_rowptr = dptr<int>(c, L.sh_rowptr);
-    A.sh_list = dptr<int>(c, L.sh_list);
     A.n_interior = p.n_interior;
     A.n_shared = p.n_shared;
     A.src = dptr<double>(c, L.src);
@@ -607,7 +607,7 @@ static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < K && e == cudaSuccess; k++) {
         e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
-        if (e == cudaSuccess) e = tled::launch_shared_step(c->A, c->npe, k, c->cap);
+        if (e == cudaSuccess) e = tled::launch_shared_step(c->A, k, c->cap);
     }
     if (e == cudaSuccess)
         e = tled::launch_bump(dptr<double>(c, c->L.time_base), dptr<int64_t>(c, c->L.step_base), K, c->dt, c->cap);
@@ -721,7 +721,7 @@ int tled_get_state(tled_ctx *c, double *u, double *v, double *T, double *Omega, 
         for (int64_t e = 0; e < nep; e++) {
             const int64_t eo = p.elem_old[e];
             if (eo < 0) continue;
-            for (int q = 0; q < np * 6; q++) visc[eo * np * 6 + q] = vs[(size_t)q * nep + e];
+            for (int q = 0; q < np * 6; q++) visc[eo * np * 6 + q] = vs[visc_index(np, e, q)];
         }
     if (t) *t = c->t;
     if (step) *step = c->step;
@@ -740,7 +740,7 @@ int tled_step_timed(tled_ctx *c, int64_t n, double *ms) {
         cudaEventRecord(ev[3 * i], c->stream);
         err = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
         cudaEventRecord(ev[3 * i + 1], c->stream);
-        if (err == cudaSuccess) err = tled::launch_shared_step(c->A, c->npe, 0, c->stream);
+        if (err == cudaSuccess) err = tled::launch_shared_step(c->A, 0, c->stream);
         cudaEventRecord(ev[3 * i + 2], c->stream);
         if (err == cudaSuccess)
             err = tled::launch_bump(dptr<double>(c, c->L.time_base), dptr<int64_t>(c, c->L.step_base), 1, c->dt,

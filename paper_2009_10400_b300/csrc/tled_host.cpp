@@ -177,8 +177,8 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     p.npe = npe;
     p.nn = nn;
     p.ne = ne;
-    if (tile_elems <= 0) tile_elems = kMaxTileElems;
-    tile_elems = std::min(tile_elems, kMaxTileElems);
+    if (tile_elems <= 0) tile_elems = kTile;
+    tile_elems = std::min(tile_elems, kTile);
     // --- Morton order of element centroids
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = 0; i < nn; i++)
@@ -247,12 +247,11 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         }
 
     // --- numbering: interior nodes tile by tile, then shared nodes by first tile.
-    // Element slots are padded so that every tile starts at a multiple of 4
-    // (16-byte aligned bulk copies of the per-element streams).
+    // Every tile owns kTile element slots (tile-blocked device records).
     p.node_new.assign(nn, -1);
     p.tile_info.assign((size_t)p.n_tiles * kTileInfo, 0);
     std::vector<int64_t> tile_pad(p.n_tiles + 1, 0);
-    for (int tt = 0; tt < p.n_tiles; tt++) tile_pad[tt + 1] = tile_pad[tt] + ((tile_begin[tt + 1] - tile_begin[tt] + 3) & ~3);
+    for (int tt = 0; tt < p.n_tiles; tt++) tile_pad[tt + 1] = tile_pad[tt] + kTile;
     p.ne_pad = tile_pad[p.n_tiles];
     if (p.ne_pad > 0x7fffffff) {
         err = "mesh too large";
@@ -288,9 +287,10 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     for (int tt = 0; tt < p.n_tiles; tt++)
         for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) p.elem_old[tile_pad[tt] + (i - tile_begin[tt])] = sorted_old[i];
     p.conn_local.assign((size_t)p.ne_pad * npe, 0);
-    p.slots.assign((size_t)p.ne_pad * npe, 0);
+    const int rec = csr_rec_u16(npe);
+    p.csr.assign((size_t)p.n_tiles * rec, 0);
     std::vector<int32_t> local(nn, -1);
-    std::vector<std::vector<int32_t>> sh_slots(p.n_shared);
+    std::vector<int32_t> sh_n(p.n_shared, 0);  // tiles touching each shared node so far
     int64_t part = 0;
     for (int tt = 0; tt < p.n_tiles; tt++) {
         int32_t *ti = &p.tile_info[(size_t)tt * kTileInfo];
@@ -314,12 +314,11 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         }
         ti[4] = nl;
         ti[5] = (int32_t)p.tile_shared.size();
-        while (p.rowptr.size() % 8) p.rowptr.push_back(0);
-        ti[6] = (int32_t)p.rowptr.size();
-        ti[7] = (int32_t)part;
+        ti[6] = (int32_t)part;
+        ti[7] = 0;
         for (size_t j = 0; j < shared.size(); j++) {
             p.tile_shared.push_back(shared[j]);
-            sh_slots[shared[j] - p.n_interior].push_back((int32_t)(part + (int64_t)j));
+            p.part_pos.push_back(sh_n[shared[j] - p.n_interior]++);  // rank; made absolute below
         }
         part += (int64_t)shared.size();
         // local index of every node of the tile
@@ -336,34 +335,26 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
                 p.conn_local[(size_t)i * npe + a] = (uint16_t)l;
             }
         }
-        // gather lists, one segment per chunk of kChunk elements: for every local
-        // node the slot offsets (corner * kChunk + element-in-chunk) of its
-        // incident corners, ascending element then corner; segment 1 follows
-        // segment 0 in the tile's code list.
-        int w = 0;
-        for (int ch = 0; ch < 2; ch++) {
-            const int64_t c0 = e0 + (int64_t)ch * kChunk, c1 = std::min<int64_t>(e0 + ne_t, c0 + kChunk);
-            std::vector<int32_t> cnt(nl + 1, 0);
-            for (int64_t i = c0; i < c1; i++)
-                for (int a = 0; a < npe; a++) cnt[p.conn_local[(size_t)i * npe + a] + 1]++;
-            cnt[0] = w;
-            for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
-            for (int l = 0; l <= nl; l++) p.rowptr.push_back((uint16_t)cnt[l]);
-            std::vector<int32_t> cur(cnt.begin(), cnt.end() - 1);
-            for (int64_t i = c0; i < c1; i++)
-                for (int a = 0; a < npe; a++) {
-                    int l = p.conn_local[(size_t)i * npe + a];
-                    p.slots[(size_t)e0 * npe + cur[l]++] = (uint16_t)(a * kChunk + (int)(i - c0));
-                }
-            w = cnt[nl];
-        }
+        // gather list: for every local node the slot offsets (corner * kTile +
+        // element) of its incident corners, ascending element then corner
+        uint16_t *rec_codes = &p.csr[(size_t)tt * rec];
+        uint16_t *rec_row = rec_codes + kTile * npe;
+        std::vector<int32_t> cnt(nl + 1, 0);
+        for (int64_t i = e0; i < e0 + ne_t; i++)
+            for (int a = 0; a < npe; a++) cnt[p.conn_local[(size_t)i * npe + a] + 1]++;
+        for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
+        for (int l = 0; l <= nl; l++) rec_row[l] = (uint16_t)cnt[l];
+        std::vector<int32_t> cur(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = e0; i < e0 + ne_t; i++)
+            for (int a = 0; a < npe; a++) {
+                int l = p.conn_local[(size_t)i * npe + a];
+                rec_codes[cur[l]++] = (uint16_t)(a * kTile + (int)(i - e0));
+            }
     }
-    while (p.rowptr.size() % 8) p.rowptr.push_back(0);
     p.n_partials = part;
     p.sh_rowptr.assign(p.n_shared + 1, 0);
-    for (int64_t s = 0; s < p.n_shared; s++) p.sh_rowptr[s + 1] = p.sh_rowptr[s] + (int32_t)sh_slots[s].size();
-    p.sh_list.reserve(part);
-    for (int64_t s = 0; s < p.n_shared; s++) p.sh_list.insert(p.sh_list.end(), sh_slots[s].begin(), sh_slots[s].end());
+    for (int64_t s = 0; s < p.n_shared; s++) p.sh_rowptr[s + 1] = p.sh_rowptr[s] + sh_n[s];
+    for (size_t j = 0; j < p.tile_shared.size(); j++) p.part_pos[j] += p.sh_rowptr[p.tile_shared[j] - p.n_interior];
     return TLED_OK;
 }
 

@@ -11,10 +11,12 @@
 
 namespace tled {
 
-constexpr int kBlock = 256;        // threads per CTA of the tile kernel = elements per chunk
-constexpr int kChunk = 256;        // a tile is processed in chunks of kChunk elements (one per thread)
-constexpr int kMaxTileElems = 512; // at most two chunks per tile
-constexpr int kMaxLocal = 768;     // max nodes touched by one tile (shared memory)
+constexpr int kBlock = 256;        // threads per CTA of the tile kernel
+constexpr int kTile = 256;         // elements per tile (one per thread); every tile owns kTile element slots
+constexpr int kMaxLocal = 448;     // max nodes touched by one tile (shared memory)
+constexpr int kNsMax = 256;        // interior nodes whose state is staged in shared memory
+// per-tile gather record (uint16): slot offsets [kTile * npe], then row offsets [kMaxLocal + 8]
+constexpr int csr_rec_u16(int npe) { return kTile * npe + kMaxLocal + 8; }
 constexpr int kMaxSources = 16;
 constexpr int kTileInfo = 8;       // ints per tile record
 
@@ -30,21 +32,20 @@ constexpr uint32_t kStatusTimeout = 4u;
 struct Plan {
     int npe = 0;
     int64_t nn = 0, ne = 0;
-    int64_t ne_pad = 0;                 // padded element count: every tile starts at a multiple of 4
-    std::vector<int32_t> elem_old;      // padded element slot -> caller element (-1 = padding)
+    int64_t ne_pad = 0;                 // n_tiles * kTile element slots
+    std::vector<int32_t> elem_old;      // element slot (tile * kTile + i) -> caller element (-1 = padding)
     std::vector<int32_t> node_new;      // caller node -> new node
     std::vector<int32_t> node_old;      // new node -> caller node
     int64_t n_interior = 0, n_shared = 0;
     int n_tiles = 0;
-    std::vector<int32_t> tile_info;     // [n_tiles][8]: e0 (padded slot, multiple of 4), ne, int_begin, n_int,
-                                        //   n_local, sh_off, row_off (multiple of 8), part_off
+    std::vector<int32_t> tile_info;     // [n_tiles][8]: e0 (= tile * kTile), ne, int_begin, n_int,
+                                        //   n_local, sh_off, part_off, 0
     std::vector<int32_t> tile_shared;   // per tile: new ids of its shared nodes (ascending)
     std::vector<uint16_t> conn_local;   // [ne_pad][npe] tile-local node index
-    std::vector<uint16_t> rowptr;       // per tile: 2 x (n_local + 1) offsets (one segment per chunk), padded to 8
-    std::vector<uint16_t> slots;        // [ne_pad*npe] slot offsets corner * kChunk + element-in-chunk, grouped
-                                        //   by chunk, then local node, ascending element within a node
-    std::vector<int32_t> sh_rowptr;     // [n_shared + 1]
-    std::vector<int32_t> sh_list;       // partial-slot indices, ascending tile order
+    std::vector<uint16_t> csr;          // [n_tiles][csr_rec_u16]: slot offsets corner * kTile + element, grouped
+                                        //   by local node (ascending element, corner), then the n_local + 1 row offsets
+    std::vector<int32_t> sh_rowptr;     // [n_shared + 1]: node-major partial positions, tile order within a node
+    std::vector<int32_t> part_pos;      // parallel to tile_shared: partial position of that (tile, node)
     int64_t n_partials = 0;
 };
 
@@ -57,22 +58,21 @@ struct StepArgs {
     const float4 *X0;      // X.xyz, lumped volume V_i
     const float4 *nodec;   // m_i, Cth_i, mask bits (as float bits), 0
     const float4 *ubar;    // prescribed displacement or nullptr
-    // element arrays (new numbering, SoA with stride ne)
-    const uint16_t *conn_local;
-    const float *jinv;     // [9][ne] inverse reference Jacobian at the integration point
-    const float *V0;       // [ne]
-    const float *mat;      // [6][ne] mu, kappa, k1, k2, k, alpha  or nullptr (uniform)
-    const float *fib;      // [3][ne] or nullptr (uniform)
-    float *visc;           // [n_prony*6][ne]
-    int64_t ne;
+    // element data, tile-blocked: tile t's record at elem_rec + t * rec_bytes holds the local
+    // connectivity [kTile][npe] (uint16) then float components [q][kTile]: J0^-1 (9), V0,
+    // [mu kappa k1 k2 k alpha], [fibre xyz]; the Prony state lives in visc [t][6 n_prony][kTile]
+    const char *elem_rec;
+    int64_t rec_bytes;
+    int has_mat, has_fib;
+    float *visc;
+    int64_t ne;            // element slots (n_tiles * kTile)
     // tiles
     const int *tile_info;
     const int *tile_shared;
-    const uint16_t *rowptr;
-    const uint16_t *slots;
-    float4 *partials;
+    const uint16_t *csr;   // [n_tiles][csr_rec_u16(npe)]
+    float4 *partials;      // node-major: shared node s owns [sh_rowptr[s], sh_rowptr[s+1]), one per touching tile
+    const int *part_pos;   // per (tile, shared node) entry of tile_shared: its partial's position
     const int *sh_rowptr;
-    const int *sh_list;
     int64_t n_interior, n_shared;
     // sources and time
     const double *src;     // [kMaxSources][10]
@@ -81,9 +81,9 @@ struct StepArgs {
     const int64_t *step_base;
     unsigned int *status;  // [4]: bits, first bad element (padded slot), first bad node (new id), spare
     // dynamic shared-memory layout of the tile kernel (bytes)
-    int sm_chunk_in;       // bytes of one chunk's staged element inputs
-    int sm_ch_stride;      // max(sm_chunk_in, slot buffer bytes), 128-aligned
-    int sm_codes, sm_rowptr, sm_xu, sm_X, sm_acc, sm_bar, sm_total;
+    int sm_in;             // bytes of a tile's staged element inputs (record + Prony state)
+    int sm_buf;            // max(sm_in, slot buffer bytes), 128-aligned; two such buffers
+    int sm_ns, sm_csr, sm_xu, sm_X, sm_bar, sm_total;
     int n_tiles;
     int n_comp;            // staged float components per element (J0^-1 9, V0, [mat 6], [fibre 3], Prony 6 n)
     // scalars
@@ -107,7 +107,7 @@ struct StepArgs {
 // kernel launchers (tled_kernels.cu)
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s);
 int tile_grid(const StepArgs &a, int npe, int n_sm);  // persistent grid size
-cudaError_t launch_shared_step(const StepArgs &a, int npe, int k, cudaStream_t s);
+cudaError_t launch_shared_step(const StepArgs &a, int k, cudaStream_t s);
 cudaError_t launch_bump(double *time_base, int64_t *step_base, int K, double dt, cudaStream_t s);
 // read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction
 cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,

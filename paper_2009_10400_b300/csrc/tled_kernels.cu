@@ -220,8 +220,9 @@ struct ElemIn {
     float vs[4][6];
 };
 
-// Element inputs staged in shared memory for one chunk: connectivity, then
-// float components [q][kChunk]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz], Prony state.
+// Element inputs staged in shared memory for one tile: local connectivity
+// [kTile][NPE] (uint16), then float components [q][kTile]: J0^-1 (9), V0,
+// [mu kappa k1 k2 k alpha], [fibre xyz], Prony state (6 per term).
 template <int NPE>
 __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, int ec, int *cl, ElemIn &E) {
     if constexpr (NPE == 8) {
@@ -232,26 +233,26 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, i
         const uint2 c = reinterpret_cast<const uint2 *>(base)[ec];
         cl[0] = c.x & 0xffff; cl[1] = c.x >> 16; cl[2] = c.y & 0xffff; cl[3] = c.y >> 16;
     }
-    const float *cp = reinterpret_cast<const float *>(base + kChunk * NPE * 2) + ec;
+    const float *cp = reinterpret_cast<const float *>(base + kTile * NPE * 2) + ec;
     int q = 0;
 #pragma unroll
-    for (int k = 0; k < 9; k++) E.Ji[k] = cp[(q++) * kChunk];
-    E.V = cp[(q++) * kChunk];
-    if (A.mat) {
-        E.mu = cp[(q++) * kChunk]; E.kap = cp[(q++) * kChunk]; E.k1 = cp[(q++) * kChunk];
-        E.k2 = cp[(q++) * kChunk]; E.kc = cp[(q++) * kChunk]; E.al = cp[(q++) * kChunk];
+    for (int k = 0; k < 9; k++) E.Ji[k] = cp[(q++) * kTile];
+    E.V = cp[(q++) * kTile];
+    if (A.has_mat) {
+        E.mu = cp[(q++) * kTile]; E.kap = cp[(q++) * kTile]; E.k1 = cp[(q++) * kTile];
+        E.k2 = cp[(q++) * kTile]; E.kc = cp[(q++) * kTile]; E.al = cp[(q++) * kTile];
     } else {
         E.mu = A.mu; E.kap = A.kappa; E.k1 = A.k1; E.k2 = A.k2; E.kc = A.kc; E.al = A.alpha;
     }
-    if (A.fib) {
-        E.ax = cp[(q++) * kChunk]; E.ay = cp[(q++) * kChunk]; E.az = cp[(q++) * kChunk];
+    if (A.has_fib) {
+        E.ax = cp[(q++) * kTile]; E.ay = cp[(q++) * kTile]; E.az = cp[(q++) * kTile];
     } else {
         E.ax = A.a0x; E.ay = A.a0y; E.az = A.a0z;
     }
 #pragma unroll
     for (int p = 0; p < 4; p++)
 #pragma unroll
-        for (int s = 0; s < 6; s++) E.vs[p][s] = (p < A.n_prony) ? cp[(q + p * 6 + s) * kChunk] : 0.f;
+        for (int s = 0; s < 6; s++) E.vs[p][s] = (p < A.n_prony) ? cp[(q + p * 6 + s) * kTile] : 0.f;
 }
 
 // One element: deformation gradient, thermal split, stress, Prony, nodal
@@ -260,8 +261,7 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, i
 template <int NPE>
 __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int ec, const int *cl, ElemIn &E,
                                              const float4 *__restrict__ s_xu, const float4 *__restrict__ s_X,
-                                             float4 *__restrict__ slot) {
-    const int64_t ne = A.ne;
+                                             float4 *__restrict__ slot, float *__restrict__ gvisc) {
     const float *Ji = E.Ji;
     const float V = E.V, mu = E.mu, kap = E.kap, k1 = E.k1, k2 = E.k2, kc = E.kc, al = E.al;
     const float ax = E.ax, ay = E.ay, az = E.az;
@@ -405,7 +405,7 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
 #pragma unroll
                 for (int s = 0; s < 6; s++) {
                     const float tp = A.pr_a[p] * S0[s] + A.pr_b[p] * E.vs[p][s];
-                    A.visc[(int64_t)(p * 6 + s) * ne + e] = tp;
+                    gvisc[(p * 6 + s) * kTile] = tp;
                     St[s] -= tp;
                 }
             }
@@ -481,13 +481,13 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
         ft[3] = khgT * qT[0]; ft[6] = khgT * qT[1]; ft[5] = khgT * qT[2]; ft[7] = -khgT * qT[3];
         wht8(fx); wht8(fy); wht8(fz); wht8(ft);
 #pragma unroll
-        for (int i = 0; i < 8; i++) slot[wht_corner(i) * kChunk + ec] = make_float4(fx[i], fy[i], fz[i], ft[i]);
+        for (int i = 0; i < 8; i++) slot[wht_corner(i) * kTile + ec] = make_float4(fx[i], fy[i], fz[i], ft[i]);
     } else {
         // T4: dh_0 = -(dh_1 + dh_2 + dh_3), dh_{j+1} = row j of J0^-1
         slot[ec] = make_float4(-(Qm[0][0] + Qm[0][1] + Qm[0][2]), -(Qm[1][0] + Qm[1][1] + Qm[1][2]),
                                -(Qm[2][0] + Qm[2][1] + Qm[2][2]), -(r[0] + r[1] + r[2]));
 #pragma unroll
-        for (int j = 0; j < 3; j++) slot[(1 + j) * kChunk + ec] = make_float4(Qm[0][j], Qm[1][j], Qm[2][j], r[j]);
+        for (int j = 0; j < 3; j++) slot[(1 + j) * kTile + ec] = make_float4(Qm[0][j], Qm[1][j], Qm[2][j], r[j]);
     }
 }
 
@@ -499,31 +499,42 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 }
 
 struct TileInfo {
-    int e0, ne_t, ib, n_int, nl, sh_off, row_off, part_off;
+    int e0, ne_t, ib, n_int, nl, sh_off, part_off;
 };
 __device__ __forceinline__ TileInfo tile_info(const StepArgs &A, int t) {
     const int4 a = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t);
     const int4 b = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t + 1);
-    return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z};
 }
-__device__ __forceinline__ uint32_t rowptr_bytes(int nl) { return (uint32_t)(((2 * (nl + 1)) + 7) & ~7) * 2; }
 
-// Warm L2 with a tile's streams (issued one tile ahead, so the bulk copies of
-// the next tile hit L2 while this one computes).
+__device__ __forceinline__ uint32_t visc_tile_bytes(const StepArgs &A) { return (uint32_t)(A.n_prony * 6 * kTile * 4); }
+
+// element record + Prony state of tile t -> buf
+__device__ __forceinline__ void stage_elem(const StepArgs &A, int t, char *buf, uint64_t *bar) {
+    const uint32_t rb = (uint32_t)A.rec_bytes, vb = visc_tile_bytes(A);
+    mbar_expect_tx(bar, rb + vb);
+    bulk_g2s(buf, A.elem_rec + (int64_t)t * A.rec_bytes, rb, bar);
+    if (vb) bulk_g2s(buf + rb, A.visc + (int64_t)t * (vb / 4), vb, bar);
+}
+// gather record and interior (u, theta, X0) of tile T
 template <int NPE>
-__device__ void prefetch_tile(const StepArgs &A, const TileInfo &T) {
-    const int64_t ne = A.ne;
-    const uint32_t n4 = (uint32_t)((T.ne_t + 3) & ~3);
-    prefetch_l2(A.conn_local + (int64_t)T.e0 * NPE, n4 * NPE * 2);
-    for (int j = 0; j < 9; j++) prefetch_l2(A.jinv + j * ne + T.e0, n4 * 4);
-    prefetch_l2(A.V0 + T.e0, n4 * 4);
-    if (A.mat)
-        for (int j = 0; j < 6; j++) prefetch_l2(A.mat + j * ne + T.e0, n4 * 4);
-    if (A.fib)
-        for (int j = 0; j < 3; j++) prefetch_l2(A.fib + j * ne + T.e0, n4 * 4);
-    for (int j = 0; j < 6 * A.n_prony; j++) prefetch_l2(A.visc + j * ne + T.e0, n4 * 4);
-    prefetch_l2(A.slots + (int64_t)T.e0 * NPE, n4 * NPE * 2);
-    prefetch_l2(A.rowptr + T.row_off, rowptr_bytes(T.nl));
+__device__ __forceinline__ void stage_nodes(const StepArgs &A, int t, const TileInfo &T, char *smem, uint64_t *bar) {
+    const uint32_t cb = (uint32_t)csr_rec_u16(NPE) * 2;
+    mbar_expect_tx(bar, cb + 32u * T.n_int);
+    bulk_g2s(smem + A.sm_csr, A.csr + (int64_t)t * csr_rec_u16(NPE), cb, bar);
+    if (T.n_int > 0) {
+        bulk_g2s(smem + A.sm_xu, A.xu + T.ib, 16u * T.n_int, bar);
+        bulk_g2s(smem + A.sm_X, A.X0 + T.ib, 16u * T.n_int, bar);
+    }
+}
+// warm L2 with tile t's streams
+template <int NPE>
+__device__ void prefetch_tile(const StepArgs &A, int t) {
+    const TileInfo T = tile_info(A, t);
+    prefetch_l2(A.elem_rec + (int64_t)t * A.rec_bytes, (uint32_t)A.rec_bytes);
+    const uint32_t vb = visc_tile_bytes(A);
+    if (vb) prefetch_l2(A.visc + (int64_t)t * (vb / 4), vb);
+    prefetch_l2(A.csr + (int64_t)t * csr_rec_u16(NPE), (uint32_t)csr_rec_u16(NPE) * 2);
     if (T.n_int > 0) {
         const uint32_t nb = 16u * T.n_int;
         prefetch_l2(A.xu + T.ib, nb);
@@ -535,137 +546,94 @@ __device__ void prefetch_tile(const StepArgs &A, const TileInfo &T) {
 }
 
 template <int NPE>
-__device__ void stage_tile(const StepArgs &A, const TileInfo &T, char *smem, uint64_t *bar) {
-    const int64_t ne = A.ne;
-    const int nch = (T.ne_t + kChunk - 1) / kChunk;
-    const int cin = kChunk * NPE * 2;
-    uint32_t tx = 0;
-    for (int c = 0; c < nch; c++) {
-        const int n4 = ((min(kChunk, T.ne_t - c * kChunk)) + 3) & ~3;
-        tx += n4 * NPE * 2 + A.n_comp * n4 * 4;
-    }
-    tx += (((T.ne_t + 3) & ~3) * NPE * 2) + rowptr_bytes(T.nl) + 32u * T.n_int;
-    mbar_expect_tx(bar, tx);
-    for (int c = 0; c < nch; c++) {
-        const int64_t eb = (int64_t)T.e0 + c * kChunk;
-        const int n4 = ((min(kChunk, T.ne_t - c * kChunk)) + 3) & ~3;
-        char *base = smem + c * A.sm_ch_stride;
-        bulk_g2s(base, A.conn_local + eb * NPE, n4 * NPE * 2, bar);
-        char *cp = base + cin;
-        int q = 0;
-        for (int j = 0; j < 9; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.jinv + j * ne + eb, n4 * 4, bar);
-        bulk_g2s(cp + (q++) * kChunk * 4, A.V0 + eb, n4 * 4, bar);
-        if (A.mat)
-            for (int j = 0; j < 6; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.mat + j * ne + eb, n4 * 4, bar);
-        if (A.fib)
-            for (int j = 0; j < 3; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.fib + j * ne + eb, n4 * 4, bar);
-        for (int j = 0; j < 6 * A.n_prony; j++) bulk_g2s(cp + (q++) * kChunk * 4, A.visc + j * ne + eb, n4 * 4, bar);
-    }
-    bulk_g2s(smem + A.sm_codes, A.slots + (int64_t)T.e0 * NPE, ((T.ne_t + 3) & ~3) * NPE * 2, bar);
-    bulk_g2s(smem + A.sm_rowptr, A.rowptr + T.row_off, rowptr_bytes(T.nl), bar);
-    if (T.n_int > 0) {
-        bulk_g2s(smem + A.sm_xu, A.xu + T.ib, 16u * T.n_int, bar);
-        bulk_g2s(smem + A.sm_X, A.X0 + T.ib, 16u * T.n_int, bar);
-    }
-}
-
-template <int NPE>
 __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
     __shared__ SrcSmem S;
     __shared__ int s_abort;
-    char *R = smem;  // chunk inputs at c * ch_stride; slot buffer at 0
-    const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_codes);
-    const uint16_t *s_row = reinterpret_cast<const uint16_t *>(smem + A.sm_rowptr);
+    const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_csr);
+    const uint16_t *s_row = s_code + kTile * NPE;
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
     float4 *s_X = reinterpret_cast<float4 *>(smem + A.sm_X);
-    float4 *s_acc = reinterpret_cast<float4 *>(smem + A.sm_acc);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);
-    float4 *slot = reinterpret_cast<float4 *>(R);
-    float4 *ns = reinterpret_cast<float4 *>(R + A.sm_ch_stride);
+    float4 *ns = reinterpret_cast<float4 *>(smem + A.sm_ns);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);  // [0,1] element buffers, [2] nodes, [3] node state
+    const int G = gridDim.x;
 
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int b = 0; b < 4; b++) mbar_init(&bar[b], 1);
         fence_barrier_init();
         s_abort = 0;
+        if ((int)blockIdx.x < A.n_tiles) {
+            stage_elem(A, blockIdx.x, smem, &bar[0]);
+            stage_nodes<NPE>(A, blockIdx.x, tile_info(A, blockIdx.x), smem, &bar[2]);
+        }
     }
     prepare_sources(A, k, S);  // __syncthreads inside: barrier init visible to all
-    uint32_t ph0 = 0, ph1 = 0;
-    for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
+    uint32_t ph_s = 0;
+    int i = 0;
+    for (int t = blockIdx.x; t < A.n_tiles; t += G, i++) {
         const TileInfo T = tile_info(A, t);
-        const int nch = (T.ne_t + kChunk - 1) / kChunk;
-        // node state of interior nodes goes to the second chunk's input area once that is consumed
-        const bool ns_smem = T.n_int > 0 && 48 * T.n_int <= A.sm_chunk_in;
-        // ---- 1. one thread stages the tile with bulk copies and warms L2 for the next one
-        if (threadIdx.x == 0) {
-            fence_proxy_async();
-            stage_tile<NPE>(A, T, smem, &bar[0]);
-            if (t + (int)gridDim.x < A.n_tiles) prefetch_tile<NPE>(A, tile_info(A, t + gridDim.x));
-        }
-        // ---- 2. meanwhile: the tile's shared nodes with ordinary loads (mostly L2 hits)
+        const int b = i & 1;
+        char *buf = smem + b * A.sm_buf;
+        float4 *slot = reinterpret_cast<float4 *>(buf);
+        const bool ns_smem = T.n_int > 0 && T.n_int <= kNsMax;
+        // ---- 1. shared nodes of the tile: ordinary loads (mostly L2 hits)
         for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
             const int64_t g = __ldg(A.tile_shared + T.sh_off + l - T.n_int);
             s_xu[l] = A.xu[g];
             s_X[l] = __ldg(&A.X0[g]);
         }
-        if (!mbar_wait(&bar[0], ph0)) {
+        bool ok = mbar_wait(&bar[2], i & 1);
+        ok = mbar_wait(&bar[b], (i >> 1) & 1) && ok;
+        if (!ok) {
             atomicOr(A.status, kStatusTimeout);
             s_abort = 1;
-            mbar_wait(&bar[0], ph0);
         }
-        ph0 ^= 1;
+        // ---- 2. element inputs -> registers; the buffer then becomes the slot buffer
+        const int ec = threadIdx.x;
+        const bool active = ec < T.ne_t;
+        int cl[NPE];
+        ElemIn E;
+        if (active) load_elem<NPE>(A, buf, ec, cl, E);
         __syncthreads();
         if (s_abort) return;
-        // ---- 3. element chunks: inputs -> registers, slots, fixed-order accumulation
-        for (int c = 0; c < nch; c++) {
-            const int ec = threadIdx.x;
-            const int el = c * kChunk + ec;
-            const bool active = el < T.ne_t;
-            int cl[NPE];
-            ElemIn E;
-            if (active) load_elem<NPE>(A, R + c * A.sm_ch_stride, ec, cl, E);
-            __syncthreads();  // chunk inputs consumed: the slot buffer may overwrite them
-            if (c == nch - 1 && ns_smem && threadIdx.x == 0) {
-                fence_proxy_async();
-                mbar_expect_tx(&bar[1], 48u * T.n_int);
-                bulk_g2s(ns, A.lo + T.ib, 16u * T.n_int, &bar[1]);
-                bulk_g2s(ns + T.n_int, A.vel + T.ib, 16u * T.n_int, &bar[1]);
-                bulk_g2s(ns + 2 * T.n_int, A.nodec + T.ib, 16u * T.n_int, &bar[1]);
+        if (threadIdx.x == 0) {
+            fence_proxy_async();
+            if (t + G < A.n_tiles) stage_elem(A, t + G, smem + (b ^ 1) * A.sm_buf, &bar[b ^ 1]);
+            if (ns_smem) {
+                mbar_expect_tx(&bar[3], 48u * T.n_int);
+                bulk_g2s(ns, A.lo + T.ib, 16u * T.n_int, &bar[3]);
+                bulk_g2s(ns + T.n_int, A.vel + T.ib, 16u * T.n_int, &bar[3]);
+                bulk_g2s(ns + 2 * T.n_int, A.nodec + T.ib, 16u * T.n_int, &bar[3]);
             }
-            if (active) element_step<NPE>(A, (int64_t)T.e0 + el, ec, cl, E, s_xu, s_X, slot);
-            __syncthreads();
-            const uint16_t *rp = s_row + c * (T.nl + 1);
-            for (int l = threadIdx.x; l < T.nl; l += kBlock) {
-                int r = rp[l];
-                const int r1 = rp[l + 1];
-                float4 a0 = c == 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : s_acc[l];
-                float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (; r + 1 < r1; r += 2) {
-                    const float4 v0 = slot[s_code[r]];
-                    const float4 v1 = slot[s_code[r + 1]];
-                    a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
-                    a1.x += v1.x; a1.y += v1.y; a1.z += v1.z; a1.w += v1.w;
-                }
-                if (r < r1) {
-                    const float4 v0 = slot[s_code[r]];
-                    a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
-                }
-                s_acc[l] = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
-            }
-            __syncthreads();
+            if (t + 2 * G < A.n_tiles) prefetch_tile<NPE>(A, t + 2 * G);
         }
-        // ---- 4. nodal update of interior nodes; partial sums of shared nodes
+        // ---- 3. element pass
+        if (active) {
+            float *gv = A.visc + (int64_t)t * A.n_prony * 6 * kTile + ec;
+            element_step<NPE>(A, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+        }
+        __syncthreads();
+        // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum,
+        //         and the last of the node's tiles to arrive sums the partials in tile order
         if (ns_smem) {
-            if (!mbar_wait(&bar[1], ph1)) {
-                atomicOr(A.status, kStatusTimeout);
-                mbar_wait(&bar[1], ph1);
-                return;
-            }
-            ph1 ^= 1;
+            if (!mbar_wait(&bar[3], ph_s)) atomicOr(A.status, kStatusTimeout);
+            ph_s ^= 1;
         }
         for (int l = threadIdx.x; l < T.nl; l += kBlock) {
-            const float4 acc = s_acc[l];
+            int r = s_row[l];
+            const int r1 = s_row[l + 1];
+            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+            for (; r + 1 < r1; r += 2) {
+                const float4 v0 = slot[s_code[r]];
+                const float4 v1 = slot[s_code[r + 1]];
+                a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
+                a1.x += v1.x; a1.y += v1.y; a1.z += v1.z; a1.w += v1.w;
+            }
+            if (r < r1) {
+                const float4 v0 = slot[s_code[r]];
+                a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
+            }
+            const float4 acc = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
             if (l < T.n_int) {
                 const int64_t g = (int64_t)T.ib + l;
                 float4 lo, vo, nc;
@@ -676,13 +644,20 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
                 }
                 node_update(A, g, acc, s_xu[l], s_X[l], lo, vo, nc, S);
             } else {
-                A.partials[T.part_off + l - T.n_int] = acc;
+                A.partials[__ldg(A.part_pos + T.sh_off + l - T.n_int)] = acc;
             }
         }
-        __syncthreads();  // all shared-memory reads of this tile done before the next staging
+        __syncthreads();
+        // ---- 5. stage the next tile's gather record and interior nodes
+        if (threadIdx.x == 0 && t + G < A.n_tiles) {
+            fence_proxy_async();
+            stage_nodes<NPE>(A, t + G, tile_info(A, t + G), smem, &bar[2]);
+        }
     }
 }
 
+// Nodes touched by several tiles: sum the node's partial sums in tile order,
+// then the same nodal update as the tile kernel.
 __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, const int k) {
     __shared__ SrcSmem S;
     prepare_sources(A, k, S);
@@ -692,8 +667,8 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
     const int64_t g = A.n_interior + s;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     const int r0 = __ldg(A.sh_rowptr + s), r1 = __ldg(A.sh_rowptr + s + 1);
-    for (int r = r0; r < r1; r++) {
-        const float4 c = A.partials[__ldg(A.sh_list + r)];
+    for (int r = r0; r < r1; r++) {  // the node's partial sums, in tile order
+        const float4 c = A.partials[r];
         acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
     }
     node_update(A, g, acc, A.xu[g], __ldg(&A.X0[g]), A.lo[g], A.vel[g], __ldg(&A.nodec[g]), S);
@@ -772,22 +747,20 @@ __global__ void stats_final_kernel(const double *partials, int nb, double *out) 
 static int align128(int x) { return (x + 127) & ~127; }
 
 void tile_smem_layout(StepArgs &a, int npe) {
-    a.n_comp = 10 + (a.mat ? 6 : 0) + (a.fib ? 3 : 0) + 6 * a.n_prony;
-    a.sm_chunk_in = align128(kChunk * npe * 2 + a.n_comp * kChunk * 4);
-    a.sm_ch_stride = std::max(a.sm_chunk_in, kChunk * npe * 16);
-    int off = a.sm_ch_stride + a.sm_chunk_in;  // two chunks (the second also hosts the interior node state)
-    a.sm_codes = off;
-    off = align128(off + kMaxTileElems * npe * 2);
-    a.sm_rowptr = off;
-    off = align128(off + (2 * (kMaxLocal + 1) + 8) * 2);
+    a.n_comp = 10 + (a.has_mat ? 6 : 0) + (a.has_fib ? 3 : 0) + 6 * a.n_prony;
+    a.sm_in = align128(kTile * npe * 2 + a.n_comp * kTile * 4);
+    a.sm_buf = std::max(a.sm_in, kTile * npe * 16);
+    int off = 2 * a.sm_buf;  // double-buffered element inputs; the current one is then the slot buffer
+    a.sm_ns = off;
+    off = align128(off + kNsMax * 48);
+    a.sm_csr = off;
+    off = align128(off + csr_rec_u16(npe) * 2);
     a.sm_xu = off;
     off = align128(off + kMaxLocal * 16);
     a.sm_X = off;
     off = align128(off + kMaxLocal * 16);
-    a.sm_acc = off;
-    off = align128(off + kMaxLocal * 16);
     a.sm_bar = off;
-    off = align128(off + 16);
+    off = align128(off + 32);
     a.sm_total = off;
 }
 
@@ -815,8 +788,7 @@ cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_shared_step(const StepArgs &a, int npe, int k, cudaStream_t s) {
-    (void)npe;
+cudaError_t launch_shared_step(const StepArgs &a, int k, cudaStream_t s) {
     if (a.n_shared <= 0) return cudaSuccess;
     const int nb = (int)((a.n_shared + 255) / 256);
     shared_step_kernel<<<nb, 256, 0, s>>>(a, k);

@@ -47,18 +47,22 @@ def test_plan_counts_structured_block():
     prob = W.block_h8(n=16, h=3e-3)
     p = _planner(prob)
     info = p.plan_info()
-    # Morton order cuts 16^3 into eight 8^3 tiles of 512 elements
-    assert info["n_tiles"] == 8
+    # Morton order cuts 16^3 into sixteen 8x8x4 tiles of 256 elements
+    assert info["n_tiles"] == 16
     assert info["n_interior"] + info["n_shared"] == prob.nn
-    # shared nodes are exactly those on the three internal planes i, j or k = 8
-    assert info["n_shared"] == 17 ** 3 - 16 ** 3
+    # shared nodes are exactly those on the internal planes i = 8, j = 8, k = 4, 8, 12
+    idx = np.arange(17)
+    on_plane = lambda v, planes: np.isin(v, planes)
+    I, J, K = np.meshgrid(idx, idx, idx, indexing="ij")
+    shared = on_plane(I, [8]) | on_plane(J, [8]) | on_plane(K, [4, 8, 12])
+    assert info["n_shared"] == int(shared.sum())
     assert info["workspace"] > 0
 
 
 def test_plan_single_tile_has_no_shared_nodes():
-    prob = W.cube_h8(n=8)
+    prob = W.cube_h8(n=6)
     info = _planner(prob).plan_info()
-    assert info["n_tiles"] == 1 and info["n_shared"] == 0 and info["n_interior"] == 729
+    assert info["n_tiles"] == 1 and info["n_shared"] == 0 and info["n_interior"] == 343
 
 
 def test_plan_tile_size_parameter():
