@@ -238,6 +238,30 @@ int tled_plan_info(tled_ctx *ctx, int64_t *info);
  * (deterministic).  Synchronises. */
 int tled_get_stats(tled_ctx *ctx, tled_stats *s);
 
+/* Allocation-free diagnostics (the paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory when they want the
+ * numbers -- code running during CUDA graph capture, where cudaMalloc is not
+ * allowed; real-time loops in which an allocation would synchronise the
+ * device; processes whose device memory is fully held by another caching
+ * allocator).  Enqueues on the context stream the same FP64 reduction as
+ * tled_get_stats and writes six doubles to the DEVICE buffer `out`:
+ *   out[0] kinetic energy sum_i 1/2 m_i |v_i|^2          (J)
+ *   out[1] heat content sum_i C_i (T_i - T0)              (J)
+ *   out[2] max_i (T_i - T0), out[3] min_i (T_i - T0)       (K)
+ *   out[4] max_i |u_i|^2                                   (m^2)
+ *   out[5] sum of lumped volumes with Omega >= 1           (m^3)
+ * n_blocks: reduction blocks, 0 = 296; values above 296 are rejected with
+ * E_ARG (the block partial sums live in a static device array of 296 x 8
+ * doubles, 18,944 bytes, that every GPU loading the library keeps until the
+ * process exits).  Allocates nothing (no cudaMalloc, no allocating library
+ * call) and does not synchronise.  The first call on a device looks up that
+ * array's device address; make that first call before any stream capture.
+ * All calls in the process share the array: each call overwrites the partial
+ * sums it reads, so nothing needs clearing, but calls whose kernels overlap
+ * on the GPU (different streams, or different contexts on one device) race
+ * on it and must be ordered by the caller. */
+int tled_get_stats_noalloc(tled_ctx *ctx, int32_t n_blocks, double *out);
+
 /* Checkpoint: serialise the exact device state (bitwise) with a header and
  * checksum.  Call with buf NULL to get *bytes; then with a buffer of that
  * size.  load verifies magic, sizes, a hash of the set-up and the checksum

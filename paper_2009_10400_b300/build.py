@@ -13,7 +13,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtled.so")
-SOURCES = ["tled_host.cpp", "tled_capi.cpp", "tled_kernels.cu"]
+SOURCES = ["tled_host.cpp", "tled_capi.cpp", "tled_kernels.cu", "tled_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 

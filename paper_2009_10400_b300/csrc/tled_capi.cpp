@@ -803,6 +803,20 @@ int tled_get_stats(tled_ctx *c, tled_stats *s) {
     return TLED_OK;
 }
 
+int tled_get_stats_noalloc(tled_ctx *c, int32_t n_blocks, double *out) {
+    if (!c || !out) return fail(c, TLED_E_ARG, "NULL context or output");
+    if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
+    if (n_blocks == 0) n_blocks = tled::kNoAllocMaxBlocks;
+    if (n_blocks < 0 || n_blocks > tled::kNoAllocMaxBlocks)
+        return fail(c, TLED_E_ARG, "n_blocks must be 1.." + std::to_string(tled::kNoAllocMaxBlocks) +
+                                       " (size of the static scratch array), got " + std::to_string(n_blocks));
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    double *scratch = nullptr;
+    CUDA_TRY(c, tled::noalloc_scratch(c->device, &scratch));
+    CUDA_TRY(c, tled::launch_stats_blocks(c->A, c->nn, n_blocks, scratch, out, c->stream));
+    return TLED_OK;
+}
+
 // --- checkpoints -----------------------------------------------------------
 namespace {
 struct CkptHeader {

@@ -118,6 +118,12 @@ cudaError_t tile_kernel_setup(const StepArgs &a, int npe);
 // damaged volume; deterministic two-stage reduction through `partials` [kStatBlocks][8].
 constexpr int kStatBlocks = 296;
 cudaError_t launch_stats(const StepArgs &a, int64_t nn, double *partials, double *out, cudaStream_t s);
+// the same reduction over a caller-chosen number of blocks (partials [n_blocks][8])
+cudaError_t launch_stats_blocks(const StepArgs &a, int64_t nn, int n_blocks, double *partials, double *out,
+                                cudaStream_t s);
+// allocation-free variant: block partials in a static device array (tled_noalloc.cu)
+constexpr int kNoAllocMaxBlocks = 296;
+cudaError_t noalloc_scratch(int device, double **ptr);
 
 // host geometry and planning (tled_host.cpp)
 bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V);

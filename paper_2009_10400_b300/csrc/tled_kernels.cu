@@ -813,4 +813,11 @@ cudaError_t launch_stats(const StepArgs &a, int64_t nn, double *partials, double
     return cudaGetLastError();
 }
 
+cudaError_t launch_stats_blocks(const StepArgs &a, int64_t nn, int n_blocks, double *partials, double *out,
+                                cudaStream_t s) {
+    stats_partial_kernel<<<n_blocks, 256, 0, s>>>(a, nn, partials);
+    stats_final_kernel<<<1, 32, 0, s>>>(partials, n_blocks, out);
+    return cudaGetLastError();
+}
+
 }  // namespace tled

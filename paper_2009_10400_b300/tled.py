@@ -86,6 +86,7 @@ _SIGS = {
     "tled_get_state": ([C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_int64)], C.c_int),
     "tled_get_stats": ([C.c_void_p, C.POINTER(Stats)], C.c_int),
     "tled_step_timed": ([C.c_void_p, C.c_int64, _dp], C.c_int),
+    "tled_get_stats_noalloc": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "tled_plan_info": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_save_state": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_load_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
@@ -347,6 +348,13 @@ class Solver:
         s = Stats()
         self._check(lib().tled_get_stats(self.h, C.byref(s)))
         return s.as_dict()
+
+    def stats_noalloc(self, out, n_blocks=0):
+        """Allocation-free diagnostics into a device float64 tensor of 6 entries
+        (enqueued on the solver's stream, no synchronisation)."""
+        assert out.is_cuda and out.dtype.is_floating_point and out.element_size() == 8 and out.numel() >= 6
+        self._check(lib().tled_get_stats_noalloc(self.h, int(n_blocks), C.c_void_p(out.data_ptr())))
+        return out
 
     def save_state(self) -> bytes:
         n = C.c_int64()
