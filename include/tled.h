@@ -231,8 +231,55 @@ int tled_step_timed(tled_ctx *ctx, int64_t n, double *ms);
 
 /* Plan summary after tled_workspace_size(): info[0] tiles, [1] interior
  * nodes, [2] shared nodes, [3] partial slots, [4] workspace bytes, [5]
- * element type. */
+ * element type, [6] scenarios, [7] persistent CTAs of the tile kernel (after
+ * init).  info has 8 entries. */
 int tled_plan_info(tled_ctx *ctx, int64_t *info);
+
+/* ---- probes (temperature and damage at points, e.g. a 16^3 lattice) ----
+ * Set-up call of a single-scenario context: n points xyz [n][3] (host
+ * float64, reference coordinates).  Each point is located in the mesh when
+ * the context is planned (E_ARG if a point lies outside every element) and
+ * is interpolated with the element's shape functions. */
+int tled_set_probes(tled_ctx *ctx, int64_t n, const double *xyz);
+/* out [2][n_probes] float64: temperature (C) then damage fraction, in probe
+ * order (for a batch: scenario 0's probes, then scenario 1's, ...).  where as
+ * for the field read-backs. */
+int tled_get_probes(tled_ctx *ctx, double *out, int where);
+
+/* ---- batches: many independent scenarios advanced by the same launches ----
+ * Treatment planning runs many scenarios (meshes, sources, tissue parameters,
+ * durations) at once.  A batch context holds copies of fully set-up single
+ * scenario contexts; their meshes are concatenated (caller numbering:
+ * scenario 0 first), tiled without crossing scenarios, and one launch of the
+ * step kernels per step advances all unfinished scenarios, each with its own
+ * time step.  A scenario stops after n_steps steps (its state then stays
+ * fixed).  Scenarios must share the element type, number of Prony terms,
+ * T0, Ta, Arrhenius constants, c/k slopes, flags, hourglass coefficients and
+ * ramp time (E_ARG otherwise).  After tled_batch_add the usual
+ * tled_workspace_size / tled_init / tled_step / tled_get_* / tled_get_probes /
+ * checkpoint calls apply to the whole batch. */
+int tled_batch_create(tled_ctx **out, int device, void *cuda_stream);
+/* Append a copy of `scenario`'s set-up (mesh, material, BCs, sources,
+ * params, probes); *index receives its scenario index. */
+int tled_batch_add(tled_ctx *batch, const tled_ctx *scenario, int64_t n_steps, int32_t *index);
+/* Run until every scenario has taken its n_steps (enqueued; *steps receives
+ * the number of launches-steps run). */
+int tled_batch_run(tled_ctx *batch, int64_t *steps);
+/* info[0] node offset, [1] nodes, [2] element offset, [3] elements, [4]
+ * n_steps (-1 = unbounded), [5] steps taken, [6] probe offset, [7] probes. */
+int tled_scenario_info(tled_ctx *ctx, int32_t index, int64_t *info);
+/* time step of one scenario (after init) */
+int tled_scenario_dt(tled_ctx *ctx, int32_t index, double *dt);
+
+/* ---- autotuner ----
+ * Time the candidate tilings (elements per tile 256 / 192 / 128, persistent
+ * grid of one or two CTAs per SM) for `trial_steps` steps each in the
+ * caller's workspace (bytes of it), keep the fastest, and leave the context
+ * initialised with it at t = 0 (state reset).  The choice is cached in the
+ * process per element type, size (log2 of the element count), material
+ * layout and scenario count; a cached choice is applied without timing.
+ * choice[0] elements per tile, [1] CTAs, [2] 1 if it came from the cache. */
+int tled_autotune(tled_ctx *ctx, void *dev_workspace, int64_t bytes, int32_t trial_steps, int32_t *choice);
 
 /* Scalar diagnostics, reduced on the device in FP64 in a fixed order
  * (deterministic).  Synchronises. */

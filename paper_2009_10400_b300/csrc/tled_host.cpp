@@ -171,8 +171,8 @@ static inline uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
     return v;
 }
 
-int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, int tile_elems, Plan &p,
-               std::string &err) {
+int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const int32_t *group,
+               int tile_elems, Plan &p, std::string &err) {
     p = Plan();
     p.npe = npe;
     p.nn = nn;
@@ -202,18 +202,25 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     }
     p.elem_old.resize(ne);
     std::iota(p.elem_old.begin(), p.elem_old.end(), 0);
-    std::stable_sort(p.elem_old.begin(), p.elem_old.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    // elements ordered by group (scenario rank), then along the Morton curve
+    std::stable_sort(p.elem_old.begin(), p.elem_old.end(), [&](int32_t a, int32_t b) {
+        const int32_t ga = group ? group[a] : 0, gb = group ? group[b] : 0;
+        return ga != gb ? ga < gb : key[a] < key[b];
+    });
 
     // --- cut tiles: at most tile_elems elements and kMaxLocal distinct nodes
     std::vector<int32_t> mark(nn, -1);
     std::vector<int32_t> tile_begin;
     int n_local = 0, n_in = 0, t = -1;
+    int32_t prev_group = -1;
     for (int64_t i = 0; i < ne; i++) {
         const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
+        const int32_t gi = group ? group[p.elem_old[i]] : 0;
         int fresh = 0;
         if (t >= 0)
             for (int a = 0; a < npe; a++) fresh += (mark[cn[a]] != t);
-        if (t < 0 || n_in == tile_elems || n_local + fresh > kMaxLocal) {
+        if (t < 0 || n_in == tile_elems || n_local + fresh > kMaxLocal || gi != prev_group) {  // tiles never span groups
+            prev_group = gi;
             t++;
             tile_begin.push_back((int32_t)i);
             n_local = 0;

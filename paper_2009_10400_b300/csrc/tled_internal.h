@@ -49,6 +49,17 @@ struct Plan {
     int64_t n_partials = 0;
 };
 
+// Constant per-scenario parameters (device table).
+struct ScenDev {
+    double dt;
+    float dtf, inv_dt;
+    float damp_a, damp_b;  // v+ = damp_a v - damp_b f / m: (1 - g dt/2)/(1 + g dt/2), dt/(1 + g dt/2)
+    float pr_a[4], pr_b[4];  // Prony: dt phi/(dt + tau), tau/(dt + tau)
+    float Qm;              // metabolic heat W/m^3
+    int src_off, n_src;    // sources [src_off, src_off + n_src) of the global table
+    int pad;
+};
+
 // Arguments of the step kernels (passed by value).
 struct StepArgs {
     // node arrays (new numbering)
@@ -74,31 +85,29 @@ struct StepArgs {
     const int *part_pos;   // per (tile, shared node) entry of tile_shared: its partial's position
     const int *sh_rowptr;
     int64_t n_interior, n_shared;
-    // sources and time
-    const double *src;     // [kMaxSources][10]
-    const int *n_src;      // device scalar (sources may change between chunks)
-    const double *time_base;
-    const int64_t *step_base;
-    unsigned int *status;  // [4]: bits, first bad element (padded slot), first bad node (new id), spare
+    // scenarios (a single problem is one scenario)
+    const struct ScenDev *scn;  // [n_scn] constant per-scenario parameters
+    const double *src;     // [total sources][10]: c0 xyz, velocity xyz, sigma, peak, t_on, t_off
+    double *scn_time;      // [n_scn] time t0 at step 0; step n is at t0 + n dt
+    int64_t *scn_step;     // [n_scn] steps taken at the start of the current graph chunk
+    const int *tile_scn;   // [n_tiles] scenario of each tile
+    const int *shared_scn; // [n_shared] scenario of each shared node
+    const int *n_active;   // device [2]: active tiles, active shared nodes (prefixes of the orders)
+    int n_scn;
+    unsigned int *status;  // [4]: bits, first bad element (slot), first bad node (new id), spare
     // dynamic shared-memory layout of the tile kernel (bytes)
     int sm_in;             // bytes of a tile's staged element inputs (record + Prony state)
     int sm_buf;            // max(sm_in, slot buffer bytes), 128-aligned; two such buffers
     int sm_ns, sm_csr, sm_xu, sm_X, sm_bar, sm_total;
     int n_tiles;
     int n_comp;            // staged float components per element (J0^-1 9, V0, [mat 6], [fibre 3], Prony 6 n)
-    // scalars
-    double dt;
-    float dtf;
-    float inv_dt;
-    float damp_a, damp_b;  // v+ = damp_a v + damp_b (-f/m) with damp_a = (1-g dt/2)/(1+g dt/2), damp_b = dt/(1+g dt/2)
-    float mu, kappa, k1, k2, kc, alpha;   // uniform material
-    float a0x, a0y, a0z;
+    // batch-wide scalars
+    float mu, kappa, k1, k2, kc, alpha;   // uniform material (used when has_mat == 0)
+    float a0x, a0y, a0z;                  // uniform fibre (used when has_fib == 0)
     int n_prony;
-    float pr_a[4], pr_b[4];               // Prony coefficients dt phi/(dt+tau), tau/(dt+tau)
     unsigned int flags;
     float beta_c, beta_k, Tref_m_T0;      // T_ref - T0
     float theta_a;                        // Ta - T0
-    float wbcb, Qm;
     float lnA, Ea_R, T0_K;                // T0 + 273.15
     float khg, khgT;                      // kappa_hg, kappa_hgT
     double ramp_time;
@@ -108,7 +117,10 @@ struct StepArgs {
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s);
 int tile_grid(const StepArgs &a, int npe, int n_sm);  // persistent grid size
 cudaError_t launch_shared_step(const StepArgs &a, int k, cudaStream_t s);
-cudaError_t launch_bump(double *time_base, int64_t *step_base, int K, double dt, cudaStream_t s);
+cudaError_t launch_bump(const StepArgs &a, int K, cudaStream_t s);
+// temperature and damage at probe points: out [2][n]
+cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w, int64_t n, double T0, double *out,
+                          cudaStream_t s);
 // read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction
 cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,
                             cudaStream_t s);
@@ -129,7 +141,9 @@ cudaError_t noalloc_scratch(int device, double **ptr);
 bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V);
 void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const tled_material &m,
                const double *mat6, const tled_params &p, double *dt_mech, double *dt_th);
-int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, int tile_elems, Plan &p,
-               std::string &err);
+// group: optional [ne] group id per element (scenario rank); tiles never span groups and
+// follow ascending group order.
+int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const int32_t *group,
+               int tile_elems, Plan &p, std::string &err);
 
 }  // namespace tled

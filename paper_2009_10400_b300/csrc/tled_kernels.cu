@@ -56,28 +56,42 @@ __device__ __forceinline__ void add_ff(float &hi, float &lo, float d) {
     hi = h2;
 }
 
-struct SrcSmem {
-    float cx[kMaxSources], cy[kMaxSources], cz[kMaxSources], inv2s2[kMaxSources], P[kMaxSources];
-    double t;
+// Per-scenario values of one step: time, step size, damping and Prony
+// coefficients, and the heat sources' centres c(t) = c0 + v t and powers.
+struct ScenStep {
+    double t, dt;
+    float dtf, inv_dt, damp_a, damp_b, Qm;
+    float pr_a[4], pr_b[4];
     int n;
+    float cx[kMaxSources], cy[kMaxSources], cz[kMaxSources], inv2s2[kMaxSources], P[kMaxSources];
 };
 
-// Source centres c(t) = c0 + vel t at this step's time, once per CTA.
-__device__ __forceinline__ void prepare_sources(const StepArgs &A, int k, SrcSmem &S) {
-    if (threadIdx.x == 0) {
-        S.t = *A.time_base + (double)k * A.dt;
-        S.n = *A.n_src;
+// Fill P for scenario s at step k of the current chunk.  Called by all threads of
+// a group; thread `lane` handles source `lane`, lane 0 the scalars (no barrier inside).
+__device__ __forceinline__ void prepare_scen(const StepArgs &A, int s, int k, ScenStep &P, int lane, int nlanes) {
+    const ScenDev &D = A.scn[s];
+    const double t = A.scn_time[s] + (double)(A.scn_step[s] + k) * D.dt;  // t0 + n dt, no accumulation
+    if (lane == 0) {
+        P.t = t;
+        P.dt = D.dt;
+        P.dtf = D.dtf;
+        P.inv_dt = D.inv_dt;
+        P.damp_a = D.damp_a;
+        P.damp_b = D.damp_b;
+        P.Qm = D.Qm;
+        for (int i = 0; i < 4; i++) {
+            P.pr_a[i] = D.pr_a[i];
+            P.pr_b[i] = D.pr_b[i];
+        }
+        P.n = D.n_src;
     }
-    __syncthreads();
-    const int s = threadIdx.x;
-    if (s < S.n) {
-        const double *p = A.src + 10 * s;
-        const double t = S.t;
-        S.cx[s] = (float)(p[0] + p[3] * t);
-        S.cy[s] = (float)(p[1] + p[4] * t);
-        S.cz[s] = (float)(p[2] + p[5] * t);
-        S.inv2s2[s] = (float)(0.5 / (p[6] * p[6]));
-        S.P[s] = (t >= p[8] && t < p[9]) ? (float)p[7] : 0.f;
+    for (int q = lane; q < D.n_src; q += nlanes) {
+        const double *p = A.src + 10 * (int64_t)(D.src_off + q);
+        P.cx[q] = (float)(p[0] + p[3] * t);
+        P.cy[q] = (float)(p[1] + p[4] * t);
+        P.cz[q] = (float)(p[2] + p[5] * t);
+        P.inv2s2[q] = (float)(0.5 / (p[6] * p[6]));
+        P.P[q] = (t >= p[8] && t < p[9]) ? (float)p[7] : 0.f;
     }
 }
 
@@ -126,12 +140,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // nodal update: Eq. (27) in velocity form, Eq. (20), Arrhenius
 // ---------------------------------------------------------------------------
 // xu: (u_hi, theta_hi); X: (X0, V_i); lo: (u_lo, theta_lo); vo: (v, Omega);
-// nc: (1/m_i, 1/C_i, mask bits, 0); f: (internal force, thermal load).
-__device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4 f, float4 xu, float4 X, float4 lo,
-                                            float4 vo, float4 nc, const SrcSmem &S) {
+// nc: (1/m_i, 1/C_i, mask bits, K_b,i); f: (internal force, thermal load).
+// nc.w: perfusion conductance w_b c_b V_i of the node.
+__device__ __forceinline__ void node_update(const StepArgs &A, const ScenStep &S, int64_t g, float4 f, float4 xu,
+                                            float4 X, float4 lo, float4 vo, float4 nc) {
     const unsigned mask = __float_as_uint(nc.z);
     const bool comp = (A.flags & TLED_COMPENSATED) != 0;
-    const float dt = A.dtf;
+    const float dt = S.dtf;
     // current position for the heat source (state at t)
     const float px = X.x + (xu.x + lo.x), py = X.y + (xu.y + lo.y), pz = X.z + (xu.z + lo.z);
 
@@ -144,17 +159,17 @@ __device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4
             // prescribed: u(t+dt) = ubar * ramp(t+dt), v consistent with it
             float target = 0.f;
             if (A.ubar) {
-                const double tn = S.t + A.dt;
+                const double tn = S.t + S.dt;
                 const double r = (A.ramp_time > 0.0 && tn < A.ramp_time) ? tn / A.ramp_time : 1.0;
                 const float4 ub = __ldg(&A.ubar[g]);
                 target = (float)((d == 0 ? ub.x : d == 1 ? ub.y : ub.z) * r);
             }
-            v[d] = (target - u[d] - ul[d]) * A.inv_dt;
+            v[d] = (target - u[d] - ul[d]) * S.inv_dt;
             u[d] = target;
             ul[d] = 0.f;
         } else {
             // v+ = [(1 - g dt/2) v + dt (R - f)/m] / (1 + g dt/2), R = 0; u+ = u + dt v+
-            v[d] = A.damp_a * v[d] - A.damp_b * fv[d] * im;
+            v[d] = S.damp_a * v[d] - S.damp_b * fv[d] * im;
             if (comp)
                 add_ff(u[d], ul[d], dt * v[d]);
             else
@@ -166,13 +181,13 @@ __device__ __forceinline__ void node_update(const StepArgs &A, int64_t g, float4
     const float theta = th + tl;
     float iC = nc.y;
     if (A.flags & TLED_TEMP_DEP) iC = __fdividef(iC, 1.f + A.beta_c * (theta - A.Tref_m_T0));
-    float Q = A.Qm;
+    float Q = S.Qm;
     for (int s = 0; s < S.n; s++) {
         const float dx = px - S.cx[s], dy = py - S.cy[s], dz = pz - S.cz[s];
         Q += S.P[s] * __expf(-(dx * dx + dy * dy + dz * dz) * S.inv2s2[s]);
     }
     if (!(mask & TLED_FIX_T)) {
-        const float dth = dt * iC * (-f.w + X.w * (Q - A.wbcb * (theta - A.theta_a)));
+        const float dth = dt * iC * (-f.w + X.w * Q - nc.w * (theta - A.theta_a));
         if (comp)
             add_ff(th, tl, dth);
         else
@@ -259,9 +274,10 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, i
 // forces + hourglass, thermal loads.  Corner contributions are written to the
 // chunk's slot buffer at [corner][ec] (conflict-free).
 template <int NPE>
-__device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int ec, const int *cl, ElemIn &E,
-                                             const float4 *__restrict__ s_xu, const float4 *__restrict__ s_X,
-                                             float4 *__restrict__ slot, float *__restrict__ gvisc) {
+__device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &SP, int64_t e, int ec, const int *cl,
+                                             ElemIn &E, const float4 *__restrict__ s_xu,
+                                             const float4 *__restrict__ s_X, float4 *__restrict__ slot,
+                                             float *__restrict__ gvisc) {
     const float *Ji = E.Ji;
     const float V = E.V, mu = E.mu, kap = E.kap, k1 = E.k1, k2 = E.k2, kc = E.kc, al = E.al;
     const float ax = E.ax, ay = E.ay, az = E.az;
@@ -404,7 +420,7 @@ __device__ __forceinline__ void element_step(const StepArgs &A, int64_t e, int e
             if (p < A.n_prony) {
 #pragma unroll
                 for (int s = 0; s < 6; s++) {
-                    const float tp = A.pr_a[p] * S0[s] + A.pr_b[p] * E.vs[p][s];
+                    const float tp = SP.pr_a[p] * S0[s] + SP.pr_b[p] * E.vs[p][s];
                     gvisc[(p * 6 + s) * kTile] = tp;
                     St[s] -= tp;
                 }
@@ -548,7 +564,7 @@ __device__ void prefetch_tile(const StepArgs &A, int t) {
 template <int NPE>
 __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
-    __shared__ SrcSmem S;
+    __shared__ ScenStep S;
     __shared__ int s_abort;
     const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_csr);
     const uint16_t *s_row = s_code + kTile * NPE;
@@ -558,24 +574,30 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);  // [0,1] element buffers, [2] nodes, [3] node state
     const int G = gridDim.x;
 
+    const int n_tiles = *A.n_active;  // tiles of unfinished scenarios form a prefix
     if (threadIdx.x == 0) {
         for (int b = 0; b < 4; b++) mbar_init(&bar[b], 1);
         fence_barrier_init();
         s_abort = 0;
-        if ((int)blockIdx.x < A.n_tiles) {
+        if ((int)blockIdx.x < n_tiles) {
             stage_elem(A, blockIdx.x, smem, &bar[0]);
             stage_nodes<NPE>(A, blockIdx.x, tile_info(A, blockIdx.x), smem, &bar[2]);
         }
     }
-    prepare_sources(A, k, S);  // __syncthreads inside: barrier init visible to all
+    __syncthreads();  // barrier init visible to all
     uint32_t ph_s = 0;
-    int i = 0;
-    for (int t = blockIdx.x; t < A.n_tiles; t += G, i++) {
+    int i = 0, cur_scn = -1;
+    for (int t = blockIdx.x; t < n_tiles; t += G, i++) {
         const TileInfo T = tile_info(A, t);
         const int b = i & 1;
         char *buf = smem + b * A.sm_buf;
         float4 *slot = reinterpret_cast<float4 *>(buf);
         const bool ns_smem = T.n_int > 0 && T.n_int <= kNsMax;
+        const int scn = __ldg(A.tile_scn + t);
+        if (scn != cur_scn) {  // published by the barrier after the element inputs are read
+            prepare_scen(A, scn, k, S, threadIdx.x, kBlock);
+            cur_scn = scn;
+        }
         // ---- 1. shared nodes of the tile: ordinary loads (mostly L2 hits)
         for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
             const int64_t g = __ldg(A.tile_shared + T.sh_off + l - T.n_int);
@@ -598,19 +620,19 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
         if (s_abort) return;
         if (threadIdx.x == 0) {
             fence_proxy_async();
-            if (t + G < A.n_tiles) stage_elem(A, t + G, smem + (b ^ 1) * A.sm_buf, &bar[b ^ 1]);
+            if (t + G < n_tiles) stage_elem(A, t + G, smem + (b ^ 1) * A.sm_buf, &bar[b ^ 1]);
             if (ns_smem) {
                 mbar_expect_tx(&bar[3], 48u * T.n_int);
                 bulk_g2s(ns, A.lo + T.ib, 16u * T.n_int, &bar[3]);
                 bulk_g2s(ns + T.n_int, A.vel + T.ib, 16u * T.n_int, &bar[3]);
                 bulk_g2s(ns + 2 * T.n_int, A.nodec + T.ib, 16u * T.n_int, &bar[3]);
             }
-            if (t + 2 * G < A.n_tiles) prefetch_tile<NPE>(A, t + 2 * G);
+            if (t + 2 * G < n_tiles) prefetch_tile<NPE>(A, t + 2 * G);
         }
         // ---- 3. element pass
         if (active) {
             float *gv = A.visc + (int64_t)t * A.n_prony * 6 * kTile + ec;
-            element_step<NPE>(A, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            element_step<NPE>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
         }
         __syncthreads();
         // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum,
@@ -642,14 +664,14 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
                 } else {
                     lo = A.lo[g]; vo = A.vel[g]; nc = __ldg(&A.nodec[g]);
                 }
-                node_update(A, g, acc, s_xu[l], s_X[l], lo, vo, nc, S);
+                node_update(A, S, g, acc, s_xu[l], s_X[l], lo, vo, nc);
             } else {
                 A.partials[__ldg(A.part_pos + T.sh_off + l - T.n_int)] = acc;
             }
         }
         __syncthreads();
         // ---- 5. stage the next tile's gather record and interior nodes
-        if (threadIdx.x == 0 && t + G < A.n_tiles) {
+        if (threadIdx.x == 0 && t + G < n_tiles) {
             fence_proxy_async();
             stage_nodes<NPE>(A, t + G, tile_info(A, t + G), smem, &bar[2]);
         }
@@ -659,11 +681,15 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
 // Nodes touched by several tiles: sum the node's partial sums in tile order,
 // then the same nodal update as the tile kernel.
 __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, const int k) {
-    __shared__ SrcSmem S;
-    prepare_sources(A, k, S);
+    __shared__ ScenStep S;
+    const int64_t n_sh = A.n_active[1];  // shared nodes of unfinished scenarios form a prefix
+    const int64_t s0 = (int64_t)blockIdx.x * blockDim.x;
+    if (s0 >= n_sh) return;
+    const int scn0 = __ldg(A.shared_scn + s0);  // the block's first node's scenario, in shared memory
+    prepare_scen(A, scn0, k, S, threadIdx.x, blockDim.x);
     __syncthreads();
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= A.n_shared) return;
+    const int64_t s = s0 + threadIdx.x;
+    if (s >= n_sh) return;
     const int64_t g = A.n_interior + s;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     const int r0 = __ldg(A.sh_rowptr + s), r1 = __ldg(A.sh_rowptr + s + 1);
@@ -671,12 +697,38 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
         const float4 c = A.partials[r];
         acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
     }
-    node_update(A, g, acc, A.xu[g], __ldg(&A.X0[g]), A.lo[g], A.vel[g], __ldg(&A.nodec[g]), S);
+    const int scn = __ldg(A.shared_scn + s);
+    if (scn == scn0) {
+        node_update(A, S, g, acc, A.xu[g], __ldg(&A.X0[g]), A.lo[g], A.vel[g], __ldg(&A.nodec[g]));
+    } else {  // block spans a scenario boundary: this thread's own step values
+        ScenStep L;
+        prepare_scen(A, scn, k, L, 0, 1);
+        node_update(A, L, g, acc, A.xu[g], __ldg(&A.X0[g]), A.lo[g], A.vel[g], __ldg(&A.nodec[g]));
+    }
 }
 
-__global__ void bump_kernel(double *time_base, int64_t *step_base, int K, double dt) {
-    *time_base += (double)K * dt;
-    *step_base += K;
+// advance every scenario's step counter by K (its time is t0 + n dt)
+__global__ void bump_kernel(const StepArgs A, int K) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.n_scn; s += gridDim.x * blockDim.x) A.scn_step[s] += K;
+}
+
+// Temperature and damage fraction at probe points: shape-function weights of
+// the containing element applied to the nodal fields; out [2][n].
+__global__ void probe_kernel(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
+                             const float4 *__restrict__ vel, const int32_t *__restrict__ node,
+                             const float *__restrict__ w, int64_t n, double T0, double *__restrict__ out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double th = 0.0, dmg = 0.0;
+    for (int a = 0; a < 8; a++) {
+        const double wa = w[8 * p + a];
+        if (wa == 0.0) continue;
+        const int64_t g = node[8 * p + a];
+        th += wa * ((double)hi[g].w + (double)lo[g].w);
+        dmg += wa * -expm1(-(double)vel[g].w);
+    }
+    out[p] = T0 + th;
+    out[n + p] = dmg;
 }
 
 __global__ void readback_kernel(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
@@ -795,8 +847,8 @@ cudaError_t launch_shared_step(const StepArgs &a, int k, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_bump(double *time_base, int64_t *step_base, int K, double dt, cudaStream_t s) {
-    bump_kernel<<<1, 1, 0, s>>>(time_base, step_base, K, dt);
+cudaError_t launch_bump(const StepArgs &a, int K, cudaStream_t s) {
+    bump_kernel<<<(a.n_scn + 255) / 256, 256, 0, s>>>(a, K);
     return cudaGetLastError();
 }
 
@@ -804,6 +856,12 @@ cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t 
                             cudaStream_t s) {
     const int nb = (int)((nn + 255) / 256);
     readback_kernel<<<nb, 256, 0, s>>>(a.xu, a.lo, a.vel, node_new, nn, T0, mode, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w, int64_t n, double T0, double *out,
+                          cudaStream_t s) {
+    probe_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(a.xu, a.lo, a.vel, node, w, n, T0, out);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,14 @@ _SIGS = {
     "tled_step_timed": ([C.c_void_p, C.c_int64, _dp], C.c_int),
     "tled_get_stats_noalloc": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "tled_plan_info": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "tled_set_probes": ([C.c_void_p, C.c_int64, _dp], C.c_int),
+    "tled_get_probes": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "tled_batch_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p], C.c_int),
+    "tled_batch_add": ([C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int32)], C.c_int),
+    "tled_batch_run": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "tled_scenario_info": ([C.c_void_p, C.c_int32, C.POINTER(C.c_int64)], C.c_int),
+    "tled_scenario_dt": ([C.c_void_p, C.c_int32, _dp], C.c_int),
+    "tled_autotune": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "tled_save_state": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_load_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
 }
@@ -146,10 +154,10 @@ def sources_array(rows) -> tuple:
 
 
 def plan_info(h, check) -> dict:
-    info = (C.c_int64 * 6)()
+    info = (C.c_int64 * 8)()
     check(lib().tled_plan_info(h, info))
     return dict(n_tiles=info[0], n_interior=info[1], n_shared=info[2], n_partials=info[3], workspace=info[4],
-                npe=info[5])
+                npe=info[5], n_scenarios=info[6], ctas=info[7])
 
 
 class HostPlanner:
@@ -255,6 +263,11 @@ class Solver:
         n, arr = sources_array(rows)
         self._check(lib().tled_set_heat_sources(self.h, n, arr))
 
+    def set_probes(self, xyz):
+        xyz = np.ascontiguousarray(xyz, np.float64).reshape(-1, 3)
+        self.n_probes = xyz.shape[0]
+        self._check(lib().tled_set_probes(self.h, xyz.shape[0], _p(xyz)))
+
     def set_params(self, dt=0.0, dt_safety=0.8, gamma=0.0, mass_scale=1.0, kappa_hg=0.1, kappa_hgT=0.1,
                    flags=EXPANSION | COMPENSATED, tile_elems=0):
         p = Params(dt, dt_safety, gamma, mass_scale, kappa_hg, kappa_hgT, flags, tile_elems)
@@ -268,14 +281,24 @@ class Solver:
     def init(self):
         torch = self._torch
         n = self.workspace_size()
-        self.ws = torch.empty(n + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
+        if self.ws is None or self.ws.numel() < n + 256:
+            self.ws = torch.empty(n + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
         base = self.ws.data_ptr()
         ptr = (base + 255) & ~255
         self._check(lib().tled_init(self.h, C.c_void_p(ptr), n))
 
     @classmethod
-    def from_problem(cls, prob, device=0, stream=None, dt=None, flags=None, tile_elems=0):
+    def from_problem(cls, prob, device=0, stream=None, dt=None, flags=None, tile_elems=0, probes=None,
+                     init=True):
         s = cls(device, stream)
+        s.setup_from(prob, dt=dt, flags=flags, tile_elems=tile_elems, probes=probes)
+        if init:
+            s.init()
+        return s
+
+    def setup_from(self, prob, dt=None, flags=None, tile_elems=0, probes=None):
+        """Set-up calls for a workloads.Problem (no init)."""
+        s = self
         s.set_mesh(prob.npe, prob.X, prob.conn)
         per = np.stack([prob.mu, prob.kappa, prob.k1, prob.k2, prob.kc, prob.alpha], 1) if prob.per_element else None
         fib = prob.a0 if prob.per_element else None
@@ -287,7 +310,8 @@ class Solver:
         s.set_params(dt=float(prob.dt if dt is None else dt), dt_safety=prob.dt_safety, gamma=prob.gamma,
                      mass_scale=prob.mass_scale, kappa_hg=prob.kappa_hg, kappa_hgT=prob.kappa_hgT, flags=flags,
                      tile_elems=tile_elems)
-        s.init()
+        if probes is not None:
+            s.set_probes(probes)
         return s
 
     # -- stepping ----------------------------------------------------------
@@ -349,6 +373,28 @@ class Solver:
         self._check(lib().tled_get_stats(self.h, C.byref(s)))
         return s.as_dict()
 
+    def probes(self, out=None):
+        """(temperature, damage) at the probe points."""
+        n = getattr(self, "n_probes", 0)
+        if out is None:
+            a = np.empty((2, n), np.float64)
+            if n:
+                self._check(lib().tled_get_probes(self.h, a.ctypes.data_as(C.c_void_p), HOST))
+            return a
+        self._check(lib().tled_get_probes(self.h, C.c_void_p(out.data_ptr()), DEVICE if out.is_cuda else HOST))
+        return out
+
+    def autotune(self, trial_steps=20, workspace_bytes=None):
+        """Pick the fastest tiling by timing (see tled_autotune); re-initialises the state."""
+        torch = self._torch
+        if self.ws is None or (workspace_bytes and self.ws.numel() < workspace_bytes):
+            n = workspace_bytes or int(self.workspace_size() * 1.6) + (1 << 20)
+            self.ws = torch.empty(n + 256, dtype=torch.uint8, device=f"cuda:{self.device}")
+        base = (self.ws.data_ptr() + 255) & ~255
+        ch = (C.c_int32 * 3)()
+        self._check(lib().tled_autotune(self.h, C.c_void_p(base), self.ws.numel() - 256, int(trial_steps), ch))
+        return dict(tile_elems=ch[0], ctas=ch[1], cached=bool(ch[2]))
+
     def stats_noalloc(self, out, n_blocks=0):
         """Allocation-free diagnostics into a device float64 tensor of 6 entries
         (enqueued on the solver's stream, no synchronisation)."""
@@ -366,3 +412,61 @@ class Solver:
     def load_state(self, blob: bytes):
         buf = C.create_string_buffer(blob, len(blob))
         self._check(lib().tled_load_state(self.h, buf, len(blob)))
+
+
+class Batch(Solver):
+    """Many independent scenarios advanced together (tled_batch_*).
+
+    ``add(problem, n_steps)`` copies a scenario's set-up; after ``init()``,
+    ``run()`` steps every scenario to its own n_steps in the same launches;
+    field read-backs return all scenarios concatenated (see ``scenario``)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libtled needs a CUDA device; there is no CPU fallback")
+        self._torch = torch
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        self._check(lib().tled_batch_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream)), h)
+        self.h = h
+        self.ws = None
+        self.n_scn = 0
+        self.n_probes = 0
+
+    def add(self, prob, n_steps, dt=None, flags=None, probes=None):
+        one = Solver(self.device, self.stream)
+        one.setup_from(prob, dt=dt, flags=flags, probes=probes)
+        idx = C.c_int32()
+        self._check(lib().tled_batch_add(self.h, one.h, int(n_steps), C.byref(idx)))
+        one.close()
+        self.n_scn += 1
+        self.n_prony = len(prob.prony_g)
+        self.n_probes += 0 if probes is None else len(probes)
+        return idx.value
+
+    def init(self):
+        super().init()
+        info = self.plan_info()
+        tot = [self.scenario(i) for i in range(self.n_scn)]
+        self.nn = sum(t["nodes"] for t in tot)
+        self.ne = sum(t["elements"] for t in tot)
+        return info
+
+    def run(self):
+        n = C.c_int64()
+        self._check(lib().tled_batch_run(self.h, C.byref(n)))
+        return n.value
+
+    def scenario(self, i) -> dict:
+        info = (C.c_int64 * 8)()
+        self._check(lib().tled_scenario_info(self.h, int(i), info))
+        return dict(node_off=info[0], nodes=info[1], elem_off=info[2], elements=info[3], n_steps=info[4],
+                    steps=info[5], probe_off=info[6], probes=info[7])
+
+    def scenario_dt(self, i) -> float:
+        d = C.c_double()
+        self._check(lib().tled_scenario_dt(self.h, int(i), C.byref(d)))
+        return d.value

@@ -1,0 +1,123 @@
+"""Batched scenarios, probe interpolation and the autotuner, against the FP64
+oracle run scenario by scenario."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import TOL_DAMAGE, TOL_E, compare
+from paper_2009_10400_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _tled():
+    from paper_2009_10400_b300 import tled
+    return tled
+
+
+def _scenarios_h8():
+    rng = np.random.default_rng(21)
+    out = []
+    for i, n in enumerate((4, 6, 5)):
+        p = W.cube_h8(n=n, jitter=0.1 * i, seed=30 + i)
+        p.mu[:] *= rng.uniform(0.8, 1.2)
+        p.kc[:] *= rng.uniform(0.8, 1.2)
+        p.sources = np.array([W.source(rng.uniform(0.0125, 0.0375, 3), rng.uniform(1e6, 1e7),
+                                       vel=rng.uniform(-0.01, 0.01, 3))])
+        p.gamma = [0.0, 5.0, 2.0][i]
+        out.append(p)
+    return out
+
+
+def _oracle_final(p, n_steps, dt):
+    m = oracle.OracleModel(p, dt=dt)
+    s = m.init_state()
+    m.step(s, n_steps)
+    return s
+
+
+def test_batch_h8_each_scenario_matches_oracle():
+    """Three H8 scenarios of different size, material, damping, moving source,
+    step size and step count run in the same launches; each stops at its own
+    step count and matches its oracle run."""
+    tled = _tled()
+    scen = _scenarios_h8()
+    n_steps = [300, 120, 210]
+    dts = [None, 2.0e-4, None]
+    b = tled.Batch()
+    for p, n, dt in zip(scen, n_steps, dts):
+        b.add(p, n, dt=dt)
+    b.init()
+    ran = b.run()
+    b.sync()
+    assert ran == max(n_steps)
+    u, T, d = b.displacement(), b.temperature(), b.damage()
+    for i, (p, n) in enumerate(zip(scen, n_steps)):
+        info = b.scenario(i)
+        assert info["steps"] == n and info["nodes"] == p.nn
+        sl = slice(info["node_off"], info["node_off"] + info["nodes"])
+        ref = _oracle_final(p, n, b.scenario_dt(i))
+        c = compare(u[sl], T[sl], d[sl], ref.u, ref.T, ref.Omega)
+        assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E and c["d_abs"] <= TOL_DAMAGE, (i, c)
+
+
+def test_batch_t4_matches_single_runs():
+    tled = _tled()
+    probs = [W.cube_t4(n=4, seed=40), W.cube_t4(n=5, seed=41)]
+    b = tled.Batch()
+    for p in probs:
+        b.add(p, 150)
+    b.init()
+    b.run()
+    b.sync()
+    T = b.temperature()
+    for i, p in enumerate(probs):
+        info = b.scenario(i)
+        sl = slice(info["node_off"], info["node_off"] + info["nodes"])
+        ref = _oracle_final(p, 150, b.scenario_dt(i))
+        assert np.linalg.norm(T[sl] - ref.T) / np.linalg.norm(ref.T - 37) <= TOL_E
+
+
+def test_probes_at_centroids_and_points():
+    """Probes at H8 centroids give the mean of the 8 corners; probes at nodes give
+    the nodal value; T4 probes give barycentric interpolation."""
+    tled = _tled()
+    p = W.cube_h8(n=6)
+    X, conn = p.X, p.conn
+    cen = X[conn].mean(1)[::5]
+    nodes = X[[0, 17, 100]]
+    s = tled.Solver.from_problem(p, probes=np.vstack([cen, nodes]))
+    s.step(200)
+    pr = s.probes()
+    T, dmg = s.temperature(), s.damage()
+    np.testing.assert_allclose(pr[0, :len(cen)], T[conn[::5]].mean(1), rtol=0, atol=1e-9)
+    np.testing.assert_allclose(pr[1, :len(cen)], dmg[conn[::5]].mean(1), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(pr[0, len(cen):], T[[0, 17, 100]], rtol=0, atol=1e-9)
+    # T4: a point inside a tetrahedron, barycentric weights
+    q = W.cube_t4(n=3)
+    e = 7
+    bary = np.array([0.1, 0.2, 0.3, 0.4])
+    pt = bary @ q.X[q.conn[e]]
+    s4 = tled.Solver.from_problem(q, probes=pt[None])
+    s4.step(100)
+    T4 = s4.temperature()
+    np.testing.assert_allclose(s4.probes()[0, 0], bary @ T4[q.conn[e]], rtol=0, atol=1e-9)
+    with pytest.raises(tled.TledError):
+        tled.Solver.from_problem(q, probes=np.array([[1.0, 1.0, 1.0]]))
+
+
+def test_autotune_then_parity():
+    tled = _tled()
+    p = W.block_h8(n=12, h=4e-3)
+    s = tled.Solver.from_problem(p)
+    ch = s.autotune(trial_steps=10)
+    assert ch["tile_elems"] in (256, 192, 128) and ch["ctas"] >= 1 and not ch["cached"]
+    s2 = tled.Solver.from_problem(p)
+    assert s2.autotune(trial_steps=10)["cached"]
+    m = oracle.OracleModel(p, dt=s.get_dt()[0])
+    o = m.init_state()
+    m.step(o, 200)
+    s.step(200)
+    s.sync()
+    c = compare(s.displacement(), s.temperature(), s.damage(), o.u, o.T, o.Omega)
+    assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E

@@ -132,3 +132,31 @@ def test_call_order_errors():
     with pytest.raises(tled.TledError) as e:
         p2.init()
     assert e.value.code == tled.E_STATE
+
+
+def test_batch_planning_keeps_scenarios_apart():
+    """Host-only batch: tiles never span scenarios, so the tile count is the sum
+    of the per-scenario counts, and shared nodes never join two scenarios."""
+    import ctypes as C
+    probs = [W.cube_h8(n=6), W.cube_h8(n=9, seed=2), W.cube_h8(n=5, seed=3)]
+    h = C.c_void_p()
+    assert tled.lib().tled_batch_create(C.byref(h), -1, None) == 0
+    singles = []
+    for i, p in enumerate(probs):
+        one = _planner(p)
+        singles.append(one.plan_info())
+        idx = C.c_int32()
+        assert tled.lib().tled_batch_add(h, one.h, 100 * (i + 1), C.byref(idx)) == 0, tled.lib().tled_last_error(h)
+        assert idx.value == i
+    info = (C.c_int64 * 8)()
+    assert tled.lib().tled_plan_info(h, info) == 0
+    assert info[6] == 3
+    assert info[0] == sum(s["n_tiles"] for s in singles)
+    assert info[1] + info[2] == sum(p.nn for p in probs)
+    sinfo = (C.c_int64 * 8)()
+    assert tled.lib().tled_scenario_info(h, 1, sinfo) == 0
+    assert (sinfo[0], sinfo[1], sinfo[2], sinfo[3], sinfo[4]) == (probs[0].nn, probs[1].nn, probs[0].ne, probs[1].ne, 200)
+    # mixing element types is refused
+    t4 = _planner(W.cube_t4(n=2))
+    assert tled.lib().tled_batch_add(h, t4.h, 10, None) == tled.E_ARG
+    tled.lib().tled_destroy(h)
