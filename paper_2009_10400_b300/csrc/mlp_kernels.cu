@@ -1,0 +1,376 @@
+// Surrogate MLP on the 5th-generation tensor cores (sm_103a): BF16 operands,
+// FP32 accumulation in tensor memory, GELU activations, MSE loss, Adam.
+//
+// GEMM: D[M][N] = A[M][K] * B[N][K]^T with both operands K-major BF16 in
+// global memory.  One CTA computes a 128 x BN tile: warp 0 streams 128 x 64 and
+// BN x 64 operand boxes with TMA (128-byte swizzle) through a 4-stage
+// mbarrier pipeline, one thread of warp 1 issues tcgen05.mma (K = 16 each)
+// into a TMEM accumulator and commits stage releases, and warps 2-5 read the
+// accumulator with tcgen05.ld (one row per thread) and apply the epilogue:
+//   kEpiBiasF32   Y = D + b                        (float output)
+//   kEpiGelu      Z = D + b, A = GELU(Z)           (Z float; A bf16 and its transpose)
+//   kEpiGeluGrad  dZ = D * GELU'(Zprev)            (bf16 and its transpose)
+//   kEpiF32       G = D                            (float, weight gradients)
+// Every mbarrier wait is bounded; a time-out sets an error word and the CTA
+// drains its copies, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "mlp_internal.h"
+
+namespace tmlp {
+
+constexpr int kStages = 4;
+constexpr int kBM = 128;
+constexpr int kBK = 64;  // 64 bf16 = 128 bytes = one swizzle row
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok)
+                 : "r"(su32(b)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// bounded wait: about 2^31 cycles (around a second) before giving up
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!bar_try(b, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+// UMMA shared-memory descriptor, K-major operand in the canonical 128-byte
+// swizzled layout: rows of 128 B, 8-row atoms 1024 B apart (SBO), version 1,
+// layout type 2 (SWIZZLE_128B); the tile base is 1024-byte aligned.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused with 128-byte swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M = 128, N = BN
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+template <int BN, int MODE>
+__global__ void __launch_bounds__(192, 1)
+    umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t full[kStages], empty[kStages], accum;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail;
+    uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
+    uint8_t *sA = smem, *sB = smem + kStages * kABytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int KB = g.K / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; s++) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        bar_init(&accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                     "r"((uint32_t)BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    int issued = 0;  // producer: k-blocks whose loads were issued
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer
+        for (int kb = 0; kb < KB; kb++) {
+            const int s = kb % kStages;
+            if (kb >= kStages && !bar_wait(&empty[s], ((kb / kStages) - 1) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            bar_expect(&full[s], kABytes + kBBytes);
+            tma_load_2d(sA + s * kABytes, &tmA, kb * kBK, m0, &full[s]);
+            tma_load_2d(sB + s * kBBytes, &tmB, kb * kBK, n0, &full[s]);
+            issued++;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer
+        constexpr uint32_t idesc = idesc_bf16<BN>();
+        for (int kb = 0; kb < KB; kb++) {
+            const int s = kb % kStages;
+            if (!bar_wait(&full[s], (kb / kStages) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = su32(sA + s * kABytes), b0 = su32(sB + s * kBBytes);
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; kk++)  // advance 16 elements = 32 bytes along K inside the swizzle row
+                umma(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (kb | kk) != 0);
+            umma_commit(&empty[s]);  // stage reusable once these MMAs completed
+        }
+        umma_commit(&accum);
+    } else if (warp >= 2) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
+        const int lg = warp & 3;
+        const int row = m0 + lg * 32 + lane;
+        const bool ok = bar_wait(&accum, 0);
+        if (!ok) s_fail = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) {
+#pragma unroll 1
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < g.M) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int col = n0 + c0 + j;
+                        float v = __uint_as_float(r[j]);
+                        if constexpr (MODE == kEpiBiasF32) {
+                            v += g.bias[col];
+                            g.out_f32[(int64_t)row * g.ld_f32 + col] = v;
+                        } else if constexpr (MODE == kEpiGelu) {
+                            v += g.bias[col];
+                            g.z_out[(int64_t)row * g.ld_z + col] = v;
+                            const __nv_bfloat16 a = __float2bfloat16_rn(gelu(v));
+                            g.out_bf[(int64_t)row * g.ld_bf + col] = a;
+                            g.out_bfT[(int64_t)col * g.ld_bfT + row] = a;
+                        } else if constexpr (MODE == kEpiGeluGrad) {
+                            const float dz = v * gelu_grad(g.z_in[(int64_t)row * g.ld_z + col]);
+                            const __nv_bfloat16 a = __float2bfloat16_rn(dz);
+                            g.out_bf[(int64_t)row * g.ld_bf + col] = a;
+                            g.out_bfT[(int64_t)col * g.ld_bfT + row] = a;
+                        } else {
+                            g.out_f32[(int64_t)row * g.ld_f32 + col] = v;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0) {
+            atomicOr(g.status, 1u);
+            // let this CTA's issued copies land before its shared memory is released
+            for (int kb = 0; kb < issued; kb++) bar_wait(&full[kb % kStages], (kb / kStages) & 1);
+        }
+        __syncthreads();
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels
+// ---------------------------------------------------------------------------
+// x [B][n_in] float -> bf16 [B][ld] (zero padded) and its transpose [ld][B]
+__global__ void input_kernel(const float *__restrict__ x, int B, int n_in, int ld, __nv_bfloat16 *xb,
+                             __nv_bfloat16 *xt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)B * ld) return;
+    const int b = (int)(i / ld), k = (int)(i % ld);
+    const __nv_bfloat16 v = __float2bfloat16_rn(k < n_in ? x[(int64_t)b * n_in + k] : 0.f);
+    xb[i] = v;
+    xt[(int64_t)k * B + b] = v;
+}
+
+// MSE loss 1/(B N) sum (y - t)^2 and dY = 2 (y - t) / (B N) in bf16 (+ transpose);
+// per-block partial sums of the loss (fixed order, reduced by loss_final_kernel)
+__global__ void loss_kernel(const float *__restrict__ y, const float *__restrict__ t, int B, int N,
+                            __nv_bfloat16 *dy, __nv_bfloat16 *dyt, double *partials) {
+    __shared__ double sh[256];
+    const double scale = 1.0 / ((double)B * N);
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)B * N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = y[i] - t[i];
+        acc += (double)d * d;
+        const __nv_bfloat16 g = __float2bfloat16_rn((float)(2.0 * scale) * d);
+        const int b = (int)(i / N), n = (int)(i % N);
+        dy[i] = g;
+        dyt[(int64_t)n * B + b] = g;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0] * scale;
+}
+__global__ void loss_final_kernel(const double *partials, int n, float *loss) {
+    if (threadIdx.x) return;
+    double s = 0;
+    for (int i = 0; i < n; i++) s += partials[i];
+    *loss = (float)s;
+}
+
+// bias gradient: db[n] = sum_b dZ[b][n], read from the transposed copy dZt [N][B]
+__global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dzt, int B, int N, float *db) {
+    const int n = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (n >= N) return;
+    float s = 0.f;
+    for (int b = lane; b < B; b += 32) s += __bfloat162float(dzt[(int64_t)n * B + b]);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) db[n] = s;
+}
+
+// Adam on FP32 master parameters; refresh the bf16 weights W [N][ld] and W^T [ld][N]
+__global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ grad, int64_t n, float lr, float b1, float b2, float eps,
+                            float bc1, float bc2, int N, int K, int ld, __nv_bfloat16 *wb, __nv_bfloat16 *wt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gr = grad[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gr;
+    const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    w[i] = wi;
+    if (wb && i < (int64_t)N * K) {  // weight matrix part (the bias follows it)
+        const int r = (int)(i / K), c = (int)(i % K);
+        const __nv_bfloat16 h = __float2bfloat16_rn(wi);
+        wb[(int64_t)r * ld + c] = h;
+        wt[(int64_t)c * N + r] = h;
+    }
+}
+
+// gradient of a layer's weights from the padded FP32 GEMM output G [N][ld]
+__global__ void gather_grad_kernel(const float *__restrict__ G, const float *__restrict__ db, int N, int K, int ld,
+                                   float *grad) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)N * K + N) return;
+    if (i < (int64_t)N * K) {
+        const int r = (int)(i / K), c = (int)(i % K);
+        grad[i] = G[(int64_t)r * ld + c];
+    } else {
+        grad[i] = db[i - (int64_t)N * K];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int BN, int MODE>
+static cudaError_t launch_one(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s) {
+    const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
+    auto kern = umma_gemm_kernel<BN, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(g.M / kBM, g.N / BN);
+    kern<<<grid, 192, smem, s>>>(a, b, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, int bn, int mode,
+                        cudaStream_t s) {
+    if (bn == 64) {
+        switch (mode) {
+            case kEpiBiasF32: return launch_one<64, kEpiBiasF32>(a, b, g, s);
+            case kEpiGelu: return launch_one<64, kEpiGelu>(a, b, g, s);
+            case kEpiGeluGrad: return launch_one<64, kEpiGeluGrad>(a, b, g, s);
+            default: return launch_one<64, kEpiF32>(a, b, g, s);
+        }
+    }
+    switch (mode) {
+        case kEpiBiasF32: return launch_one<128, kEpiBiasF32>(a, b, g, s);
+        case kEpiGelu: return launch_one<128, kEpiGelu>(a, b, g, s);
+        case kEpiGeluGrad: return launch_one<128, kEpiGeluGrad>(a, b, g, s);
+        default: return launch_one<128, kEpiF32>(a, b, g, s);
+    }
+}
+
+cudaError_t launch_input(const float *x, int B, int n_in, int ld, __nv_bfloat16 *xb, __nv_bfloat16 *xt,
+                         cudaStream_t s) {
+    const int64_t n = (int64_t)B * ld;
+    input_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(x, B, n_in, ld, xb, xt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const float *y, const float *t, int B, int N, __nv_bfloat16 *dy, __nv_bfloat16 *dyt,
+                        double *partials, float *loss, cudaStream_t s) {
+    loss_kernel<<<kLossBlocks, 256, 0, s>>>(y, t, B, N, dy, dyt, partials);
+    loss_final_kernel<<<1, 32, 0, s>>>(partials, kLossBlocks, loss);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bias_grad(const __nv_bfloat16 *dzt, int B, int N, float *db, cudaStream_t s) {
+    bias_grad_kernel<<<(N + 7) / 8, 256, 0, s>>>(dzt, B, N, db);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *w, float *m, float *v, const float *grad, int64_t n, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, int N, int K, int ld, __nv_bfloat16 *wb, __nv_bfloat16 *wt,
+                        cudaStream_t s) {
+    adam_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w, m, v, grad, n, lr, b1, b2, eps, bc1, bc2, N, K, ld, wb, wt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_grad(const float *G, const float *db, int N, int K, int ld, float *grad, cudaStream_t s) {
+    const int64_t n = (int64_t)N * K + N;
+    gather_grad_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(G, db, N, K, ld, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace tmlp

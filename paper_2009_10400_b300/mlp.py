@@ -1,0 +1,122 @@
+"""ctypes binding of the surrogate MLP in ``libtled`` (include/tled_mlp.h).
+
+Marshalling only: the forward, backward and Adam passes run in the library's
+tcgen05 kernels.  Tensors are PyTorch CUDA float32 tensors (row-major).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from .tled import TledError, lib as _tled_lib
+
+_SIGS = {
+    "tled_mlp_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_int32],
+                        C.c_int),
+    "tled_mlp_destroy": ([C.c_void_p], C.c_int),
+    "tled_mlp_last_error": ([C.c_void_p], C.c_char_p),
+    "tled_mlp_num_params": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "tled_mlp_workspace_size": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "tled_mlp_init": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
+    "tled_mlp_set_params": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "tled_mlp_get_params": ([C.c_void_p, C.POINTER(C.c_float)], C.c_int),
+    "tled_mlp_forward": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
+    "tled_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
+    "tled_mlp_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p], C.c_int),
+    "tled_mlp_sync": ([C.c_void_p], C.c_int),
+}
+_ready = False
+
+
+def lib():
+    global _ready
+    L = _tled_lib()
+    if not _ready:
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _ready = True
+    return L
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+class MLP:
+    """A network dims[0] -> dims[1] -> ... -> dims[-1] with GELU hidden layers."""
+
+    def __init__(self, dims, max_batch, device=0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the surrogate MLP needs a CUDA device; there is no CPU fallback")
+        self._torch = torch
+        self.dims = list(dims)
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        d = (C.c_int32 * len(dims))(*dims)
+        h = C.c_void_p()
+        rc = lib().tled_mlp_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream), len(dims) - 1, d,
+                                   int(max_batch))
+        if rc:
+            raise TledError(rc, "invalid MLP dimensions (widths and outputs multiples of 128, batch of 128)")
+        self.h = h
+        n = C.c_int64()
+        self._check(lib().tled_mlp_num_params(h, C.byref(n)))
+        self.n_params = n.value
+        self._check(lib().tled_mlp_workspace_size(h, C.byref(n)))
+        self.ws = torch.empty(n.value + 256, dtype=torch.uint8, device=f"cuda:{device}")
+        self._check(lib().tled_mlp_init(h, C.c_void_p((self.ws.data_ptr() + 255) & ~255), n.value))
+        self.loss_buf = torch.zeros(1, dtype=torch.float32, device=f"cuda:{device}")
+
+    def _check(self, rc):
+        if rc:
+            raise TledError(rc, lib().tled_mlp_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tled_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.size == self.n_params
+        self._check(lib().tled_mlp_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def get_params(self):
+        p = np.empty(self.n_params, np.float32)
+        self._check(lib().tled_mlp_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+        return p
+
+    def forward(self, x, out=None):
+        torch = self._torch
+        B = x.shape[0]
+        if out is None:
+            out = torch.empty(B, self.dims[-1], dtype=torch.float32, device=x.device)
+        self._check(lib().tled_mlp_forward(self.h, C.c_void_p(x.data_ptr()), B, C.c_void_p(out.data_ptr())))
+        return out
+
+    def gradients(self, x, t):
+        torch = self._torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        self._check(lib().tled_mlp_gradients(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+                                             C.c_void_p(g.data_ptr()), C.c_void_p(self.loss_buf.data_ptr())))
+        return g, self.loss_buf
+
+    def train_step(self, x, t, lr):
+        self._check(lib().tled_mlp_train_step(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
+                                              float(lr), C.c_void_p(self.loss_buf.data_ptr())))
+        return self.loss_buf
+
+    def sync(self):
+        self._check(lib().tled_mlp_sync(self.h))

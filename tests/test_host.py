@@ -28,7 +28,8 @@ def test_library_exports_every_declared_symbol():
     assert len(names) >= 24
     for n in names:
         assert hasattr(L, n), n
-    assert set(names) <= set(tled.exported_symbols()) | {"tled_version"}
+    from paper_2009_10400_b300 import mlp
+    assert set(names) <= set(tled.exported_symbols()) | set(mlp.exported_symbols()) | {"tled_version"}
     assert L.tled_version() == 1
 
 

@@ -1,0 +1,118 @@
+"""Surrogate MLP: the FP64 oracle against finite differences and an independent
+bfloat16 conversion (CPU), and the tensor-core kernels against the oracle (GPU)."""
+import numpy as np
+import pytest
+
+from oracle.mlp import MLPOracle, bf16_round, gelu, gelu_grad
+
+
+def test_oracle_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    m = MLPOracle([5, 7, 6, 3])
+    p = m.init_params(rng)
+    x = rng.normal(size=(4, 5))
+    t = rng.normal(size=(4, 3))
+    _, g = m.loss_and_grad(p, x, t)
+    eps = 1e-6
+    for i in rng.choice(m.n_params, 40, replace=False):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += eps
+        pm[i] -= eps
+        num = (m.loss_and_grad(pp, x, t)[0] - m.loss_and_grad(pm, x, t)[0]) / (2 * eps)
+        assert abs(num - g[i]) <= 1e-6 * max(1.0, abs(num)), (i, num, g[i])
+
+
+def test_gelu_derivative_and_values():
+    z = np.linspace(-6, 6, 101)
+    np.testing.assert_allclose(gelu_grad(z), (gelu(z + 1e-6) - gelu(z - 1e-6)) / 2e-6, rtol=1e-6, atol=1e-9)
+    # GELU(z) -> z for large z, -> 0 for very negative z, GELU(0) = 0
+    assert abs(gelu(np.array(8.0)) - 8.0) < 1e-12 and abs(gelu(np.array(-8.0))) < 1e-12 and gelu(np.array(0.0)) == 0
+
+
+def test_bf16_round_matches_torch():
+    import torch
+    rng = np.random.default_rng(1)
+    a = np.concatenate([rng.normal(size=2000) * 10 ** rng.uniform(-8, 8, 2000), [0.0, -0.0, 1.0, 3.0 / 7.0]])
+    ref = torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(bf16_round(a), ref)
+
+
+def test_oracle_adam_first_step_is_sign_times_lr():
+    """With zero moments the first Adam step moves every parameter by lr * sign(g)
+    (up to eps): the bias corrections cancel the (1 - beta) factors."""
+    p = np.zeros(5)
+    g = np.array([1.0, -2.0, 0.5, -1e-3, 3.0])
+    p1, _, _ = MLPOracle.adam(p, g, np.zeros(5), np.zeros(5), 1, lr=1e-3)
+    np.testing.assert_allclose(p1, -1e-3 * np.sign(g), rtol=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# GPU: tensor-core kernels against the oracle with the same bf16 rounding
+# ---------------------------------------------------------------------------
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a, float) - b) / max(np.linalg.norm(b), 1e-30)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("dims,B", [([12, 128, 256, 128], 128), ([12, 512, 512, 512, 512, 512, 1024], 256)])
+def test_mlp_forward_and_gradients_match_oracle(dims, B):
+    import torch
+
+    from paper_2009_10400_b300.mlp import MLP
+    rng = np.random.default_rng(3)
+    orc = MLPOracle(dims)
+    p = orc.init_params(rng).astype(np.float32).astype(np.float64)
+    x = rng.uniform(-1, 1, (B, dims[0]))
+    t = rng.normal(size=(B, dims[-1])) * 0.1
+    net = MLP(dims, max_batch=max(B, 256))
+    net.set_params(p)
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    y = net.forward(xd)
+    g, loss = net.gradients(xd, td)
+    net.sync()
+    x32 = x.astype(np.float32).astype(np.float64)
+    t32 = t.astype(np.float32).astype(np.float64)
+    y_ref, _, _ = orc.forward(p, x32, bf16=True)
+    loss_ref, g_ref = orc.loss_and_grad(p, x32, t32, bf16=True)
+    assert _rel(y.cpu().numpy(), y_ref) < 2e-3, _rel(y.cpu().numpy(), y_ref)
+    assert abs(loss.item() - loss_ref) < 2e-3 * loss_ref
+    g = g.cpu().numpy()
+    for (a, b, c, N, K) in orc.offsets:  # per layer, weights and biases
+        assert _rel(g[a:b], g_ref[a:b]) < 1e-2, ("W", N, K, _rel(g[a:b], g_ref[a:b]))
+        assert _rel(g[b:c], g_ref[b:c]) < 1e-2, ("b", N, _rel(g[b:c], g_ref[b:c]))
+    # and against the unrounded FP64 gradient, the bf16 training precision
+    _, g64 = orc.loss_and_grad(p, x32, t32, bf16=False)
+    assert _rel(g, g64) < 5e-2
+
+
+@pytest.mark.gpu
+def test_mlp_adam_step_and_training_reduces_loss():
+    import torch
+
+    from paper_2009_10400_b300.mlp import MLP
+    rng = np.random.default_rng(4)
+    dims = [12, 256, 256, 128]
+    orc = MLPOracle(dims)
+    p = orc.init_params(rng).astype(np.float32).astype(np.float64)
+    B = 256
+    x = rng.uniform(-1, 1, (B, 12))
+    w_true = rng.normal(size=(12, 128)) / 4
+    t = np.tanh(x @ w_true)
+    net = MLP(dims, max_batch=B)
+    net.set_params(p)
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    net.train_step(xd, td, 1e-3)
+    net.sync()
+    p1 = net.get_params().astype(np.float64)
+    _, g_ref = orc.loss_and_grad(p, x.astype(np.float32).astype(np.float64), t.astype(np.float32).astype(np.float64),
+                                 bf16=True)
+    p1_ref, _, _ = MLPOracle.adam(p, g_ref, np.zeros_like(p), np.zeros_like(p), 1, 1e-3)
+    moved = np.abs(p1_ref - p) > 5e-4  # parameters with a clear gradient sign
+    assert np.mean(np.sign(p1 - p)[moved] == np.sign(p1_ref - p)[moved]) > 0.98
+    losses = []
+    for _ in range(300):
+        losses.append(net.train_step(xd, td, 1e-3).item())
+    net.sync()
+    assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
