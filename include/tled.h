@@ -193,6 +193,11 @@ int tled_init(tled_ctx *ctx, void *dev_workspace, int64_t bytes);
  * (mechanical CFL and thermal Gershgorin, before the safety factor). */
 int tled_get_dt(tled_ctx *ctx, double *dt, double *dt_mech, double *dt_thermal);
 
+/* The two stable-step bounds of the current set-up (no GPU needed): the
+ * mechanical CFL bound (with the set mass scale) and the thermal Gershgorin
+ * bound, before the safety factor. */
+int tled_stable_dt(tled_ctx *ctx, double *dt_mech, double *dt_thermal);
+
 /* Enqueue n explicit coupled steps (element pass, deterministic node gather,
  * nodal updates of u, T and damage).  Asynchronous: device faults such as
  * NaN or inversion are reported by the next tled_sync(). */

@@ -316,8 +316,14 @@ template <int BN, int MODE>
 static cudaError_t launch_one(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s) {
     const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
     auto kern = umma_gemm_kernel<BN, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+    static int set_device = -1;  // the attribute is per device: set it on first use there
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (set_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        set_device = dev;
+    }
     dim3 grid(g.M / kBM, g.N / BN);
     kern<<<grid, 192, smem, s>>>(a, b, g);
     return cudaGetLastError();

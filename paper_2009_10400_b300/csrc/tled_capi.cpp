@@ -995,6 +995,16 @@ int tled_get_dt(tled_ctx *c, double *dt, double *dt_mech, double *dt_thermal) {
     return TLED_OK;
 }
 
+int tled_stable_dt(tled_ctx *c, double *dt_mech, double *dt_thermal) {
+    if (!c || !dt_mech || !dt_thermal) return fail(c, TLED_E_ARG, "NULL argument");
+    if (int rc = require_single(c)) return rc;
+    const Scenario &s = single(c);
+    if (s.npe == 0 || !s.have_mat) return fail(c, TLED_E_STATE, "set the mesh and the material first");
+    tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
+                    s.prm, dt_mech, dt_thermal);
+    return TLED_OK;
+}
+
 int tled_scenario_dt(tled_ctx *c, int32_t idx, double *dt) {
     if (!c || !dt) return fail(c, TLED_E_ARG, "NULL argument");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");

@@ -95,6 +95,7 @@ _SIGS = {
     "tled_batch_run": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_scenario_info": ([C.c_void_p, C.c_int32, C.POINTER(C.c_int64)], C.c_int),
     "tled_scenario_dt": ([C.c_void_p, C.c_int32, _dp], C.c_int),
+    "tled_stable_dt": ([C.c_void_p, _dp, _dp], C.c_int),
     "tled_autotune": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "tled_save_state": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_load_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
@@ -193,10 +194,17 @@ class HostPlanner:
     set_bcs = lambda self, *a, **k: Solver.set_bcs(self, *a, **k)  # noqa: E731
     set_heat_sources = lambda self, *a, **k: Solver.set_heat_sources(self, *a, **k)  # noqa: E731
     set_params = lambda self, *a, **k: Solver.set_params(self, *a, **k)  # noqa: E731
+    set_probes = lambda self, *a, **k: Solver.set_probes(self, *a, **k)  # noqa: E731
+    setup_from = lambda self, *a, **k: Solver.setup_from(self, *a, **k)  # noqa: E731
     workspace_size = lambda self: Solver.workspace_size(self)  # noqa: E731
 
     def plan_info(self):
         return plan_info(self.h, self._check)
+
+    def stable_dt(self):
+        a, b = C.c_double(), C.c_double()
+        self._check(lib().tled_stable_dt(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
 
     def init(self, ptr=1 << 20, n=1 << 30):
         self._check(lib().tled_init(self.h, C.c_void_p(ptr), n))
@@ -437,7 +445,7 @@ class Batch(Solver):
         self.n_probes = 0
 
     def add(self, prob, n_steps, dt=None, flags=None, probes=None):
-        one = Solver(self.device, self.stream)
+        one = HostPlanner()  # set-up only: the batch copies it
         one.setup_from(prob, dt=dt, flags=flags, probes=probes)
         idx = C.c_int32()
         self._check(lib().tled_batch_add(self.h, one.h, int(n_steps), C.byref(idx)))

@@ -319,3 +319,53 @@ def random_state(prob: Problem, seed: int, u_scale=1e-3, v_scale=1e-3, theta_sca
         u[sel, d] = 0.0 if prob.ubar is None else prob.ubar[sel, d]
         v[sel, d] = 0.0
     return dict(u=u, v=v, T=T, Omega=Om, visc=visc)
+
+
+# ---------------------------------------------------------------------------
+# treatment-planning scenarios for the batched solver and the surrogate
+# ---------------------------------------------------------------------------
+SURROGATE_INPUTS = ("power", "x", "y", "z", "duration", "mu", "kappa", "k", "c", "perfusion", "alpha", "fibre_angle")
+
+
+def surrogate_ranges(side=0.05):
+    """Sampling ranges of the 12 scenario inputs: source peak power (W/m^3),
+    position (inner half of the cube), heating duration (s), shear and bulk
+    modulus and conductivity (+-20 %), heat capacity and expansion (+-20 %),
+    perfusion rate omega (x U(0.5, 1.5) of 0.0064 1/s), fibre angle in the
+    x-y plane (rad)."""
+    lo = np.array([1e6, side / 4, side / 4, side / 4, 60.0, 0.8 * 3e3, 0.8 * 3e5, 0.8 * 0.5, 0.8 * 3600.0,
+                   0.5 * 0.0064, 0.8e-4, 0.0])
+    hi = np.array([1e7, 3 * side / 4, 3 * side / 4, 3 * side / 4, 600.0, 1.2 * 3e3, 1.2 * 3e5, 1.2 * 0.5,
+                   1.2 * 3600.0, 1.5 * 0.0064, 1.2e-4, np.pi])
+    return lo, hi
+
+
+def sample_scenarios(n, seed=5, side=0.05, duration=None):
+    """n x 12 scenario inputs drawn uniformly in `surrogate_ranges` (seeded);
+    `duration` = (lo, hi) overrides the heating-time range."""
+    rng = np.random.default_rng(seed)
+    lo, hi = surrogate_ranges(side)
+    if duration is not None:
+        lo[4], hi[4] = duration
+    return lo + (hi - lo) * rng.uniform(size=(n, 12))
+
+
+def scenario_problem(q, n=16, side=0.05, dt=0.01, gamma=5.0, sigma=5e-3):
+    """Problem of one scenario row q (see SURROGATE_INPUTS) on an n^3 H8 cube,
+    bottom fixed, fixed time step dt and damping gamma (mass scaling is chosen
+    by the solver driver); its probes are the n^3 element centroids."""
+    X, conn = hex_grid((n, n, n), (side, side, side))
+    ne = conn.shape[0]
+    ang = q[11]
+    mat = _material(ne, mu=q[5], kappa=q[6], kc=q[7], alpha=q[10])
+    mat["a0"] = np.tile([np.cos(ang), np.sin(ang), 0.0], (ne, 1))
+    mat["per_element"] = False
+    mask = np.where(np.isclose(X[:, 2], 0.0), MASK_U, 0).astype(np.uint8)
+    p = Problem(name=f"scenario_h8_{n}", npe=8, X=X, conn=conn, **mat, c_heat=q[8],
+                wbcb=BLOOD_RHO * q[9] * BLOOD_CB, sources=[source(q[1:4], q[0], sigma=sigma)], mask=mask,
+                dt=dt, gamma=gamma, n_steps=int(round(q[4] / dt)))
+    return p
+
+
+def centroids(prob):
+    return prob.X[prob.conn].mean(1)

@@ -1,0 +1,67 @@
+"""Learned surrogate: the mass-scaled planning scenarios against the oracle,
+and what a trained ensemble gains over running the solver (a small instance of
+the surrogate workload: 8^3 cube, 512 probes, short heating)."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import TOL_E, compare
+from paper_2009_10400_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_mass_scaled_planning_scenario_matches_oracle():
+    """Fixed dt = 0.01 s with mass scaling, damping 5 1/s, inputs from the
+    scenario sampler; 300 steps against the oracle with the same mass scale."""
+    from paper_2009_10400_b300 import surrogate, tled
+    q = W.sample_scenarios(4, seed=11)[2]
+    p = surrogate.mass_scaled(W.scenario_problem(q, n=8, dt=0.01))
+    assert p.mass_scale > 1.0
+    m = oracle.OracleModel(p)
+    s = m.init_state()
+    m.step(s, 300)
+    g = tled.Solver.from_problem(p)
+    g.step(300)
+    g.sync()
+    c = compare(g.displacement(), g.temperature(), g.damage(), s.u, s.T, s.Omega)
+    assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E, c
+
+
+def test_surrogate_learns_and_falls_back():
+    import time
+
+    from paper_2009_10400_b300 import surrogate
+    n, dt = 8, 0.05
+    Q = W.sample_scenarios(1152, seed=12, duration=(5.0, 30.0))
+    T, D, tm = surrogate.solve_scenarios(Q, n=n, dt=dt)
+    assert np.all(np.isfinite(T)) and T.max() > 40.0
+    Y = np.concatenate([T, D], 1)
+    tr, te = slice(0, 1024), slice(1024, 1152)
+    sur = surrogate.Surrogate(n_out=2 * n ** 3, width=256, depth=4, members=3, max_batch=4096)
+    hist = sur.fit(Q[tr], Y[tr], epochs=60, batch=128, lr=2e-3, seed=1)
+    assert hist[0][-1] < 0.25 * hist[0][0]
+    mean, std = sur.predict(Q[te])
+    big = np.repeat(Q[te], 32, axis=0)  # 4096 scenarios, one inference batch per member
+    sur.predict(big)
+    t0 = time.perf_counter()
+    sur.predict(big)
+    t_sur = time.perf_counter() - t0
+    P = n ** 3
+    mae = np.abs(mean[:, :P] - T[te]).mean()
+    mae_base = np.abs(Y[tr, :P].mean(0) - T[te]).mean()  # predicting the training mean
+    assert mae < 0.6 * mae_base, (mae, mae_base)
+    # the ensemble spread flags its own large errors
+    err = np.abs(mean[:, :P] - T[te]).max(1)
+    spread = std[:, :P].max(1)
+    assert np.corrcoef(err, spread)[0, 1] > 0.2
+    # fallback: the uncertain cases come back from the solver exactly
+    tol = float(np.quantile(spread, 0.75))
+    out, fb, info = sur.solve(Q[te], P, tol=tol, n=n, dt=dt)
+    assert 0 < fb.sum() < len(fb)
+    np.testing.assert_allclose(out[fb], Y[te][fb], rtol=0, atol=1e-9)
+    # speed: surrogate predictions vs solver scenarios per second
+    solver_rate = len(Q) / tm["seconds"]
+    sur_rate = len(big) / t_sur
+    print(f"solver {solver_rate:.1f} scen/s, surrogate {sur_rate:.1f} scen/s, mae {mae:.3f} K (base {mae_base:.3f})")
+    assert sur_rate > 3 * solver_rate
