@@ -52,6 +52,13 @@ def make_problem(workload):
     raise SystemExit(f"unknown workload {workload}")
 
 
+def probe_lattice(prob, n):
+    """n^3 probe points on a lattice spanning the inner 80 % of the mesh's box."""
+    lo, hi = prob.X.min(0), prob.X.max(0)
+    g = [np.linspace(lo[j] + 0.1 * (hi[j] - lo[j]), hi[j] - 0.1 * (hi[j] - lo[j]), n) for j in range(3)]
+    return np.stack(np.meshgrid(*g, indexing="ij"), -1).reshape(-1, 3)
+
+
 def algorithmic_bytes(prob, n_prony):
     """Bytes the method must move per step in this library's layout: every
     element constant once, the Prony state read and written, and every nodal
@@ -147,31 +154,38 @@ def barrier(ws):
         dist.barrier()
 
 
-def cpu_oracle_sample(prob, steps, threads_note="1 (single-threaded C)"):
-    """Time the FP64 oracle as it stands on a bounded sample of the workload."""
+def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1):
+    """Time the FP64 oracle as it stands on a bounded sample of the workload:
+    `warmup` untimed steps, then as many full steps as fit in about `seconds`
+    (at least 1, at most max_steps)."""
     import oracle
 
     t0 = time.perf_counter()
     m = oracle.OracleModel(prob)
     setup = time.perf_counter() - t0
     s = m.init_state()
-    m.step(s, 1)  # warm caches
+    t0 = time.perf_counter()
+    m.step(s, max(1, warmup))
+    one = (time.perf_counter() - t0) / max(1, warmup)
+    steps = int(max(1, min(max_steps, seconds // max(one, 1e-9))))
     t0 = time.perf_counter()
     m.step(s, steps)
     el = time.perf_counter() - t0
     return {"value": prob.ne * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{prob.name}: {steps} steps after 1 warm-up step ({el:.1f} s, setup {setup:.1f} s), "
-                      f"FP64 C oracle, threads {threads_note}"}
+            "sample": f"{prob.name}: {steps} full steps after {max(1, warmup)} warm-up step(s) ({el:.1f} s, "
+                      f"set-up {setup:.1f} s), FP64 C oracle, single-threaded", "steps": steps}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, same workload,
+    metric and unit; each step a full oracle step, as many as fit in about
+    --ref-seconds (at most --steps)."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return 0
-    prob = make_problem(args.workload)
-    steps = max(1, args.ref_steps)
-    r = cpu_oracle_sample(prob, steps * max(1, args.steps) // max(1, args.steps))
-    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 0, "steps": steps,
+    prob = make_problem(args.workload if args.workload != "surrogate" else "block_h8")
+    r = cpu_oracle_sample(prob, args.steps, seconds=args.ref_seconds, warmup=min(args.warmup, 1))
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 0, "steps": r["steps"],
             "warmup": 1, "ms_per_step": 1e3 * prob.ne / r["value"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn},
@@ -180,6 +194,176 @@ def run_reference(args):
     print(json.dumps(line))
     return 0
 
+
+def planning_bench(args, device, stream):
+    """Batched treatment planning: every scenario to the end of its heating
+    time in one batch (one launch per step, autotuned tiling), against running
+    a stratified subset of the same scenarios one solver at a time; both timed
+    with CUDA events on the solver stream, set-up excluded.  The subset's plain
+    results are compared with the batch's to show both are the same solve."""
+    import torch
+
+    from paper_2009_10400_b300 import surrogate, tled
+    from paper_2009_10400_b300 import workloads as W
+
+    t_setup = time.perf_counter()
+    scen = [surrogate.mass_scaled(p) for p in W.planning_scenarios(args.plan_scenarios)]
+    b = tled.Batch(device=device, stream=stream)
+    for p in scen:
+        b.add(p, p.n_steps)
+    b.init()
+    tune = b.autotune(trial_steps=10)
+    setup_s = time.perf_counter() - t_setup
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    launch_steps = b.run()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    batch_s = ev0.elapsed_time(ev1) * 1e-3
+    st = b.stats()
+    Tb = b.temperature()
+    Db = b.damage()
+    infos = [b.scenario(i) for i in range(len(scen))]
+    b.close()
+
+    sub = list(range(0, len(scen), max(1, len(scen) // args.plan_subset)))[:args.plan_subset]
+    plain_s, du, dT, dD = 0.0, 0.0, 0.0, 0.0
+    for i in sub:
+        p = scen[i]
+        s = tled.Solver.from_problem(p, device=device, stream=stream)
+        s.step(1)  # graph capture outside the timed region; advances one step
+        s.sync()
+        ev0.record(stream)
+        s.step(p.n_steps - 1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        plain_s += ev0.elapsed_time(ev1) * 1e-3 * p.n_steps / max(1, p.n_steps - 1)
+        sl = slice(infos[i]["node_off"], infos[i]["node_off"] + infos[i]["nodes"])
+        dT = max(dT, float(np.abs(s.temperature() - Tb[sl]).max()))
+        dD = max(dD, float(np.abs(s.damage() - Db[sl]).max()))
+        s.close()
+    n = len(scen)
+    el_steps = sum(p.ne * p.n_steps for p in scen)
+    plain_rate = len(sub) / plain_s
+    return {
+        "workload": f"planning_{n}: hex or tet 5 cm cube, 2k-60k elements (log-uniform), 60-600 s at dt 0.01 s "
+                    "with mass scaling, 1-10 MW/m^3 source in the inner half, mu and k x U(0.8, 1.2)",
+        "scenarios": n, "elements": int(sum(p.ne for p in scen)), "element_steps": int(el_steps),
+        "batched_solves_per_s": n / batch_s, "batched_s": batch_s, "launch_steps": int(launch_steps),
+        "batched_element_steps_per_s": el_steps / batch_s,
+        "plain_solves_per_s": plain_rate, "plain_subset": len(sub), "plain_subset_s": plain_s,
+        "speedup": (n / batch_s) / plain_rate,
+        "autotune": tune, "setup_s": setup_s,
+        "subset_max_abs_diff": {"T_K": dT, "damage": dD},
+        "status": st["status"],
+    }
+
+
+def run_surrogate(args):
+    """Learned surrogate workload: training data from the batched solver, the
+    ensemble trained on the tensor-core kernels, then inference on a batch of
+    4096 scenarios (device-timed: the members' forward passes and the ensemble
+    kernel) and end to end (scenario rows from pinned host memory, answers and
+    fallback flags back to pinned host memory), and the fallback to the solver
+    on the test scenarios above the spread tolerance."""
+    import torch
+
+    from paper_2009_10400_b300 import surrogate
+    from paper_2009_10400_b300 import workloads as W
+
+    torch.cuda.set_device(0)
+    dev = "cuda:0"
+    stream = torch.cuda.current_stream()
+    n, P = args.sur_grid, args.sur_grid ** 3
+    n_train, n_test = args.sur_scenarios, args.sur_test
+    Q = W.sample_scenarios(n_train + n_test, seed=5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    T, D, tm = surrogate.solve_scenarios(Q, n=n, dt=0.01, chunk=args.sur_chunk)
+    gen_s = time.perf_counter() - t0
+    Y = np.concatenate([T, D], 1)
+    tr, te = slice(0, n_train), slice(n_train, n_train + n_test)
+    sur = surrogate.Surrogate(n_out=2 * P, width=512, depth=6, members=args.sur_members, max_batch=4096)
+    t0 = time.perf_counter()
+    hist = sur.fit(Q[tr], Y[tr], epochs=args.sur_epochs, batch=256, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    n_train_steps = args.sur_members * args.sur_epochs * (n_train // 256)
+
+    # ---- inference, device-timed: members' forwards + ensemble kernel, inputs resident
+    Bq = 4096
+    big = np.resize(Q[te], (Bq, Q.shape[1]))
+    Xd = torch.tensor(big, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        sur.predict_device(Xd, P, args.sur_tol)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        sur.predict_device(Xd, P, args.sur_tol)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    inf_s = ev0.elapsed_time(ev1) * 1e-3 / reps
+    flop = 2.0 * Bq * args.sur_members * sum(k * m for k, m in zip(sur.dims[:-1], sur.dims[1:]))
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        psrc = "measured"
+    except Exception:
+        peak, psrc = 1800.0, "fallback"
+    # ---- end to end: pinned host rows in, mean (float32), spread and flags out
+    Xh = torch.tensor(big, dtype=torch.float32).pin_memory()
+    Mh = torch.empty((Bq, 2 * P), dtype=torch.float32).pin_memory()
+    Sh = torch.empty(Bq, dtype=torch.float32).pin_memory()
+    Fh = torch.empty(Bq, dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        xd = Xh.to(dev, non_blocking=True)
+        mean, _, spread, fbd = sur.predict_device(xd, P, args.sur_tol, want_std=False)
+        Mh.copy_(mean, non_blocking=True)
+        Sh.copy_(spread, non_blocking=True)
+        Fh.copy_(fbd, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / reps
+
+    # ---- test scenarios: surrogate alone, then with the solver fallback
+    mean_te, std_te = sur.predict(Q[te])
+    out, fb, info = sur.solve(Q[te], P, tol=args.sur_tol, n=n, dt=0.01)
+    err_sur = np.abs(mean_te[:, :P] - T[te]).max(1)
+    err_out = np.abs(out[:, :P] - T[te]).max(1)
+    acc = ~fb
+    solver_rate = (n_train + n_test) / tm["seconds"]
+    line = {
+        "metric": "surrogate scenario-solves/s", "value": Bq / inf_s, "unit": "scenario-solves/s",
+        "n_gpus": 1, "steps": reps, "warmup": 3, "ms_per_step": 1e3 * inf_s, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+        "config": {"workload": f"surrogate: {n}^3 H8 cube, {P} probes, {2 * P} outputs, MLP {sur.dims}, "
+                               f"{args.sur_members} members, {args.sur_epochs} epochs, batch 256, inference {Bq}",
+                   "train_scenarios": n_train, "test_scenarios": n_test, "tol_K": args.sur_tol,
+                   "step": f"one ensemble inference of {Bq} scenarios (members' forwards + ensemble statistics)"},
+        "roofline": {"bound": "tensor", "achieved": flop / inf_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                     "frac": flop / inf_s / 1e12 / peak, "traffic": None, "peak_source": psrc,
+                     "kernel": "umma_gemm_kernel (tcgen05, bf16) over the ensemble's forward passes"},
+        "e2e": {"value": Bq / e2e_s, "unit": "scenario-solves/s", "h2d_bytes_per_step": int(Xh.numel() * 4),
+                "d2h_bytes_per_step": int(Mh.numel() * 4 + Sh.numel() * 4 + Fh.numel())},
+        "solver_solves_per_s": solver_rate, "data_generation_s": gen_s,
+        "fit_s": fit_s, "train_steps": n_train_steps,
+        "train_tflops": 3 * 2.0 * 256 * n_train_steps * sum(k * m for k, m in zip(sur.dims[:-1], sur.dims[1:]))
+                        / fit_s / 1e12,
+        "final_train_loss": [h[-1] for h in hist],
+        "test_mae_K": float(np.abs(mean_te[:, :P] - T[te]).mean()),
+        "test_max_err_K_surrogate_only": float(err_sur.max()),
+        "fallback_fraction": float(fb.mean()),
+        "accepted_max_err_K": float(err_sur[acc].max()) if acc.any() else None,
+        "answered_max_err_K": float(err_out.max()),
+        "solve_with_fallback_s": info["seconds"],
+        "effective_solves_per_s": n_test / info["seconds"],
+        "speedup_vs_solver": (Bq / inf_s) / solver_rate,
+    }
+    print(json.dumps(line))
+    return 0
 
 def run_gpu(args):
     import torch
@@ -194,7 +378,8 @@ def run_gpu(args):
 
     prob = make_problem(args.workload)
     stream = torch.cuda.current_stream()
-    s = tled.Solver.from_problem(prob, device=local, stream=stream)
+    probes = probe_lattice(prob, args.probes)
+    s = tled.Solver.from_problem(prob, device=local, stream=stream, probes=probes)
     info = s.plan_info()
     dt = s.get_dt()[0]
     n_prony = len(prob.prony_g)
@@ -218,7 +403,7 @@ def run_gpu(args):
     ms = reduce_max(ms, ws, f"cuda:{local}")
     value = ws * prob.ne * args.steps / (ms * 1e-3)
     launches_per_step = 1 + (1 if info["n_shared"] > 0 else 0)
-    gpu_launches = args.steps * launches_per_step + (args.steps + 31) // 32
+    gpu_launches = args.steps * launches_per_step + (args.steps + 31) // 32  # + one clock bump per graph
 
     # ---- live per-kernel timing for the roofline (CUDA events on the launching stream)
     k_tile, k_sh = s.step_timed(args.roofline_steps)
@@ -235,33 +420,40 @@ def run_gpu(args):
         except Exception:
             traffic = None
 
-    # ---- end to end through the C ABI with host buffers
-    chunk = args.e2e_chunk
-    n_calls = max(1, args.steps // chunk)
-    T_host = torch.empty(prob.nn, dtype=torch.float64).pin_memory()
-    D_host = torch.empty(prob.nn, dtype=torch.float64).pin_memory()
-    src_rows = np.array(prob.sources)
+    # ---- end to end through the C ABI with host buffers, every step: the step's
+    #      source settings from pinned host memory, one step, and the step's result
+    #      (temperature and damage at the probe lattice) back to pinned host memory
+    n_e2e = min(args.steps, args.e2e_steps)
+    src_host = torch.tensor(np.array(prob.sources), dtype=torch.float64).pin_memory()
+    P_host = torch.empty((2, len(probes)), dtype=torch.float64).pin_memory()
     barrier(ws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for i in range(n_calls):
-        s.set_heat_sources(src_rows)          # H2D: this call's source settings
-        s.step(chunk)
-        s.temperature(out=T_host)             # D2H: temperature field (synchronises)
-        s.damage(out=D_host)                  # D2H: damage field
+    for i in range(n_e2e):
+        s.set_heat_sources(src_host.numpy())  # H2D: this step's source settings
+        s.step(1)
+        s.probes(out=P_host)                  # D2H: probe temperatures and damage (synchronises)
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, ws, f"cuda:{local}")
-    e2e_value = ws * prob.ne * chunk * n_calls / e2e_s
+    e2e_value = ws * prob.ne * n_e2e / e2e_s
     s.sync()
+
+    st = s.stats()
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    plan = None
+    if not args.no_planning and prob.name.startswith("block_h8"):
+        plan = planning_bench(args, local, stream)
+        plan["scenario_solves_per_s"] = ws * plan["batched_solves_per_s"]
 
     out = None
     if rank == 0:
-        st = s.stats()
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
             from paper_2009_10400_b300 import workloads as W
 
-            cpu = cpu_oracle_sample(prob, args.cpu_steps)
+            cpu = cpu_oracle_sample(prob, args.cpu_steps, seconds=args.cpu_seconds)
         clocks = clk.summary()
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -279,13 +471,14 @@ def run_gpu(args):
                          "kernel_ms_per_step": per_step_kernel_ms,
                          "tile_kernel_ms": k_tile / args.roofline_steps,
                          "shared_kernel_ms": k_sh / args.roofline_steps, "peak_source": src},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(src_rows.size * 8),
-                    "d2h_bytes_per_step": int(2 * 8 * prob.nn), "steps_per_call": chunk,
-                    "note": "per call: set_heat_sources from host, step(%d), temperature and damage to pinned host"
-                            % chunk},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(src_host.numel() * 8),
+                    "d2h_bytes_per_step": int(P_host.numel() * 8), "steps": n_e2e,
+                    "note": "every step: tled_set_heat_sources from pinned host, tled_step(1), tled_get_probes "
+                            "(T and damage at a %d-point lattice) to pinned host" % len(probes)},
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "planning": plan,
             "final": {"T_max": st["T_max"], "u_max": st["u_max"], "status": st["status"]},
         }
         print(json.dumps(out))
@@ -299,20 +492,34 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--workload", default="block_h8")
     ap.add_argument("--roofline-steps", type=int, default=50)
-    ap.add_argument("--e2e-chunk", type=int, default=50)
-    ap.add_argument("--cpu-steps", type=int, default=2)
-    ap.add_argument("--ref-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--probes", type=int, default=16)
+    ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--ref-seconds", type=float, default=30.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-planning", action="store_true")
+    ap.add_argument("--plan-scenarios", type=int, default=256)
+    ap.add_argument("--plan-subset", type=int, default=32)
+    ap.add_argument("--sur-grid", type=int, default=16)
+    ap.add_argument("--sur-scenarios", type=int, default=2048)
+    ap.add_argument("--sur-test", type=int, default=256)
+    ap.add_argument("--sur-chunk", type=int, default=512)
+    ap.add_argument("--sur-members", type=int, default=5)
+    ap.add_argument("--sur-epochs", type=int, default=50)
+    ap.add_argument("--sur-tol", type=float, default=1.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     return run_gpu(args)
 
 

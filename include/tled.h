@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define TLED_VERSION 1
+#define TLED_VERSION 2
 
 /* status codes */
 #define TLED_OK 0
@@ -129,7 +129,11 @@ typedef struct tled_stats {
     double u_max;           /* max nodal |u|, m */
     double damage_volume;   /* sum of lumped volumes with Omega >= 1, m^3 */
     double heat_content;    /* sum_i C_i (T_i - T0), J (thermal mass at T_ref) */
-    double kinetic_energy;  /* sum_i 1/2 m_i |v_i|^2, J (mechanical, mass-scaled) */
+    double kinetic_energy;  /* sum_i 1/2 m_i |v_i|^2, J (mechanical, mass-scaled; v at the last half step) */
+    double strain_energy;   /* sum_e V0 lambda^3 Psi(F/lambda), J: stored energy of Eq. 9's potential
+                               (Table 5 terms, fibre term as in the step) with the thermal split of
+                               Eqs. 7-11, at the current u and theta */
+    double hourglass_energy;/* sum_e 1/2 k_hg sum_al |q_al|^2, J (H8 hourglass control; 0 for T4) */
     uint32_t status;        /* device status bits (0 = healthy) */
     int32_t pad;
 } tled_stats;
@@ -287,7 +291,10 @@ int tled_scenario_dt(tled_ctx *ctx, int32_t index, double *dt);
 int tled_autotune(tled_ctx *ctx, void *dev_workspace, int64_t bytes, int32_t trial_steps, int32_t *choice);
 
 /* Scalar diagnostics, reduced on the device in FP64 in a fixed order
- * (deterministic).  Synchronises. */
+ * (deterministic).  With no damping, no viscous terms, fixed or free
+ * boundaries and no thermal load, kinetic_energy + strain_energy +
+ * hourglass_energy is the mechanical energy the central-difference scheme
+ * conserves up to O(dt^2) oscillation (energy balance).  Synchronises. */
 int tled_get_stats(tled_ctx *ctx, tled_stats *s);
 
 /* Allocation-free diagnostics (the paper has no counterpart: this is a

@@ -45,6 +45,11 @@ int tled_mlp_init(tled_mlp *m, void *dev_workspace, int64_t bytes);
 /* copy all parameters from / to host float32 memory; setting resets Adam */
 int tled_mlp_set_params(tled_mlp *m, const float *params);
 int tled_mlp_get_params(tled_mlp *m, float *params);
+/* Affine map of the inputs, applied inside every forward pass before the
+ * first layer: x' = (x - shift) * scale, shift and scale host float32 arrays
+ * of dims[0] entries (copied; synchronises).  Both NULL: identity (the
+ * default after tled_mlp_init).  Errors: E_ARG (only one given, non-finite). */
+int tled_mlp_set_input_scaling(tled_mlp *m, const float *shift, const float *scale);
 /* y [B][outputs] = network(x [B][inputs]); B a multiple of 128 <= max_batch */
 int tled_mlp_forward(tled_mlp *m, const float *x, int32_t B, float *y);
 /* gradient of the MSE loss mean((y - t)^2) over B x outputs into grad
@@ -53,6 +58,25 @@ int tled_mlp_forward(tled_mlp *m, const float *x, int32_t B, float *y);
 int tled_mlp_gradients(tled_mlp *m, const float *x, const float *t, int32_t B, float *grad, float *loss);
 /* one Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr */
 int tled_mlp_train_step(tled_mlp *m, const float *x, const float *t, int32_t B, float lr, float *loss);
+/* the same on the batch of rows rows[0..B) (device int32) of a data set
+ * x [n][inputs], t [n][outputs] resident on the device (an epoch's shuffled
+ * mini-batches without copying them); rows must lie in [0, n) */
+int tled_mlp_train_step_rows(tled_mlp *m, const float *x, const float *t, const int32_t *rows, int32_t B, float lr,
+                             float *loss);
+/* Ensemble statistics of n_members (1..16) network outputs y[k] [B][n_out]
+ * (device float32, e.g. tled_mlp_forward of each member on the same inputs),
+ * enqueued on `stream` of `device`; no context, nothing allocated.  Each
+ * output is first mapped to z = y * out_scale + out_shift (device [n_out];
+ * both NULL: identity), then, over the members in order:
+ *   mean [B][n_out]  ensemble mean of z
+ *   std  [B][n_out]  population standard deviation of z (two-pass)
+ *   spread [B]       max of std over outputs [0, n_spread)
+ *   fallback [B]     1 where spread > tol, else 0 (uint8)
+ * Any of the four outputs may be NULL.  Used to accept a surrogate answer or
+ * send the scenario back to the solver.  Errors: E_ARG, E_CUDA. */
+int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *const *y, int32_t B, int32_t n_out,
+                      const float *out_scale, const float *out_shift, int32_t n_spread, float tol, float *mean,
+                      float *std, float *spread, uint8_t *fallback);
 /* wait for the stream; E_TIMEOUT if a bounded pipeline wait gave up */
 int tled_mlp_sync(tled_mlp *m);
 

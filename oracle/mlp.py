@@ -94,3 +94,17 @@ class MLPOracle:
         v = b2 * v + (1 - b2) * g * g
         p = p - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps)
         return p, m, v
+
+
+def ensemble_stats(ys, scale=None, shift=None, n_spread=0, tol=0.0):
+    """Ensemble statistics by their definitions, in FP64: members' outputs
+    mapped to z = y * scale + shift, mean and population standard deviation
+    over the members, spread = max of the std over the first n_spread outputs,
+    fallback = spread > tol.  ys: sequence of [B][n_out] arrays."""
+    Z = np.stack([np.asarray(y, np.float64) for y in ys])
+    if scale is not None:
+        Z = Z * np.asarray(scale, np.float64) + np.asarray(shift, np.float64)
+    mean = Z.sum(0) / len(ys)
+    std = np.sqrt(((Z - mean) ** 2).sum(0) / len(ys))
+    spread = std[:, :n_spread].max(1) if n_spread > 0 else np.zeros(len(mean))
+    return mean, std, spread, spread > tol

@@ -37,6 +37,8 @@ struct tled_mlp {
     std::vector<Layer> layer;
     int64_t n_params = 0;
     size_t p_w = 0, p_m = 0, p_v = 0, p_g = 0, x_b = 0, x_t = 0, y = 0, loss_part = 0, loss = 0, status = 0, total = 0;
+    size_t in_shift = 0, in_scale = 0;  // input affine map (x - shift) * scale, [n_in] each
+    bool has_scaling = false;
     char *ws = nullptr;
     bool inited = false;
     int64_t adam_t = 0;
@@ -104,9 +106,12 @@ int check_batch(tled_mlp *m, int B) {
     return TLED_OK;
 }
 
-int forward(tled_mlp *m, const float *x, int B, float *y) {
+int forward(tled_mlp *m, const float *x, const int32_t *rows, int B, float *y) {
     const Layer &l0 = m->layer[0];
-    MCUDA(m, launch_input(x, B, l0.K, l0.Kp, P<__nv_bfloat16>(m, m->x_b), P<__nv_bfloat16>(m, m->x_t), m->stream));
+    const float *sh = m->has_scaling ? P<float>(m, m->in_shift) : nullptr;
+    const float *sc = m->has_scaling ? P<float>(m, m->in_scale) : nullptr;
+    MCUDA(m, launch_input(x, rows, B, l0.K, l0.Kp, sh, sc, P<__nv_bfloat16>(m, m->x_b), P<__nv_bfloat16>(m, m->x_t),
+                          m->stream));
     for (int l = 0; l < m->L; l++) {
         const Layer &ly = m->layer[l];
         const void *Ain = l == 0 ? (const void *)P<char>(m, m->x_b) : (const void *)P<char>(m, m->layer[l - 1].a);
@@ -130,9 +135,9 @@ int forward(tled_mlp *m, const float *x, int B, float *y) {
 }
 
 // gradients of the mean squared error into p_g (and the loss into `loss`)
-int backward(tled_mlp *m, const float *t, int B, float *loss) {
+int backward(tled_mlp *m, const float *t, const int32_t *rows, int B, float *loss) {
     const Layer &last = m->layer[m->L - 1];
-    MCUDA(m, launch_loss(P<float>(m, m->y), t, B, last.N, P<__nv_bfloat16>(m, last.dz), P<__nv_bfloat16>(m, last.dzt),
+    MCUDA(m, launch_loss(P<float>(m, m->y), t, rows, B, last.N, P<__nv_bfloat16>(m, last.dz), P<__nv_bfloat16>(m, last.dzt),
                          P<double>(m, m->loss_part), loss ? loss : P<float>(m, m->loss), m->stream));
     for (int l = m->L - 1; l >= 0; l--) {
         const Layer &ly = m->layer[l];
@@ -232,6 +237,8 @@ int tled_mlp_create(tled_mlp **out, int device, void *stream, int32_t n_layers, 
     m->loss_part = take(8 * kLossBlocks);
     m->loss = take(8);
     m->status = take(16);
+    m->in_shift = take(4 * (size_t)m->layer[0].K);
+    m->in_scale = take(4 * (size_t)m->layer[0].K);
     m->total = off;
     *out = m;
     return TLED_OK;
@@ -266,6 +273,7 @@ int tled_mlp_init(tled_mlp *m, void *ws, int64_t bytes) {
     MCUDA(m, cudaStreamSynchronize(m->stream));
     m->inited = true;
     m->adam_t = 0;
+    m->has_scaling = false;
     return TLED_OK;
 }
 
@@ -282,6 +290,50 @@ int tled_mlp_set_params(tled_mlp *m, const float *params) {
     return TLED_OK;
 }
 
+int tled_mlp_set_input_scaling(tled_mlp *m, const float *shift, const float *scale) {
+    if (!m) return TLED_E_ARG;
+    if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
+    if (!shift != !scale) return fail(m, TLED_E_ARG, "give both shift and scale, or neither");
+    MCUDA(m, cudaSetDevice(m->device));
+    if (!shift) {
+        m->has_scaling = false;
+        return TLED_OK;
+    }
+    const int n = m->layer[0].K;
+    for (int k = 0; k < n; k++)
+        if (!std::isfinite(shift[k]) || !std::isfinite(scale[k])) return fail(m, TLED_E_ARG, "non-finite scaling");
+    MCUDA(m, cudaMemcpyAsync(m->ws + m->in_shift, shift, 4 * (size_t)n, cudaMemcpyHostToDevice, m->stream));
+    MCUDA(m, cudaMemcpyAsync(m->ws + m->in_scale, scale, 4 * (size_t)n, cudaMemcpyHostToDevice, m->stream));
+    MCUDA(m, cudaStreamSynchronize(m->stream));  // the host arrays may go away
+    m->has_scaling = true;
+    return TLED_OK;
+}
+
+int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *const *y, int32_t B, int32_t n_out,
+                      const float *out_scale, const float *out_shift, int32_t n_spread, float tol, float *mean,
+                      float *std, float *spread, uint8_t *fallback) {
+    if (n_members < 1 || n_members > kMaxMembers || !y || B < 0 || n_out < 1 || n_spread < 0 || n_spread > n_out ||
+        !(tol >= 0))
+        return TLED_E_ARG;
+    EnsembleArgs e{};
+    for (int k = 0; k < n_members; k++) {
+        if (!y[k]) return TLED_E_ARG;
+        e.y[k] = y[k];
+    }
+    e.n_members = n_members;
+    e.n_out = n_out;
+    e.n_spread = n_spread;
+    e.scale = out_scale;
+    e.shift = out_shift;
+    e.tol = tol;
+    e.mean = mean;
+    e.std = std;
+    e.spread = spread;
+    e.fallback = fallback;
+    if (cudaSetDevice(device) != cudaSuccess) return TLED_E_CUDA;
+    return launch_ensemble(e, B, (cudaStream_t)stream) == cudaSuccess ? TLED_OK : TLED_E_CUDA;
+}
+
 int tled_mlp_get_params(tled_mlp *m, float *params) {
     if (!m || !params) return fail(m, TLED_E_ARG, "NULL parameters");
     if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
@@ -296,7 +348,7 @@ int tled_mlp_forward(tled_mlp *m, const float *x, int32_t B, float *y) {
     if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
     if (int rc = check_batch(m, B)) return rc;
     MCUDA(m, cudaSetDevice(m->device));
-    return forward(m, x, B, y);
+    return forward(m, x, nullptr, B, y);
 }
 
 int tled_mlp_gradients(tled_mlp *m, const float *x, const float *t, int32_t B, float *grad, float *loss) {
@@ -304,20 +356,25 @@ int tled_mlp_gradients(tled_mlp *m, const float *x, const float *t, int32_t B, f
     if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
     if (int rc = check_batch(m, B)) return rc;
     MCUDA(m, cudaSetDevice(m->device));
-    if (int rc = forward(m, x, B, P<float>(m, m->y))) return rc;
-    if (int rc = backward(m, t, B, loss)) return rc;
+    if (int rc = forward(m, x, nullptr, B, P<float>(m, m->y))) return rc;
+    if (int rc = backward(m, t, nullptr, B, loss)) return rc;
     if (grad) MCUDA(m, cudaMemcpyAsync(grad, m->ws + m->p_g, 4 * m->n_params, cudaMemcpyDeviceToDevice, m->stream));
     return TLED_OK;
 }
 
 int tled_mlp_train_step(tled_mlp *m, const float *x, const float *t, int32_t B, float lr, float *loss) {
+    return tled_mlp_train_step_rows(m, x, t, nullptr, B, lr, loss);
+}
+
+int tled_mlp_train_step_rows(tled_mlp *m, const float *x, const float *t, const int32_t *rows, int32_t B, float lr,
+                             float *loss) {
     if (!m || !x || !t) return fail(m, TLED_E_ARG, "NULL argument");
     if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
     if (int rc = check_batch(m, B)) return rc;
     if (!(lr > 0) || !std::isfinite(lr)) return fail(m, TLED_E_ARG, "learning rate must be positive");
     MCUDA(m, cudaSetDevice(m->device));
-    if (int rc = forward(m, x, B, P<float>(m, m->y))) return rc;
-    if (int rc = backward(m, t, B, loss)) return rc;
+    if (int rc = forward(m, x, rows, B, P<float>(m, m->y))) return rc;
+    if (int rc = backward(m, t, rows, B, loss)) return rc;
     m->adam_t++;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float bc1 = (float)(1.0 - std::pow(0.9, (double)m->adam_t));

@@ -26,12 +26,23 @@ struct GemmArgs {
     unsigned int *status;        // error word (bit 0: a bounded wait timed out)
 };
 
+constexpr int kMaxMembers = 16;
+struct EnsembleArgs {
+    const float *y[kMaxMembers];  // member outputs [B][n_out]
+    int n_members, n_out, n_spread;
+    const float *scale, *shift;   // [n_out] or NULL
+    float tol;
+    float *mean, *std, *spread;   // [B][n_out], [B][n_out], [B]; each may be NULL
+    uint8_t *fallback;            // [B] or NULL
+};
+cudaError_t launch_ensemble(const EnsembleArgs &e, int B, cudaStream_t s);
+
 cudaError_t launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, int bn, int mode,
                         cudaStream_t s);
-cudaError_t launch_input(const float *x, int B, int n_in, int ld, __nv_bfloat16 *xb, __nv_bfloat16 *xt,
-                         cudaStream_t s);
-cudaError_t launch_loss(const float *y, const float *t, int B, int N, __nv_bfloat16 *dy, __nv_bfloat16 *dyt,
-                        double *partials, float *loss, cudaStream_t s);
+cudaError_t launch_input(const float *x, const int32_t *rows, int B, int n_in, int ld, const float *shift,
+                         const float *scale, __nv_bfloat16 *xb, __nv_bfloat16 *xt, cudaStream_t s);
+cudaError_t launch_loss(const float *y, const float *t, const int32_t *rows, int B, int N, __nv_bfloat16 *dy,
+                        __nv_bfloat16 *dyt, double *partials, float *loss, cudaStream_t s);
 cudaError_t launch_bias_grad(const __nv_bfloat16 *dzt, int B, int N, float *db, cudaStream_t s);
 cudaError_t launch_adam(float *w, float *m, float *v, const float *grad, int64_t n, float lr, float b1, float b2,
                         float eps, float bc1, float bc2, int N, int K, int ld, __nv_bfloat16 *wb, __nv_bfloat16 *wt,

@@ -223,30 +223,40 @@ __global__ void __launch_bounds__(192, 1)
 // ---------------------------------------------------------------------------
 // elementwise kernels
 // ---------------------------------------------------------------------------
-// x [B][n_in] float -> bf16 [B][ld] (zero padded) and its transpose [ld][B]
-__global__ void input_kernel(const float *__restrict__ x, int B, int n_in, int ld, __nv_bfloat16 *xb,
+// batch row b = x[rows[b]] (rows NULL: x[b]) of x [*][n_in] float, mapped to
+// (x - shift) * scale (NULL: identity), -> bf16 [B][ld] (zero padded) and its transpose [ld][B]
+__global__ void input_kernel(const float *__restrict__ x, const int32_t *__restrict__ rows, int B, int n_in, int ld,
+                             const float *__restrict__ shift, const float *__restrict__ scale, __nv_bfloat16 *xb,
                              __nv_bfloat16 *xt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)B * ld) return;
     const int b = (int)(i / ld), k = (int)(i % ld);
-    const __nv_bfloat16 v = __float2bfloat16_rn(k < n_in ? x[(int64_t)b * n_in + k] : 0.f);
-    xb[i] = v;
-    xt[(int64_t)k * B + b] = v;
+    float v = 0.f;
+    if (k < n_in) {
+        const int64_t r = rows ? (int64_t)rows[b] : (int64_t)b;
+        v = x[r * n_in + k];
+        if (shift) v = (v - shift[k]) * scale[k];
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    xb[i] = h;
+    xt[(int64_t)k * B + b] = h;
 }
 
 // MSE loss 1/(B N) sum (y - t)^2 and dY = 2 (y - t) / (B N) in bf16 (+ transpose);
 // per-block partial sums of the loss (fixed order, reduced by loss_final_kernel)
-__global__ void loss_kernel(const float *__restrict__ y, const float *__restrict__ t, int B, int N,
-                            __nv_bfloat16 *dy, __nv_bfloat16 *dyt, double *partials) {
+// (targets of batch row b: t[rows[b]], or t[b] when rows is NULL)
+__global__ void loss_kernel(const float *__restrict__ y, const float *__restrict__ t, const int32_t *__restrict__ rows,
+                            int B, int N, __nv_bfloat16 *dy, __nv_bfloat16 *dyt, double *partials) {
     __shared__ double sh[256];
     const double scale = 1.0 / ((double)B * N);
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)B * N;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float d = y[i] - t[i];
+        const int b = (int)(i / N), n = (int)(i % N);
+        const int64_t r = rows ? (int64_t)rows[b] : (int64_t)b;
+        const float d = y[i] - t[r * N + n];
         acc += (double)d * d;
         const __nv_bfloat16 g = __float2bfloat16_rn((float)(2.0 * scale) * d);
-        const int b = (int)(i / N), n = (int)(i % N);
         dy[i] = g;
         dyt[(int64_t)n * B + b] = g;
     }
@@ -309,6 +319,51 @@ __global__ void gather_grad_kernel(const float *__restrict__ G, const float *__r
     }
 }
 
+// Ensemble statistics, one block per batch row b: z_k = y_k * scale + shift for
+// the members k (summed in member order), mean and population standard
+// deviation (two passes), spread = max of std over the first n_spread outputs,
+// fallback = spread > tol.
+__global__ void __launch_bounds__(256) ensemble_kernel(const EnsembleArgs E) {
+    const int b = blockIdx.x;
+    float smax = 0.f;
+    for (int n = threadIdx.x; n < E.n_out; n += blockDim.x) {
+        const int64_t i = (int64_t)b * E.n_out + n;
+        const float sc = E.scale ? E.scale[n] : 1.f, sh = E.shift ? E.shift[n] : 0.f;
+        float z[kMaxMembers];
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMaxMembers; k++) {
+            if (k < E.n_members) {
+                z[k] = fmaf(E.y[k][i], sc, sh);
+                sum += z[k];
+            }
+        }
+        const float mean = sum / (float)E.n_members;
+        float var = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMaxMembers; k++) {
+            if (k < E.n_members) {
+                const float d = z[k] - mean;
+                var = fmaf(d, d, var);
+            }
+        }
+        const float sd = sqrtf(var / (float)E.n_members);
+        if (E.mean) E.mean[i] = mean;
+        if (E.std) E.std[i] = sd;
+        if (n < E.n_spread) smax = fmaxf(smax, sd);
+    }
+    for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = smax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) m = fmaxf(m, red[w]);
+        if (E.spread) E.spread[b] = m;
+        if (E.fallback) E.fallback[b] = m > E.tol ? 1 : 0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -347,16 +402,16 @@ cudaError_t launch_gemm(const CUtensorMap &a, const CUtensorMap &b, const GemmAr
     }
 }
 
-cudaError_t launch_input(const float *x, int B, int n_in, int ld, __nv_bfloat16 *xb, __nv_bfloat16 *xt,
-                         cudaStream_t s) {
+cudaError_t launch_input(const float *x, const int32_t *rows, int B, int n_in, int ld, const float *shift,
+                         const float *scale, __nv_bfloat16 *xb, __nv_bfloat16 *xt, cudaStream_t s) {
     const int64_t n = (int64_t)B * ld;
-    input_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(x, B, n_in, ld, xb, xt);
+    input_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(x, rows, B, n_in, ld, shift, scale, xb, xt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const float *y, const float *t, int B, int N, __nv_bfloat16 *dy, __nv_bfloat16 *dyt,
-                        double *partials, float *loss, cudaStream_t s) {
-    loss_kernel<<<kLossBlocks, 256, 0, s>>>(y, t, B, N, dy, dyt, partials);
+cudaError_t launch_loss(const float *y, const float *t, const int32_t *rows, int B, int N, __nv_bfloat16 *dy,
+                        __nv_bfloat16 *dyt, double *partials, float *loss, cudaStream_t s) {
+    loss_kernel<<<kLossBlocks, 256, 0, s>>>(y, t, rows, B, N, dy, dyt, partials);
     loss_final_kernel<<<1, 32, 0, s>>>(partials, kLossBlocks, loss);
     return cudaGetLastError();
 }
@@ -370,6 +425,11 @@ cudaError_t launch_adam(float *w, float *m, float *v, const float *grad, int64_t
                         float eps, float bc1, float bc2, int N, int K, int ld, __nv_bfloat16 *wb, __nv_bfloat16 *wt,
                         cudaStream_t s) {
     adam_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w, m, v, grad, n, lr, b1, b2, eps, bc1, bc2, N, K, ld, wb, wt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ensemble(const EnsembleArgs &e, int B, cudaStream_t s) {
+    if (B > 0) ensemble_kernel<<<B, 256, 0, s>>>(e);
     return cudaGetLastError();
 }
 

@@ -88,8 +88,8 @@ struct tled_ctx {
     std::string err;
     bool batch = false;
     std::vector<Scenario> sc;
-    // combined problem
-    int npe = 0;
+    // combined problem; npe = 0 when a batch mixes T4 and H8 scenarios
+    int npe = 0, npe_max = 0;
     int64_t nn = 0, ne = 0, n_probes = 0;
     bool has_mat = false, has_fib = false;
     std::vector<int> rank_of;      // scenario -> rank (order of decreasing n_steps)
@@ -142,9 +142,10 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ULL) {
 Scenario &single(tled_ctx *c) { return c->sc[0]; }
 int n_prony(const tled_ctx *c) { return c->sc.empty() ? 0 : c->sc[0].mat.n_prony; }
 
-size_t rec_bytes(const tled_ctx *c) {
+// element record bytes of a tile of npe-node elements; the tile stride is rec_bytes(c, c->npe_max)
+size_t rec_bytes(const tled_ctx *c, int npe) {
     const int ncomp = 10 + (c->has_mat ? 6 : 0) + (c->has_fib ? 3 : 0);
-    return (size_t)tled::kTile * c->npe * 2 + (size_t)ncomp * tled::kTile * 4;
+    return (size_t)tled::kTile * npe * 2 + (size_t)ncomp * tled::kTile * 4;
 }
 // Prony state index of element slot e, component q (tile-blocked [t][6 n_prony][kTile])
 inline size_t visc_index(int np, int64_t e, int q) {
@@ -177,7 +178,7 @@ Layout make_layout(const tled_ctx *c) {
     L.X0 = take(16 * nn);
     L.nodec = take(16 * nn);
     L.ubar = take(any_ubar ? 16 * nn : 0);
-    L.elem_rec = take((size_t)p.n_tiles * rec_bytes(c));
+    L.elem_rec = take((size_t)p.n_tiles * rec_bytes(c, c->npe_max));
     L.visc = take(4 * 6 * (size_t)std::max(n_prony(c), 0) * ne);
     L.tile_info = take(4 * p.tile_info.size());
     L.tile_shared = take(4 * p.tile_shared.size());
@@ -335,7 +336,11 @@ int ensure_plan(tled_ctx *c) {
         if (!s.have_mat) return fail(c, TLED_E_STATE, "tled_set_material has not been called");
     }
     const int ns = (int)c->sc.size();
-    c->npe = c->sc[0].npe;
+    c->npe = c->npe_max = c->sc[0].npe;
+    for (auto &s : c->sc) {
+        if (s.npe != c->npe) c->npe = 0;
+        c->npe_max = std::max(c->npe_max, s.npe);
+    }
     c->nn = c->ne = c->n_probes = 0;
     c->has_mat = c->has_fib = false;
     const tled_material &m0 = c->sc[0].mat;
@@ -360,18 +365,23 @@ int ensure_plan(tled_ctx *c) {
                      [&](int a, int b) { return c->sc[a].n_steps > c->sc[b].n_steps; });
     c->rank_of.assign(ns, 0);
     for (int r = 0; r < ns; r++) c->rank_of[c->scn_of_rank[r]] = r;
-    // concatenated mesh
+    // concatenated mesh (connectivity stride npe_max; per-element type when mixed)
+    const int cs = c->npe_max;
     std::vector<double> X(3 * c->nn);
-    std::vector<int32_t> conn(c->npe * c->ne), group(c->ne);
+    std::vector<int32_t> conn((size_t)cs * c->ne, 0), group(c->ne);
+    std::vector<int8_t> etype(c->npe ? 0 : c->ne);
     for (int si = 0; si < ns; si++) {
         const Scenario &s = c->sc[si];
         std::copy(s.X.begin(), s.X.end(), X.begin() + 3 * s.node_off);
-        for (int64_t i = 0; i < s.npe * s.ne; i++) conn[s.npe * s.elem_off + i] = s.conn[i] + (int32_t)s.node_off;
+        for (int64_t e = 0; e < s.ne; e++)
+            for (int a = 0; a < s.npe; a++)
+                conn[(size_t)cs * (s.elem_off + e) + a] = s.conn[(size_t)s.npe * e + a] + (int32_t)s.node_off;
+        if (!etype.empty()) std::fill(etype.begin() + s.elem_off, etype.begin() + s.elem_off + s.ne, (int8_t)s.npe);
         std::fill(group.begin() + s.elem_off, group.begin() + s.elem_off + s.ne, c->rank_of[si]);
     }
     const int te = c->tile_override ? c->tile_override : c->sc[0].prm.tile_elems;
-    int rc = tled::build_plan(c->npe, c->nn, X.data(), c->ne, conn.data(), ns > 1 ? group.data() : nullptr, te,
-                              c->plan, c->err);
+    int rc = tled::build_plan(cs, c->nn, X.data(), c->ne, conn.data(), etype.empty() ? nullptr : etype.data(),
+                              ns > 1 ? group.data() : nullptr, te, c->plan, c->err);
     if (rc) return rc;
     // active prefixes per rank
     const Plan &p = c->plan;
@@ -762,7 +772,6 @@ int tled_batch_add(tled_ctx *b, const tled_ctx *scenario, int64_t n_steps, int32
     if (!b->sc.empty()) {
         const Scenario &f = b->sc[0];
         const tled_material &a = f.mat, &m = s.mat;
-        if (s.npe != f.npe) return fail(b, TLED_E_ARG, "all scenarios of a batch need the same element type");
         bool same = a.n_prony == m.n_prony && a.T0 == m.T0 && a.Ta == m.Ta && a.lnA == m.lnA && a.Ea == m.Ea &&
                     a.beta_c == m.beta_c && a.beta_k == m.beta_k && a.T_ref == m.T_ref &&
                     f.prm.flags == s.prm.flags && f.prm.kappa_hg == s.prm.kappa_hg &&
@@ -815,13 +824,13 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     c->inited = false;
     c->ws = (char *)dev_workspace;
     const Plan &p = c->plan;
-    const int npe = c->npe;
+    const int npe = c->npe;  // 0 for a mixed batch
     const int64_t nn = c->nn;
     const int ns = (int)c->sc.size();
     // --- per-scenario time steps and source offsets
     int src_off = 0;
     for (auto &s : c->sc) {
-        tled::stable_dt(npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
+        tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
                         s.prm, &s.dt_mech, &s.dt_th);
         s.dt = s.prm.dt > 0 ? s.prm.dt : s.prm.dt_safety * std::min(s.dt_mech, s.dt_th);
         s.src_off = src_off;
@@ -829,7 +838,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     }
     // --- element records (tile-blocked), lumped masses, nodal constants
     const int64_t nep = p.ne_pad;
-    const size_t rb = rec_bytes(c);
+    const size_t rb = rec_bytes(c, c->npe_max);  // tile stride
     const int kT = tled::kTile;
     std::vector<int32_t> scn_of_elem(c->ne);
     for (int si = 0; si < ns; si++)
@@ -841,13 +850,14 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         if (eo < 0) continue;  // padding slot
         const Scenario &s = c->sc[scn_of_elem[eo]];
         const int64_t el = eo - s.elem_off;
-        const int32_t *cn = s.conn.data() + el * npe;
+        const int ke = s.npe;  // this element's (and its tile's) type
+        const int32_t *cn = s.conn.data() + el * ke;
         double Ji[9], V;
-        tled::element_geometry(npe, s.X.data(), cn, Ji, &V);
+        tled::element_geometry(ke, s.X.data(), cn, Ji, &V);
         char *r = rec.data() + (size_t)(e / kT) * rb;
         const int ei = (int)(e % kT);
-        std::memcpy(r + (size_t)ei * npe * 2, &p.conn_local[(size_t)e * npe], (size_t)npe * 2);
-        float *cf = reinterpret_cast<float *>(r + (size_t)kT * npe * 2) + ei;
+        std::memcpy(r + (size_t)ei * ke * 2, &p.conn_local[(size_t)e * p.npe], (size_t)ke * 2);
+        float *cf = reinterpret_cast<float *>(r + (size_t)kT * ke * 2) + ei;
         int q = 0;
         for (int j = 0; j < 9; j++) cf[(q++) * kT] = (float)Ji[j];
         cf[(q++) * kT] = (float)V;
@@ -861,12 +871,12 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         }
         if (c->has_fib)
             for (int j = 0; j < 3; j++) cf[(q++) * kT] = (float)(s.fib.empty() ? s.mat.a0[j] : s.fib[3 * el + j]);
-        for (int a = 0; a < npe; a++) {
+        for (int a = 0; a < ke; a++) {
             const int64_t i = cn[a] + s.node_off;
-            Mn[i] += s.prm.mass_scale * s.mat.rho * V / npe;
-            Cn[i] += s.mat.rho * s.mat.c * V / npe;
-            Vn[i] += V / npe;
-            Kb[i] += s.mat.wb_cb * V / npe;
+            Mn[i] += s.prm.mass_scale * s.mat.rho * V / ke;
+            Cn[i] += s.mat.rho * s.mat.c * V / ke;
+            Vn[i] += V / ke;
+            Kb[i] += s.mat.wb_cb * V / ke;
         }
     }
     std::vector<float4> X0(nn), nodec(nn), ub;
@@ -1241,8 +1251,8 @@ int tled_get_stats(tled_ctx *c, tled_stats *s) {
     if (!c || !s) return fail(c, TLED_E_ARG, "NULL stats");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
     CUDA_TRY(c, cudaSetDevice(c->device));
-    CUDA_TRY(c, tled::launch_stats(c->A, c->nn, dptr<double>(c, c->L.stat_part), dptr<double>(c, c->L.stat_out),
-                                   c->stream));
+    CUDA_TRY(c, tled::launch_stats(c->A, c->npe, c->nn, dptr<double>(c, c->L.stat_part),
+                                   dptr<double>(c, c->L.stat_out), c->stream));
     double o[8];
     unsigned st[4];
     CUDA_TRY(c, cudaMemcpyAsync(o, c->ws + c->L.stat_out, 64, cudaMemcpyDeviceToHost, c->stream));
@@ -1253,6 +1263,8 @@ int tled_get_stats(tled_ctx *c, tled_stats *s) {
     s->t = c->t0 + c->step * c->sc[0].dt;
     s->dt = c->sc[0].dt;
     s->kinetic_energy = o[0];
+    s->strain_energy = o[6];
+    s->hourglass_energy = o[7];
     s->heat_content = o[1];
     s->T_max = c->sc[0].mat.T0 + o[2];
     s->T_min = c->sc[0].mat.T0 + o[3];

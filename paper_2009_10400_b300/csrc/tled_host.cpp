@@ -171,9 +171,11 @@ static inline uint64_t spread3(uint64_t v) {  // 21 bits -> every third bit
     return v;
 }
 
-int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const int32_t *group,
-               int tile_elems, Plan &p, std::string &err) {
+int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const int8_t *etype,
+               const int32_t *group, int tile_elems, Plan &p, std::string &err) {
     p = Plan();
+    // element e has nc(e) corners: etype[e] (4 or 8) in a mixed mesh, else npe; conn stride npe
+    auto nc = [&](int64_t e) { return etype ? (int)etype[e] : npe; };
     p.npe = npe;
     p.nn = nn;
     p.ne = ne;
@@ -190,11 +192,12 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     std::vector<uint64_t> key(ne);
     for (int64_t e = 0; e < ne; e++) {
         double c[3] = {0, 0, 0};
-        for (int a = 0; a < npe; a++)
+        const int ke = nc(e);
+        for (int a = 0; a < ke; a++)
             for (int j = 0; j < 3; j++) c[j] += X[3 * (int64_t)conn[e * npe + a] + j];
         uint64_t k = 0;
         for (int j = 0; j < 3; j++) {
-            double q = (c[j] / npe - lo[j]) / ext;
+            double q = (c[j] / ke - lo[j]) / ext;
             uint64_t iq = (uint64_t)std::min(std::max(q, 0.0) * 2097151.0, 2097151.0);
             k |= spread3(iq) << j;
         }
@@ -208,25 +211,29 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         return ga != gb ? ga < gb : key[a] < key[b];
     });
 
-    // --- cut tiles: at most tile_elems elements and kMaxLocal distinct nodes
+    // --- cut tiles: at most tile_elems elements and kMaxLocal distinct nodes; a tile
+    //     holds one group and one element type
     std::vector<int32_t> mark(nn, -1);
     std::vector<int32_t> tile_begin;
     int n_local = 0, n_in = 0, t = -1;
     int32_t prev_group = -1;
+    int prev_type = -1;
     for (int64_t i = 0; i < ne; i++) {
         const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
         const int32_t gi = group ? group[p.elem_old[i]] : 0;
+        const int ki = nc(p.elem_old[i]);
         int fresh = 0;
         if (t >= 0)
-            for (int a = 0; a < npe; a++) fresh += (mark[cn[a]] != t);
-        if (t < 0 || n_in == tile_elems || n_local + fresh > kMaxLocal || gi != prev_group) {  // tiles never span groups
+            for (int a = 0; a < ki; a++) fresh += (mark[cn[a]] != t);
+        if (t < 0 || n_in == tile_elems || n_local + fresh > kMaxLocal || gi != prev_group || ki != prev_type) {
             prev_group = gi;
+            prev_type = ki;
             t++;
             tile_begin.push_back((int32_t)i);
             n_local = 0;
             n_in = 0;
         }
-        for (int a = 0; a < npe; a++)
+        for (int a = 0; a < ki; a++)
             if (mark[cn[a]] != t) {
                 mark[cn[a]] = t;
                 n_local++;
@@ -241,7 +248,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     for (int tt = 0; tt < p.n_tiles; tt++)
         for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
-            for (int a = 0; a < npe; a++)
+            for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++)
                 if (last[cn[a]] != tt) {
                     last[cn[a]] = tt;
                     ntouch[cn[a]]++;
@@ -272,7 +279,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         ti[2] = next;
         for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
-            for (int a = 0; a < npe; a++)
+            for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++)
                 if (ntouch[cn[a]] == 1 && p.node_new[cn[a]] < 0) p.node_new[cn[a]] = next++;
         }
         ti[3] = next - ti[2];
@@ -281,7 +288,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     for (int tt = 0; tt < p.n_tiles; tt++)
         for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
-            for (int a = 0; a < npe; a++)
+            for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++)
                 if (p.node_new[cn[a]] < 0) p.node_new[cn[a]] = next++;
         }
     p.n_shared = next - p.n_interior;
@@ -305,7 +312,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         std::vector<int32_t> shared;
         for (int64_t i = e0; i < e0 + ne_t; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
-            for (int a = 0; a < npe; a++) {
+            for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++) {
                 int32_t g = p.node_new[cn[a]];
                 if (g >= p.n_interior && local[g] != -2 - tt) {
                     local[g] = -2 - tt;  // seen in this tile
@@ -322,7 +329,8 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         ti[4] = nl;
         ti[5] = (int32_t)p.tile_shared.size();
         ti[6] = (int32_t)part;
-        ti[7] = 0;
+        const int kt = nc(p.elem_old[e0]);
+        ti[7] = kt;  // element type of the tile (4 or 8)
         for (size_t j = 0; j < shared.size(); j++) {
             p.tile_shared.push_back(shared[j]);
             p.part_pos.push_back(sh_n[shared[j] - p.n_interior]++);  // rank; made absolute below
@@ -331,7 +339,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         // local index of every node of the tile
         for (int64_t i = e0; i < e0 + ne_t; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
-            for (int a = 0; a < npe; a++) {
+            for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++) {
                 int32_t g = p.node_new[cn[a]];
                 int l;
                 if (g < p.n_interior) {
@@ -345,15 +353,15 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         // gather list: for every local node the slot offsets (corner * kTile +
         // element) of its incident corners, ascending element then corner
         uint16_t *rec_codes = &p.csr[(size_t)tt * rec];
-        uint16_t *rec_row = rec_codes + kTile * npe;
+        uint16_t *rec_row = rec_codes + kTile * kt;
         std::vector<int32_t> cnt(nl + 1, 0);
         for (int64_t i = e0; i < e0 + ne_t; i++)
-            for (int a = 0; a < npe; a++) cnt[p.conn_local[(size_t)i * npe + a] + 1]++;
+            for (int a = 0; a < kt; a++) cnt[p.conn_local[(size_t)i * npe + a] + 1]++;
         for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
         for (int l = 0; l <= nl; l++) rec_row[l] = (uint16_t)cnt[l];
         std::vector<int32_t> cur(cnt.begin(), cnt.end() - 1);
         for (int64_t i = e0; i < e0 + ne_t; i++)
-            for (int a = 0; a < npe; a++) {
+            for (int a = 0; a < kt; a++) {
                 int l = p.conn_local[(size_t)i * npe + a];
                 rec_codes[cur[l]++] = (uint16_t)(a * kTile + (int)(i - e0));
             }

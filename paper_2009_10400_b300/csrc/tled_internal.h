@@ -39,7 +39,7 @@ struct Plan {
     int64_t n_interior = 0, n_shared = 0;
     int n_tiles = 0;
     std::vector<int32_t> tile_info;     // [n_tiles][8]: e0 (= tile * kTile), ne, int_begin, n_int,
-                                        //   n_local, sh_off, part_off, 0
+                                        //   n_local, sh_off, part_off, element type (4 or 8)
     std::vector<int32_t> tile_shared;   // per tile: new ids of its shared nodes (ascending)
     std::vector<uint16_t> conn_local;   // [ne_pad][npe] tile-local node index
     std::vector<uint16_t> csr;          // [n_tiles][csr_rec_u16]: slot offsets corner * kTile + element, grouped
@@ -70,8 +70,9 @@ struct StepArgs {
     const float4 *nodec;   // m_i, Cth_i, mask bits (as float bits), 0
     const float4 *ubar;    // prescribed displacement or nullptr
     // element data, tile-blocked: tile t's record at elem_rec + t * rec_bytes holds the local
-    // connectivity [kTile][npe] (uint16) then float components [q][kTile]: J0^-1 (9), V0,
-    // [mu kappa k1 k2 k alpha], [fibre xyz]; the Prony state lives in visc [t][6 n_prony][kTile]
+    // connectivity [kTile][npe] (uint16, npe = the tile's element type) then float components
+    // [q][kTile]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz]; the Prony state lives in
+    // visc [t][6 n_prony][kTile].  rec_bytes is the stride (the largest element type's record).
     const char *elem_rec;
     int64_t rec_bytes;
     int has_mat, has_fib;
@@ -80,7 +81,7 @@ struct StepArgs {
     // tiles
     const int *tile_info;
     const int *tile_shared;
-    const uint16_t *csr;   // [n_tiles][csr_rec_u16(npe)]
+    const uint16_t *csr;   // [n_tiles][csr_stride]: csr_rec_u16(npe of the tile) entries used
     float4 *partials;      // node-major: shared node s owns [sh_rowptr[s], sh_rowptr[s+1]), one per touching tile
     const int *part_pos;   // per (tile, shared node) entry of tile_shared: its partial's position
     const int *sh_rowptr;
@@ -100,6 +101,7 @@ struct StepArgs {
     int sm_buf;            // max(sm_in, slot buffer bytes), 128-aligned; two such buffers
     int sm_ns, sm_csr, sm_xu, sm_X, sm_bar, sm_total;
     int n_tiles;
+    int csr_stride;        // uint16 entries between consecutive tiles' gather records
     int n_comp;            // staged float components per element (J0^-1 9, V0, [mat 6], [fibre 3], Prony 6 n)
     // batch-wide scalars
     float mu, kappa, k1, k2, kc, alpha;   // uniform material (used when has_mat == 0)
@@ -113,7 +115,7 @@ struct StepArgs {
     double ramp_time;
 };
 
-// kernel launchers (tled_kernels.cu)
+// kernel launchers (tled_kernels.cu); npe 4 or 8, or 0 for a batch mixing both element types
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s);
 int tile_grid(const StepArgs &a, int npe, int n_sm);  // persistent grid size
 cudaError_t launch_shared_step(const StepArgs &a, int k, cudaStream_t s);
@@ -124,13 +126,14 @@ cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w
 // read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction
 cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,
                             cudaStream_t s);
-void tile_smem_layout(StepArgs &a, int npe);  // fills the sm_* fields
+void tile_smem_layout(StepArgs &a, int npe);  // fills the sm_* fields and csr_stride
 cudaError_t tile_kernel_setup(const StepArgs &a, int npe);
 // FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
-// damaged volume; deterministic two-stage reduction through `partials` [kStatBlocks][8].
+// damaged volume, out[6..7] = stored (hyperelastic) energy and hourglass energy; deterministic
+// two-stage reduction through `partials` [kStatBlocks][8].
 constexpr int kStatBlocks = 296;
-cudaError_t launch_stats(const StepArgs &a, int64_t nn, double *partials, double *out, cudaStream_t s);
-// the same reduction over a caller-chosen number of blocks (partials [n_blocks][8])
+cudaError_t launch_stats(const StepArgs &a, int npe, int64_t nn, double *partials, double *out, cudaStream_t s);
+// the nodal part (out[0..5]) over a caller-chosen number of blocks (partials [n_blocks][8])
 cudaError_t launch_stats_blocks(const StepArgs &a, int64_t nn, int n_blocks, double *partials, double *out,
                                 cudaStream_t s);
 // allocation-free variant: block partials in a static device array (tled_noalloc.cu)
@@ -143,7 +146,8 @@ void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
                const double *mat6, const tled_params &p, double *dt_mech, double *dt_th);
 // group: optional [ne] group id per element (scenario rank); tiles never span groups and
 // follow ascending group order.
-int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const int32_t *group,
+int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const int8_t *etype,
+               const int32_t *group,
                int tile_elems, Plan &p, std::string &err);
 
 }  // namespace tled

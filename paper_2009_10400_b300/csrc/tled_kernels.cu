@@ -515,19 +515,29 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 }
 
 struct TileInfo {
-    int e0, ne_t, ib, n_int, nl, sh_off, part_off;
+    int e0, ne_t, ib, n_int, nl, sh_off, part_off, npe;
 };
 __device__ __forceinline__ TileInfo tile_info(const StepArgs &A, int t) {
     const int4 a = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t);
     const int4 b = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t + 1);
-    return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z};
+    return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+// element type of tile t: the kernel's own, or the tile's in a mixed batch (NPE = 0)
+template <int NPE>
+__device__ __forceinline__ int tile_npe(const StepArgs &A, int t) {
+    if constexpr (NPE != 0) return NPE;
+    return __ldg(A.tile_info + kTileInfo * t + 7);
+}
+// bytes of a tile's element record for its element type (the stride is rec_bytes)
+__device__ __forceinline__ uint32_t rec_len(const StepArgs &A, int npe) {
+    return (uint32_t)(kTile * npe * 2 + (A.n_comp - 6 * A.n_prony) * kTile * 4);
 }
 
 __device__ __forceinline__ uint32_t visc_tile_bytes(const StepArgs &A) { return (uint32_t)(A.n_prony * 6 * kTile * 4); }
 
-// element record + Prony state of tile t -> buf
-__device__ __forceinline__ void stage_elem(const StepArgs &A, int t, char *buf, uint64_t *bar) {
-    const uint32_t rb = (uint32_t)A.rec_bytes, vb = visc_tile_bytes(A);
+// element record + Prony state of tile t (element type npe) -> buf
+__device__ __forceinline__ void stage_elem(const StepArgs &A, int t, int npe, char *buf, uint64_t *bar) {
+    const uint32_t rb = rec_len(A, npe), vb = visc_tile_bytes(A);
     mbar_expect_tx(bar, rb + vb);
     bulk_g2s(buf, A.elem_rec + (int64_t)t * A.rec_bytes, rb, bar);
     if (vb) bulk_g2s(buf + rb, A.visc + (int64_t)t * (vb / 4), vb, bar);
@@ -535,9 +545,9 @@ __device__ __forceinline__ void stage_elem(const StepArgs &A, int t, char *buf, 
 // gather record and interior (u, theta, X0) of tile T
 template <int NPE>
 __device__ __forceinline__ void stage_nodes(const StepArgs &A, int t, const TileInfo &T, char *smem, uint64_t *bar) {
-    const uint32_t cb = (uint32_t)csr_rec_u16(NPE) * 2;
+    const uint32_t cb = (uint32_t)csr_rec_u16(NPE ? NPE : T.npe) * 2;
     mbar_expect_tx(bar, cb + 32u * T.n_int);
-    bulk_g2s(smem + A.sm_csr, A.csr + (int64_t)t * csr_rec_u16(NPE), cb, bar);
+    bulk_g2s(smem + A.sm_csr, A.csr + (int64_t)t * A.csr_stride, cb, bar);
     if (T.n_int > 0) {
         bulk_g2s(smem + A.sm_xu, A.xu + T.ib, 16u * T.n_int, bar);
         bulk_g2s(smem + A.sm_X, A.X0 + T.ib, 16u * T.n_int, bar);
@@ -547,10 +557,11 @@ __device__ __forceinline__ void stage_nodes(const StepArgs &A, int t, const Tile
 template <int NPE>
 __device__ void prefetch_tile(const StepArgs &A, int t) {
     const TileInfo T = tile_info(A, t);
-    prefetch_l2(A.elem_rec + (int64_t)t * A.rec_bytes, (uint32_t)A.rec_bytes);
+    const int npe = NPE ? NPE : T.npe;
+    prefetch_l2(A.elem_rec + (int64_t)t * A.rec_bytes, rec_len(A, npe));
     const uint32_t vb = visc_tile_bytes(A);
     if (vb) prefetch_l2(A.visc + (int64_t)t * (vb / 4), vb);
-    prefetch_l2(A.csr + (int64_t)t * csr_rec_u16(NPE), (uint32_t)csr_rec_u16(NPE) * 2);
+    prefetch_l2(A.csr + (int64_t)t * A.csr_stride, (uint32_t)csr_rec_u16(npe) * 2);
     if (T.n_int > 0) {
         const uint32_t nb = 16u * T.n_int;
         prefetch_l2(A.xu + T.ib, nb);
@@ -567,7 +578,6 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
     __shared__ ScenStep S;
     __shared__ int s_abort;
     const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_csr);
-    const uint16_t *s_row = s_code + kTile * NPE;
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
     float4 *s_X = reinterpret_cast<float4 *>(smem + A.sm_X);
     float4 *ns = reinterpret_cast<float4 *>(smem + A.sm_ns);
@@ -580,7 +590,7 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
         fence_barrier_init();
         s_abort = 0;
         if ((int)blockIdx.x < n_tiles) {
-            stage_elem(A, blockIdx.x, smem, &bar[0]);
+            stage_elem(A, blockIdx.x, tile_npe<NPE>(A, blockIdx.x), smem, &bar[0]);
             stage_nodes<NPE>(A, blockIdx.x, tile_info(A, blockIdx.x), smem, &bar[2]);
         }
     }
@@ -589,6 +599,8 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
     int i = 0, cur_scn = -1;
     for (int t = blockIdx.x; t < n_tiles; t += G, i++) {
         const TileInfo T = tile_info(A, t);
+        const int npe = NPE ? NPE : T.npe;
+        const uint16_t *s_row = s_code + kTile * npe;
         const int b = i & 1;
         char *buf = smem + b * A.sm_buf;
         float4 *slot = reinterpret_cast<float4 *>(buf);
@@ -613,14 +625,18 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
         // ---- 2. element inputs -> registers; the buffer then becomes the slot buffer
         const int ec = threadIdx.x;
         const bool active = ec < T.ne_t;
-        int cl[NPE];
+        int cl[NPE ? NPE : 8];
         ElemIn E;
-        if (active) load_elem<NPE>(A, buf, ec, cl, E);
+        if (active) {
+            if constexpr (NPE != 0) load_elem<NPE>(A, buf, ec, cl, E);
+            else if (npe == 8) load_elem<8>(A, buf, ec, cl, E);
+            else load_elem<4>(A, buf, ec, cl, E);
+        }
         __syncthreads();
         if (s_abort) return;
         if (threadIdx.x == 0) {
             fence_proxy_async();
-            if (t + G < n_tiles) stage_elem(A, t + G, smem + (b ^ 1) * A.sm_buf, &bar[b ^ 1]);
+            if (t + G < n_tiles) stage_elem(A, t + G, tile_npe<NPE>(A, t + G), smem + (b ^ 1) * A.sm_buf, &bar[b ^ 1]);
             if (ns_smem) {
                 mbar_expect_tx(&bar[3], 48u * T.n_int);
                 bulk_g2s(ns, A.lo + T.ib, 16u * T.n_int, &bar[3]);
@@ -632,7 +648,9 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
         // ---- 3. element pass
         if (active) {
             float *gv = A.visc + (int64_t)t * A.n_prony * 6 * kTile + ec;
-            element_step<NPE>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            if constexpr (NPE != 0) element_step<NPE>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else if (npe == 8) element_step<8>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else element_step<4>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
         }
         __syncthreads();
         // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum,
@@ -782,15 +800,142 @@ __global__ void __launch_bounds__(256) stats_partial_kernel(const StepArgs A, in
     if (threadIdx.x < 6) partials[(size_t)blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void stats_final_kernel(const double *partials, int nb, double *out) {
+// n_out = 6 (nodal diagnostics) or 8 (with the two energy sums of energy_partial_kernel)
+__global__ void stats_final_kernel(const double *partials, int nb, int n_out, double *out) {
     if (threadIdx.x != 0) return;
-    double ke = 0, heat = 0, tmax = -1e300, tmin = 1e300, umax = 0, dvol = 0;
+    double ke = 0, heat = 0, tmax = -1e300, tmin = 1e300, umax = 0, dvol = 0, wel = 0, whg = 0;
     for (int b = 0; b < nb; b++) {
         const double *p = partials + (size_t)b * 8;
         ke += p[0]; heat += p[1]; tmax = fmax(tmax, p[2]); tmin = fmin(tmin, p[3]); umax = fmax(umax, p[4]);
         dvol += p[5];
+        if (n_out > 6) {
+            wel += p[6];
+            whg += p[7];
+        }
     }
     out[0] = ke; out[1] = heat; out[2] = tmax; out[3] = tmin; out[4] = umax; out[5] = dvol;
+    if (n_out > 6) {
+        out[6] = wel;
+        out[7] = whg;
+    }
+}
+
+// Mechanical energy in FP64 (diagnostics): per element the stored energy of
+// the thermally split potential in the reference configuration, V0 lambda^3
+// Psi(F_el) (Eqs. 7-11, Table 5, fibre term as in the step), and the H8
+// hourglass energy 1/2 k_hg sum_al |q_al|^2 whose gradient is the hourglass
+// force of the step.  Block b sums tiles b, b + gridDim.x, ... in a fixed tree
+// and writes partials[8 b + 6] (stored energy) and [8 b + 7] (hourglass).
+template <int NPE>
+__global__ void __launch_bounds__(256) energy_partial_kernel(const StepArgs A, double *partials) {
+    double w_el = 0.0, w_hg = 0.0;
+    for (int t = blockIdx.x; t < A.n_tiles; t += gridDim.x) {
+        const TileInfo T = tile_info(A, t);
+        const int npe = NPE ? NPE : T.npe;
+        const int ec = threadIdx.x;
+        if (ec >= T.ne_t) continue;
+        const char *base = A.elem_rec + (int64_t)t * A.rec_bytes;
+        const uint16_t *cl = reinterpret_cast<const uint16_t *>(base) + ec * npe;
+        const float *cp = reinterpret_cast<const float *>(base + kTile * npe * 2) + ec;
+        double Ji[9];
+        int q = 0;
+        for (int k = 0; k < 9; k++) Ji[k] = cp[(q++) * kTile];
+        const double V = cp[(q++) * kTile];
+        double mu = A.mu, kap = A.kappa, k1 = A.k1, k2 = A.k2, al = A.alpha;
+        if (A.has_mat) {
+            mu = cp[q * kTile]; kap = cp[(q + 1) * kTile]; k1 = cp[(q + 2) * kTile]; k2 = cp[(q + 3) * kTile];
+            al = cp[(q + 5) * kTile];
+            q += 6;
+        }
+        double a0[3] = {A.a0x, A.a0y, A.a0z};
+        if (A.has_fib)
+            for (int j = 0; j < 3; j++) a0[j] = cp[(q + j) * kTile];
+        double u[8][3], X[8][3], the = 0.0;
+        for (int a = 0; a < npe; a++) {
+            const int l = cl[a];
+            const int64_t g = l < T.n_int ? (int64_t)T.ib + l : (int64_t)__ldg(A.tile_shared + T.sh_off + l - T.n_int);
+            const float4 h = A.xu[g], lo = A.lo[g], x = A.X0[g];
+            u[a][0] = (double)h.x + lo.x; u[a][1] = (double)h.y + lo.y; u[a][2] = (double)h.z + lo.z;
+            the += (double)h.w + lo.w;
+            X[a][0] = x.x; X[a][1] = x.y; X[a][2] = x.z;
+        }
+        the /= npe;
+        // shape-function derivatives dh_a/dX_j (H8: centroid, corner signs; T4: rows of J0^-1)
+        double dh[8][3];
+        for (int a = 0; a < npe; a++)
+            for (int j = 0; j < 3; j++) {
+                if (npe == 8) {
+                    dh[a][j] = 0.125 * (sgn(a, 0) * Ji[j] + sgn(a, 1) * Ji[3 + j] + sgn(a, 2) * Ji[6 + j]);
+                } else {
+                    dh[a][j] = a == 0 ? -(Ji[j] + Ji[3 + j] + Ji[6 + j]) : Ji[3 * (a - 1) + j];
+                }
+            }
+        double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+        for (int a = 0; a < npe; a++)
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) H[i][j] += u[a][i] * dh[a][j];
+        const double dl = (A.flags & TLED_EXPANSION) ? al * the : 0.0;
+        const double lam = 1.0 + dl;
+        const double trH = H[0][0] + H[1][1] + H[2][2];
+        double trH2 = 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) trH2 += H[i][j] * H[j][i];
+        const double detH = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) -
+                            H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+                            H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+        const double Jm1 = trH + 0.5 * (trH * trH - trH2) + detH;
+        // E_el = (E - (delta + delta^2/2) I) / lambda^2, E = (H + H^T + H^T H) / 2
+        double Ee[3][3];
+        const double d1 = dl + 0.5 * dl * dl, il2 = 1.0 / (lam * lam);
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) {
+                double e = 0.5 * (H[i][j] + H[j][i]);
+                for (int k = 0; k < 3; k++) e += 0.5 * H[k][i] * H[k][j];
+                Ee[i][j] = (e - (i == j ? d1 : 0.0)) * il2;
+            }
+        const double jel = (Jm1 - dl * (3.0 + dl * (3.0 + dl))) * il2 / lam;  // J_el - 1
+        const double Jm23m1 = expm1(-(2.0 / 3.0) * log1p(jel));
+        const double Jm23 = 1.0 + Jm23m1;
+        const double trE = Ee[0][0] + Ee[1][1] + Ee[2][2];
+        double aEa = 0.0;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++) aEa += a0[i] * Ee[i][j] * a0[j];
+        const double I1m3 = 3.0 * Jm23m1 + 2.0 * Jm23 * trE;  // I1bar - 3
+        const double x4 = Jm23m1 + 2.0 * Jm23 * aEa;          // I4bar - 1
+        const double psif = k2 > 0.0 ? k1 / (2.0 * k2) * expm1(k2 * x4 * x4) : 0.5 * k1 * x4 * x4;
+        w_el += V * lam * lam * lam * (0.5 * mu * I1m3 + 0.5 * kap * jel * jel + psif);
+        if (npe == 8) {
+            double jn2 = 0.0;
+            for (int k = 0; k < 9; k++) jn2 += Ji[k] * Ji[k];
+            const double khg = (double)A.khg * (kap + (4.0 / 3.0) * mu) * V * jn2 / 64.0;
+            for (int l = 0; l < 4; l++) {
+                double hu[3] = {0, 0, 0}, cX[3] = {0, 0, 0};
+                for (int b = 0; b < 8; b++) {
+                    const double h = hgv(b, l);
+                    for (int i = 0; i < 3; i++) {
+                        hu[i] += h * u[b][i];
+                        cX[i] += h * X[b][i];
+                    }
+                }
+                for (int i = 0; i < 3; i++) {
+                    const double qi = hu[i] - (H[i][0] * cX[0] + H[i][1] * cX[1] + H[i][2] * cX[2]);
+                    w_hg += 0.5 * khg * qi * qi;
+                }
+            }
+        }
+    }
+    __shared__ double sh[2][256];
+    sh[0][threadIdx.x] = w_el;
+    sh[1][threadIdx.x] = w_hg;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) partials[(size_t)blockIdx.x * 8 + 6 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
 // ---------------------------------------------------------------------------
@@ -799,6 +944,8 @@ __global__ void stats_final_kernel(const double *partials, int nb, double *out) 
 static int align128(int x) { return (x + 127) & ~127; }
 
 void tile_smem_layout(StepArgs &a, int npe) {
+    if (npe == 0) npe = 8;  // a mixed batch sizes everything for the larger element
+    a.csr_stride = csr_rec_u16(npe);
     a.n_comp = 10 + (a.has_mat ? 6 : 0) + (a.has_fib ? 3 : 0) + 6 * a.n_prony;
     a.sm_in = align128(kTile * npe * 2 + a.n_comp * kTile * 4);
     a.sm_buf = std::max(a.sm_in, kTile * npe * 16);
@@ -816,16 +963,22 @@ void tile_smem_layout(StepArgs &a, int npe) {
     a.sm_total = off;
 }
 
+template <class K>
+static cudaError_t set_smem(K kern, int bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
 cudaError_t tile_kernel_setup(const StepArgs &a, int npe) {
-    if (npe == 8)
-        return cudaFuncSetAttribute(tile_step_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.sm_total);
-    return cudaFuncSetAttribute(tile_step_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, a.sm_total);
+    if (npe == 8) return set_smem(tile_step_kernel<8>, a.sm_total);
+    if (npe == 4) return set_smem(tile_step_kernel<4>, a.sm_total);
+    return set_smem(tile_step_kernel<0>, a.sm_total);
 }
 
 int tile_grid(const StepArgs &a, int npe, int n_sm) {
     int per_sm = 0;
-    cudaError_t e = npe == 8 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<8>, kBlock, a.sm_total)
-                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<4>, kBlock, a.sm_total);
+    cudaError_t e =
+        npe == 8   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<8>, kBlock, a.sm_total)
+        : npe == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<4>, kBlock, a.sm_total)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<0>, kBlock, a.sm_total);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return std::max(1, std::min(a.n_tiles, per_sm * n_sm));
 }
@@ -835,8 +988,10 @@ cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cuda
     const size_t sm = (size_t)a.sm_total;
     if (npe == 8)
         tile_step_kernel<8><<<n_ctas, kBlock, sm, s>>>(a, k);
-    else
+    else if (npe == 4)
         tile_step_kernel<4><<<n_ctas, kBlock, sm, s>>>(a, k);
+    else
+        tile_step_kernel<0><<<n_ctas, kBlock, sm, s>>>(a, k);
     return cudaGetLastError();
 }
 
@@ -865,16 +1020,22 @@ cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w
     return cudaGetLastError();
 }
 
-cudaError_t launch_stats(const StepArgs &a, int64_t nn, double *partials, double *out, cudaStream_t s) {
+cudaError_t launch_stats(const StepArgs &a, int npe, int64_t nn, double *partials, double *out, cudaStream_t s) {
     stats_partial_kernel<<<kStatBlocks, 256, 0, s>>>(a, nn, partials);
-    stats_final_kernel<<<1, 32, 0, s>>>(partials, kStatBlocks, out);
+    if (npe == 8)
+        energy_partial_kernel<8><<<kStatBlocks, 256, 0, s>>>(a, partials);
+    else if (npe == 4)
+        energy_partial_kernel<4><<<kStatBlocks, 256, 0, s>>>(a, partials);
+    else
+        energy_partial_kernel<0><<<kStatBlocks, 256, 0, s>>>(a, partials);
+    stats_final_kernel<<<1, 32, 0, s>>>(partials, kStatBlocks, 8, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stats_blocks(const StepArgs &a, int64_t nn, int n_blocks, double *partials, double *out,
                                 cudaStream_t s) {
     stats_partial_kernel<<<n_blocks, 256, 0, s>>>(a, nn, partials);
-    stats_final_kernel<<<1, 32, 0, s>>>(partials, n_blocks, out);
+    stats_final_kernel<<<1, 32, 0, s>>>(partials, n_blocks, 6, out);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,11 @@ _SIGS = {
     "tled_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "tled_mlp_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p], C.c_int),
     "tled_mlp_sync": ([C.c_void_p], C.c_int),
+    "tled_mlp_set_input_scaling": ([C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+    "tled_mlp_train_step_rows": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p],
+                                 C.c_int),
+    "tled_mlp_ensemble": ([C.c_int, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_void_p,
+                           C.c_void_p, C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
 _ready = False
 
@@ -113,6 +118,25 @@ class MLP:
                                              C.c_void_p(g.data_ptr()), C.c_void_p(self.loss_buf.data_ptr())))
         return g, self.loss_buf
 
+    def set_input_scaling(self, shift=None, scale=None):
+        """Inputs enter the first layer as (x - shift) * scale (None: identity)."""
+        if shift is None:
+            self._check(lib().tled_mlp_set_input_scaling(self.h, None, None))
+            return
+        sh = np.ascontiguousarray(shift, np.float32)
+        sc = np.ascontiguousarray(scale, np.float32)
+        assert sh.size == self.dims[0] and sc.size == self.dims[0]
+        fp = C.POINTER(C.c_float)
+        self._check(lib().tled_mlp_set_input_scaling(self.h, sh.ctypes.data_as(fp), sc.ctypes.data_as(fp)))
+
+    def train_step_rows(self, x, t, rows, lr):
+        """Adam step on rows `rows` (device int32) of the device data set x, t."""
+        assert rows.dtype == self._torch.int32 and rows.is_cuda
+        self._check(lib().tled_mlp_train_step_rows(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                                   C.c_void_p(rows.data_ptr()), rows.numel(), float(lr),
+                                                   C.c_void_p(self.loss_buf.data_ptr())))
+        return self.loss_buf
+
     def train_step(self, x, t, lr):
         self._check(lib().tled_mlp_train_step(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()), x.shape[0],
                                               float(lr), C.c_void_p(self.loss_buf.data_ptr())))
@@ -120,3 +144,24 @@ class MLP:
 
     def sync(self):
         self._check(lib().tled_mlp_sync(self.h))
+
+
+def ensemble(ys, out_scale=None, out_shift=None, n_spread=0, tol=0.0, device=0, stream=None, want_std=True):
+    """Ensemble mean, std, spread and fallback flags of member outputs ys
+    (list of device float32 tensors [B][n_out]) in the library's kernel."""
+    import torch
+
+    B, n_out = ys[0].shape
+    dev = ys[0].device
+    stream = stream if stream is not None else torch.cuda.current_stream(dev)
+    mean = torch.empty(B, n_out, dtype=torch.float32, device=dev)
+    std = torch.empty(B, n_out, dtype=torch.float32, device=dev) if want_std else None
+    spread = torch.empty(B, dtype=torch.float32, device=dev)
+    fb = torch.empty(B, dtype=torch.uint8, device=dev)
+    ptrs = (C.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
+    vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    rc = lib().tled_mlp_ensemble(device, C.c_void_p(stream.cuda_stream), len(ys), ptrs, B, n_out, vp(out_scale),
+                                 vp(out_shift), int(n_spread), float(tol), vp(mean), vp(std), vp(spread), vp(fb))
+    if rc:
+        raise TledError(rc, "tled_mlp_ensemble: invalid arguments or CUDA error")
+    return mean, std, spread, fb

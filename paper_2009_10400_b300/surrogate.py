@@ -3,9 +3,11 @@ and damage at probe points after heating, trained on data from the batched
 coupled solver, with an ensemble spread test that sends uncertain cases back
 to the solver.
 
-The network runs on the library's tensor-core kernels (``mlp.MLP``); the data
-and the fallback come from ``tled.Batch``.  Normalisation, batching and the
-ensemble statistics are plain tensor bookkeeping around those calls.
+The network runs on the library's tensor-core kernels (``mlp.MLP``): the input
+map, the mini-batch row gather, training, inference and the ensemble
+statistics with the fallback decision are library kernels; the data and the
+fallback answers come from ``tled.Batch``.  The Python side only shuffles row
+indices, standardises the training targets once and moves arrays.
 """
 from __future__ import annotations
 
@@ -72,83 +74,97 @@ def he_init(dims, rng):
 
 
 class Surrogate:
-    """Ensemble of MLPs (inputs scaled to [-1, 1] over the sampling ranges,
-    outputs standardised per probe value)."""
+    """Ensemble of MLPs.  Inputs are mapped to [-1, 1] over the sampling ranges
+    inside the first layer's input kernel; outputs are learned standardised per
+    probe value and mapped back by the ensemble kernel."""
 
     def __init__(self, n_out, width=512, depth=6, members=5, max_batch=4096, device=0, n_in=12):
         self.dims = [n_in] + [width] * (depth - 1) + [n_out]
         self.members = [MLP(self.dims, max_batch=max_batch, device=device) for _ in range(members)]
         self.max_batch = max_batch
         self.device = device
-        self.in_lo, self.in_hi = W.surrogate_ranges()
+        lo, hi = W.surrogate_ranges()
+        for net in self.members:
+            net.set_input_scaling(0.5 * (lo + hi), 2.0 / (hi - lo))
         self.y_mean = self.y_std = None
+        self._ys = None
 
-    def _x(self, Q):
-        import torch
-        Xn = 2.0 * (np.atleast_2d(Q) - self.in_lo) / (self.in_hi - self.in_lo) - 1.0
-        return torch.tensor(Xn, dtype=torch.float32, device=f"cuda:{self.device}")
+    def _dev(self):
+        return f"cuda:{self.device}"
 
     def fit(self, Q, Y, epochs=50, batch=256, lr=1e-3, seed=0):
         """Adam on the mean squared error of the standardised outputs, every
-        member from its own initialisation and sample order; returns the mean
-        training loss per epoch of each member."""
+        member from its own initialisation and sample order (one seeded
+        permutation of the rows per epoch, consumed in contiguous mini-batches
+        of the device-resident data set); returns the mean training loss per
+        epoch of each member."""
         import torch
         Y = np.asarray(Y, np.float64)
         self.y_mean = Y.mean(0)
         self.y_std = np.maximum(Y.std(0), 1e-3 * max(Y.std(), 1e-12))
-        dev = f"cuda:{self.device}"
-        Xd = self._x(Q)
+        dev = self._dev()
+        self._scale = torch.tensor(self.y_std, dtype=torch.float32, device=dev)
+        self._shift = torch.tensor(self.y_mean, dtype=torch.float32, device=dev)
+        Xd = torch.tensor(np.atleast_2d(Q), dtype=torch.float32, device=dev)
         Yd = torch.tensor((Y - self.y_mean) / self.y_std, dtype=torch.float32, device=dev)
         n = len(Q) - len(Q) % batch
         hist = []
         for mi, net in enumerate(self.members):
             rng = np.random.default_rng(seed + 1000 * mi)
             net.set_params(he_init(self.dims, rng))
-            g = torch.Generator(device=dev)
-            g.manual_seed(seed + mi)
             losses = []
             for _ in range(epochs):
-                perm = torch.randperm(len(Q), device=dev, generator=g)[:n]
-                xs, ys = Xd[perm], Yd[perm]  # one shuffle per epoch, then contiguous batches
+                perm = torch.tensor(rng.permutation(len(Q))[:n].astype(np.int32), device=dev)
                 acc = torch.zeros(1, dtype=torch.float32, device=dev)
                 for b0 in range(0, n, batch):
-                    acc += net.train_step(xs[b0:b0 + batch], ys[b0:b0 + batch], lr)
+                    acc += net.train_step_rows(Xd, Yd, perm[b0:b0 + batch], lr)
                 losses.append(acc)
             net.sync()
             hist.append([float(v) / (n // batch) for v in torch.stack(losses).cpu()])
         return hist
 
-    def predict(self, Q):
-        """Ensemble mean and standard deviation of the outputs, physical units."""
+    def predict_device(self, Xd, n_spread, tol, want_std=True):
+        """Ensemble answer for raw scenario rows Xd (device float32 [m][12]):
+        mean and std [m][n_out] in physical units, spread [m] (max std over the
+        first n_spread outputs) and fallback flags [m], all on the device."""
         import torch
-        Xd = self._x(Q)
-        m = len(Q)
-        B = self.max_batch
+        from .mlp import ensemble
+        m = Xd.shape[0]
         pad = (-m) % 128
         if pad:
-            Xd = torch.cat([Xd, torch.zeros(pad, Xd.shape[1], device=Xd.device)])
-        outs = []
-        for net in self.members:
-            ys = [net.forward(Xd[b0:b0 + B]) for b0 in range(0, len(Xd), B)]
-            outs.append(torch.cat(ys)[:m])
-        S = torch.stack(outs)
-        scale = torch.tensor(self.y_std, dtype=torch.float32, device=S.device)
-        shift = torch.tensor(self.y_mean, dtype=torch.float32, device=S.device)
-        mean = (S.mean(0) * scale + shift).double().cpu().numpy()
-        std = (S.std(0, unbiased=False) * scale).double().cpu().numpy()
-        return mean, std
+            Xd = torch.cat([Xd, torch.zeros(pad, Xd.shape[1], dtype=Xd.dtype, device=Xd.device)])
+        mp = m + pad
+        if self._ys is None or self._ys[0].shape[0] < mp:
+            self._ys = [torch.empty(mp, self.dims[-1], dtype=torch.float32, device=Xd.device)
+                        for _ in self.members]
+        ys = [y[:mp] for y in self._ys]
+        for net, y in zip(self.members, ys):
+            for b0 in range(0, mp, self.max_batch):
+                net.forward(Xd[b0:b0 + self.max_batch], out=y[b0:b0 + self.max_batch])
+        mean, std, spread, fb = ensemble(ys, self._scale, self._shift, n_spread, tol, device=self.device,
+                                         want_std=want_std)
+        return mean[:m], (std[:m] if std is not None else None), spread[:m], fb[:m]
+
+    def predict(self, Q, n_spread=0, tol=0.0):
+        """Ensemble mean and standard deviation of the outputs, physical units
+        (host float64 arrays)."""
+        import torch
+        Xd = torch.tensor(np.atleast_2d(Q), dtype=torch.float32, device=self._dev())
+        mean, std, _, _ = self.predict_device(Xd, n_spread, tol)
+        return mean.double().cpu().numpy(), std.double().cpu().numpy()
 
     def solve(self, Q, n_probe_T, tol=1.0, n=16, dt=0.01):
         """Surrogate answers; cases whose ensemble spread of temperature (max over
         probes) exceeds tol kelvin are re-run by the batched solver.  Returns
         (outputs, fallback mask, timings)."""
+        import torch
         t0 = time.perf_counter()
-        mean, std = self.predict(Q)
+        Xd = torch.tensor(np.atleast_2d(Q), dtype=torch.float32, device=self._dev())
+        mean, _, spread, fbd = self.predict_device(Xd, n_probe_T, tol, want_std=False)
+        out = mean.double().cpu().numpy()
+        fb = fbd.cpu().numpy().astype(bool)
         t1 = time.perf_counter()
-        spread = std[:, :n_probe_T].max(1)
-        fb = spread > tol
-        out = mean.copy()
-        info = dict(surrogate_seconds=t1 - t0, fallback=int(fb.sum()))
+        info = dict(surrogate_seconds=t1 - t0, fallback=int(fb.sum()), spread=spread.cpu().numpy())
         if fb.any():
             T, D, tm = solve_scenarios(np.atleast_2d(Q)[fb], n=n, dt=dt)
             out[fb] = np.concatenate([T, D], 1)

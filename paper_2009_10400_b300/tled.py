@@ -48,7 +48,8 @@ class Params(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("t", C.c_double), ("dt", C.c_double), ("T_max", C.c_double),
                 ("T_min", C.c_double), ("u_max", C.c_double), ("damage_volume", C.c_double),
-                ("heat_content", C.c_double), ("kinetic_energy", C.c_double), ("status", C.c_uint32),
+                ("heat_content", C.c_double), ("kinetic_energy", C.c_double), ("strain_energy", C.c_double),
+                ("hourglass_energy", C.c_double), ("status", C.c_uint32),
                 ("pad", C.c_int32)]
 
     def as_dict(self):

@@ -369,3 +369,35 @@ def scenario_problem(q, n=16, side=0.05, dt=0.01, gamma=5.0, sigma=5e-3):
 
 def centroids(prob):
     return prob.X[prob.conn].mean(1)
+
+
+def planning_scenarios(n=256, seed=4, side=0.05, dt=0.01, gamma=5.0, ne_range=(2000, 60000),
+                       duration=(60.0, 600.0)):
+    """Batched treatment planning: n scenarios, each a hexahedral (jittered n^3
+    H8) or tetrahedral (Kuhn-split jittered grid) mesh of the 5 cm cube with a
+    log-uniform element count, one Gaussian source of U(1, 10) MW/m^3 in the
+    inner half, heating time U(60, 600) s at a fixed dt, shear modulus and
+    conductivity x U(0.8, 1.2), bottom fixed.  Returns a list of Problems
+    (n_steps = heating time / dt)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ne = float(np.exp(rng.uniform(np.log(ne_range[0]), np.log(ne_range[1]))))
+        hexa = rng.uniform() < 0.5
+        if hexa:
+            m = max(2, int(round(ne ** (1.0 / 3.0))))
+            X, conn = hex_grid((m, m, m), (side, side, side))
+        else:
+            m = max(2, int(round((ne / 6.0) ** (1.0 / 3.0))))
+            X, conn = kuhn_tets((m, m, m), (side, side, side))
+        interior = np.all((X > 1e-9) & (X < side - 1e-9), axis=1)
+        X[interior] += rng.uniform(-0.1, 0.1, (interior.sum(), 3)) * (side / m)
+        if not hexa:
+            conn = _orient_tets(X, conn)
+        mat = _material(conn.shape[0], mu=3e3 * rng.uniform(0.8, 1.2), kc=0.5 * rng.uniform(0.8, 1.2))
+        mask = np.where(np.isclose(X[:, 2], 0.0), MASK_U, 0).astype(np.uint8)
+        T = rng.uniform(*duration)
+        src = [source(rng.uniform(side / 4, 3 * side / 4, 3), rng.uniform(1e6, 1e7))]
+        out.append(Problem(name=f"plan_{'h8' if hexa else 't4'}_{i}", npe=8 if hexa else 4, X=X, conn=conn, **mat,
+                           sources=src, mask=mask, dt=dt, gamma=gamma, n_steps=int(round(T / dt))))
+    return out

@@ -61,6 +61,35 @@ def test_batch_h8_each_scenario_matches_oracle():
         assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E and c["d_abs"] <= TOL_DAMAGE, (i, c)
 
 
+
+def test_batch_mixed_h8_t4_matches_oracle():
+    """Hexahedral and tetrahedral scenarios in one batch (one launch per step,
+    the element type chosen per tile), interleaved in the add order, with
+    different step counts and a planning-style mass-scaled fixed step; each
+    matches its own oracle run."""
+    tled = _tled()
+    from paper_2009_10400_b300 import surrogate
+    scen = [W.cube_h8(n=5, seed=50), W.cube_t4(n=4, seed=51), W.cube_h8(n=4, jitter=0.1, seed=52),
+            W.cube_t4(n=5, seed=53)]
+    n_steps = [160, 240, 90, 200]
+    for p in scen[2:]:  # the planning workloads' fixed dt with mass scaling and damping
+        p.dt, p.gamma = 0.01, 5.0
+        surrogate.mass_scaled(p)
+    b = tled.Batch()
+    for p, n in zip(scen, n_steps):
+        b.add(p, n, dt=p.dt)
+    b.init()
+    assert b.plan_info()["npe"] == 0
+    assert b.run() == max(n_steps)
+    b.sync()
+    u, T, d = b.displacement(), b.temperature(), b.damage()
+    for i, (p, n) in enumerate(zip(scen, n_steps)):
+        info = b.scenario(i)
+        sl = slice(info["node_off"], info["node_off"] + info["nodes"])
+        ref = _oracle_final(p, n, b.scenario_dt(i))
+        c = compare(u[sl], T[sl], d[sl], ref.u, ref.T, ref.Omega)
+        assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E and c["d_abs"] <= TOL_DAMAGE, (i, c)
+
 def test_batch_t4_matches_single_runs():
     tled = _tled()
     probs = [W.cube_t4(n=4, seed=40), W.cube_t4(n=5, seed=41)]

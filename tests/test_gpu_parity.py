@@ -169,6 +169,54 @@ def test_stats_match_state():
     np.testing.assert_allclose(st["heat_content"], (m.Cth * (T - 37.0)).sum(), rtol=1e-6)
 
 
+
+def test_energy_reduction_matches_oracle():
+    """The FP64 stored and hourglass energies of tled_get_stats against the
+    oracle's element energies on random mid-run states with strains of order
+    0.1-0.3 (H8 with hourglass energy, T4 with per-element fibres)."""
+    tled = _tled()
+    for prob in (W.cube_h8(n=6, jitter=0.1, seed=8), W.cube_t4(n=5, seed=9)):
+        st = W.random_state(prob, seed=3, u_scale=2e-3)
+        s = tled.Solver.from_problem(prob)
+        s.set_state(st["u"], st["v"], st["T"], st["Omega"], st["visc"])
+        r = s.stats()
+        m = oracle.OracleModel(prob)
+        ref = sum(m.energy(e, st["u"], st["T"]) for e in range(prob.ne))
+        got = r["strain_energy"] + r["hourglass_energy"]
+        assert abs(got - ref) <= 1e-5 * abs(ref), (prob.name, got, ref)
+        if prob.npe == 4:
+            assert r["hourglass_energy"] == 0.0
+        else:
+            assert 0.0 < r["hourglass_energy"] < r["strain_energy"]
+        v = st["v"]
+        ke = 0.5 * np.sum(m.M[:, None] * v * v)
+        np.testing.assert_allclose(r["kinetic_energy"], ke, rtol=1e-6)
+
+
+def test_energy_balance_on_gpu():
+    """P9 on the device: the mechanical energy (mean kinetic energy of the two
+    half steps around u_n plus the stored and hourglass energies, all from the
+    FP64 reduction) only oscillates, within 1 % over 1500 steps, and follows
+    the oracle's energy history."""
+    from helpers import p9_energy_history, p9_initial, p9_problem
+    tled = _tled()
+    p = p9_problem()
+    u0 = p9_initial(p)
+    s = tled.Solver.from_problem(p)
+    z = np.zeros_like(u0)
+    s.set_state(u0, z, np.full(p.nn, p.T0), np.zeros(p.nn))
+    E = []
+    for _ in range(30):
+        a = s.stats()
+        s.step(1)
+        b = s.stats()
+        E.append(0.5 * (a["kinetic_energy"] + b["kinetic_energy"]) + a["strain_energy"] + a["hourglass_energy"])
+        s.step(49)
+    E = np.array(E)
+    assert np.ptp(E) / E[0] < 1e-2
+    ref = p9_energy_history(oracle.OracleModel(p, dt=s.get_dt()[0]), p, u0, 30, 50)
+    np.testing.assert_allclose(E, ref, rtol=1e-4)
+
 def test_inversion_is_reported():
     """A huge prescribed compression of a single element inverts it; the device
     flags the element and tled_sync reports E_INVERTED (no device trap)."""

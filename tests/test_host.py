@@ -30,7 +30,7 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n), n
     from paper_2009_10400_b300 import mlp
     assert set(names) <= set(tled.exported_symbols()) | set(mlp.exported_symbols()) | {"tled_version"}
-    assert L.tled_version() == 1
+    assert L.tled_version() == 2
 
 
 def _planner(prob, **kw):
@@ -136,8 +136,9 @@ def test_call_order_errors():
 
 
 def test_batch_planning_keeps_scenarios_apart():
-    """Host-only batch: tiles never span scenarios, so the tile count is the sum
-    of the per-scenario counts, and shared nodes never join two scenarios."""
+    """Host-only batch: tiles never span scenarios (nor element types), so the
+    tile count is the sum of the per-scenario counts, and shared nodes never join
+    two scenarios."""
     import ctypes as C
     probs = [W.cube_h8(n=6), W.cube_h8(n=9, seed=2), W.cube_h8(n=5, seed=3)]
     h = C.c_void_p()
@@ -157,7 +158,15 @@ def test_batch_planning_keeps_scenarios_apart():
     sinfo = (C.c_int64 * 8)()
     assert tled.lib().tled_scenario_info(h, 1, sinfo) == 0
     assert (sinfo[0], sinfo[1], sinfo[2], sinfo[3], sinfo[4]) == (probs[0].nn, probs[1].nn, probs[0].ne, probs[1].ne, 200)
-    # mixing element types is refused
-    t4 = _planner(W.cube_t4(n=2))
-    assert tled.lib().tled_batch_add(h, t4.h, 10, None) == tled.E_ARG
+    assert info[5] == 8
+    # a tetrahedral scenario joins the hexahedral ones: tiles hold one element type
+    # each, so the count is still the per-scenario sum; the plan reports type 0 (mixed)
+    t4p = W.cube_t4(n=4)
+    t4 = _planner(t4p)
+    n_t4 = t4.plan_info()["n_tiles"]
+    assert tled.lib().tled_batch_add(h, t4.h, 10, None) == 0, tled.lib().tled_last_error(h)
+    assert tled.lib().tled_plan_info(h, info) == 0
+    assert info[6] == 4 and info[5] == 0
+    assert info[0] == sum(s["n_tiles"] for s in singles) + n_t4
+    assert info[1] + info[2] == sum(p.nn for p in probs) + t4p.nn
     tled.lib().tled_destroy(h)

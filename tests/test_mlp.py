@@ -3,7 +3,7 @@ bfloat16 conversion (CPU), and the tensor-core kernels against the oracle (GPU).
 import numpy as np
 import pytest
 
-from oracle.mlp import MLPOracle, bf16_round, gelu, gelu_grad
+from oracle.mlp import MLPOracle, bf16_round, ensemble_stats, gelu, gelu_grad
 
 
 def test_oracle_gradient_matches_finite_differences():
@@ -45,6 +45,20 @@ def test_oracle_adam_first_step_is_sign_times_lr():
     p1, _, _ = MLPOracle.adam(p, g, np.zeros(5), np.zeros(5), 1, lr=1e-3)
     np.testing.assert_allclose(p1, -1e-3 * np.sign(g), rtol=1e-4)
 
+
+
+def test_ensemble_stats_closed_forms():
+    """Two members a, b: mean (a + b)/2 and std |a - b|/2; identical members:
+    std 0 and no fallback; the affine map applies before the statistics."""
+    a = np.array([[1.0, 5.0, -2.0]])
+    b = np.array([[3.0, 5.0, 2.0]])
+    mean, std, spread, fb = ensemble_stats([a, b], n_spread=2, tol=0.5)
+    np.testing.assert_array_equal(mean, [[2.0, 5.0, 0.0]])
+    np.testing.assert_array_equal(std, [[1.0, 0.0, 2.0]])
+    assert spread[0] == 1.0 and fb[0]  # the third output is outside n_spread
+    mean, std, spread, fb = ensemble_stats([a, a, a], scale=[2.0, 1.0, 1.0], shift=[1.0, 0.0, 0.0], n_spread=3, tol=0.0)
+    np.testing.assert_array_equal(mean, [[3.0, 5.0, -2.0]])
+    assert np.all(std == 0) and spread[0] == 0 and not fb[0]
 
 # ---------------------------------------------------------------------------
 # GPU: tensor-core kernels against the oracle with the same bf16 rounding
@@ -116,3 +130,62 @@ def test_mlp_adam_step_and_training_reduces_loss():
         losses.append(net.train_step(xd, td, 1e-3).item())
     net.sync()
     assert losses[-1] < 0.2 * losses[0], (losses[0], losses[-1])
+
+
+
+@pytest.mark.gpu
+def test_ensemble_kernel_matches_oracle():
+    import torch
+
+    from paper_2009_10400_b300.mlp import ensemble
+    rng = np.random.default_rng(7)
+    B, N, E = 300, 1000, 5
+    ys = [rng.normal(size=(B, N)).astype(np.float32) for _ in range(E)]
+    scale = rng.uniform(0.5, 3.0, N).astype(np.float32)
+    shift = rng.uniform(-40, 40, N).astype(np.float32)
+    d = [torch.tensor(y, device="cuda") for y in ys]
+    mean, std, spread, fb = ensemble(d, torch.tensor(scale, device="cuda"), torch.tensor(shift, device="cuda"),
+                                     n_spread=700, tol=4.0)
+    torch.cuda.synchronize()
+    m_ref, s_ref, sp_ref, fb_ref = ensemble_stats(ys, scale, shift, n_spread=700, tol=4.0)
+    np.testing.assert_allclose(mean.cpu().numpy(), m_ref, rtol=1e-5, atol=1e-5 * np.abs(shift).max())
+    np.testing.assert_allclose(std.cpu().numpy(), s_ref, rtol=1e-4, atol=1e-5)
+    np.testing.assert_allclose(spread.cpu().numpy(), sp_ref, rtol=1e-4)
+    clear = np.abs(sp_ref - 4.0) > 1e-3 * 4.0  # decisions away from the threshold are exact
+    assert clear.sum() > B // 2
+    np.testing.assert_array_equal(fb.cpu().numpy().astype(bool)[clear], fb_ref[clear])
+
+
+@pytest.mark.gpu
+def test_input_scaling_and_row_gather():
+    """The input map inside the first kernel equals scaling the inputs on the
+    host (same FP32 arithmetic: bitwise), and an Adam step on gathered rows of
+    a device data set equals a step on the copied rows (bitwise)."""
+    import torch
+
+    from paper_2009_10400_b300.mlp import MLP
+    rng = np.random.default_rng(8)
+    dims = [12, 128, 256]
+    p = MLPOracle(dims).init_params(rng).astype(np.float32)
+    shift = rng.uniform(-1, 1, 12).astype(np.float32)
+    scale = rng.uniform(0.1, 2.0, 12).astype(np.float32)
+    x = rng.uniform(-3, 3, (512, 12)).astype(np.float32)
+    t = rng.normal(size=(512, 256)).astype(np.float32)
+    a, b = MLP(dims, max_batch=256), MLP(dims, max_batch=256)
+    a.set_params(p)
+    b.set_params(p)
+    a.set_input_scaling(shift, scale)
+    xd, td = torch.tensor(x, device="cuda"), torch.tensor(t, device="cuda")
+    xs = torch.tensor((x - shift) * scale, device="cuda")
+    ya = a.forward(xd[:256]).cpu().numpy()
+    yb = b.forward(xs[:256]).cpu().numpy()
+    np.testing.assert_array_equal(ya, yb)
+    rows = rng.permutation(512)[:256].astype(np.int32)
+    rd = torch.tensor(rows, device="cuda")
+    for _ in range(3):
+        la = a.train_step_rows(xd, td, rd, 1e-3).item()
+        lb = b.train_step(xs[rd.long()].contiguous(), td[rd.long()].contiguous(), 1e-3).item()
+        assert la == lb
+    a.sync()
+    b.sync()
+    np.testing.assert_array_equal(a.get_params(), b.get_params())

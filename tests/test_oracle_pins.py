@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from helpers import p9_energy_history, p9_initial, p9_problem
 from paper_2009_10400_b300 import workloads as W
 
 
@@ -389,6 +390,34 @@ def test_p8_rigid_translation_with_damping():
     expect = 0.001 + p.dt * v0 * r * (1 - r ** 200) / (1 - r)
     np.testing.assert_allclose(s.u, np.broadcast_to(expect, s.u.shape), rtol=1e-10)
 
+
+
+# ---------------------------------------------------------------------------
+# P9: energy balance of the central-difference scheme
+# ---------------------------------------------------------------------------
+def test_p9_energy_balance_is_second_order():
+    """With no damping, no Prony terms, no thermal load and a fixed face, the
+    mechanical energy of the explicit scheme only oscillates, and the
+    oscillation shrinks like dt^2 (central difference is second order and
+    symplectic); it does not drift.  Stored energy and kinetic energy are
+    independent code paths (element potential vs nodal masses), so a wrong
+    force (sign, factor, missing term) or a wrong mass breaks this balance."""
+    p = p9_problem()
+    u0 = p9_initial(p)
+    m1 = oracle.OracleModel(p)
+    dt = m1.dt
+    E1 = p9_energy_history(m1, p, u0, 30, 50)
+    m2 = oracle.OracleModel(p, dt=dt / 2)
+    E2 = p9_energy_history(m2, p, u0, 30, 100)
+    f1 = np.ptp(E1) / E1[0]
+    f2 = np.ptp(E2) / E2[0]
+    assert f1 < 1e-2, f1
+    assert 3.0 < f1 / f2 < 5.0, (f1, f2)
+    # the energy did move between kinetic and stored (the test is not vacuous)
+    v = m1.state_from(u0, np.zeros_like(u0), np.full(p.nn, p.T0), np.zeros(p.nn), None)
+    m1.step(v, 200)
+    k = 0.5 * np.sum(m1.M[:, None] * ((v.u - v.u_prev) / m1.dt) ** 2)
+    assert k > 0.05 * E1[0], (k, E1[0])
 
 # ---------------------------------------------------------------------------
 # P10: Arrhenius integral
