@@ -60,17 +60,53 @@ def probe_lattice(prob, n):
 
 
 def algorithmic_bytes(prob, n_prony):
-    """Bytes the method must move per step in this library's layout: every
-    element constant once, the Prony state read and written, and every nodal
-    state array read and written once (see the design notes)."""
+    """Layout-independent floor of the bytes one coupled step must move: every
+    element constant and state array touched once -- connectivity (int32),
+    shape-function derivatives dh/dX (3 floats per corner), V0, the
+    per-element material (mu, kappa, k1, k2, k, alpha) and fibre when they
+    vary, the Prony state read and written (6 floats per term each way) -- and
+    per node the gather of u and theta (16 B), X0 (12), u hi/lo read and write
+    (48), v read and write (24), theta hi/lo read and write (16), Omega read
+    and write (8) and m, V, mask (12): 136 B.  (H8 with per-element material
+    and one Prony term: 204 B per element + 136 B per node.)"""
     npe = prob.npe
-    elem = 2 * npe + 9 * 4 + 4 + 2 * 4 * 6 * n_prony  # local conn, J0^-1, V0, Prony R+W
+    elem = npe * (4 + 12) + 4 + 2 * 4 * 6 * n_prony
     if prob.per_element:
-        elem += 6 * 4  # mu, kappa, k1, k2, k, alpha
+        if not all(np.allclose(getattr(prob, f), getattr(prob, f)[0]) for f in ("mu", "kappa", "k1", "k2", "kc",
+                                                                                  "alpha")):
+            elem += 6 * 4
         if not np.allclose(prob.a0, prob.a0[0]):
-            elem += 3 * 4  # fibres
-    node = 5 * 16 + 3 * 16  # read u_hi/theta, X0/V, lo, v/Omega, m/C/mask; write hi, lo, v/Omega
-    return elem * prob.ne + node * prob.nn
+            elem += 3 * 4
+    return elem * prob.ne + 136 * prob.nn
+
+
+def layout_bytes(prob, n_prony):
+    """Bytes the same step moves in this library's layout (uint16 local
+    connectivity, J0^-1 instead of dh/dX, float4 nodal records): element record
+    2 npe + 40 B (+24 material, +12 fibre) and the Prony state, 128 B per node."""
+    npe = prob.npe
+    elem = 2 * npe + 9 * 4 + 4 + 2 * 4 * 6 * n_prony
+    if prob.per_element:
+        elem += 6 * 4
+        if not np.allclose(prob.a0, prob.a0[0]):
+            elem += 3 * 4
+    return elem * prob.ne + 128 * prob.nn
+
+
+def kernel_traffic(workload):
+    """DRAM bytes (read + write) per step of the tile and shared-node kernels
+    from the committed ncu capture, or None when there is none for this
+    workload or the kernel source has changed since it was taken."""
+    import hashlib
+
+    try:
+        entry = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[workload]
+        src = open(os.path.join(ROOT, "paper_2009_10400_b300", "csrc", "tled_kernels.cu"), "rb").read()
+        if hashlib.sha1(src).hexdigest() != entry["kernel_source_sha1"]:
+            return None
+        return float(entry["dram_bytes_per_step"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 class ClockSampler:
@@ -193,6 +229,35 @@ def run_reference(args):
                                        "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+def small_configs(device, stream, steps=2000):
+    """The L2-resident workloads (8^3 H8 cube; ~120k-tet ellipsoid): steps/s,
+    element-steps/s and the floor bytes per second they stream from L2 (no HBM
+    fraction is claimed for them)."""
+    import torch
+
+    from paper_2009_10400_b300 import tled
+    from paper_2009_10400_b300 import workloads as W
+
+    out = []
+    for prob in (W.cube_h8(n=8), W.ellipsoid_t4()):
+        s = tled.Solver.from_problem(prob, device=device, stream=stream)
+        s.step(64)
+        s.sync()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        s.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sec = ev0.elapsed_time(ev1) * 1e-3
+        s.sync()
+        s.close()
+        out.append({"workload": prob.name, "elements": prob.ne, "nodes": prob.nn, "steps": steps,
+                    "steps_per_s": steps / sec, "element_steps_per_s": prob.ne * steps / sec,
+                    "floor_bytes_per_step": algorithmic_bytes(prob, len(prob.prony_g)),
+                    "l2_gbs": algorithmic_bytes(prob, len(prob.prony_g)) * steps / sec / 1e9})
+    return out
 
 
 def planning_bench(args, device, stream):
@@ -412,13 +477,7 @@ def run_gpu(args):
     alg = algorithmic_bytes(prob, n_prony)
     hbm, src = peaks()
     achieved = alg / (per_step_kernel_ms * 1e-3) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            traffic = json.load(open(tr_path)).get(prob.name)
-        except Exception:
-            traffic = None
+    traffic = kernel_traffic(prob.name)
 
     # ---- end to end through the C ABI with host buffers, every step: the step's
     #      source settings from pinned host memory, one step, and the step's result
@@ -442,6 +501,7 @@ def run_gpu(args):
     s.close()
     del s
     torch.cuda.empty_cache()
+    smalls = None if args.no_planning else small_configs(local, stream)
     plan = None
     if not args.no_planning and prob.name.startswith("block_h8"):
         plan = planning_bench(args, local, stream)
@@ -462,12 +522,14 @@ def run_gpu(args):
             "config": {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn,
                        "element": "H8" if prob.npe == 8 else "T4", "dt_s": dt,
                        "tiles": info["n_tiles"], "shared_nodes": info["n_shared"],
-                       "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (alg / 1e6),
+                       "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (layout_bytes(prob, n_prony) / 1e6),
                        "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "tile_step_kernel + shared_step_kernel (one step)",
                          "algorithmic_bytes_per_step": alg,
+                         "algorithmic_bytes_per_element_step": alg / prob.ne,
+                         "layout_bytes_per_step": layout_bytes(prob, n_prony),
                          "kernel_ms_per_step": per_step_kernel_ms,
                          "tile_kernel_ms": k_tile / args.roofline_steps,
                          "shared_kernel_ms": k_sh / args.roofline_steps, "peak_source": src},
@@ -479,6 +541,7 @@ def run_gpu(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "planning": plan,
+            "small_configs": smalls,
             "final": {"T_max": st["T_max"], "u_max": st["u_max"], "status": st["status"]},
         }
         print(json.dumps(out))

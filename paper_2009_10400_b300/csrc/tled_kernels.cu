@@ -709,19 +709,29 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
     const int64_t s = s0 + threadIdx.x;
     if (s >= n_sh) return;
     const int64_t g = A.n_interior + s;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    // every load of the node issued up front: its state, then its first four partial
+    // sums (a node of a tile-boundary face has 2, of an edge 4); more follow in order
+    const float4 xu = A.xu[g], X = __ldg(&A.X0[g]), lo = A.lo[g], vo = A.vel[g], nc = __ldg(&A.nodec[g]);
     const int r0 = __ldg(A.sh_rowptr + s), r1 = __ldg(A.sh_rowptr + s + 1);
-    for (int r = r0; r < r1; r++) {  // the node's partial sums, in tile order
-        const float4 c = A.partials[r];
-        acc.x += c.x; acc.y += c.y; acc.z += c.z; acc.w += c.w;
-    }
     const int scn = __ldg(A.shared_scn + s);
+    float4 c[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) c[j] = r0 + j < r1 ? A.partials[r0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {  // the node's partial sums, in tile order (adding 0 changes nothing)
+        acc.x += c[j].x; acc.y += c[j].y; acc.z += c[j].z; acc.w += c[j].w;
+    }
+    for (int r = r0 + 4; r < r1; r++) {
+        const float4 d = A.partials[r];
+        acc.x += d.x; acc.y += d.y; acc.z += d.z; acc.w += d.w;
+    }
     if (scn == scn0) {
-        node_update(A, S, g, acc, A.xu[g], __ldg(&A.X0[g]), A.lo[g], A.vel[g], __ldg(&A.nodec[g]));
+        node_update(A, S, g, acc, xu, X, lo, vo, nc);
     } else {  // block spans a scenario boundary: this thread's own step values
         ScenStep L;
         prepare_scen(A, scn, k, L, 0, 1);
-        node_update(A, L, g, acc, A.xu[g], __ldg(&A.X0[g]), A.lo[g], A.vel[g], __ldg(&A.nodec[g]));
+        node_update(A, L, g, acc, xu, X, lo, vo, nc);
     }
 }
 
