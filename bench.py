@@ -393,13 +393,19 @@ def run_surrogate(args):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / reps
 
-    # ---- test scenarios: surrogate alone, then with the solver fallback
+    # ---- held-out scenarios: the first half calibrates the spread threshold against
+    #      the solver's answers, the second half is answered (surrogate or fallback)
+    n_cal = n_test // 2
+    cal = slice(n_train, n_train + n_cal)
+    ev = slice(n_train + n_cal, n_train + n_test)
     mean_te, std_te = sur.predict(Q[te])
-    out, fb, info = sur.solve(Q[te], P, tol=args.sur_tol, n=n, dt=0.01)
     err_sur = np.abs(mean_te[:, :P] - T[te]).max(1)
-    err_out = np.abs(out[:, :P] - T[te]).max(1)
+    spread_te = std_te[:, :P].max(1)
+    raw_acc = spread_te <= args.sur_tol
+    tau, cal_acc = sur.calibrate(Q[cal], Y[cal], P, tol=args.sur_tol, coverage=args.sur_coverage)
+    out, fb, info = sur.solve(Q[ev], P, tol=args.sur_tol, n=n, dt=0.01)
+    err_out = np.abs(out[:, :P] - T[ev]).max(1)
     acc = ~fb
-    solver_rate = (n_train + n_test) / tm["seconds"]
     line = {
         "metric": "surrogate scenario-solves/s", "value": Bq / inf_s, "unit": "scenario-solves/s",
         "n_gpus": 1, "steps": reps, "warmup": 3, "ms_per_step": 1e3 * inf_s, "higher_is_better": True,
@@ -419,12 +425,19 @@ def run_surrogate(args):
                         / fit_s / 1e12,
         "final_train_loss": [h[-1] for h in hist],
         "test_mae_K": float(np.abs(mean_te[:, :P] - T[te]).mean()),
+        "test_median_max_err_K": float(np.median(err_sur)),
         "test_max_err_K_surrogate_only": float(err_sur.max()),
-        "fallback_fraction": float(fb.mean()),
-        "accepted_max_err_K": float(err_sur[acc].max()) if acc.any() else None,
-        "answered_max_err_K": float(err_out.max()),
-        "solve_with_fallback_s": info["seconds"],
-        "effective_solves_per_s": n_test / info["seconds"],
+        "spread_rule": {"accepted_fraction": float(raw_acc.mean()),
+                        "accepted_with_err_above_tol": float(np.mean(err_sur[raw_acc] > args.sur_tol))
+                        if raw_acc.any() else None},
+        "calibrated": {"tau_K": tau, "coverage": args.sur_coverage, "calibration_accepted": cal_acc,
+                       "eval_scenarios": int(ev.stop - ev.start), "fallback_fraction": float(fb.mean()),
+                       "accepted_max_err_K": float(err_out[acc].max()) if acc.any() else None,
+                       "accepted_with_err_above_tol": float(np.mean(err_out[acc] > args.sur_tol))
+                       if acc.any() else None,
+                       "answered_max_err_K": float(err_out.max()),
+                       "solve_with_fallback_s": info["seconds"],
+                       "effective_solves_per_s": (ev.stop - ev.start) / info["seconds"]},
         "speedup_vs_solver": (Bq / inf_s) / solver_rate,
     }
     print(json.dumps(line))
@@ -576,6 +589,7 @@ def main():
     ap.add_argument("--sur-members", type=int, default=5)
     ap.add_argument("--sur-epochs", type=int, default=50)
     ap.add_argument("--sur-tol", type=float, default=1.0)
+    ap.add_argument("--sur-coverage", type=float, default=0.95)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

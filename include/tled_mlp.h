@@ -66,8 +66,13 @@ int tled_mlp_train_step_rows(tled_mlp *m, const float *x, const float *t, const 
 /* Ensemble statistics of n_members (1..16) network outputs y[k] [B][n_out]
  * (device float32, e.g. tled_mlp_forward of each member on the same inputs),
  * enqueued on `stream` of `device`; no context, nothing allocated.  Each
- * output is first mapped to z = y * out_scale + out_shift (device [n_out];
- * both NULL: identity), then, over the members in order:
+ * output is first mapped to z = (y * out_scale + out_shift) * r_b + out_offset
+ * (out_scale, out_shift, out_offset: device [n_out], NULL = 1, 0, 0), where
+ * the row factor r_b = row_src[b * row_stride] * row_mult applies to the
+ * first n_row_scaled outputs only (row_src NULL: r_b = 1) -- e.g. a network
+ * that learned temperature rise per unit source power, scaled back by each
+ * scenario's power read from its raw input row -- then, over the members in
+ * order:
  *   mean [B][n_out]  ensemble mean of z
  *   std  [B][n_out]  population standard deviation of z (two-pass)
  *   spread [B]       max of std over outputs [0, n_spread)
@@ -75,8 +80,9 @@ int tled_mlp_train_step_rows(tled_mlp *m, const float *x, const float *t, const 
  * Any of the four outputs may be NULL.  Used to accept a surrogate answer or
  * send the scenario back to the solver.  Errors: E_ARG, E_CUDA. */
 int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *const *y, int32_t B, int32_t n_out,
-                      const float *out_scale, const float *out_shift, int32_t n_spread, float tol, float *mean,
-                      float *std, float *spread, uint8_t *fallback);
+                      const float *out_scale, const float *out_shift, const float *row_src, int32_t row_stride,
+                      float row_mult, int32_t n_row_scaled, const float *out_offset, int32_t n_spread, float tol,
+                      float *mean, float *std, float *spread, uint8_t *fallback);
 /* wait for the stream; E_TIMEOUT if a bounded pipeline wait gave up */
 int tled_mlp_sync(tled_mlp *m);
 

@@ -96,14 +96,19 @@ class MLPOracle:
         return p, m, v
 
 
-def ensemble_stats(ys, scale=None, shift=None, n_spread=0, tol=0.0):
+def ensemble_stats(ys, scale=None, shift=None, n_spread=0, tol=0.0, row=None, n_row=0, offset=None):
     """Ensemble statistics by their definitions, in FP64: members' outputs
-    mapped to z = y * scale + shift, mean and population standard deviation
-    over the members, spread = max of the std over the first n_spread outputs,
-    fallback = spread > tol.  ys: sequence of [B][n_out] arrays."""
+    mapped to z = (y * scale + shift) * row_b + offset (row_b, one factor per
+    batch row, on the first n_row outputs only), mean and population standard
+    deviation over the members, spread = max of the std over the first
+    n_spread outputs, fallback = spread > tol.  ys: sequence of [B][n_out]."""
     Z = np.stack([np.asarray(y, np.float64) for y in ys])
     if scale is not None:
         Z = Z * np.asarray(scale, np.float64) + np.asarray(shift, np.float64)
+    if row is not None:
+        Z[:, :, :n_row] *= np.asarray(row, np.float64)[None, :, None]
+    if offset is not None:
+        Z = Z + np.asarray(offset, np.float64)
     mean = Z.sum(0) / len(ys)
     std = np.sqrt(((Z - mean) ** 2).sum(0) / len(ys))
     spread = std[:, :n_spread].max(1) if n_spread > 0 else np.zeros(len(mean))

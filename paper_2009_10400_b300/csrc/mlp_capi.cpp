@@ -310,10 +310,12 @@ int tled_mlp_set_input_scaling(tled_mlp *m, const float *shift, const float *sca
 }
 
 int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *const *y, int32_t B, int32_t n_out,
-                      const float *out_scale, const float *out_shift, int32_t n_spread, float tol, float *mean,
-                      float *std, float *spread, uint8_t *fallback) {
+                      const float *out_scale, const float *out_shift, const float *row_src, int32_t row_stride,
+                      float row_mult, int32_t n_row_scaled, const float *out_offset, int32_t n_spread, float tol,
+                      float *mean, float *std, float *spread, uint8_t *fallback) {
     if (n_members < 1 || n_members > kMaxMembers || !y || B < 0 || n_out < 1 || n_spread < 0 || n_spread > n_out ||
-        !(tol >= 0))
+        !(tol >= 0) || n_row_scaled < 0 || n_row_scaled > n_out || (row_src && row_stride < 1) ||
+        !std::isfinite(row_mult))
         return TLED_E_ARG;
     EnsembleArgs e{};
     for (int k = 0; k < n_members; k++) {
@@ -325,6 +327,11 @@ int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *
     e.n_spread = n_spread;
     e.scale = out_scale;
     e.shift = out_shift;
+    e.row_src = row_src;
+    e.row_stride = row_stride;
+    e.row_mult = row_mult;
+    e.n_row_scaled = row_src ? n_row_scaled : 0;
+    e.offset = out_offset;
     e.tol = tol;
     e.mean = mean;
     e.std = std;

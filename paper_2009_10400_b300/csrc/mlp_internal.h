@@ -31,6 +31,10 @@ struct EnsembleArgs {
     const float *y[kMaxMembers];  // member outputs [B][n_out]
     int n_members, n_out, n_spread;
     const float *scale, *shift;   // [n_out] or NULL
+    const float *row_src;         // per-row factor r_b = row_src[b * row_stride] * row_mult, or NULL (r_b = 1)
+    int row_stride, n_row_scaled; // r_b multiplies outputs [0, n_row_scaled)
+    float row_mult;
+    const float *offset;          // [n_out] added after the row factor, or NULL
     float tol;
     float *mean, *std, *spread;   // [B][n_out], [B][n_out], [B]; each may be NULL
     uint8_t *fallback;            // [B] or NULL

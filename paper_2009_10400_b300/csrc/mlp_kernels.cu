@@ -319,22 +319,25 @@ __global__ void gather_grad_kernel(const float *__restrict__ G, const float *__r
     }
 }
 
-// Ensemble statistics, one block per batch row b: z_k = y_k * scale + shift for
-// the members k (summed in member order), mean and population standard
-// deviation (two passes), spread = max of std over the first n_spread outputs,
-// fallback = spread > tol.
+// Ensemble statistics, one block per batch row b: z_k = (y_k * scale + shift)
+// * r_b + offset for the members k (r_b only on the first n_row_scaled outputs;
+// summed in member order), mean and population standard deviation (two
+// passes), spread = max of std over the first n_spread outputs, fallback =
+// spread > tol.
 __global__ void __launch_bounds__(256) ensemble_kernel(const EnsembleArgs E) {
     const int b = blockIdx.x;
+    const float rb = E.row_src ? E.row_src[(int64_t)b * E.row_stride] * E.row_mult : 1.f;
     float smax = 0.f;
     for (int n = threadIdx.x; n < E.n_out; n += blockDim.x) {
         const int64_t i = (int64_t)b * E.n_out + n;
         const float sc = E.scale ? E.scale[n] : 1.f, sh = E.shift ? E.shift[n] : 0.f;
+        const float r = n < E.n_row_scaled ? rb : 1.f, off = E.offset ? E.offset[n] : 0.f;
         float z[kMaxMembers];
         float sum = 0.f;
 #pragma unroll
         for (int k = 0; k < kMaxMembers; k++) {
             if (k < E.n_members) {
-                z[k] = fmaf(E.y[k][i], sc, sh);
+                z[k] = fmaf(fmaf(E.y[k][i], sc, sh), r, off);
                 sum += z[k];
             }
         }

@@ -110,6 +110,7 @@ struct tled_ctx {
     uint64_t setup_hash = 0;
     std::map<int, cudaGraphExec_t> graphs;
     int tile_ctas = 1;
+    int shared_blocks = 1;         // persistent grid of the shared-node kernel
     int active_host[2] = {0, 0};   // last uploaded active prefix lengths
 };
 
@@ -982,6 +983,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     int n_sm = 0;
     CUDA_TRY(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
     c->tile_ctas = tled::tile_grid(A, npe, n_sm);
+    c->shared_blocks = tled::shared_grid(A, n_sm);
     if (c->grid_override > 0) c->tile_ctas = std::min(c->tile_ctas, c->grid_override);
     // set-up hash for checkpoints
     uint64_t h = 1469598103934665603ULL;
@@ -1033,7 +1035,7 @@ static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < K && e == cudaSuccess; k++) {
         e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
-        if (e == cudaSuccess) e = tled::launch_shared_step(c->A, k, c->cap);
+        if (e == cudaSuccess) e = tled::launch_shared_step(c->A, c->shared_blocks, k, c->cap);
     }
     if (e == cudaSuccess) e = tled::launch_bump(c->A, K, c->cap);
     cudaGraph_t graph = nullptr;
@@ -1210,7 +1212,7 @@ int tled_step_timed(tled_ctx *c, int64_t n, double *ms) {
         cudaEventRecord(ev[3 * i], c->stream);
         err = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
         cudaEventRecord(ev[3 * i + 1], c->stream);
-        if (err == cudaSuccess) err = tled::launch_shared_step(c->A, 0, c->stream);
+        if (err == cudaSuccess) err = tled::launch_shared_step(c->A, c->shared_blocks, 0, c->stream);
         cudaEventRecord(ev[3 * i + 2], c->stream);
         if (err == cudaSuccess) err = tled::launch_bump(c->A, 1, c->stream);
     }

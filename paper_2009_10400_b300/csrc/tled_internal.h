@@ -13,6 +13,7 @@ namespace tled {
 
 constexpr int kBlock = 256;        // threads per CTA of the tile kernel
 constexpr int kTile = 256;         // elements per tile (one per thread); every tile owns kTile element slots
+constexpr int kTileCtasPerSm = 3; // tile kernel CTAs resident per SM (register budget 85 per thread)
 constexpr int kMaxLocal = 448;     // max nodes touched by one tile (shared memory)
 constexpr int kNsMax = 256;        // interior nodes whose state is staged in shared memory
 // per-tile gather record (uint16): slot offsets [kTile * npe], then row offsets [kMaxLocal + 8]
@@ -118,7 +119,8 @@ struct StepArgs {
 // kernel launchers (tled_kernels.cu); npe 4 or 8, or 0 for a batch mixing both element types
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s);
 int tile_grid(const StepArgs &a, int npe, int n_sm);  // persistent grid size
-cudaError_t launch_shared_step(const StepArgs &a, int k, cudaStream_t s);
+int shared_grid(const StepArgs &a, int n_sm);  // persistent grid of the shared-node kernel
+cudaError_t launch_shared_step(const StepArgs &a, int n_blocks, int k, cudaStream_t s);
 cudaError_t launch_bump(const StepArgs &a, int K, cudaStream_t s);
 // temperature and damage at probe points: out [2][n]
 cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w, int64_t n, double T0, double *out,

@@ -227,19 +227,21 @@ __device__ __forceinline__ void wht8(float *x) {
 // WHT index -> VTK corner (an involution)
 __device__ __forceinline__ constexpr int wht_corner(int i) { return i == 2 ? 3 : i == 3 ? 2 : i == 6 ? 7 : i == 7 ? 6 : i; }
 
+// NPR: Prony terms (a compile-time count, so that only the terms in use take registers)
+template <int NPR>
 struct ElemIn {
     float Ji[9];
     float V;
     float mu, kap, k1, k2, kc, al;
     float ax, ay, az;
-    float vs[4][6];
+    float vs[NPR > 0 ? NPR : 1][6];
 };
 
 // Element inputs staged in shared memory for one tile: local connectivity
 // [kTile][NPE] (uint16), then float components [q][kTile]: J0^-1 (9), V0,
 // [mu kappa k1 k2 k alpha], [fibre xyz], Prony state (6 per term).
-template <int NPE>
-__device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, int ec, int *cl, ElemIn &E) {
+template <int NPE, int NPR>
+__device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, int ec, int *cl, ElemIn<NPR> &E) {
     if constexpr (NPE == 8) {
         const uint4 c = reinterpret_cast<const uint4 *>(base)[ec];
         cl[0] = c.x & 0xffff; cl[1] = c.x >> 16; cl[2] = c.y & 0xffff; cl[3] = c.y >> 16;
@@ -265,17 +267,17 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, i
         E.ax = A.a0x; E.ay = A.a0y; E.az = A.a0z;
     }
 #pragma unroll
-    for (int p = 0; p < 4; p++)
+    for (int p = 0; p < NPR; p++)
 #pragma unroll
-        for (int s = 0; s < 6; s++) E.vs[p][s] = (p < A.n_prony) ? cp[(q + p * 6 + s) * kTile] : 0.f;
+        for (int s = 0; s < 6; s++) E.vs[p][s] = cp[(q + p * 6 + s) * kTile];
 }
 
 // One element: deformation gradient, thermal split, stress, Prony, nodal
 // forces + hourglass, thermal loads.  Corner contributions are written to the
 // chunk's slot buffer at [corner][ec] (conflict-free).
-template <int NPE>
+template <int NPE, int NPR>
 __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &SP, int64_t e, int ec, const int *cl,
-                                             ElemIn &E, const float4 *__restrict__ s_xu,
+                                             ElemIn<NPR> &E, const float4 *__restrict__ s_xu,
                                              const float4 *__restrict__ s_X, float4 *__restrict__ slot,
                                              float *__restrict__ gvisc) {
     const float *Ji = E.Ji;
@@ -416,14 +418,12 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
 #pragma unroll
         for (int s = 0; s < 6; s++) S0[s] = St[s];
 #pragma unroll
-        for (int p = 0; p < 4; p++) {
-            if (p < A.n_prony) {
+        for (int p = 0; p < NPR; p++) {
 #pragma unroll
-                for (int s = 0; s < 6; s++) {
-                    const float tp = SP.pr_a[p] * S0[s] + SP.pr_b[p] * E.vs[p][s];
-                    gvisc[(p * 6 + s) * kTile] = tp;
-                    St[s] -= tp;
-                }
+            for (int s = 0; s < 6; s++) {
+                const float tp = SP.pr_a[p] * S0[s] + SP.pr_b[p] * E.vs[p][s];
+                gvisc[(p * 6 + s) * kTile] = tp;
+                St[s] -= tp;
             }
         }
     }
@@ -572,8 +572,8 @@ __device__ void prefetch_tile(const StepArgs &A, int t) {
     }
 }
 
-template <int NPE>
-__global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, const int k) {
+template <int NPE, int NPR>
+__global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
     __shared__ ScenStep S;
     __shared__ int s_abort;
@@ -601,8 +601,7 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
         const TileInfo T = tile_info(A, t);
         const int npe = NPE ? NPE : T.npe;
         const uint16_t *s_row = s_code + kTile * npe;
-        const int b = i & 1;
-        char *buf = smem + b * A.sm_buf;
+        char *buf = smem;  // element inputs, then this tile's corner slots
         float4 *slot = reinterpret_cast<float4 *>(buf);
         const bool ns_smem = T.n_int > 0 && T.n_int <= kNsMax;
         const int scn = __ldg(A.tile_scn + t);
@@ -617,7 +616,7 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
             s_X[l] = __ldg(&A.X0[g]);
         }
         bool ok = mbar_wait(&bar[2], i & 1);
-        ok = mbar_wait(&bar[b], (i >> 1) & 1) && ok;
+        ok = mbar_wait(&bar[0], i & 1) && ok;
         if (!ok) {
             atomicOr(A.status, kStatusTimeout);
             s_abort = 1;
@@ -626,17 +625,16 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
         const int ec = threadIdx.x;
         const bool active = ec < T.ne_t;
         int cl[NPE ? NPE : 8];
-        ElemIn E;
+        ElemIn<NPR> E;
         if (active) {
-            if constexpr (NPE != 0) load_elem<NPE>(A, buf, ec, cl, E);
-            else if (npe == 8) load_elem<8>(A, buf, ec, cl, E);
-            else load_elem<4>(A, buf, ec, cl, E);
+            if constexpr (NPE != 0) load_elem<NPE, NPR>(A, buf, ec, cl, E);
+            else if (npe == 8) load_elem<8, NPR>(A, buf, ec, cl, E);
+            else load_elem<4, NPR>(A, buf, ec, cl, E);
         }
         __syncthreads();
         if (s_abort) return;
         if (threadIdx.x == 0) {
             fence_proxy_async();
-            if (t + G < n_tiles) stage_elem(A, t + G, tile_npe<NPE>(A, t + G), smem + (b ^ 1) * A.sm_buf, &bar[b ^ 1]);
             if (ns_smem) {
                 mbar_expect_tx(&bar[3], 48u * T.n_int);
                 bulk_g2s(ns, A.lo + T.ib, 16u * T.n_int, &bar[3]);
@@ -648,9 +646,9 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
         // ---- 3. element pass
         if (active) {
             float *gv = A.visc + (int64_t)t * A.n_prony * 6 * kTile + ec;
-            if constexpr (NPE != 0) element_step<NPE>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
-            else if (npe == 8) element_step<8>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
-            else element_step<4>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            if constexpr (NPE != 0) element_step<NPE, NPR>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else if (npe == 8) element_step<8, NPR>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else element_step<4, NPR>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
         }
         __syncthreads();
         // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum,
@@ -688,50 +686,61 @@ __global__ void __launch_bounds__(kBlock, 2) tile_step_kernel(const StepArgs A, 
             }
         }
         __syncthreads();
-        // ---- 5. stage the next tile's gather record and interior nodes
+        // ---- 5. stage the next tile's element record (into the consumed slot buffer),
+        //         gather record and interior nodes
         if (threadIdx.x == 0 && t + G < n_tiles) {
             fence_proxy_async();
+            stage_elem(A, t + G, tile_npe<NPE>(A, t + G), smem, &bar[0]);
             stage_nodes<NPE>(A, t + G, tile_info(A, t + G), smem, &bar[2]);
         }
     }
 }
 
 // Nodes touched by several tiles: sum the node's partial sums in tile order,
-// then the same nodal update as the tile kernel.
+// then the same nodal update as the tile kernel.  Persistent: block b takes the
+// 256-node chunks b, b + gridDim.x, ...; the scenario's step values are
+// prepared only when a chunk's first node belongs to another scenario than the
+// previous chunk's (once per launch for a single problem).
 __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, const int k) {
     __shared__ ScenStep S;
     const int64_t n_sh = A.n_active[1];  // shared nodes of unfinished scenarios form a prefix
-    const int64_t s0 = (int64_t)blockIdx.x * blockDim.x;
-    if (s0 >= n_sh) return;
-    const int scn0 = __ldg(A.shared_scn + s0);  // the block's first node's scenario, in shared memory
-    prepare_scen(A, scn0, k, S, threadIdx.x, blockDim.x);
-    __syncthreads();
-    const int64_t s = s0 + threadIdx.x;
-    if (s >= n_sh) return;
-    const int64_t g = A.n_interior + s;
-    // every load of the node issued up front: its state, then its first four partial
-    // sums (a node of a tile-boundary face has 2, of an edge 4); more follow in order
-    const float4 xu = A.xu[g], X = __ldg(&A.X0[g]), lo = A.lo[g], vo = A.vel[g], nc = __ldg(&A.nodec[g]);
-    const int r0 = __ldg(A.sh_rowptr + s), r1 = __ldg(A.sh_rowptr + s + 1);
-    const int scn = __ldg(A.shared_scn + s);
-    float4 c[4];
+    int cur = -1;
+    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < n_sh; c0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = c0 + threadIdx.x;
+        const bool live = s < n_sh;
+        // every load of the node issued up front: its state, then its first four partial
+        // sums (a node of a tile-boundary face has 2, of an edge 4); more follow in order
+        const int64_t g = A.n_interior + (live ? s : c0);
+        const float4 xu = A.xu[g], X = __ldg(&A.X0[g]), lo = A.lo[g], vo = A.vel[g], nc = __ldg(&A.nodec[g]);
+        const int r0 = live ? __ldg(A.sh_rowptr + s) : 0, r1 = live ? __ldg(A.sh_rowptr + s + 1) : 0;
+        const int scn = live ? __ldg(A.shared_scn + s) : -1;
+        float4 c[4];
 #pragma unroll
-    for (int j = 0; j < 4; j++) c[j] = r0 + j < r1 ? A.partials[r0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < 4; j++) c[j] = r0 + j < r1 ? A.partials[r0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int scn0 = __ldg(A.shared_scn + c0);  // the chunk's first node's scenario (block-uniform)
+        if (scn0 != cur) {
+            __syncthreads();  // nobody still reads the previous step values
+            prepare_scen(A, scn0, k, S, threadIdx.x, blockDim.x);
+            __syncthreads();
+            cur = scn0;
+        }
+        if (!live) continue;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < 4; j++) {  // the node's partial sums, in tile order (adding 0 changes nothing)
-        acc.x += c[j].x; acc.y += c[j].y; acc.z += c[j].z; acc.w += c[j].w;
-    }
-    for (int r = r0 + 4; r < r1; r++) {
-        const float4 d = A.partials[r];
-        acc.x += d.x; acc.y += d.y; acc.z += d.z; acc.w += d.w;
-    }
-    if (scn == scn0) {
-        node_update(A, S, g, acc, xu, X, lo, vo, nc);
-    } else {  // block spans a scenario boundary: this thread's own step values
-        ScenStep L;
-        prepare_scen(A, scn, k, L, 0, 1);
-        node_update(A, L, g, acc, xu, X, lo, vo, nc);
+        for (int j = 0; j < 4; j++) {  // the node's partial sums, in tile order (adding 0 changes nothing)
+            acc.x += c[j].x; acc.y += c[j].y; acc.z += c[j].z; acc.w += c[j].w;
+        }
+        for (int r = r0 + 4; r < r1; r++) {
+            const float4 d = A.partials[r];
+            acc.x += d.x; acc.y += d.y; acc.z += d.z; acc.w += d.w;
+        }
+        if (scn == scn0) {
+            node_update(A, S, g, acc, xu, X, lo, vo, nc);
+        } else {  // chunk spans a scenario boundary: this thread's own step values
+            ScenStep L;
+            prepare_scen(A, scn, k, L, 0, 1);
+            node_update(A, L, g, acc, xu, X, lo, vo, nc);
+        }
     }
 }
 
@@ -959,7 +968,7 @@ void tile_smem_layout(StepArgs &a, int npe) {
     a.n_comp = 10 + (a.has_mat ? 6 : 0) + (a.has_fib ? 3 : 0) + 6 * a.n_prony;
     a.sm_in = align128(kTile * npe * 2 + a.n_comp * kTile * 4);
     a.sm_buf = std::max(a.sm_in, kTile * npe * 16);
-    int off = 2 * a.sm_buf;  // double-buffered element inputs; the current one is then the slot buffer
+    int off = a.sm_buf;  // element inputs; once read into registers, the corner slot buffer
     a.sm_ns = off;
     off = align128(off + kNsMax * 48);
     a.sm_csr = off;
@@ -977,38 +986,48 @@ template <class K>
 static cudaError_t set_smem(K kern, int bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
-cudaError_t tile_kernel_setup(const StepArgs &a, int npe) {
-    if (npe == 8) return set_smem(tile_step_kernel<8>, a.sm_total);
-    if (npe == 4) return set_smem(tile_step_kernel<4>, a.sm_total);
-    return set_smem(tile_step_kernel<0>, a.sm_total);
+
+// the tile kernel instance for (element type, Prony terms): npe 8, 4 or 0 (mixed), n_prony 0..4
+using TileKernel = void (*)(const StepArgs, const int);
+template <int NPE>
+static TileKernel tile_kernel_npr(int n_prony) {
+    switch (n_prony) {
+        case 0: return tile_step_kernel<NPE, 0>;
+        case 1: return tile_step_kernel<NPE, 1>;
+        case 2: return tile_step_kernel<NPE, 2>;
+        case 3: return tile_step_kernel<NPE, 3>;
+        default: return tile_step_kernel<NPE, 4>;
+    }
 }
+static TileKernel tile_kernel(int npe, int n_prony) {
+    return npe == 8 ? tile_kernel_npr<8>(n_prony) : npe == 4 ? tile_kernel_npr<4>(n_prony) : tile_kernel_npr<0>(n_prony);
+}
+
+cudaError_t tile_kernel_setup(const StepArgs &a, int npe) { return set_smem(tile_kernel(npe, a.n_prony), a.sm_total); }
 
 int tile_grid(const StepArgs &a, int npe, int n_sm) {
     int per_sm = 0;
-    cudaError_t e =
-        npe == 8   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<8>, kBlock, a.sm_total)
-        : npe == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<4>, kBlock, a.sm_total)
-                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_step_kernel<0>, kBlock, a.sm_total);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel(npe, a.n_prony), kBlock, a.sm_total);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return std::max(1, std::min(a.n_tiles, per_sm * n_sm));
 }
 
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s) {
     if (a.n_tiles <= 0) return cudaSuccess;
-    const size_t sm = (size_t)a.sm_total;
-    if (npe == 8)
-        tile_step_kernel<8><<<n_ctas, kBlock, sm, s>>>(a, k);
-    else if (npe == 4)
-        tile_step_kernel<4><<<n_ctas, kBlock, sm, s>>>(a, k);
-    else
-        tile_step_kernel<0><<<n_ctas, kBlock, sm, s>>>(a, k);
+    tile_kernel(npe, a.n_prony)<<<n_ctas, kBlock, (size_t)a.sm_total, s>>>(a, k);
     return cudaGetLastError();
 }
 
-cudaError_t launch_shared_step(const StepArgs &a, int k, cudaStream_t s) {
+int shared_grid(const StepArgs &a, int n_sm) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shared_step_kernel, 256, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>((a.n_shared + 255) / 256, (int64_t)per_sm * n_sm));
+}
+
+cudaError_t launch_shared_step(const StepArgs &a, int n_blocks, int k, cudaStream_t s) {
     if (a.n_shared <= 0) return cudaSuccess;
-    const int nb = (int)((a.n_shared + 255) / 256);
-    shared_step_kernel<<<nb, 256, 0, s>>>(a, k);
+    shared_step_kernel<<<n_blocks, 256, 0, s>>>(a, k);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,8 @@ _SIGS = {
     "tled_mlp_train_step_rows": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p],
                                  C.c_int),
     "tled_mlp_ensemble": ([C.c_int, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_void_p,
-                           C.c_void_p, C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+                           C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_void_p, C.c_int32, C.c_float,
+                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
 _ready = False
 
@@ -146,9 +147,12 @@ class MLP:
         self._check(lib().tled_mlp_sync(self.h))
 
 
-def ensemble(ys, out_scale=None, out_shift=None, n_spread=0, tol=0.0, device=0, stream=None, want_std=True):
+def ensemble(ys, out_scale=None, out_shift=None, n_spread=0, tol=0.0, device=0, stream=None, want_std=True,
+             row_src=None, row_mult=1.0, n_row_scaled=0, out_offset=None):
     """Ensemble mean, std, spread and fallback flags of member outputs ys
-    (list of device float32 tensors [B][n_out]) in the library's kernel."""
+    (list of device float32 tensors [B][n_out]) in the library's kernel.
+    row_src: device float32 matrix whose column 0 (row stride = its width),
+    times row_mult, scales the first n_row_scaled outputs of each row."""
     import torch
 
     B, n_out = ys[0].shape
@@ -160,8 +164,10 @@ def ensemble(ys, out_scale=None, out_shift=None, n_spread=0, tol=0.0, device=0, 
     fb = torch.empty(B, dtype=torch.uint8, device=dev)
     ptrs = (C.c_void_p * len(ys))(*[y.data_ptr() for y in ys])
     vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    stride = row_src.stride(0) if row_src is not None else 1
     rc = lib().tled_mlp_ensemble(device, C.c_void_p(stream.cuda_stream), len(ys), ptrs, B, n_out, vp(out_scale),
-                                 vp(out_shift), int(n_spread), float(tol), vp(mean), vp(std), vp(spread), vp(fb))
+                                 vp(out_shift), vp(row_src), int(stride), float(row_mult), int(n_row_scaled),
+                                 vp(out_offset), int(n_spread), float(tol), vp(mean), vp(std), vp(spread), vp(fb))
     if rc:
         raise TledError(rc, "tled_mlp_ensemble: invalid arguments or CUDA error")
     return mean, std, spread, fb

@@ -64,6 +64,25 @@ def solve_scenarios(Q, n=16, dt=0.01, chunk=512, device=0):
     return T, D, dict(seconds=time.perf_counter() - t0, launch_steps=steps)
 
 
+def spread_threshold(spread, err, tol, coverage=1.0):
+    """Largest spread threshold tau (<= tol) such that the cases with spread <=
+    tau -- a prefix of the cases sorted by spread -- have err <= tol in at least
+    a `coverage` fraction; -1 if no prefix qualifies (everything to the solver).
+    Returns (tau, accepted fraction)."""
+    spread, err = np.asarray(spread, float), np.asarray(err, float)
+    order = np.argsort(spread, kind="stable")
+    ok = np.cumsum(err[order] <= tol) / np.arange(1, len(order) + 1)  # coverage of each prefix
+    good = np.nonzero(ok >= coverage)[0]
+    if not len(good):
+        return -1.0, 0.0
+    k = int(good[-1]) + 1  # the longest qualifying prefix
+    tau = float(spread[order[k - 1]])
+    if tau > tol:  # never accept a spread above the tolerance itself
+        k = int(np.searchsorted(spread[order], tol, side="right"))
+        tau = tol
+    return tau, k / len(order)
+
+
 def he_init(dims, rng):
     """He-normal weights, zero biases, in the library's parameter order."""
     parts = []
@@ -73,12 +92,26 @@ def he_init(dims, rng):
     return np.concatenate(parts).astype(np.float32)
 
 
+P_REF = 5e6  # W/m^3: the temperature outputs are learned per unit of power / P_REF
+T_REF = 37.0  # C: initial and arterial temperature of the scenarios
+
+
 class Surrogate:
     """Ensemble of MLPs.  Inputs are mapped to [-1, 1] over the sampling ranges
-    inside the first layer's input kernel; outputs are learned standardised per
-    probe value and mapped back by the ensemble kernel."""
+    inside the first layer's input kernel.  The first n_T outputs are
+    temperatures: with `per_power` the network learns the temperature rise per
+    unit source power, (T - T_REF) / (P / P_REF) -- the bioheat part of the
+    model is linear in the source power (c and k temperature independent, the
+    source centre moves with displacements of ~1e-5 m), which removes a factor
+    of ten of dynamic range from the regression -- and the ensemble kernel
+    multiplies it back by each scenario's power read from its raw input row.
+    All outputs are learned standardised per output and mapped back by the
+    ensemble kernel."""
 
-    def __init__(self, n_out, width=512, depth=6, members=5, max_batch=4096, device=0, n_in=12):
+    def __init__(self, n_out, width=512, depth=6, members=5, max_batch=4096, device=0, n_in=12, n_T=None,
+                 per_power=True):
+        self.n_T = n_out // 2 if n_T is None else n_T
+        self.per_power = per_power
         self.dims = [n_in] + [width] * (depth - 1) + [n_out]
         self.members = [MLP(self.dims, max_batch=max_batch, device=device) for _ in range(members)]
         self.max_batch = max_batch
@@ -99,12 +132,18 @@ class Surrogate:
         of the device-resident data set); returns the mean training loss per
         epoch of each member."""
         import torch
-        Y = np.asarray(Y, np.float64)
+        Y = np.array(Y, np.float64)
+        if self.per_power:
+            Y[:, :self.n_T] = (Y[:, :self.n_T] - T_REF) / (np.atleast_2d(Q)[:, :1] / P_REF)
         self.y_mean = Y.mean(0)
         self.y_std = np.maximum(Y.std(0), 1e-3 * max(Y.std(), 1e-12))
         dev = self._dev()
         self._scale = torch.tensor(self.y_std, dtype=torch.float32, device=dev)
         self._shift = torch.tensor(self.y_mean, dtype=torch.float32, device=dev)
+        off = np.zeros(self.dims[-1])
+        if self.per_power:
+            off[:self.n_T] = T_REF
+        self._offset = torch.tensor(off, dtype=torch.float32, device=dev)
         Xd = torch.tensor(np.atleast_2d(Q), dtype=torch.float32, device=dev)
         Yd = torch.tensor((Y - self.y_mean) / self.y_std, dtype=torch.float32, device=dev)
         n = len(Q) - len(Q) % batch
@@ -141,8 +180,13 @@ class Surrogate:
         for net, y in zip(self.members, ys):
             for b0 in range(0, mp, self.max_batch):
                 net.forward(Xd[b0:b0 + self.max_batch], out=y[b0:b0 + self.max_batch])
-        mean, std, spread, fb = ensemble(ys, self._scale, self._shift, n_spread, tol, device=self.device,
-                                         want_std=want_std)
+        if self.per_power:
+            mean, std, spread, fb = ensemble(ys, self._scale, self._shift, n_spread, tol, device=self.device,
+                                             want_std=want_std, row_src=Xd, row_mult=1.0 / P_REF,
+                                             n_row_scaled=self.n_T, out_offset=self._offset)
+        else:
+            mean, std, spread, fb = ensemble(ys, self._scale, self._shift, n_spread, tol, device=self.device,
+                                             want_std=want_std)
         return mean[:m], (std[:m] if std is not None else None), spread[:m], fb[:m]
 
     def predict(self, Q, n_spread=0, tol=0.0):
@@ -153,16 +197,34 @@ class Surrogate:
         mean, std, _, _ = self.predict_device(Xd, n_spread, tol)
         return mean.double().cpu().numpy(), std.double().cpu().numpy()
 
+    def calibrate(self, Q, Y, n_probe_T, tol=1.0, coverage=1.0):
+        """Spread threshold from solver answers: on calibration scenarios Q with
+        solver outputs Y, the largest threshold tau on the ensemble spread such
+        that, among the cases with spread <= tau, at least `coverage` of them
+        have a temperature error (max over probes) <= tol.  solve() then sends
+        cases with spread > tau to the solver.  Returns (tau, accepted fraction
+        of the calibration set)."""
+        mean, std = self.predict(Q)
+        err = np.abs(mean[:, :n_probe_T] - np.asarray(Y)[:, :n_probe_T]).max(1)
+        spread = std[:, :n_probe_T].max(1)
+        self.tau, frac = spread_threshold(spread, err, tol, coverage)
+        return self.tau, frac
+
     def solve(self, Q, n_probe_T, tol=1.0, n=16, dt=0.01):
         """Surrogate answers; cases whose ensemble spread of temperature (max over
-        probes) exceeds tol kelvin are re-run by the batched solver.  Returns
+        probes) exceeds the threshold -- tol kelvin, or the calibrated threshold
+        when calibrate() was called -- are re-run by the batched solver.  Returns
         (outputs, fallback mask, timings)."""
         import torch
         t0 = time.perf_counter()
         Xd = torch.tensor(np.atleast_2d(Q), dtype=torch.float32, device=self._dev())
-        mean, _, spread, fbd = self.predict_device(Xd, n_probe_T, tol, want_std=False)
+        thr = getattr(self, "tau", None)
+        mean, _, spread, fbd = self.predict_device(Xd, n_probe_T, tol if thr is None else max(thr, 0.0),
+                                                   want_std=False)
         out = mean.double().cpu().numpy()
         fb = fbd.cpu().numpy().astype(bool)
+        if thr is not None and thr < 0:  # calibration accepted nothing
+            fb[:] = True
         t1 = time.perf_counter()
         info = dict(surrogate_seconds=t1 - t0, fallback=int(fb.sum()), spread=spread.cpu().numpy())
         if fb.any():

@@ -60,6 +60,14 @@ def test_surrogate_learns_and_falls_back():
     out, fb, info = sur.solve(Q[te], P, tol=tol, n=n, dt=dt)
     assert 0 < fb.sum() < len(fb)
     np.testing.assert_allclose(out[fb], Y[te][fb], rtol=0, atol=1e-9)
+    # calibration against solver answers: with coverage 1, every calibration case
+    # whose spread is at or below the threshold meets the tolerance
+    tol_c = float(np.median(err))
+    cal = slice(0, 64)
+    tau, frac = sur.calibrate(Q[te][cal], Y[te][cal], P, tol=tol_c, coverage=1.0)
+    assert frac < 1.0 and tau <= tol_c
+    acc = spread[cal] <= tau
+    assert acc.sum() == round(frac * 64) and np.all(err[cal][acc] <= tol_c)
     # speed: surrogate predictions vs solver scenarios per second
     solver_rate = len(Q) / tm["seconds"]
     sur_rate = len(big) / t_sur

@@ -170,3 +170,16 @@ def test_batch_planning_keeps_scenarios_apart():
     assert info[0] == sum(s["n_tiles"] for s in singles) + n_t4
     assert info[1] + info[2] == sum(p.nn for p in probs) + t4p.nn
     tled.lib().tled_destroy(h)
+
+
+def test_surrogate_spread_threshold_rule():
+    """Calibration picks the longest prefix (by spread) whose errors meet the
+    tolerance at the requested coverage, never above the tolerance itself."""
+    from paper_2009_10400_b300.surrogate import spread_threshold
+    spread = [0.1, 0.2, 0.3, 0.4, 0.5, 0.6]
+    err = [0.5, 0.8, 1.5, 0.9, 2.0, 0.7]
+    assert spread_threshold(spread, err, tol=1.0, coverage=1.0) == (0.2, 2 / 6)
+    assert spread_threshold(spread, err, tol=1.0, coverage=0.75) == (0.4, 4 / 6)
+    assert spread_threshold(spread, [2.0] + err[1:], tol=1.0, coverage=1.0) == (-1.0, 0.0)
+    tau, frac = spread_threshold([0.5, 2.0, 3.0], [0.1, 0.1, 0.1], tol=1.0)
+    assert tau == 1.0 and frac == 1 / 3

@@ -59,6 +59,10 @@ def test_ensemble_stats_closed_forms():
     mean, std, spread, fb = ensemble_stats([a, a, a], scale=[2.0, 1.0, 1.0], shift=[1.0, 0.0, 0.0], n_spread=3, tol=0.0)
     np.testing.assert_array_equal(mean, [[3.0, 5.0, -2.0]])
     assert np.all(std == 0) and spread[0] == 0 and not fb[0]
+    # a row factor on the first output only, then an offset: std scales with |row|
+    mean, std, _, _ = ensemble_stats([a, b], row=[3.0], n_row=1, offset=[10.0, 0.0, 0.0])
+    np.testing.assert_array_equal(mean, [[16.0, 5.0, 0.0]])
+    np.testing.assert_array_equal(std, [[3.0, 0.0, 2.0]])
 
 # ---------------------------------------------------------------------------
 # GPU: tensor-core kernels against the oracle with the same bf16 rounding
@@ -144,11 +148,15 @@ def test_ensemble_kernel_matches_oracle():
     scale = rng.uniform(0.5, 3.0, N).astype(np.float32)
     shift = rng.uniform(-40, 40, N).astype(np.float32)
     d = [torch.tensor(y, device="cuda") for y in ys]
+    X = rng.uniform(1e6, 1e7, (B, 12)).astype(np.float32)  # raw input rows; column 0 gives the row factor
+    offset = np.where(np.arange(N) < 500, 37.0, 0.0).astype(np.float32)
     mean, std, spread, fb = ensemble(d, torch.tensor(scale, device="cuda"), torch.tensor(shift, device="cuda"),
-                                     n_spread=700, tol=4.0)
+                                     n_spread=700, tol=4.0, row_src=torch.tensor(X, device="cuda"), row_mult=2e-7,
+                                     n_row_scaled=500, out_offset=torch.tensor(offset, device="cuda"))
     torch.cuda.synchronize()
-    m_ref, s_ref, sp_ref, fb_ref = ensemble_stats(ys, scale, shift, n_spread=700, tol=4.0)
-    np.testing.assert_allclose(mean.cpu().numpy(), m_ref, rtol=1e-5, atol=1e-5 * np.abs(shift).max())
+    m_ref, s_ref, sp_ref, fb_ref = ensemble_stats(ys, scale, shift, n_spread=700, tol=4.0,
+                                                  row=X[:, 0].astype(np.float64) * 2e-7, n_row=500, offset=offset)
+    np.testing.assert_allclose(mean.cpu().numpy(), m_ref, rtol=1e-5, atol=2e-5 * np.abs(m_ref).max())
     np.testing.assert_allclose(std.cpu().numpy(), s_ref, rtol=1e-4, atol=1e-5)
     np.testing.assert_allclose(spread.cpu().numpy(), sp_ref, rtol=1e-4)
     clear = np.abs(sp_ref - 4.0) > 1e-3 * 4.0  # decisions away from the threshold are exact
