@@ -194,7 +194,7 @@ __device__ __forceinline__ void node_update(const StepArgs &A, const ScenStep &S
             th += dth;
     }
     // Arrhenius damage integral, explicit in T(t); exp(ln A - Ea/(R T)) avoids A > FLT_MAX
-    const float Om = vo.w + dt * expf(A.lnA - __fdividef(A.Ea_R, theta + A.T0_K));
+    const float Om = vo.w + dt * __expf(A.lnA - __fdividef(A.Ea_R, theta + A.T0_K));
     if (!(isfinite(th) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) {
         atomicOr(A.status, kStatusNaN);
         atomicMin(A.status + 2, (unsigned)g);
@@ -338,7 +338,7 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     // ---- thermal split (Eqs. 7-11, isotropic): lambda = 1 + delta, delta = alpha theta_e
     const float dl = (A.flags & TLED_EXPANSION) ? al * the : 0.f;
     const float lam = 1.f + dl;
-    const float il = __frcp_rn(lam);
+    const float il = __fdividef(1.f, lam);
     const float il2 = il * il;
     // J - 1 = tr H + [(tr H)^2 - tr(H^2)]/2 + det H
     const float trH = H[0][0] + H[1][1] + H[2][2];
@@ -370,7 +370,7 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     // C_el = I + 2 E_el and its inverse adj(C_el) / J_el^2
     const float c00 = 1.f + 2.f * Ee[0], c11 = 1.f + 2.f * Ee[1], c22 = 1.f + 2.f * Ee[2];
     const float c01 = 2.f * Ee[3], c12 = 2.f * Ee[4], c02 = 2.f * Ee[5];
-    const float iJ2 = __frcp_rn(Jel * Jel);
+    const float iJ2 = __fdividef(1.f, Jel * Jel);
     float Ci[6];
     Ci[0] = (c11 * c22 - c12 * c12) * iJ2;
     Ci[1] = (c00 * c22 - c02 * c02) * iJ2;
@@ -403,7 +403,7 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
                       2.f * (ax * ay * Ee[3] + ay * az * Ee[4] + ax * az * Ee[5]);
     const float I4 = 1.f + 2.f * aEa;
     const float x4 = Jm23m1 + 2.f * Jm23 * aEa;
-    const float psi4 = k1 * x4 * expf(k2 * x4 * x4);
+    const float psi4 = k1 * x4 * __expf(k2 * x4 * x4);
     const float cf = 2.f * psi4 * Jm23;
     const float cI4 = I4 * (1.f / 3.f);
     const float ciso = 2.f * mu * Jm23;
@@ -577,6 +577,7 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
     extern __shared__ __align__(128) char smem[];
     __shared__ ScenStep S;
     __shared__ int s_abort;
+    __shared__ int s_ppos[kMaxLocal];  // partial-sum positions of the tile's shared nodes
     const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_csr);
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
     float4 *s_X = reinterpret_cast<float4 *>(smem + A.sm_X);
@@ -612,6 +613,7 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         // ---- 1. shared nodes of the tile: ordinary loads (mostly L2 hits)
         for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
             const int64_t g = __ldg(A.tile_shared + T.sh_off + l - T.n_int);
+            s_ppos[l - T.n_int] = __ldg(A.part_pos + T.sh_off + l - T.n_int);
             s_xu[l] = A.xu[g];
             s_X[l] = __ldg(&A.X0[g]);
         }
@@ -682,7 +684,7 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
                 }
                 node_update(A, S, g, acc, s_xu[l], s_X[l], lo, vo, nc);
             } else {
-                A.partials[__ldg(A.part_pos + T.sh_off + l - T.n_int)] = acc;
+                A.partials[s_ppos[l - T.n_int]] = acc;
             }
         }
         __syncthreads();
