@@ -406,6 +406,7 @@ def run_surrogate(args):
     out, fb, info = sur.solve(Q[ev], P, tol=args.sur_tol, n=n, dt=0.01)
     err_out = np.abs(out[:, :P] - T[ev]).max(1)
     acc = ~fb
+    solver_rate = (n_train + n_test) / tm["seconds"]
     line = {
         "metric": "surrogate scenario-solves/s", "value": Bq / inf_s, "unit": "scenario-solves/s",
         "n_gpus": 1, "steps": reps, "warmup": 3, "ms_per_step": 1e3 * inf_s, "higher_is_better": True,
