@@ -40,7 +40,7 @@
 extern "C" {
 #endif
 
-#define TLED_VERSION 2
+#define TLED_VERSION 4
 
 /* status codes */
 #define TLED_OK 0
@@ -66,6 +66,7 @@ extern "C" {
 #define TLED_EXPANSION (1u << 0)   /* thermal expansion split, Eqs. (7)-(11) */
 #define TLED_TEMP_DEP (1u << 1)    /* c(T), k(T) linear in T (Table 5) */
 #define TLED_COMPENSATED (1u << 2) /* float-float accumulation of u and T */
+#define TLED_CEM43 (1u << 3)       /* accumulate the CEM43 thermal dose per node (single problems only) */
 
 /* boundary mask bits (per node) */
 #define TLED_FIX_X 1u
@@ -99,16 +100,29 @@ typedef struct tled_material {
     double Ta;            /* arterial blood temperature, C */
     double lnA;           /* natural log of the Arrhenius frequency factor, ln(1/s) */
     double Ea;            /* Arrhenius activation energy, J/mol */
+    /* Anisotropic thermal physics (0 or 1 = isotropic): thermal expansion along the
+     * fibre a0 relative to the transverse alpha, F_th = lambda_i I + (lambda_m - lambda_i)
+     * a0 (x) a0 (Eq. 11, transversely isotropic), lambda_m = 1 + alpha_fibre_ratio alpha
+     * theta; conductivity along the current fibre F a0 / |F a0| relative to the
+     * transverse k.  The H8 thermal hourglass uses the transverse k. */
+    double alpha_fibre_ratio;
+    double k_fibre_ratio;
 } tled_material;
 
-/* A Gaussian volumetric heat source Q(x, t) = power exp(-|x - c(t)|^2 / (2 sigma^2))
- * with c(t) = c0 + vel t, active for t_on <= t < t_off; x is the current
- * nodal position X + u(t). */
+/* A volumetric heat source with centre c(t) = c0 + vel t, active for
+ * t_on <= t < t_off.  Heat source shapes: a Gaussian P exp(-|x - c(t)|^2 / (2 sigma^2)), or (the
+ * paper's liver case, Section 6.3) a uniform density P inside the sphere
+ * |x - c(t)| <= sigma.  x is the current nodal position X + u(t). */
+#define TLED_SRC_GAUSSIAN 0
+#define TLED_SRC_SPHERE 1
+
 typedef struct tled_source {
     double c0[3], vel[3];
-    double sigma;  /* m */
+    double sigma;  /* m: standard deviation (Gaussian) or radius (sphere) */
     double power;  /* peak density, W/m^3 */
     double t_on, t_off;
+    int32_t shape; /* TLED_SRC_GAUSSIAN or TLED_SRC_SPHERE */
+    int32_t pad;
 } tled_source;
 
 typedef struct tled_params {
@@ -220,6 +234,16 @@ int tled_sync(tled_ctx *ctx);
 int tled_get_displacement(tled_ctx *ctx, double *out, int where);
 int tled_get_temperature(tled_ctx *ctx, double *out, int where);
 int tled_get_damage(tled_ctx *ctx, double *out, int where);
+/* CEM43 thermal dose per node, equivalent minutes at 43 C (Sapareto-Dewey:
+ * sum of dt/60 R^(43 - T(t)), R = 0.5 at or above 43 C, 0.25 below, explicit
+ * in T(t) like the Arrhenius integral), accumulated in FP64 by a small kernel
+ * before each step when the flags hold TLED_CEM43; [n_nodes] float64, caller
+ * order.  E_STATE without TLED_CEM43. */
+int tled_get_cem43(tled_ctx *ctx, double *out, int where);
+/* Volume of tissue at or above T_iso (C), sum of the lumped nodal volumes of
+ * the nodes with T >= T_iso (the paper reads the ablation zone off the 60 C
+ * isotherm, Section 6.3); deterministic FP64 reduction.  Synchronises. */
+int tled_get_isotherm_volume(tled_ctx *ctx, double T_iso, double *volume);
 
 /* Overwrite the full state from host float64 arrays (caller order):
  * u [n][3], v [n][3] (velocity at t - dt/2), T [n], Omega [n], and visc

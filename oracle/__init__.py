@@ -40,6 +40,7 @@ class _Model(C.Structure):
         ("kappa_hgT", C.c_double), ("dt", C.c_double),
         ("n_src", C.c_int32), ("pad2", C.c_int32), ("src", _dp),
         ("mask", C.POINTER(C.c_uint8)), ("ubar", _dp), ("ramp_time", C.c_double),
+        ("aniso_alpha", C.c_double), ("aniso_k", C.c_double),
         ("dhdX", _dp), ("V0", _dp), ("hg_gamma", _dp), ("khg", _dp), ("khgT", _dp),
         ("M", _dp), ("Cth", _dp), ("Vn", _dp),
     ]
@@ -47,7 +48,7 @@ class _Model(C.Structure):
 
 class _State(C.Structure):
     _fields_ = [("u", _dp), ("u_prev", _dp), ("T", _dp), ("Omega", _dp), ("visc", _dp),
-                ("t", C.c_double), ("step", C.c_int64)]
+                ("t", C.c_double), ("step", C.c_int64), ("cem", _dp)]
 
 
 def build(force: bool = False) -> str:
@@ -86,7 +87,8 @@ def _p(a):
 
 
 class OracleState:
-    """FP64 state: u(t), u(t - dt) (Eq. 27), absolute T, Omega, Prony state."""
+    """FP64 state: u(t), u(t - dt) (Eq. 27), absolute T, Omega, Prony state, and
+    the CEM43 thermal dose (equivalent minutes at 43 C) of every node."""
 
     def __init__(self, nn, ne, n_prony, T0):
         self.u = np.zeros((nn, 3))
@@ -94,16 +96,17 @@ class OracleState:
         self.T = np.full(nn, float(T0))
         self.Omega = np.zeros(nn)
         self.visc = np.zeros((ne, max(n_prony, 1), 6))
+        self.cem = np.zeros(nn)
         self.t = 0.0
         self.step = 0
 
     def _c(self):
         return _State(_p(self.u), _p(self.u_prev), _p(self.T), _p(self.Omega), _p(self.visc),
-                      self.t, self.step)
+                      self.t, self.step, _p(self.cem))
 
     def copy(self):
         s = OracleState.__new__(OracleState)
-        for k in ("u", "u_prev", "T", "Omega", "visc"):
+        for k in ("u", "u_prev", "T", "Omega", "visc", "cem"):
             setattr(s, k, getattr(self, k).copy())
         s.t, s.step = self.t, self.step
         return s
@@ -126,7 +129,11 @@ class OracleModel:
         self.M = np.zeros(nn)
         self.Cth = np.zeros(nn)
         self.Vn = np.zeros(nn)
-        self._keep = [prob.X, prob.conn, prob.a0, prob.sources, prob.mask, prob.ubar]
+        src = np.asarray(prob.sources, np.float64).reshape(-1, np.shape(prob.sources)[-1] if np.size(prob.sources) else 11)
+        if src.shape[1] == 10:  # rows without a shape column are Gaussian
+            src = np.concatenate([src, np.zeros((len(src), 1))], 1)
+        self._src = np.ascontiguousarray(src)
+        self._keep = [prob.X, prob.conn, prob.a0, self._src, prob.mask, prob.ubar]
         m = _Model()
         m.npe, m.nn, m.ne = npe, nn, ne
         m.X = _p(prob.X)
@@ -138,12 +145,12 @@ class OracleModel:
             m.prony_g[i] = prob.prony_g[i]
             m.prony_tau[i] = prob.prony_tau[i]
         for f in ("c_heat", "beta_c", "beta_k", "T_ref", "wbcb", "Qm", "T0", "Ta", "lnA", "Ea", "gamma",
-                  "mass_scale", "kappa_hg", "kappa_hgT", "ramp_time"):
+                  "mass_scale", "kappa_hg", "kappa_hgT", "ramp_time", "aniso_alpha", "aniso_k"):
             setattr(m, f, float(getattr(prob, f)))
         m.expansion = int(bool(prob.expansion))
         m.temp_dep = int(bool(prob.temp_dep))
-        m.n_src = prob.sources.shape[0]
-        m.src = _p(prob.sources) if m.n_src else None
+        m.n_src = self._src.shape[0]
+        m.src = _p(self._src) if m.n_src else None
         m.mask = prob.mask.ctypes.data_as(C.POINTER(C.c_uint8))
         m.ubar = _p(prob.ubar)
         m.dhdX, m.V0, m.hg_gamma = _p(self.dhdX), _p(self.V0), _p(self.hg_gamma)

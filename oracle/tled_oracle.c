@@ -26,6 +26,12 @@
  *   R14 Gaussian heat sources evaluated at the current nodal position.
  *   R16 stable dt = safety * min(element CFL, thermal Gershgorin bound).
  *   R18 Arrhenius rate A exp(-Ea / (R T_abs)) evaluated at T(t).
+ *   R24 CEM43 dose accumulated explicitly at T(t): dt R^(43 - T) / 60 minutes,
+ *       R = 0.5 (T >= 43 C) or 0.25.
+ *   R26 anisotropic thermal physics: transversely isotropic F_th about m = a0
+ *       (Eq. 11) with fibre expansion aniso_alpha * alpha; conductivity
+ *       D = k (I + (aniso_k - 1) a a), a = F a0 / |F a0|; the H8 thermal
+ *       hourglass keeps the transverse k.
  */
 #include "tled_oracle.h"
 #include <math.h>
@@ -242,9 +248,29 @@ static double element_temperature(const ora_model *m, int64_t e, const double *T
 }
 
 /* isotropic thermal deformation gradient F_th = lambda I (Eq. 11, R4) */
+/* Eq. (11): F_th = lambda_i I + (lambda_m - lambda_i) m (x) m, transversely
+ * isotropic about m = a0 (R26), lambda = 1 + alpha (T_e - T0); isotropic when
+ * the fibre expansion ratio is 1 */
 static void thermal_gradient(const ora_model *m, int64_t e, double Te, double Fth[3][3]) {
-    double lam = m->expansion ? 1.0 + m->alpha[e] * (Te - m->T0) : 1.0;
-    m_eye(Fth, lam);
+    const double th = m->expansion ? Te - m->T0 : 0.0;
+    const double li = 1.0 + m->alpha[e] * th, lm = 1.0 + m->aniso_alpha * m->alpha[e] * th;
+    const double *a = m->a0 + 3 * e;
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) Fth[i][j] = (i == j ? li : 0.0) + (lm - li) * a[i] * a[j];
+}
+
+/* spatial conductivity D = k (I + (r_k - 1) a (x) a), a = F a0 / |F a0| the
+ * current fibre direction (R26); k = conductivity at T_e */
+static void conductivity_tensor(const ora_model *m, int64_t e, const double F[3][3], double k, double D[3][3]) {
+    const double *a0 = m->a0 + 3 * e;
+    double a[3] = {0, 0, 0}, n = 0;
+    for (int i = 0; i < 3; i++) {
+        for (int j = 0; j < 3; j++) a[i] += F[i][j] * a0[j];
+        n += a[i] * a[i];
+    }
+    n = sqrt(n);
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) D[i][j] = k * ((i == j ? 1.0 : 0.0) + (m->aniso_k - 1.0) * a[i] * a[j] / (n * n));
 }
 
 static double conductivity(const ora_model *m, int64_t e, double Te) {
@@ -307,11 +333,13 @@ double ora_element(const ora_model *m, int64_t e, const double *u, const double 
             f_e[3 * a + i] = V * s;
         }
 
-    /* Eqs. (16), (18), (19): fT = V (B F^-1) D (B F^-1)^T det F T_e, D = k I */
+    /* Eqs. (16), (18), (19): fT = V (B F^-1) D (B F^-1)^T det F T_e */
     double Fi[3][3];
     m_inv(F, Fi);
     double detF = m_det(F);
     double kT = conductivity(m, e, Te);
+    double D[3][3];
+    conductivity_tensor(m, e, F, kT, D);
     double G[8][3]; /* rows: spatial gradients of the shape functions, B F^-1 */
     for (int a = 0; a < npe; a++)
         for (int j = 0; j < 3; j++) {
@@ -323,7 +351,8 @@ double ora_element(const ora_model *m, int64_t e, const double *u, const double 
         double s = 0;
         for (int b = 0; b < npe; b++) {
             double Kab = 0;
-            for (int j = 0; j < 3; j++) Kab += G[a][j] * kT * G[b][j];
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) Kab += G[a][i] * D[i][j] * G[b][j];
             s += V * detF * Kab * T[cn[b]];
         }
         fT_e[a] = s;
@@ -376,20 +405,21 @@ double ora_element_thermal_energy(const ora_model *m, int64_t e, const double *u
     const int npe = m->npe;
     const int32_t *cn = m->conn + e * npe;
     const double *B = m->dhdX + e * npe * 3;
-    double F[3][3], Ft[3][3], C[3][3], Ci[3][3];
+    double F[3][3], Fi[3][3], D[3][3];
     deformation_gradient(m, e, u, F);
-    m_transpose(F, Ft);
-    m_mul(Ft, F, C);
-    m_inv(C, Ci);
+    m_inv(F, Fi);
     double J = m_det(F);
     double kT = conductivity(m, e, Tk_fixed);
-    double g[3] = {0, 0, 0};
+    conductivity_tensor(m, e, F, kT, D);
+    double g[3] = {0, 0, 0}, h[3] = {0, 0, 0};
     for (int a = 0; a < npe; a++)
         for (int j = 0; j < 3; j++) g[j] += T[cn[a]] * B[3 * a + j];
+    for (int i = 0; i < 3; i++) /* spatial gradient F^-T grad0 T */
+        for (int j = 0; j < 3; j++) h[i] += Fi[j][i] * g[j];
     double q = 0;
     for (int i = 0; i < 3; i++)
-        for (int j = 0; j < 3; j++) q += g[i] * Ci[i][j] * g[j];
-    double W = 0.5 * m->V0[e] * J * kT * q;
+        for (int j = 0; j < 3; j++) q += h[i] * D[i][j] * h[j];
+    double W = 0.5 * m->V0[e] * J * q;
     if (npe == 8) {
         const double *Gm = m->hg_gamma + e * 32;
         for (int al = 0; al < 4; al++) {
@@ -409,11 +439,12 @@ static double ramp(const ora_model *m, double t) {
     return t >= m->ramp_time ? 1.0 : t / m->ramp_time;
 }
 
-/* regional heat source Q_r at node i (R14), W/m^3 */
+/* regional heat source Q_r at node i (R14), W/m^3: a Gaussian of standard
+ * deviation sigma, or (the paper's liver case) a uniform sphere of that radius */
 static double heat_source(const ora_model *m, int64_t i, const double *u, double t) {
     double q = 0;
     for (int s = 0; s < m->n_src; s++) {
-        const double *p = m->src + 10 * s;
+        const double *p = m->src + 11 * s;
         if (t < p[8] || t >= p[9]) continue;
         double r2 = 0;
         for (int j = 0; j < 3; j++) {
@@ -421,9 +452,19 @@ static double heat_source(const ora_model *m, int64_t i, const double *u, double
             double c = p[j] + p[3 + j] * t;
             r2 += (x - c) * (x - c);
         }
-        q += p[7] * exp(-r2 / (2.0 * p[6] * p[6]));
+        if (p[10] == 1.0)
+            q += r2 <= p[6] * p[6] ? p[7] : 0.0;
+        else
+            q += p[7] * exp(-r2 / (2.0 * p[6] * p[6]));
     }
     return q;
+}
+
+/* CEM43 rate, equivalent minutes per second at temperature T (C):
+ * R^(43 - T) / 60 with R = 0.5 at or above 43 C and 0.25 below */
+static double cem43_rate(double T) {
+    const double R = T >= 43.0 ? 0.5 : 0.25;
+    return pow(R, 43.0 - T) / 60.0;
 }
 
 /* Eqs. (27), (20) and the Arrhenius integral for one node. */
@@ -476,6 +517,7 @@ int ora_step(const ora_model *m, ora_state *s, double *f, double *fT) {
     for (int64_t i = 0; i < m->nn; i++) {
         double un[3], Tn, On;
         node_update(m, s, i, f + 3 * i, fT[i], un, &Tn, &On);
+        if (s->cem) s->cem[i] += m->dt * cem43_rate(s->T[i]);  /* explicit in T(t), like the damage */
         for (int d = 0; d < 3; d++) {
             s->u_prev[3 * i + d] = s->u[3 * i + d];
             s->u[3 * i + d] = un[d];
@@ -576,9 +618,14 @@ double ora_stable_dt(const ora_model *m, double safety, double *dt_mech, double 
         for (int a = 0; a < npe; a++) {
             double rs = 0;
             for (int b = 0; b < npe; b++) {
-                double K = 0;
-                for (int j = 0; j < 3; j++) K += B[3 * a + j] * B[3 * b + j];
-                K *= m->V0[e] * kmax;
+                /* grad h_a . D grad h_b with D = k_max (I + (r_k - 1) a0 a0) at F = I */
+                double K = 0, ma = 0, mb = 0;
+                for (int j = 0; j < 3; j++) {
+                    K += B[3 * a + j] * B[3 * b + j];
+                    ma += B[3 * a + j] * m->a0[3 * e + j];
+                    mb += B[3 * b + j] * m->a0[3 * e + j];
+                }
+                K = (K + (m->aniso_k - 1.0) * ma * mb) * m->V0[e] * kmax;
                 if (npe == 8) {
                     const double *Gm = m->hg_gamma + e * 32;
                     double Kh = 0;

@@ -52,10 +52,14 @@ typedef struct {
     double kappa_hg, kappa_hgT;/* H8 hourglass coefficients (mechanical, thermal) */
     double dt;                 /* time step, s */
     int32_t n_src, pad2;
-    const double *src;         /* [n_src][10]: c0 xyz, velocity xyz, sigma, peak W/m^3, t_on, t_off */
+    const double *src;         /* [n_src][11]: c0 xyz, velocity xyz, sigma (Gaussian) or radius
+                                  (sphere), peak W/m^3, t_on, t_off, shape (0 Gaussian, 1 uniform sphere) */
     const uint8_t *mask;       /* [nn] bit0..2: u_x,u_y,u_z prescribed; bit3: T held */
     const double *ubar;        /* [nn][3] prescribed displacement at the end of the ramp (NULL = 0) */
     double ramp_time;          /* prescribed displacement ramps linearly over this time (0 = at once) */
+    double aniso_alpha;        /* expansion along the fibre / transverse expansion (Eq. 11, transversely
+                                  isotropic form with m = a0); 1 = isotropic */
+    double aniso_k;            /* conductivity along the current fibre / transverse conductivity; 1 = isotropic */
     /* ---- precomputed by ora_setup (caller allocated) ---- */
     double *dhdX;              /* [ne][npe][3] shape-function derivatives at the integration point */
     double *V0;                /* [ne] reference element volume (8 det J0 for H8, V0 for T4) */
@@ -75,6 +79,7 @@ typedef struct {
     double *visc;              /* [ne][n_prony][6] Prony state (xx,yy,zz,xy,yz,xz) */
     double t;
     int64_t step;
+    double *cem;               /* [nn] CEM43 thermal dose, equivalent minutes at 43 C (NULL: not tracked) */
 } ora_state;
 
 #ifdef __cplusplus

@@ -39,7 +39,7 @@ struct Layout {
     size_t xu, lo, vel, X0, nodec, ubar, elem_rec, visc;
     size_t tile_info, tile_shared, part_pos, csr, partials, sh_rowptr;
     size_t scn, src, scn_time, scn_step, tile_scn, shared_scn, n_active, status;
-    size_t node_new, probe_node, probe_w, probe_out, stat_part, stat_out, staging;
+    size_t node_new, probe_node, probe_w, probe_out, stat_part, stat_out, staging, cem;
     size_t total;
 };
 
@@ -161,6 +161,12 @@ int source_capacity(const tled_ctx *c) {
     return std::max(n, 1);
 }
 
+// fibre / transverse ratio of the anisotropic thermal physics (0 means 1: isotropic)
+double fibre_ratio(double r) { return r == 0.0 ? 1.0 : r; }
+
+// CEM43 dose tracked (single problems that ask for it)
+bool cem_on(const tled_ctx *c) { return !c->batch && !c->sc.empty() && (c->sc[0].prm.flags & TLED_CEM43); }
+
 Layout make_layout(const tled_ctx *c) {
     const Plan &p = c->plan;
     Layout L{};
@@ -188,7 +194,7 @@ Layout make_layout(const tled_ctx *c) {
     L.sh_rowptr = take(4 * p.sh_rowptr.size());
     L.part_pos = take(4 * p.part_pos.size());
     L.scn = take(sizeof(ScenDev) * ns);
-    L.src = take(8 * 10 * (size_t)source_capacity(c));
+    L.src = take(8 * tled::kSrcRow * (size_t)source_capacity(c));
     L.scn_time = take(8 * ns);
     L.scn_step = take(8 * ns);
     L.tile_scn = take(4 * (size_t)p.n_tiles);
@@ -202,6 +208,7 @@ Layout make_layout(const tled_ctx *c) {
     L.stat_part = take(8 * 8 * tled::kStatBlocks);
     L.stat_out = take(8 * 8);
     L.staging = take(8 * std::max<size_t>(3 * nn, 2 * (size_t)c->n_probes));
+    L.cem = take(cem_on(c) ? 8 * nn : 0);
     L.total = off;
     return L;
 }
@@ -452,15 +459,15 @@ ScenDev scen_dev(const Scenario &s) {
 
 int upload_scenarios(tled_ctx *c) {
     std::vector<ScenDev> d(c->sc.size());
-    std::vector<double> src(10 * (size_t)source_capacity(c), 0.0);
+    std::vector<double> src(tled::kSrcRow * (size_t)source_capacity(c), 0.0);
     for (size_t i = 0; i < c->sc.size(); i++) {
         d[i] = scen_dev(c->sc[i]);
         for (size_t q = 0; q < c->sc[i].src.size(); q++) {
             const tled_source &s = c->sc[i].src[q];
-            double *r = &src[10 * (c->sc[i].src_off + q)];
+            double *r = &src[tled::kSrcRow * (c->sc[i].src_off + q)];
             r[0] = s.c0[0]; r[1] = s.c0[1]; r[2] = s.c0[2];
             r[3] = s.vel[0]; r[4] = s.vel[1]; r[5] = s.vel[2];
-            r[6] = s.sigma; r[7] = s.power; r[8] = s.t_on; r[9] = s.t_off;
+            r[6] = s.sigma; r[7] = s.power; r[8] = s.t_on; r[9] = s.t_off; r[10] = (double)s.shape;
         }
     }
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.scn, d.data(), sizeof(ScenDev) * d.size(), cudaMemcpyHostToDevice, c->stream));
@@ -503,6 +510,7 @@ int write_state(tled_ctx *c, const double *u, const double *v, const double *T, 
             for (int q = 0; q < np * 6; q++) vs[visc_index(np, e, q)] = (float)visc[eo * np * 6 + q];
         }
     if (np) CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.visc, vs.data(), vs.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    if (cem_on(c)) CUDA_TRY(c, cudaMemsetAsync(c->ws + c->L.cem, 0, 8 * (size_t)nn, c->stream));  // dose restarts
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return TLED_OK;
 }
@@ -569,6 +577,9 @@ int validate_material(tled_ctx *c, const tled_material *m, int64_t ne, const dou
         gsum += m->prony_g[i];
     }
     if (gsum >= 1.0) return fail(c, TLED_E_ARG, "sum of Prony g must be < 1");
+    if (!(m->alpha_fibre_ratio >= 0) || !(m->k_fibre_ratio >= 0) || !std::isfinite(m->alpha_fibre_ratio) ||
+        !std::isfinite(m->k_fibre_ratio))
+        return fail(c, TLED_E_ARG, "fibre ratios must be finite and >= 0 (0 or 1: isotropic)");
     if (per_elem)
         for (int64_t i = 0; i < 6 * ne; i++)
             if (!std::isfinite(per_elem[i]) || (i % 6 != 5 && per_elem[i] < 0))
@@ -730,7 +741,9 @@ int tled_set_heat_sources(tled_ctx *c, int32_t n, const tled_source *src) {
     if (int rc = require_single(c)) return rc;
     if (n < 0 || n > tled::kMaxSources || (n > 0 && !src)) return fail(c, TLED_E_ARG, "0 <= n <= 16 sources");
     for (int i = 0; i < n; i++)
-        if (!(src[i].sigma > 0) || !std::isfinite(src[i].power)) return fail(c, TLED_E_ARG, "source sigma must be > 0");
+        if (!(src[i].sigma > 0) || !std::isfinite(src[i].power) ||
+            (src[i].shape != TLED_SRC_GAUSSIAN && src[i].shape != TLED_SRC_SPHERE))
+            return fail(c, TLED_E_ARG, "source sigma must be > 0 and its shape TLED_SRC_GAUSSIAN or TLED_SRC_SPHERE");
     single(c).src.assign(src, src + n);
     if (c->inited) {
         cudaSetDevice(c->device);
@@ -770,16 +783,19 @@ int tled_batch_add(tled_ctx *b, const tled_ctx *scenario, int64_t n_steps, int32
     if (n_steps <= 0) return fail(b, TLED_E_ARG, "n_steps must be > 0");
     const Scenario &s = scenario->sc[0];
     if (s.npe == 0 || !s.have_mat) return fail(b, TLED_E_STATE, "the scenario needs a mesh and a material");
+    if (s.prm.flags & TLED_CEM43) return fail(b, TLED_E_ARG, "CEM43 is tracked for single problems only");
     if (!b->sc.empty()) {
         const Scenario &f = b->sc[0];
         const tled_material &a = f.mat, &m = s.mat;
         bool same = a.n_prony == m.n_prony && a.T0 == m.T0 && a.Ta == m.Ta && a.lnA == m.lnA && a.Ea == m.Ea &&
+                    fibre_ratio(a.alpha_fibre_ratio) == fibre_ratio(m.alpha_fibre_ratio) &&
+                    fibre_ratio(a.k_fibre_ratio) == fibre_ratio(m.k_fibre_ratio) &&
                     a.beta_c == m.beta_c && a.beta_k == m.beta_k && a.T_ref == m.T_ref &&
                     f.prm.flags == s.prm.flags && f.prm.kappa_hg == s.prm.kappa_hg &&
                     f.prm.kappa_hgT == s.prm.kappa_hgT && f.ramp == s.ramp;
         if (!same)
             return fail(b, TLED_E_ARG,
-                        "scenarios of a batch must share n_prony, T0, Ta, Arrhenius constants, c/k slopes, flags, "
+                        "scenarios of a batch must share n_prony, T0, Ta, Arrhenius constants, c/k slopes, fibre ratios, flags, "
                         "hourglass coefficients and ramp time");
     }
     invalidate(b);
@@ -832,7 +848,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     int src_off = 0;
     for (auto &s : c->sc) {
         tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
-                        s.prm, &s.dt_mech, &s.dt_th);
+                        s.fib.empty() ? nullptr : s.fib.data(), s.prm, &s.dt_mech, &s.dt_th);
         s.dt = s.prm.dt > 0 ? s.prm.dt : s.prm.dt_safety * std::min(s.dt_mech, s.dt_th);
         s.src_off = src_off;
         src_off += c->batch ? (int)s.src.size() : kSingleSources;
@@ -977,6 +993,11 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.khg = (float)s0.prm.kappa_hg;
     A.khgT = (float)s0.prm.kappa_hgT;
     A.ramp_time = s0.ramp;
+    A.cem = cem_on(c) ? dptr<double>(c, L.cem) : nullptr;
+    A.ani_alpha = (float)fibre_ratio(m.alpha_fibre_ratio);
+    A.ani_k = (float)fibre_ratio(m.k_fibre_ratio);
+    A.ani = fibre_ratio(m.alpha_fibre_ratio) != 1.0 || fibre_ratio(m.k_fibre_ratio) != 1.0;
+    A.T0 = m.T0;
     A.n_tiles = p.n_tiles;
     tled::tile_smem_layout(A, npe);
     CUDA_TRY(c, tled::tile_kernel_setup(A, npe));
@@ -1013,7 +1034,7 @@ int tled_stable_dt(tled_ctx *c, double *dt_mech, double *dt_thermal) {
     const Scenario &s = single(c);
     if (s.npe == 0 || !s.have_mat) return fail(c, TLED_E_STATE, "set the mesh and the material first");
     tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
-                    s.prm, dt_mech, dt_thermal);
+                    s.fib.empty() ? nullptr : s.fib.data(), s.prm, dt_mech, dt_thermal);
     return TLED_OK;
 }
 
@@ -1034,7 +1055,8 @@ static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     CUDA_TRY(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < K && e == cudaSuccess; k++) {
-        e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
+        if (c->A.cem) e = tled::launch_cem43(c->A, c->nn, k, c->cap);  // dose at T(t), before the update
+        if (e == cudaSuccess) e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
         if (e == cudaSuccess) e = tled::launch_shared_step(c->A, c->shared_blocks, k, c->cap);
     }
     if (e == cudaSuccess) e = tled::launch_bump(c->A, K, c->cap);
@@ -1121,6 +1143,21 @@ static int readback(tled_ctx *c, double *out, int where, int mode) {
 int tled_get_displacement(tled_ctx *c, double *out, int where) { return readback(c, out, where, 0); }
 int tled_get_temperature(tled_ctx *c, double *out, int where) { return readback(c, out, where, 1); }
 int tled_get_damage(tled_ctx *c, double *out, int where) { return readback(c, out, where, 2); }
+int tled_get_cem43(tled_ctx *c, double *out, int where) {
+    if (c && c->inited && !c->A.cem) return fail(c, TLED_E_STATE, "CEM43 is tracked only with the TLED_CEM43 flag");
+    return readback(c, out, where, 3);
+}
+
+int tled_get_isotherm_volume(tled_ctx *c, double T_iso, double *volume) {
+    if (!c || !volume || !std::isfinite(T_iso)) return fail(c, TLED_E_ARG, "NULL volume or non-finite temperature");
+    if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, tled::launch_isotherm(c->A, c->nn, T_iso - c->sc[0].mat.T0, dptr<double>(c, c->L.stat_part),
+                                      dptr<double>(c, c->L.stat_out), c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(volume, c->ws + c->L.stat_out, 8, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return TLED_OK;
+}
 
 int tled_get_probes(tled_ctx *c, double *out, int where) {
     if (!c || !out) return fail(c, TLED_E_ARG, "NULL output");
@@ -1209,8 +1246,9 @@ int tled_step_timed(tled_ctx *c, int64_t n, double *ms) {
     for (auto &e : ev) CUDA_TRY(c, cudaEventCreate(&e));
     cudaError_t err = cudaSuccess;
     for (int64_t i = 0; i < n && err == cudaSuccess; i++) {
+        if (c->A.cem) err = tled::launch_cem43(c->A, c->nn, 0, c->stream);
         cudaEventRecord(ev[3 * i], c->stream);
-        err = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
+        if (err == cudaSuccess) err = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
         cudaEventRecord(ev[3 * i + 1], c->stream);
         if (err == cudaSuccess) err = tled::launch_shared_step(c->A, c->shared_blocks, 0, c->stream);
         cudaEventRecord(ev[3 * i + 2], c->stream);
@@ -1386,8 +1424,8 @@ struct CkptHeader {
 int tled_save_state(tled_ctx *c, void *buf, int64_t *bytes) {
     if (!c || !bytes) return fail(c, TLED_E_ARG, "NULL size pointer");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
-    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->plan.ne_pad;
-    const int64_t payload = (int64_t)(3 * 16 * nn + 4 * nv);
+    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->plan.ne_pad, nc = c->A.cem ? nn : 0;
+    const int64_t payload = (int64_t)(3 * 16 * nn + 4 * nv + 8 * nc);
     const int64_t need = (int64_t)sizeof(CkptHeader) + payload;
     if (!buf) {
         *bytes = need;
@@ -1400,6 +1438,7 @@ int tled_save_state(tled_ctx *c, void *buf, int64_t *bytes) {
     CUDA_TRY(c, cudaMemcpyAsync(p + 16 * nn, c->ws + c->L.lo, 16 * nn, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(p + 32 * nn, c->ws + c->L.vel, 16 * nn, cudaMemcpyDeviceToHost, c->stream));
     if (nv) CUDA_TRY(c, cudaMemcpyAsync(p + 48 * nn, c->ws + c->L.visc, 4 * nv, cudaMemcpyDeviceToHost, c->stream));
+    if (nc) CUDA_TRY(c, cudaMemcpyAsync(p + 48 * nn + 4 * nv, c->ws + c->L.cem, 8 * nc, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     CkptHeader h{};
     std::memcpy(h.magic, "TLEDCKP2", 8);
@@ -1426,8 +1465,8 @@ int tled_load_state(tled_ctx *c, const void *buf, int64_t bytes) {
     CkptHeader h;
     std::memcpy(&h, buf, sizeof(h));
     if (std::memcmp(h.magic, "TLEDCKP2", 8) != 0) return fail(c, TLED_E_FORMAT, "bad checkpoint magic");
-    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->plan.ne_pad;
-    const int64_t payload = (int64_t)(3 * 16 * nn + 4 * nv);
+    const size_t nn = c->nn, nv = (size_t)n_prony(c) * 6 * c->plan.ne_pad, nc = c->A.cem ? nn : 0;
+    const int64_t payload = (int64_t)(3 * 16 * nn + 4 * nv + 8 * nc);
     if (h.version != TLED_VERSION || h.npe != (uint32_t)c->npe || h.nn != c->nn || h.ne != c->ne ||
         h.n_prony != n_prony(c) || h.n_scn != (int32_t)c->sc.size() || h.payload != payload ||
         bytes < (int64_t)sizeof(h) + payload)
@@ -1440,6 +1479,7 @@ int tled_load_state(tled_ctx *c, const void *buf, int64_t bytes) {
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.lo, p + 16 * nn, 16 * nn, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.vel, p + 32 * nn, 16 * nn, cudaMemcpyHostToDevice, c->stream));
     if (nv) CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.visc, p + 48 * nn, 4 * nv, cudaMemcpyHostToDevice, c->stream));
+    if (nc) CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.cem, p + 48 * nn + 4 * nv, 8 * nc, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return upload_clock(c, h.step, h.t0);  // exact clocks: the same per-scenario times as the writer's
 }

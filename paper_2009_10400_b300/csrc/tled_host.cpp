@@ -78,7 +78,8 @@ static double cross_norm_half(const double *d1, const double *d2) {
 // perfusion conductance).  Per-element moduli come from `mat6` ([ne][6], caller
 // order) when given.
 void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const tled_material &m,
-               const double *mat6, const tled_params &p, double *dt_mech, double *dt_th) {
+               const double *mat6, const double *fib, const tled_params &p, double *dt_mech, double *dt_th) {
+    const double rk = m.k_fibre_ratio == 0.0 ? 1.0 : m.k_fibre_ratio;  // conductivity along the fibre / transverse
     static const int HF[6][4] = {{0, 1, 2, 3}, {4, 5, 6, 7}, {0, 1, 5, 4}, {1, 2, 6, 5}, {2, 3, 7, 6}, {3, 0, 4, 7}};
     static const int TF[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
     const bool td = (p.flags & TLED_TEMP_DEP) != 0;
@@ -136,10 +137,14 @@ void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
             }
         }
         const double khgT = p.kappa_hgT * V * BB / 8.0;
+        const double *af = fib ? fib + 3 * e : m.a0;
+        double Bm[8];  // dh_a/dX . a0 for the anisotropic conduction D = k (I + (rk - 1) a0 a0) at F = I
+        for (int a = 0; a < npe; a++) Bm[a] = B[a][0] * af[0] + B[a][1] * af[1] + B[a][2] * af[2];
         for (int a = 0; a < npe; a++) {
             double rs = 0;
             for (int b = 0; b < npe; b++) {
-                double K = V * kmax * (B[a][0] * B[b][0] + B[a][1] * B[b][1] + B[a][2] * B[b][2]);
+                double K = V * kmax * (B[a][0] * B[b][0] + B[a][1] * B[b][1] + B[a][2] * B[b][2] +
+                                       (rk - 1.0) * Bm[a] * Bm[b]);
                 if (npe == 8)
                     K += kmax * khgT * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2] + G[a][3] * G[b][3]);
                 rs += std::fabs(K);

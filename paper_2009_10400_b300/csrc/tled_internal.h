@@ -19,6 +19,7 @@ constexpr int kNsMax = 256;        // interior nodes whose state is staged in sh
 // per-tile gather record (uint16): slot offsets [kTile * npe], then row offsets [kMaxLocal + 8]
 constexpr int csr_rec_u16(int npe) { return kTile * npe + kMaxLocal + 8; }
 constexpr int kMaxSources = 16;
+constexpr int kSrcRow = 11;        // doubles per source in the device table: c0, vel, sigma, P, t_on, t_off, shape
 constexpr int kTileInfo = 8;       // ints per tile record
 
 // device status word bits
@@ -89,7 +90,9 @@ struct StepArgs {
     int64_t n_interior, n_shared;
     // scenarios (a single problem is one scenario)
     const struct ScenDev *scn;  // [n_scn] constant per-scenario parameters
-    const double *src;     // [total sources][10]: c0 xyz, velocity xyz, sigma, peak, t_on, t_off
+    const double *src;     // [total sources][kSrcRow]: c0 xyz, velocity xyz, sigma/radius, peak, t_on, t_off, shape
+    double *cem;           // [nn] CEM43 dose (minutes), or nullptr
+    double T0;             // initial temperature, C (theta = T - T0)
     double *scn_time;      // [n_scn] time t0 at step 0; step n is at t0 + n dt
     int64_t *scn_step;     // [n_scn] steps taken at the start of the current graph chunk
     const int *tile_scn;   // [n_tiles] scenario of each tile
@@ -113,6 +116,8 @@ struct StepArgs {
     float theta_a;                        // Ta - T0
     float lnA, Ea_R, T0_K;                // T0 + 273.15
     float khg, khgT;                      // kappa_hg, kappa_hgT
+    int ani;                              // anisotropic thermal physics (the ratios below differ from 1)
+    float ani_alpha, ani_k;               // fibre / transverse expansion and conductivity
     double ramp_time;
 };
 
@@ -120,12 +125,17 @@ struct StepArgs {
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s);
 int tile_grid(const StepArgs &a, int npe, int n_sm);  // persistent grid size
 int shared_grid(const StepArgs &a, int n_sm);  // persistent grid of the shared-node kernel
+// CEM43 dose += dt R^(43 - T) / 60 at every node (single problems; before the step's update)
+cudaError_t launch_cem43(const StepArgs &a, int64_t nn, int k, cudaStream_t s);
+// sum of the lumped volumes of the nodes with theta >= theta_iso, FP64, fixed order: out[0]
+cudaError_t launch_isotherm(const StepArgs &a, int64_t nn, double theta_iso, double *partials, double *out,
+                            cudaStream_t s);
 cudaError_t launch_shared_step(const StepArgs &a, int n_blocks, int k, cudaStream_t s);
 cudaError_t launch_bump(const StepArgs &a, int K, cudaStream_t s);
 // temperature and damage at probe points: out [2][n]
 cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w, int64_t n, double T0, double *out,
                           cudaStream_t s);
-// read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction
+// read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction, 3 CEM43
 cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,
                             cudaStream_t s);
 void tile_smem_layout(StepArgs &a, int npe);  // fills the sm_* fields and csr_stride
@@ -144,8 +154,10 @@ cudaError_t noalloc_scratch(int device, double **ptr);
 
 // host geometry and planning (tled_host.cpp)
 bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V);
+// fib: per-element fibres [ne][3] or NULL (m.a0); the conduction bound uses the anisotropic
+// conductivity at F = I when m.k_fibre_ratio is not 0 or 1
 void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const tled_material &m,
-               const double *mat6, const tled_params &p, double *dt_mech, double *dt_th);
+               const double *mat6, const double *fib, const tled_params &p, double *dt_mech, double *dt_th);
 // group: optional [ne] group id per element (scenario rank); tiles never span groups and
 // follow ascending group order.
 int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const int8_t *etype,

@@ -63,7 +63,9 @@ struct ScenStep {
     float dtf, inv_dt, damp_a, damp_b, Qm;
     float pr_a[4], pr_b[4];
     int n;
-    float cx[kMaxSources], cy[kMaxSources], cz[kMaxSources], inv2s2[kMaxSources], P[kMaxSources];
+    // source s adds P exp(-d^2 inv2s2) where d^2 <= r2: a Gaussian (r2 infinite) or a
+    // uniform sphere (inv2s2 = 0, r2 = radius^2)
+    float cx[kMaxSources], cy[kMaxSources], cz[kMaxSources], inv2s2[kMaxSources], r2[kMaxSources], P[kMaxSources];
 };
 
 // Fill P for scenario s at step k of the current chunk.  Called by all threads of
@@ -86,11 +88,13 @@ __device__ __forceinline__ void prepare_scen(const StepArgs &A, int s, int k, Sc
         P.n = D.n_src;
     }
     for (int q = lane; q < D.n_src; q += nlanes) {
-        const double *p = A.src + 10 * (int64_t)(D.src_off + q);
+        const double *p = A.src + kSrcRow * (int64_t)(D.src_off + q);
         P.cx[q] = (float)(p[0] + p[3] * t);
         P.cy[q] = (float)(p[1] + p[4] * t);
         P.cz[q] = (float)(p[2] + p[5] * t);
-        P.inv2s2[q] = (float)(0.5 / (p[6] * p[6]));
+        const bool sphere = p[10] == 1.0;
+        P.inv2s2[q] = sphere ? 0.f : (float)(0.5 / (p[6] * p[6]));
+        P.r2[q] = sphere ? (float)(p[6] * p[6]) : INFINITY;
         P.P[q] = (t >= p[8] && t < p[9]) ? (float)p[7] : 0.f;
     }
 }
@@ -184,7 +188,8 @@ __device__ __forceinline__ void node_update(const StepArgs &A, const ScenStep &S
     float Q = S.Qm;
     for (int s = 0; s < S.n; s++) {
         const float dx = px - S.cx[s], dy = py - S.cy[s], dz = pz - S.cz[s];
-        Q += S.P[s] * __expf(-(dx * dx + dy * dy + dz * dz) * S.inv2s2[s]);
+        const float d2 = dx * dx + dy * dy + dz * dz;
+        Q += d2 <= S.r2[s] ? S.P[s] * __expf(-d2 * S.inv2s2[s]) : 0.f;
     }
     if (!(mask & TLED_FIX_T)) {
         const float dth = dt * iC * (-f.w + X.w * Q - nc.w * (theta - A.theta_a));
@@ -275,7 +280,9 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, i
 // One element: deformation gradient, thermal split, stress, Prony, nodal
 // forces + hourglass, thermal loads.  Corner contributions are written to the
 // chunk's slot buffer at [corner][ec] (conflict-free).
-template <int NPE, int NPR>
+// ANI: transversely isotropic thermal expansion about the fibre (Eq. 11) and
+// conductivity along the current fibre; otherwise isotropic (F_th = lambda I).
+template <int NPE, int NPR, bool ANI>
 __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &SP, int64_t e, int ec, const int *cl,
                                              ElemIn<NPR> &E, const float4 *__restrict__ s_xu,
                                              const float4 *__restrict__ s_X, float4 *__restrict__ slot,
@@ -357,11 +364,38 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     Ee[4] = 0.5f * (H[1][2] + H[2][1] + H[0][1] * H[0][2] + H[1][1] * H[1][2] + H[2][1] * H[2][2]);
     Ee[5] = 0.5f * (H[0][2] + H[2][0] + H[0][0] * H[0][2] + H[1][0] * H[1][2] + H[2][0] * H[2][2]);
     const float d1 = dl + 0.5f * dl * dl;
+    // anisotropic: F_th^-1 = (I - g m m) / lambda_i, g = (lambda_m - lambda_i) / lambda_m, m = fibre,
+    // E_el = [E - d1 I - g (m Em + Em m) + (g^2 m.E.m - g + g^2/2) m m] / lambda_i^2 (Em = E m)
+    float lm = lam, gam = 0.f, mEm = 0.f, det_th = 1.f;
+    if constexpr (ANI) {
+        const float dm = (A.flags & TLED_EXPANSION) ? A.ani_alpha * al * the : 0.f;
+        lm = 1.f + dm;
+        gam = __fdividef(dm - dl, lm);
+        const float Emx = Ee[0] * ax + Ee[3] * ay + Ee[5] * az;
+        const float Emy = Ee[3] * ax + Ee[1] * ay + Ee[4] * az;
+        const float Emz = Ee[5] * ax + Ee[4] * ay + Ee[2] * az;
+        mEm = ax * Emx + ay * Emy + az * Emz;
+        const float cmm = gam * gam * mEm - gam + 0.5f * gam * gam;
+        Ee[0] += -2.f * gam * ax * Emx + cmm * ax * ax;
+        Ee[1] += -2.f * gam * ay * Emy + cmm * ay * ay;
+        Ee[2] += -2.f * gam * az * Emz + cmm * az * az;
+        Ee[3] += -gam * (ax * Emy + Emx * ay) + cmm * ax * ay;
+        Ee[4] += -gam * (ay * Emz + Emy * az) + cmm * ay * az;
+        Ee[5] += -gam * (ax * Emz + Emx * az) + cmm * ax * az;
+    }
     Ee[0] = (Ee[0] - d1) * il2; Ee[1] = (Ee[1] - d1) * il2; Ee[2] = (Ee[2] - d1) * il2;
     Ee[3] *= il2; Ee[4] *= il2; Ee[5] *= il2;
-    // J_el - 1 = ((J - 1) - (lambda^3 - 1)) / lambda^3
-    const float l3m1 = dl * (3.f + dl * (3.f + dl));
-    const float jel = (Jm1 - l3m1) * (il2 * il);
+    // J_el - 1 = ((J - 1) - (det F_th - 1)) / det F_th; det F_th = lambda_i^2 lambda_m
+    float jel;
+    if constexpr (ANI) {
+        const float dm = lm - 1.f;
+        const float t3m1 = dl * (2.f + dl) + dm * (1.f + dl) * (1.f + dl);
+        det_th = 1.f + t3m1;
+        jel = __fdividef(Jm1 - t3m1, det_th);
+    } else {
+        const float l3m1 = dl * (3.f + dl * (3.f + dl));
+        jel = (Jm1 - l3m1) * (il2 * il);
+    }
     const float Jel = 1.f + jel;
     if (!(Jel > 0.f)) {
         atomicOr(A.status, kStatusInverted);
@@ -413,6 +447,21 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     float St[6];
 #pragma unroll
     for (int s = 0; s < 6; s++) St[s] = lam * (ciso * M[s] + cvol * Ci[s] + cf * (aa[s] - cI4 * Ci[s]));
+    if constexpr (ANI) {
+        // Eq. (10): S_0 = det F_th F_th^-1 S_i F_th^-T = lambda_m [S_i - g (m Sm + Sm m) + g^2 (m.S.m) m m]
+#pragma unroll
+        for (int s = 0; s < 6; s++) St[s] = ciso * M[s] + cvol * Ci[s] + cf * (aa[s] - cI4 * Ci[s]);  // S_i
+        const float Smx = St[0] * ax + St[3] * ay + St[5] * az;
+        const float Smy = St[3] * ax + St[1] * ay + St[4] * az;
+        const float Smz = St[5] * ax + St[4] * ay + St[2] * az;
+        const float g2 = gam * gam * (ax * Smx + ay * Smy + az * Smz);
+        St[0] = lm * (St[0] - 2.f * gam * ax * Smx + g2 * ax * ax);
+        St[1] = lm * (St[1] - 2.f * gam * ay * Smy + g2 * ay * ay);
+        St[2] = lm * (St[2] - 2.f * gam * az * Smz + g2 * az * az);
+        St[3] = lm * (St[3] - gam * (ax * Smy + Smx * ay) + g2 * ax * ay);
+        St[4] = lm * (St[4] - gam * (ay * Smz + Smy * az) + g2 * ay * az);
+        St[5] = lm * (St[5] - gam * (ax * Smz + Smx * az) + g2 * ax * az);
+    }
     {
         float S0[6];
 #pragma unroll
@@ -446,10 +495,27 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     // fT_a = V dh_a/dX . q = r . Xi_a with r = s V J0^-1 q
     float kT = kc;
     if (A.flags & TLED_TEMP_DEP) kT *= 1.f + A.beta_k * (the - A.Tref_m_T0);
-    const float kq = kT * lam * Jel;
-    const float q0 = kq * (Ci[0] * gth[0] + Ci[3] * gth[1] + Ci[5] * gth[2]);
-    const float q1 = kq * (Ci[3] * gth[0] + Ci[1] * gth[1] + Ci[4] * gth[2]);
-    const float q2 = kq * (Ci[5] * gth[0] + Ci[4] * gth[1] + Ci[2] * gth[2]);
+    float q0, q1, q2;
+    if constexpr (ANI) {
+        // J C^-1 = det F_th J_el F_th^-1 C_el^-1 F_th^-T, plus the conduction along the current
+        // fibre a = F m / |F m|: F^-1 (k_f - k) a a F^-T = (k_f - k) m m / (m.C.m), m.C.m = 1 + 2 m.E.m
+        const float mg = ax * gth[0] + ay * gth[1] + az * gth[2];
+        const float p0 = il * (gth[0] - gam * mg * ax), p1 = il * (gth[1] - gam * mg * ay), p2 = il * (gth[2] - gam * mg * az);
+        const float c0 = Ci[0] * p0 + Ci[3] * p1 + Ci[5] * p2;
+        const float c1 = Ci[3] * p0 + Ci[1] * p1 + Ci[4] * p2;
+        const float c2 = Ci[5] * p0 + Ci[4] * p1 + Ci[2] * p2;
+        const float mc = ax * c0 + ay * c1 + az * c2;
+        const float kq = kT * det_th * Jel * il;
+        const float kf = __fdividef(kT * (A.ani_k - 1.f) * (1.f + Jm1) * mg, 1.f + 2.f * mEm);
+        q0 = kq * (c0 - gam * mc * ax) + kf * ax;
+        q1 = kq * (c1 - gam * mc * ay) + kf * ay;
+        q2 = kq * (c2 - gam * mc * az) + kf * az;
+    } else {
+        const float kq = kT * lam * Jel;
+        q0 = kq * (Ci[0] * gth[0] + Ci[3] * gth[1] + Ci[5] * gth[2]);
+        q1 = kq * (Ci[3] * gth[0] + Ci[1] * gth[1] + Ci[4] * gth[2]);
+        q2 = kq * (Ci[5] * gth[0] + Ci[4] * gth[1] + Ci[2] * gth[2]);
+    }
     float r[3];
 #pragma unroll
     for (int k = 0; k < 3; k++) r[k] = sV * (Ji[3 * k] * q0 + Ji[3 * k + 1] * q1 + Ji[3 * k + 2] * q2);
@@ -572,7 +638,7 @@ __device__ void prefetch_tile(const StepArgs &A, int t) {
     }
 }
 
-template <int NPE, int NPR>
+template <int NPE, int NPR, bool ANI>
 __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
     __shared__ ScenStep S;
@@ -648,9 +714,9 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         // ---- 3. element pass
         if (active) {
             float *gv = A.visc + (int64_t)t * A.n_prony * 6 * kTile + ec;
-            if constexpr (NPE != 0) element_step<NPE, NPR>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
-            else if (npe == 8) element_step<8, NPR>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
-            else element_step<4, NPR>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            if constexpr (NPE != 0) element_step<NPE, NPR, ANI>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else if (npe == 8) element_step<8, NPR, ANI>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else element_step<4, NPR, ANI>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
         }
         __syncthreads();
         // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum,
@@ -746,6 +812,39 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
     }
 }
 
+// CEM43 thermal dose (Sapareto-Dewey), explicit in T(t): dose += dt R^(43 - T) / 60
+// minutes, R = 0.5 at or above 43 C, 0.25 below; FP64 per node, single problems
+__global__ void cem43_kernel(const StepArgs A, int64_t nn) {
+    const double dt = A.scn[0].dt;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
+        const double T = A.T0 + ((double)A.xu[g].w + (double)A.lo[g].w);
+        const double x = T - 43.0;  // R^(43 - T) = 2^(x) or 4^(x)
+        A.cem[g] += dt * exp2(T >= 43.0 ? x : 2.0 * x) / 60.0;
+    }
+}
+
+// volume at or above an isotherm: sum of V_i over theta_i >= theta_iso (fixed grid, fixed tree)
+__global__ void __launch_bounds__(256) isotherm_partial_kernel(const StepArgs A, int64_t nn, double th_iso,
+                                                               double *partials) {
+    double v = 0.0;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x)
+        if ((double)A.xu[g].w + (double)A.lo[g].w >= th_iso) v += (double)A.X0[g].w;
+    __shared__ double sh[256];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+__global__ void sum_final_kernel(const double *partials, int n, double *out) {
+    if (threadIdx.x) return;
+    double s = 0.0;
+    for (int i = 0; i < n; i++) s += partials[i];
+    out[0] = s;
+}
+
 // advance every scenario's step counter by K (its time is t0 + n dt)
 __global__ void bump_kernel(const StepArgs A, int K) {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < A.n_scn; s += gridDim.x * blockDim.x) A.scn_step[s] += K;
@@ -771,8 +870,9 @@ __global__ void probe_kernel(const float4 *__restrict__ hi, const float4 *__rest
 }
 
 __global__ void readback_kernel(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
-                                const float4 *__restrict__ vel, const int32_t *__restrict__ node_new, int64_t nn,
-                                double T0, int mode, double *__restrict__ out) {
+                                const float4 *__restrict__ vel, const double *__restrict__ cem,
+                                const int32_t *__restrict__ node_new, int64_t nn, double T0, int mode,
+                                double *__restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
     const int64_t g = node_new[i];
@@ -783,8 +883,10 @@ __global__ void readback_kernel(const float4 *__restrict__ hi, const float4 *__r
         out[3 * i + 2] = (double)h.z + (double)l.z;
     } else if (mode == 1) {
         out[i] = T0 + ((double)hi[g].w + (double)lo[g].w);
-    } else {
+    } else if (mode == 2) {
         out[i] = -expm1(-(double)vel[g].w);
+    } else {
+        out[i] = cem[g];
     }
 }
 
@@ -905,16 +1007,29 @@ __global__ void __launch_bounds__(256) energy_partial_kernel(const StepArgs A, d
                             H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
                             H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
         const double Jm1 = trH + 0.5 * (trH * trH - trH2) + detH;
-        // E_el = (E - (delta + delta^2/2) I) / lambda^2, E = (H + H^T + H^T H) / 2
-        double Ee[3][3];
-        const double d1 = dl + 0.5 * dl * dl, il2 = 1.0 / (lam * lam);
+        // E_el = F_th^-T E F_th^-1 + (F_th^-T F_th^-1 - I) / 2, E = (H + H^T + H^T H) / 2, with
+        // F_th^-1 = (I - g m m) / lambda_i, g = (lambda_m - lambda_i) / lambda_m (m the fibre;
+        // isotropic: g = 0, lambda_m = lambda_i)
+        const double dm = A.ani && (A.flags & TLED_EXPANSION) ? (double)A.ani_alpha * al * the : dl;
+        const double lm = 1.0 + dm, g = (dm - dl) / lm;
+        double E[3][3], Em[3] = {0, 0, 0}, mEm = 0.0;
         for (int i = 0; i < 3; i++)
             for (int j = 0; j < 3; j++) {
                 double e = 0.5 * (H[i][j] + H[j][i]);
                 for (int k = 0; k < 3; k++) e += 0.5 * H[k][i] * H[k][j];
-                Ee[i][j] = (e - (i == j ? d1 : 0.0)) * il2;
+                E[i][j] = e;
             }
-        const double jel = (Jm1 - dl * (3.0 + dl * (3.0 + dl))) * il2 / lam;  // J_el - 1
+        for (int i = 0; i < 3; i++) {
+            for (int j = 0; j < 3; j++) Em[i] += E[i][j] * a0[j];
+            mEm += a0[i] * Em[i];
+        }
+        double Ee[3][3];
+        const double d1 = dl + 0.5 * dl * dl, il2 = 1.0 / (lam * lam), cmm = g * g * mEm - g + 0.5 * g * g;
+        for (int i = 0; i < 3; i++)
+            for (int j = 0; j < 3; j++)
+                Ee[i][j] = (E[i][j] - (i == j ? d1 : 0.0) - g * (a0[i] * Em[j] + Em[i] * a0[j]) + cmm * a0[i] * a0[j]) * il2;
+        const double th3m1 = dl * (2.0 + dl) + dm * (1.0 + dl) * (1.0 + dl);  // det F_th - 1
+        const double jel = (Jm1 - th3m1) / (1.0 + th3m1);                      // J_el - 1
         const double Jm23m1 = expm1(-(2.0 / 3.0) * log1p(jel));
         const double Jm23 = 1.0 + Jm23m1;
         const double trE = Ee[0][0] + Ee[1][1] + Ee[2][2];
@@ -924,7 +1039,7 @@ __global__ void __launch_bounds__(256) energy_partial_kernel(const StepArgs A, d
         const double I1m3 = 3.0 * Jm23m1 + 2.0 * Jm23 * trE;  // I1bar - 3
         const double x4 = Jm23m1 + 2.0 * Jm23 * aEa;          // I4bar - 1
         const double psif = k2 > 0.0 ? k1 / (2.0 * k2) * expm1(k2 * x4 * x4) : 0.5 * k1 * x4 * x4;
-        w_el += V * lam * lam * lam * (0.5 * mu * I1m3 + 0.5 * kap * jel * jel + psif);
+        w_el += V * (1.0 + th3m1) * (0.5 * mu * I1m3 + 0.5 * kap * jel * jel + psif);
         if (npe == 8) {
             double jn2 = 0.0;
             for (int k = 0; k < 9; k++) jn2 += Ji[k] * Ji[k];
@@ -989,34 +1104,41 @@ static cudaError_t set_smem(K kern, int bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// the tile kernel instance for (element type, Prony terms): npe 8, 4 or 0 (mixed), n_prony 0..4
+// the tile kernel instance for (element type, Prony terms, anisotropic thermal physics):
+// npe 8, 4 or 0 (mixed), n_prony 0..4, ani
 using TileKernel = void (*)(const StepArgs, const int);
-template <int NPE>
+template <int NPE, bool ANI>
 static TileKernel tile_kernel_npr(int n_prony) {
     switch (n_prony) {
-        case 0: return tile_step_kernel<NPE, 0>;
-        case 1: return tile_step_kernel<NPE, 1>;
-        case 2: return tile_step_kernel<NPE, 2>;
-        case 3: return tile_step_kernel<NPE, 3>;
-        default: return tile_step_kernel<NPE, 4>;
+        case 0: return tile_step_kernel<NPE, 0, ANI>;
+        case 1: return tile_step_kernel<NPE, 1, ANI>;
+        case 2: return tile_step_kernel<NPE, 2, ANI>;
+        case 3: return tile_step_kernel<NPE, 3, ANI>;
+        default: return tile_step_kernel<NPE, 4, ANI>;
     }
 }
-static TileKernel tile_kernel(int npe, int n_prony) {
-    return npe == 8 ? tile_kernel_npr<8>(n_prony) : npe == 4 ? tile_kernel_npr<4>(n_prony) : tile_kernel_npr<0>(n_prony);
+template <bool ANI>
+static TileKernel tile_kernel_ani(int npe, int n_prony) {
+    return npe == 8 ? tile_kernel_npr<8, ANI>(n_prony)
+         : npe == 4 ? tile_kernel_npr<4, ANI>(n_prony)
+                    : tile_kernel_npr<0, ANI>(n_prony);
+}
+static TileKernel tile_kernel(const StepArgs &a, int npe) {
+    return a.ani ? tile_kernel_ani<true>(npe, a.n_prony) : tile_kernel_ani<false>(npe, a.n_prony);
 }
 
-cudaError_t tile_kernel_setup(const StepArgs &a, int npe) { return set_smem(tile_kernel(npe, a.n_prony), a.sm_total); }
+cudaError_t tile_kernel_setup(const StepArgs &a, int npe) { return set_smem(tile_kernel(a, npe), a.sm_total); }
 
 int tile_grid(const StepArgs &a, int npe, int n_sm) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel(npe, a.n_prony), kBlock, a.sm_total);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel(a, npe), kBlock, a.sm_total);
     if (e != cudaSuccess || per_sm < 1) per_sm = 1;
     return std::max(1, std::min(a.n_tiles, per_sm * n_sm));
 }
 
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s) {
     if (a.n_tiles <= 0) return cudaSuccess;
-    tile_kernel(npe, a.n_prony)<<<n_ctas, kBlock, (size_t)a.sm_total, s>>>(a, k);
+    tile_kernel(a, npe)<<<n_ctas, kBlock, (size_t)a.sm_total, s>>>(a, k);
     return cudaGetLastError();
 }
 
@@ -1033,6 +1155,19 @@ cudaError_t launch_shared_step(const StepArgs &a, int n_blocks, int k, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t launch_cem43(const StepArgs &a, int64_t nn, int k, cudaStream_t s) {
+    (void)k;  // the dose uses the state at t; the step within a graph does not enter
+    cem43_kernel<<<(int)std::min<int64_t>((nn + 255) / 256, 4 * kStatBlocks), 256, 0, s>>>(a, nn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_isotherm(const StepArgs &a, int64_t nn, double theta_iso, double *partials, double *out,
+                            cudaStream_t s) {
+    isotherm_partial_kernel<<<kStatBlocks, 256, 0, s>>>(a, nn, theta_iso, partials);
+    sum_final_kernel<<<1, 32, 0, s>>>(partials, kStatBlocks, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bump(const StepArgs &a, int K, cudaStream_t s) {
     bump_kernel<<<(a.n_scn + 255) / 256, 256, 0, s>>>(a, K);
     return cudaGetLastError();
@@ -1041,7 +1176,7 @@ cudaError_t launch_bump(const StepArgs &a, int K, cudaStream_t s) {
 cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,
                             cudaStream_t s) {
     const int nb = (int)((nn + 255) / 256);
-    readback_kernel<<<nb, 256, 0, s>>>(a.xu, a.lo, a.vel, node_new, nn, T0, mode, out);
+    readback_kernel<<<nb, 256, 0, s>>>(a.xu, a.lo, a.vel, a.cem, node_new, nn, T0, mode, out);
     return cudaGetLastError();
 }
 

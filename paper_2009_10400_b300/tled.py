@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libtled.so")
 OK, E_ARG, E_MESH, E_STATE, E_CUDA, E_UNSTABLE, E_INVERTED, E_TIMEOUT, E_NOMEM, E_FORMAT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 T4, H8 = 4, 8
 HOST, DEVICE = 0, 1
-EXPANSION, TEMP_DEP, COMPENSATED = 1, 2, 4
+EXPANSION, TEMP_DEP, COMPENSATED, CEM43 = 1, 2, 4, 8
+SRC_GAUSSIAN, SRC_SPHERE = 0, 1
 FIX_X, FIX_Y, FIX_Z, FIX_T = 1, 2, 4, 8
 
 _dp = C.POINTER(C.c_double)
@@ -31,12 +32,13 @@ class Material(C.Structure):
                 ("prony_g", C.c_double * 4), ("prony_tau", C.c_double * 4), ("alpha", C.c_double),
                 ("k", C.c_double), ("c", C.c_double), ("beta_k", C.c_double), ("beta_c", C.c_double),
                 ("T_ref", C.c_double), ("wb_cb", C.c_double), ("Qm", C.c_double), ("T0", C.c_double),
-                ("Ta", C.c_double), ("lnA", C.c_double), ("Ea", C.c_double)]
+                ("Ta", C.c_double), ("lnA", C.c_double), ("Ea", C.c_double), ("alpha_fibre_ratio", C.c_double),
+                ("k_fibre_ratio", C.c_double)]
 
 
 class Source(C.Structure):
     _fields_ = [("c0", C.c_double * 3), ("vel", C.c_double * 3), ("sigma", C.c_double), ("power", C.c_double),
-                ("t_on", C.c_double), ("t_off", C.c_double)]
+                ("t_on", C.c_double), ("t_off", C.c_double), ("shape", C.c_int32), ("pad", C.c_int32)]
 
 
 class Params(C.Structure):
@@ -83,6 +85,8 @@ _SIGS = {
     "tled_get_displacement": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "tled_get_temperature": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "tled_get_damage": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "tled_get_cem43": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
+    "tled_get_isotherm_volume": ([C.c_void_p, C.c_double, C.POINTER(C.c_double)], C.c_int),
     "tled_set_state": ([C.c_void_p, _dp, _dp, _dp, _dp, _dp, C.c_double, C.c_int64], C.c_int),
     "tled_get_state": ([C.c_void_p, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_int64)], C.c_int),
     "tled_get_stats": ([C.c_void_p, C.POINTER(Stats)], C.c_int),
@@ -141,17 +145,21 @@ def material_from_problem(prob) -> Material:
     m.c = prob.c_heat
     m.beta_k, m.beta_c, m.T_ref = prob.beta_k, prob.beta_c, prob.T_ref
     m.wb_cb, m.Qm, m.T0, m.Ta, m.lnA, m.Ea = prob.wbcb, prob.Qm, prob.T0, prob.Ta, prob.lnA, prob.Ea
+    m.alpha_fibre_ratio = getattr(prob, "aniso_alpha", 1.0)
+    m.k_fibre_ratio = getattr(prob, "aniso_k", 1.0)
     return m
 
 
 def sources_array(rows) -> tuple:
-    rows = np.asarray(rows, np.float64).reshape(-1, 10)
+    rows = np.asarray(rows, np.float64)
+    rows = rows.reshape(-1, rows.shape[-1] if rows.size else 11)  # 10 columns: Gaussian; 11th: shape
     arr = (Source * max(len(rows), 1))()
     for i, r in enumerate(rows):
         for j in range(3):
             arr[i].c0[j] = r[j]
             arr[i].vel[j] = r[3 + j]
         arr[i].sigma, arr[i].power, arr[i].t_on, arr[i].t_off = r[6], r[7], r[8], r[9]
+        arr[i].shape = int(r[10]) if len(r) > 10 else SRC_GAUSSIAN
     return len(rows), arr
 
 
@@ -315,7 +323,8 @@ class Solver:
         s.set_bcs(prob.mask, prob.ubar, prob.ramp_time)
         s.set_heat_sources(prob.sources)
         if flags is None:
-            flags = COMPENSATED | (EXPANSION if prob.expansion else 0) | (TEMP_DEP if prob.temp_dep else 0)
+            flags = (COMPENSATED | (EXPANSION if prob.expansion else 0) | (TEMP_DEP if prob.temp_dep else 0) |
+                     (CEM43 if getattr(prob, "cem43", False) else 0))
         s.set_params(dt=float(prob.dt if dt is None else dt), dt_safety=prob.dt_safety, gamma=prob.gamma,
                      mass_scale=prob.mass_scale, kappa_hg=prob.kappa_hg, kappa_hgT=prob.kappa_hgT, flags=flags,
                      tile_elems=tile_elems)
@@ -363,6 +372,16 @@ class Solver:
 
     def damage(self, out=None):
         return self._read(lib().tled_get_damage, (self.nn,), out)
+
+    def cem43(self, out=None):
+        """CEM43 thermal dose per node, equivalent minutes at 43 C (needs the CEM43 flag)."""
+        return self._read(lib().tled_get_cem43, (self.nn,), out)
+
+    def isotherm_volume(self, T_iso=60.0):
+        """Volume (m^3) of the nodes at or above T_iso (C)."""
+        v = C.c_double()
+        self._check(lib().tled_get_isotherm_volume(self.h, float(T_iso), C.byref(v)))
+        return v.value
 
     def set_state(self, u, v, T, Omega, visc=None, t=0.0, step=0):
         arrs = [np.ascontiguousarray(a, np.float64) for a in (u, v, T, Omega)]

@@ -104,6 +104,49 @@ def test_large_extension_40pct_matches_oracle(kind):
     _, s, _ = run_oracle(prob, 600, 600)
     assert np.ptp(s.u[:, 2] + prob.X[:, 2]) / L > 1.35  # the stretch was applied
 
+
+def _aniso(prob, tilt=True):
+    """Transversely isotropic thermal physics: three times the expansion and 2.5
+    times the conductivity along the fibre, expansion made large enough to
+    matter (alpha 2e-3), fibres tilted off the mesh axes."""
+    prob.aniso_alpha, prob.aniso_k = 3.0, 2.5
+    prob.alpha[:] = 2e-3
+    if tilt and not prob.per_element:
+        prob.a0[:] = np.array([1.0, 1.0, 0.5]) / 1.5
+    return prob
+
+
+@pytest.mark.parametrize("kind", ["h8", "t4"])
+def test_anisotropic_thermal_physics_matches_oracle(kind):
+    """Eq. 11's transversely isotropic thermal expansion about the fibre and
+    conduction along the current fibre: heating trajectory against the oracle
+    (H8 cube with tilted fibres, T4 cube with vMF fibres)."""
+    prob = _aniso(W.cube_h8(n=6, jitter=0.1, seed=81) if kind == "h8" else W.cube_t4(n=5, seed=82))
+    w = _check_trajectory(prob, 1500, 500)
+    print("aniso", kind, w)
+
+
+@pytest.mark.parametrize("kind", ["h8", "t4"])
+def test_anisotropic_single_step_from_random_state(kind):
+    tled = _tled()
+    prob = _aniso(W.block_h8(n=8, h=4e-3) if kind == "h8" else W.cube_t4(n=5))
+    st = W.random_state(prob, 23, theta_scale=20.0)
+    m = oracle.OracleModel(prob)
+    s = tled.Solver.from_problem(prob, dt=m.dt)
+    s.set_state(st["u"], st["v"], st["T"], st["Omega"], st["visc"], t=0.01, step=5)
+    s.step(1)
+    s.sync()
+    os_ = m.state_from(**st, t=0.01, step=5)
+    m.step(os_, 1)
+    np.testing.assert_allclose(s.displacement(), os_.u, rtol=0, atol=2e-6 * np.abs(os_.u).max())
+    np.testing.assert_allclose(s.temperature(), os_.T, rtol=0, atol=2e-6 * np.abs(os_.T - 37).max())
+    # the anisotropic stable step and stored energy agree with the oracle's
+    np.testing.assert_allclose(s.get_dt()[1:], (m.dt_mech, m.dt_th), rtol=1e-12)
+    s.set_state(st["u"], st["v"], st["T"], st["Omega"], st["visc"])
+    r = s.stats()
+    ref = sum(m.energy(e, st["u"], st["T"]) for e in range(prob.ne))
+    assert abs(r["strain_energy"] + r["hourglass_energy"] - ref) <= 1e-5 * abs(ref)
+
 def test_auto_dt_matches_oracle():
     tled = _tled()
     for prob in (W.cube_h8(n=8), W.cube_t4(n=4), W.ellipsoid_t4(spacing=1.2e-2)):

@@ -20,12 +20,13 @@ def test_mass_scaling_effect_on_temperature_over_2s():
     q = W.sample_scenarios(1, seed=41)[0]
     q[0], q[4] = 8e6, 2.0
     base = W.scenario_problem(q, n=16, dt=0.01)
+    base.dt = 0.0  # the stable step of the unscaled problem
     scaled = surrogate.mass_scaled(W.scenario_problem(q, n=16, dt=0.01))
     s_m = scaled.mass_scale
     assert s_m > 100.0
 
     def run(mass_scale, dt):
-        p = W.scenario_problem(q, n=16, dt=0.0)
+        p = W.scenario_problem(q, n=16, dt=0.01)
         p.mass_scale = mass_scale
         s = tled.Solver.from_problem(p, dt=dt)
         dt_used = s.get_dt()[0]

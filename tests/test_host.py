@@ -30,7 +30,8 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(L, n), n
     from paper_2009_10400_b300 import mlp
     assert set(names) <= set(tled.exported_symbols()) | set(mlp.exported_symbols()) | {"tled_version"}
-    assert L.tled_version() == 2
+    hdr = open(os.path.join(ROOT, "include", "tled.h")).read()
+    assert L.tled_version() == int(re.search(r"#define TLED_VERSION (\d+)", hdr).group(1))
 
 
 def _planner(prob, **kw):
@@ -183,3 +184,15 @@ def test_surrogate_spread_threshold_rule():
     assert spread_threshold(spread, [2.0] + err[1:], tol=1.0, coverage=1.0) == (-1.0, 0.0)
     tau, frac = spread_threshold([0.5, 2.0, 3.0], [0.1, 0.1, 0.1], tol=1.0)
     assert tau == 1.0 and frac == 1 / 3
+
+
+def test_cem43_is_refused_in_a_batch():
+    """The dose needs a per-node time step: batches refuse scenarios that ask for it."""
+    import ctypes as C
+    h = C.c_void_p()
+    assert tled.lib().tled_batch_create(C.byref(h), -1, None) == 0
+    prob = W.cube_h8(n=3)
+    one = _planner(prob)
+    one.set_params(flags=tled.EXPANSION | tled.COMPENSATED | tled.CEM43)
+    assert tled.lib().tled_batch_add(h, one.h, 10, None) == tled.E_ARG
+    tled.lib().tled_destroy(h)

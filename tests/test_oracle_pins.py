@@ -23,15 +23,18 @@ def _bar(n=16, L=0.08, w=0.005, **kw):
 # ---------------------------------------------------------------------------
 # P1: conduction operator, sign (R1), lumping (R10), explicit Euler (Eq. 20)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("stretch", [1.0, 1.3])
-def test_p1_cosine_mode_exact_discrete_decay(stretch):
+@pytest.mark.parametrize("stretch,aniso_k", [(1.0, 1.0), (1.3, 1.0), (1.0, 2.5), (1.3, 2.5)])
+def test_p1_cosine_mode_exact_discrete_decay(stretch, aniso_k):
     """On an adiabatic n x 1 x 1 H8 bar the one-point operator acting on an
     x-only field is the 3-point stencil, so a cosine mode decays by an exact
     factor per step.  With the bar held at a uniform stretch s (all
     displacements prescribed) conduction in the deformed configuration (Eq. 6)
-    scales the conductivity by J C^-1_xx = 1/s."""
+    scales the conductivity by J C^-1_xx = 1/s.  With fibres along the bar and
+    anisotropic conductivity the bar conducts with k_fibre = aniso_k k (the
+    current fibre stays along x, so the same 1/s applies)."""
     n, L, A = 16, 0.08, 2.0
     p = _bar(n, L)
+    p.aniso_k = aniso_k
     h = L / n
     if stretch != 1.0:
         p.mask[:] = W.MASK_U
@@ -47,7 +50,7 @@ def test_p1_cosine_mode_exact_discrete_decay(stretch):
         s.u_prev[:] = p.ubar
     nsteps = 200
     m.step(s, nsteps)
-    rho, c, k = 1000.0, p.c_heat, 0.5
+    rho, c, k = 1000.0, p.c_heat, 0.5 * aniso_k
     r = 1.0 - p.dt * 4.0 * k / (stretch * rho * c * h * h) * np.sin(np.pi * h / (2 * L)) ** 2 \
         - p.dt * p.wbcb / (rho * c)
     expect = p.T0 + A * np.cos(np.pi * x / L) * r ** nsteps
@@ -140,22 +143,31 @@ def test_temperature_dependent_heat_capacity():
 # ---------------------------------------------------------------------------
 # P2: thermal expansion split + pull-back (Eqs. 7-11)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["h8", "t4"])
-def test_p2_free_thermal_expansion_is_stress_free(kind):
-    """An unconstrained body at uniform theta with u = (lambda - 1)(X - Xc) has
-    zero nodal force: the elastic part of the deformation is the identity."""
+@pytest.mark.parametrize("kind,aniso", [("h8", False), ("t4", False), ("h8", True), ("t4", True)])
+def test_p2_free_thermal_expansion_is_stress_free(kind, aniso):
+    """An unconstrained body at uniform theta with u = (F_th - I)(X - Xc) has
+    zero nodal force: the elastic part of the deformation is the identity.
+    Isotropic F_th = lambda I, or transversely isotropic about a tilted fibre
+    m (Eq. 11) with three times the expansion along it."""
     p = W.cube_h8(n=3, jitter=0.2) if kind == "h8" else W.cube_t4(n=3)
     p.mask[:] = 0
     p.dt = 1e-5
     alpha = 1e-4
     p.alpha[:] = alpha  # uniform expansion coefficient: a homogeneous free-expansion field
+    mvec = np.array([1.0, 0.0, 0.0])
+    if aniso:
+        mvec = np.array([1.0, 1.0, 0.5]) / 1.5
+        p.a0[:] = mvec
+        p.aniso_alpha, p.aniso_k = 3.0, 2.0
     m = oracle.OracleModel(p)
     s = m.init_state()
     theta = 12.0
     s.T[:] = p.T0 + theta
     lam = 1.0 + alpha * theta
+    lam_m = 1.0 + p.aniso_alpha * alpha * theta
+    Fth = lam * np.eye(3) + (lam_m - lam) * np.outer(mvec, mvec)
     Xc = p.X.mean(0)
-    s.u[:] = (lam - 1.0) * (p.X - Xc)
+    s.u[:] = (p.X - Xc) @ (Fth - np.eye(3)).T
     s.u_prev[:] = s.u
     m.step(s, 1)
     f, fT = m.forces()
@@ -233,8 +245,11 @@ def test_p3_uniaxial_stretch_face_forces(theta):
 # ---------------------------------------------------------------------------
 # P4: forces are the gradient of the stored energy (brute-force FD)
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["h8", "t4"])
-def test_p4_force_is_energy_gradient(kind):
+@pytest.mark.parametrize("kind,aniso", [("h8", False), ("t4", False), ("h8", True), ("t4", True)])
+def test_p4_force_is_energy_gradient(kind, aniso):
+    """Forces are the gradient of the stored energy V0 det(F_th) Psi(F F_th^-1)
+    (+ hourglass), thermal loads the gradient of the conduction quadratic form;
+    also with transversely isotropic expansion and conductivity (R26)."""
     rng = np.random.default_rng(11)
     if kind == "h8":
         X, conn = W.hex_grid((2, 1, 1), (0.02, 0.01, 0.01), jitter=0.15, rng=rng)
@@ -248,6 +263,8 @@ def test_p4_force_is_energy_gradient(kind):
     fib = W.vmf_directions(ne, 2.0, (1, 1, 0), rng)
     mat = W._material(ne, rng, noise=0.2, fibre=fib, alpha=2e-3)
     p = W.Problem(name="fd", npe=npe, X=X, conn=conn, **mat, prony_g=(), prony_tau=(), kappa_hg=0.3)
+    if aniso:
+        p.aniso_alpha, p.aniso_k = 3.0, 2.5
     p.dt = 1e-4
     m = oracle.OracleModel(p)
     u = rng.uniform(-1, 1, (p.nn, 3)) * 0.001
@@ -279,9 +296,14 @@ def test_p4_force_is_energy_gradient(kind):
 # ---------------------------------------------------------------------------
 # P5: frame invariance
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("kind", ["h8", "t4"])
-def test_p5_rigid_rotation(kind):
+@pytest.mark.parametrize("kind,aniso", [("h8", False), ("t4", False), ("h8", True), ("t4", True)])
+def test_p5_rigid_rotation(kind, aniso):
+    """A rigid rotation of a deformed configuration rotates the internal forces
+    and leaves the thermal loads unchanged; with anisotropic conductivity this
+    holds only because the conductivity follows the current fibre F a0."""
     p = W.cube_h8(n=2, jitter=0.2) if kind == "h8" else W.cube_t4(n=2)
+    if aniso:
+        p.aniso_alpha, p.aniso_k = 3.0, 4.0
     p.mask[:] = 0
     p.dt = 1e-6
     rng = np.random.default_rng(5)
@@ -418,6 +440,49 @@ def test_p9_energy_balance_is_second_order():
     m1.step(v, 200)
     k = 0.5 * np.sum(m1.M[:, None] * ((v.u - v.u_prev) / m1.dt) ** 2)
     assert k > 0.05 * E1[0], (k, E1[0])
+
+
+# ---------------------------------------------------------------------------
+# the paper's own source and dose read-out (uniform spheres, CEM43)
+# ---------------------------------------------------------------------------
+def test_uniform_sphere_source_heat_balance():
+    """One step from rest with a uniform spherical source (the paper's liver
+    case) and no perfusion or metabolic heat: the element conduction loads sum
+    to zero, so the heat content rises by exactly dt * P * (sum of the lumped
+    volumes of the nodes inside the sphere), counted here independently."""
+    p = W.cube_h8(n=6, jitter=0.1, seed=71)
+    p.wbcb, p.Qm, p.expansion = 0.0, 0.0, False
+    c, r, P = np.array([0.021, 0.024, 0.027]), 0.011, 7e6
+    p.sources = np.array([W.source(c, P, sigma=r, sphere=True)])
+    d = np.linalg.norm(p.X - c, axis=1)
+    assert np.min(np.abs(d - r)) > 1e-6  # membership is unambiguous
+    inside = d <= r
+    assert 0 < inside.sum() < p.nn
+    m = oracle.OracleModel(p)
+    s = m.init_state()
+    m.step(s, 1)
+    dQ = np.sum(m.Cth * (s.T - p.T0))
+    np.testing.assert_allclose(dQ, m.dt * P * m.Vn[inside].sum(), rtol=1e-12)
+
+
+def test_cem43_at_held_temperatures():
+    """CEM43 at temperatures held fixed: t/60 * R^(43 - T) minutes exactly, with
+    R = 0.5 at or above 43 C (45 C: 4 t/60) and 0.25 below (40 C: t/60 / 64)."""
+    p = W.cube_h8(n=2)
+    p.sources = np.zeros((0, 11))
+    p.mask = p.mask | W.MASK_T  # every temperature held
+    m = oracle.OracleModel(p, dt=0.01)
+    s = m.init_state()
+    T = np.full(p.nn, 40.0)
+    T[:9] = 45.0
+    T[9:18] = 43.0
+    s.T[:] = T
+    m.step(s, 300)
+    t = 300 * 0.01
+    np.testing.assert_allclose(s.T, T)
+    np.testing.assert_allclose(s.cem[:9], 4.0 * t / 60.0, rtol=1e-13)
+    np.testing.assert_allclose(s.cem[9:18], t / 60.0, rtol=1e-13)
+    np.testing.assert_allclose(s.cem[18:], t / 60.0 / 64.0, rtol=1e-13)
 
 # ---------------------------------------------------------------------------
 # P10: Arrhenius integral
