@@ -366,9 +366,9 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     const float d1 = dl + 0.5f * dl * dl;
     // anisotropic: F_th^-1 = (I - g m m) / lambda_i, g = (lambda_m - lambda_i) / lambda_m, m = fibre,
     // E_el = [E - d1 I - g (m Em + Em m) + (g^2 m.E.m - g + g^2/2) m m] / lambda_i^2 (Em = E m)
-    float lm = lam, gam = 0.f, mEm = 0.f, det_th = 1.f;
+    float dm = dl, lm = lam, gam = 0.f, mEm = 0.f, det_th = 1.f;  // delta_m kept: 1 + tiny - 1 would lose it
     if constexpr (ANI) {
-        const float dm = (A.flags & TLED_EXPANSION) ? A.ani_alpha * al * the : 0.f;
+        dm = (A.flags & TLED_EXPANSION) ? A.ani_alpha * al * the : 0.f;
         lm = 1.f + dm;
         gam = __fdividef(dm - dl, lm);
         const float Emx = Ee[0] * ax + Ee[3] * ay + Ee[5] * az;
@@ -388,7 +388,6 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     // J_el - 1 = ((J - 1) - (det F_th - 1)) / det F_th; det F_th = lambda_i^2 lambda_m
     float jel;
     if constexpr (ANI) {
-        const float dm = lm - 1.f;
         const float t3m1 = dl * (2.f + dl) + dm * (1.f + dl) * (1.f + dl);
         det_th = 1.f + t3m1;
         jel = __fdividef(Jm1 - t3m1, det_th);

@@ -30,7 +30,7 @@ def test_liver_f2_matches_oracle_with_cem43_and_isotherm():
         cem = g.cem43()
         assert rel_l2(cem, s.cem) <= 1e-5, rel_l2(cem, s.cem)
     T = g.temperature()
-    assert (T - p.T0).max() > 0.5  # the spheres heated
+    assert (T - p.T0).max() > 0.2  # the spheres heated (0.137 s of heating)
     T_iso = float(np.quantile(T, 0.95))
     vol = g.isotherm_volume(T_iso)
     np.testing.assert_allclose(vol, m.Vn[T >= T_iso].sum(), rtol=1e-6)  # definition, on the GPU's own field

@@ -11,6 +11,19 @@ from paper_2009_10400_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
+def _increments_match(s, m, st, os_, rtol=2e-5):
+    """One step's velocity and temperature increments against the oracle's:
+    these carry the element forces and thermal loads directly (u and T
+    themselves are dominated by the state the step started from)."""
+    g = s.get_state()
+    free = m.prob.mask == 0
+    dv_g = (g["v"] - st["v"])[free]
+    dv_o = ((os_.u - os_.u_prev) / m.dt - st["v"])[free]
+    assert np.abs(dv_g - dv_o).max() <= rtol * np.abs(dv_o).max(), np.abs(dv_g - dv_o).max() / np.abs(dv_o).max()
+    dT_g, dT_o = g["T"] - st["T"], os_.T - st["T"]
+    assert np.abs(dT_g - dT_o).max() <= rtol * np.abs(dT_o).max(), np.abs(dT_g - dT_o).max() / np.abs(dT_o).max()
+
+
 def _tled():
     from paper_2009_10400_b300 import tled
     return tled
@@ -140,6 +153,7 @@ def test_anisotropic_single_step_from_random_state(kind):
     m.step(os_, 1)
     np.testing.assert_allclose(s.displacement(), os_.u, rtol=0, atol=2e-6 * np.abs(os_.u).max())
     np.testing.assert_allclose(s.temperature(), os_.T, rtol=0, atol=2e-6 * np.abs(os_.T - 37).max())
+    _increments_match(s, m, st, os_)
     # the anisotropic stable step and stored energy agree with the oracle's
     np.testing.assert_allclose(s.get_dt()[1:], (m.dt_mech, m.dt_th), rtol=1e-12)
     s.set_state(st["u"], st["v"], st["T"], st["Omega"], st["visc"])
@@ -178,6 +192,7 @@ def test_single_step_from_random_state(kind):
     np.testing.assert_allclose(d, oracle.damage_fraction(os_.Omega), rtol=0, atol=1e-6)
     g = s.get_state()
     np.testing.assert_allclose(g["visc"], os_.visc, rtol=0, atol=1e-5 * np.abs(os_.visc).max())
+    _increments_match(s, m, st, os_)
 
 
 def test_deterministic_bitwise():
