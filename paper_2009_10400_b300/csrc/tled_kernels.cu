@@ -63,6 +63,7 @@ struct ScenStep {
     float dtf, inv_dt, damp_a, damp_b, Qm;
     float pr_a[4], pr_b[4];
     int n;
+    int sph;  // 1 if a source is a uniform sphere
     // source s adds P exp(-d^2 inv2s2) where d^2 <= r2: a Gaussian (r2 infinite) or a
     // uniform sphere (inv2s2 = 0, r2 = radius^2)
     float cx[kMaxSources], cy[kMaxSources], cz[kMaxSources], inv2s2[kMaxSources], r2[kMaxSources], P[kMaxSources];
@@ -86,6 +87,8 @@ __device__ __forceinline__ void prepare_scen(const StepArgs &A, int s, int k, Sc
             P.pr_b[i] = D.pr_b[i];
         }
         P.n = D.n_src;
+        P.sph = 0;
+        for (int q = 0; q < D.n_src; q++) P.sph |= A.src[kSrcRow * (int64_t)(D.src_off + q) + 10] == 1.0;
     }
     for (int q = lane; q < D.n_src; q += nlanes) {
         const double *p = A.src + kSrcRow * (int64_t)(D.src_off + q);
@@ -186,10 +189,17 @@ __device__ __forceinline__ void node_update(const StepArgs &A, const ScenStep &S
     float iC = nc.y;
     if (A.flags & TLED_TEMP_DEP) iC = __fdividef(iC, 1.f + A.beta_c * (theta - A.Tref_m_T0));
     float Q = S.Qm;
-    for (int s = 0; s < S.n; s++) {
-        const float dx = px - S.cx[s], dy = py - S.cy[s], dz = pz - S.cz[s];
-        const float d2 = dx * dx + dy * dy + dz * dz;
-        Q += d2 <= S.r2[s] ? S.P[s] * __expf(-d2 * S.inv2s2[s]) : 0.f;
+    if (S.sph) {  // some source is a uniform sphere: P inside radius^2, or a Gaussian
+        for (int s = 0; s < S.n; s++) {
+            const float dx = px - S.cx[s], dy = py - S.cy[s], dz = pz - S.cz[s];
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            Q += d2 <= S.r2[s] ? S.P[s] * __expf(-d2 * S.inv2s2[s]) : 0.f;
+        }
+    } else {
+        for (int s = 0; s < S.n; s++) {
+            const float dx = px - S.cx[s], dy = py - S.cy[s], dz = pz - S.cz[s];
+            Q += S.P[s] * __expf(-(dx * dx + dy * dy + dz * dz) * S.inv2s2[s]);
+        }
     }
     if (!(mask & TLED_FIX_T)) {
         const float dth = dt * iC * (-f.w + X.w * Q - nc.w * (theta - A.theta_a));
