@@ -77,7 +77,8 @@ int tled_mlp_train_step_rows(tled_mlp *m, const float *x, const float *t, const 
  *   std  [B][n_out]  population standard deviation of z (two-pass)
  *   spread [B]       max of std over outputs [0, n_spread)
  *   fallback [B]     1 where spread > tol, else 0 (uint8)
- * Any of the four outputs may be NULL.  Used to accept a surrogate answer or
+ * Any of the four outputs may be NULL.  n_out must be a multiple of 4 and y,
+ * mean and std 16-byte aligned (rows are read and written as float4).  Used to accept a surrogate answer or
  * send the scenario back to the solver.  Errors: E_ARG, E_CUDA. */
 int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *const *y, int32_t B, int32_t n_out,
                       const float *out_scale, const float *out_shift, const float *row_src, int32_t row_stride,

@@ -5,7 +5,9 @@
 
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -34,6 +36,7 @@ struct tled_mlp {
     cudaStream_t stream = nullptr;
     std::string err;
     int L = 0, Bmax = 0;
+    int n_sm = 148;  // multiprocessors of the device (tile-width choice)
     std::vector<Layer> layer;
     int64_t n_params = 0;
     size_t p_w = 0, p_m = 0, p_v = 0, p_g = 0, x_b = 0, x_t = 0, y = 0, loss_part = 0, loss = 0, status = 0, total = 0;
@@ -42,6 +45,9 @@ struct tled_mlp {
     char *ws = nullptr;
     bool inited = false;
     int64_t adam_t = 0;
+    // tensor maps of the workspace operands, keyed by (address, rows, cols, box rows): every
+    // GEMM operand lives at a fixed workspace offset, so each map is encoded once
+    std::map<std::tuple<uintptr_t, int, int, int>, CUtensorMap> maps;
 };
 
 namespace {
@@ -75,6 +81,12 @@ int get_encoder(tled_mlp *m) {
 
 // tensor map of a row-major bf16 matrix [rows][cols], boxes of box_rows x 64 (128-byte swizzle)
 int make_map(tled_mlp *m, CUtensorMap *map, const void *base, int rows, int cols, int box_rows) {
+    const auto key = std::make_tuple((uintptr_t)base, rows, cols, box_rows);
+    auto it = m->maps.find(key);
+    if (it != m->maps.end()) {
+        *map = it->second;
+        return TLED_OK;
+    }
     if (int rc = get_encoder(m)) return rc;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
@@ -84,12 +96,14 @@ int make_map(tled_mlp *m, CUtensorMap *map, const void *base, int rows, int cols
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(m, TLED_E_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    m->maps[key] = *map;
     return TLED_OK;
 }
 
 // D[M][N] = A[M][K] B[N][K]^T with the given epilogue
 int gemm(tled_mlp *m, const void *A, const void *B, int M, int N, int K, GemmArgs g, int mode) {
-    const int bn = (N % 128 == 0) ? 128 : 64;
+    // 128-wide N tiles, or 64-wide when the 128-wide grid would leave SMs without two CTAs
+    const int bn = (N % 128 == 0 && (int64_t)(M / 128) * (N / 128) >= 2 * m->n_sm) ? 128 : 64;
     CUtensorMap ta, tb;
     if (int rc = make_map(m, &ta, A, M, K, 128)) return rc;
     if (int rc = make_map(m, &tb, B, N, K, bn)) return rc;
@@ -194,6 +208,7 @@ int tled_mlp_create(tled_mlp **out, int device, void *stream, int32_t n_layers, 
         if (dims[i] % 128) return TLED_E_ARG;  // layer widths and outputs: multiples of 128
     tled_mlp *m = new tled_mlp();
     m->device = device;
+    if (cudaDeviceGetAttribute(&m->n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) m->n_sm = 148;
     m->stream = (cudaStream_t)stream;
     m->L = n_layers;
     m->Bmax = max_batch;
@@ -269,6 +284,7 @@ int tled_mlp_init(tled_mlp *m, void *ws, int64_t bytes) {
     if (bytes < (int64_t)m->total) return fail(m, TLED_E_NOMEM, "workspace smaller than tled_mlp_workspace_size()");
     MCUDA(m, cudaSetDevice(m->device));
     m->ws = (char *)ws;
+    m->maps.clear();  // the maps point into the previous workspace
     MCUDA(m, cudaMemsetAsync(m->ws, 0, m->total, m->stream));
     MCUDA(m, cudaStreamSynchronize(m->stream));
     m->inited = true;
@@ -313,13 +329,14 @@ int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *
                       const float *out_scale, const float *out_shift, const float *row_src, int32_t row_stride,
                       float row_mult, int32_t n_row_scaled, const float *out_offset, int32_t n_spread, float tol,
                       float *mean, float *std, float *spread, uint8_t *fallback) {
+    if (n_out % 4 || ((uintptr_t)mean & 15) || ((uintptr_t)std & 15)) return TLED_E_ARG;  // float4 rows
     if (n_members < 1 || n_members > kMaxMembers || !y || B < 0 || n_out < 1 || n_spread < 0 || n_spread > n_out ||
         !(tol >= 0) || n_row_scaled < 0 || n_row_scaled > n_out || (row_src && row_stride < 1) ||
         !std::isfinite(row_mult))
         return TLED_E_ARG;
     EnsembleArgs e{};
     for (int k = 0; k < n_members; k++) {
-        if (!y[k]) return TLED_E_ARG;
+        if (!y[k] || ((uintptr_t)y[k] & 15)) return TLED_E_ARG;
         e.y[k] = y[k];
     }
     e.n_members = n_members;

@@ -23,8 +23,8 @@
 
 namespace tmlp {
 
-constexpr int kStages = 4;
 constexpr int kBM = 128;
+constexpr int kEpiLd = 33;  // padded row of the per-warp epilogue transpose buffer (conflict-free)
 constexpr int kBK = 64;  // 64 bf16 = 128 bytes = one swizzle row
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -94,7 +94,14 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-template <int BN, int MODE>
+// shared memory of one CTA: the operand ring (1024-byte aligned) and four 32 x 33
+// float transpose buffers of the epilogue warps
+template <int BN, int STAGES>
+constexpr int gemm_smem_bytes() {
+    return STAGES * (kBM + BN) * kBK * 2 + 1024 + 4 * 32 * kEpiLd * 4;
+}
+
+template <int BN, int MODE, int kStages>
 __global__ void __launch_bounds__(192, 1)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];
@@ -104,6 +111,7 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int kABytes = kBM * kBK * 2, kBBytes = BN * kBK * 2;
     uint8_t *sA = smem, *sB = smem + kStages * kABytes;
+    float *sEpi = reinterpret_cast<float *>(sB + kStages * kBBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
     const int KB = g.K / kBK;
@@ -159,9 +167,13 @@ __global__ void __launch_bounds__(192, 1)
         }
         umma_commit(&accum);
     } else if (warp >= 2) {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows (lane = row);
+        //      row-major traffic goes through a per-warp 32 x 33 transpose buffer so that a
+        //      warp's loads and stores cover 32 consecutive columns of one row
         const int lg = warp & 3;
-        const int row = m0 + lg * 32 + lane;
+        const int row0 = m0 + lg * 32;
+        const int row = row0 + lane;
+        float *buf = sEpi + (warp - 2) * 32 * kEpiLd;
         const bool ok = bar_wait(&accum, 0);
         if (!ok) s_fail = 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -180,29 +192,46 @@ __global__ void __launch_bounds__(192, 1)
                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < g.M) {
+                const int col0 = n0 + c0;
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+                if constexpr (MODE == kEpiGeluGrad) {  // Z of the previous layer: coalesced rows in, transposed
+#pragma unroll 4
+                    for (int rr = 0; rr < 32; rr++) buf[rr * kEpiLd + lane] = g.z_in[(int64_t)(row0 + rr) * g.ld_z + col0 + lane];
+                    __syncwarp();
+#pragma unroll
+                    for (int j = 0; j < 32; j++) v[j] *= gelu_grad(buf[lane * kEpiLd + j]);
+                    __syncwarp();
+                } else if constexpr (MODE == kEpiBiasF32 || MODE == kEpiGelu) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) v[j] += g.bias[col0 + j];
+                }
+                // row-major float output (Y, Z or G): stage and write rows
+                float *out_rm = MODE == kEpiGelu ? g.z_out : g.out_f32;
+                const int ld_rm = MODE == kEpiGelu ? g.ld_z : g.ld_f32;
+                if constexpr (MODE != kEpiGeluGrad) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) buf[lane * kEpiLd + j] = v[j];
+                    __syncwarp();
+#pragma unroll 4
+                    for (int rr = 0; rr < 32; rr++) out_rm[(int64_t)(row0 + rr) * ld_rm + col0 + lane] = buf[rr * kEpiLd + lane];
+                    __syncwarp();
+                }
+                if constexpr (MODE == kEpiGelu || MODE == kEpiGeluGrad) {
+                    // bf16 activation (or gradient): transposed copy straight from registers
+                    // (consecutive lanes = consecutive rows), row-major copy through the buffer
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
-                        const int col = n0 + c0 + j;
-                        float v = __uint_as_float(r[j]);
-                        if constexpr (MODE == kEpiBiasF32) {
-                            v += g.bias[col];
-                            g.out_f32[(int64_t)row * g.ld_f32 + col] = v;
-                        } else if constexpr (MODE == kEpiGelu) {
-                            v += g.bias[col];
-                            g.z_out[(int64_t)row * g.ld_z + col] = v;
-                            const __nv_bfloat16 a = __float2bfloat16_rn(gelu(v));
-                            g.out_bf[(int64_t)row * g.ld_bf + col] = a;
-                            g.out_bfT[(int64_t)col * g.ld_bfT + row] = a;
-                        } else if constexpr (MODE == kEpiGeluGrad) {
-                            const float dz = v * gelu_grad(g.z_in[(int64_t)row * g.ld_z + col]);
-                            const __nv_bfloat16 a = __float2bfloat16_rn(dz);
-                            g.out_bf[(int64_t)row * g.ld_bf + col] = a;
-                            g.out_bfT[(int64_t)col * g.ld_bfT + row] = a;
-                        } else {
-                            g.out_f32[(int64_t)row * g.ld_f32 + col] = v;
-                        }
+                        const __nv_bfloat16 h = __float2bfloat16_rn(MODE == kEpiGelu ? gelu(v[j]) : v[j]);
+                        g.out_bfT[(int64_t)(col0 + j) * g.ld_bfT + row] = h;
+                        buf[lane * kEpiLd + j] = __bfloat162float(h);
                     }
+                    __syncwarp();
+#pragma unroll 4
+                    for (int rr = 0; rr < 32; rr++)
+                        g.out_bf[(int64_t)(row0 + rr) * g.ld_bf + col0 + lane] = __float2bfloat16_rn(buf[rr * kEpiLd + lane]);
+                    __syncwarp();
                 }
             }
         }
@@ -328,32 +357,43 @@ __global__ void __launch_bounds__(256) ensemble_kernel(const EnsembleArgs E) {
     const int b = blockIdx.x;
     const float rb = E.row_src ? E.row_src[(int64_t)b * E.row_stride] * E.row_mult : 1.f;
     float smax = 0.f;
-    for (int n = threadIdx.x; n < E.n_out; n += blockDim.x) {
+    // four consecutive outputs per thread and iteration (n_out is a multiple of 128)
+    for (int n = 4 * threadIdx.x; n < E.n_out; n += 4 * blockDim.x) {
         const int64_t i = (int64_t)b * E.n_out + n;
-        const float sc = E.scale ? E.scale[n] : 1.f, sh = E.shift ? E.shift[n] : 0.f;
-        const float r = n < E.n_row_scaled ? rb : 1.f, off = E.offset ? E.offset[n] : 0.f;
-        float z[kMaxMembers];
-        float sum = 0.f;
+        float4 z[kMaxMembers];
 #pragma unroll
-        for (int k = 0; k < kMaxMembers; k++) {
-            if (k < E.n_members) {
-                z[k] = fmaf(fmaf(E.y[k][i], sc, sh), r, off);
-                sum += z[k];
-            }
-        }
-        const float mean = sum / (float)E.n_members;
-        float var = 0.f;
+        for (int k = 0; k < kMaxMembers; k++)
+            if (k < E.n_members) z[k] = *reinterpret_cast<const float4 *>(E.y[k] + i);
+        float mean[4], sd[4];
 #pragma unroll
-        for (int k = 0; k < kMaxMembers; k++) {
-            if (k < E.n_members) {
-                const float d = z[k] - mean;
-                var = fmaf(d, d, var);
+        for (int c = 0; c < 4; c++) {
+            const int nc = n + c;
+            const float sc = E.scale ? E.scale[nc] : 1.f, sh = E.shift ? E.shift[nc] : 0.f;
+            const float r = nc < E.n_row_scaled ? rb : 1.f, off = E.offset ? E.offset[nc] : 0.f;
+            float zc[kMaxMembers];
+            float sum = 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxMembers; k++) {
+                if (k < E.n_members) {
+                    const float y = c == 0 ? z[k].x : c == 1 ? z[k].y : c == 2 ? z[k].z : z[k].w;
+                    zc[k] = fmaf(fmaf(y, sc, sh), r, off);
+                    sum += zc[k];
+                }
             }
+            mean[c] = sum / (float)E.n_members;
+            float var = 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxMembers; k++) {
+                if (k < E.n_members) {
+                    const float d = zc[k] - mean[c];
+                    var = fmaf(d, d, var);
+                }
+            }
+            sd[c] = sqrtf(var / (float)E.n_members);
+            if (nc < E.n_spread) smax = fmaxf(smax, sd[c]);
         }
-        const float sd = sqrtf(var / (float)E.n_members);
-        if (E.mean) E.mean[i] = mean;
-        if (E.std) E.std[i] = sd;
-        if (n < E.n_spread) smax = fmaxf(smax, sd);
+        if (E.mean) *reinterpret_cast<float4 *>(E.mean + i) = make_float4(mean[0], mean[1], mean[2], mean[3]);
+        if (E.std) *reinterpret_cast<float4 *>(E.std + i) = make_float4(sd[0], sd[1], sd[2], sd[3]);
     }
     for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(0xffffffffu, smax, o));
     __shared__ float red[8];
@@ -370,10 +410,11 @@ __global__ void __launch_bounds__(256) ensemble_kernel(const EnsembleArgs E) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+constexpr int kGemmStages = 2;  // two CTAs per SM: one's epilogue overlaps the other's MMAs
 template <int BN, int MODE>
 static cudaError_t launch_one(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s) {
-    const int smem = kStages * (kBM + BN) * kBK * 2 + 1024;
-    auto kern = umma_gemm_kernel<BN, MODE>;
+    const int smem = gemm_smem_bytes<BN, kGemmStages>();
+    auto kern = umma_gemm_kernel<BN, MODE, kGemmStages>;
     static int set_device = -1;  // the attribute is per device: set it on first use there
     int dev = 0;
     cudaGetDevice(&dev);
