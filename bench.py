@@ -444,6 +444,57 @@ def run_surrogate(args):
     print(json.dumps(line))
     return 0
 
+def run_surrogate_inference(args):
+    """Kernel benchmark of the surrogate's inference path alone: the 5-member
+    ensemble of [12, 512 x 5, 8192] MLPs with seeded He-initialised weights
+    (throughput does not depend on the weight values), 4096 scenarios per
+    inference, device-timed; the tcgen05 GEMMs' FLOP rate against the measured
+    BF16 peak."""
+    import torch
+
+    from paper_2009_10400_b300 import surrogate
+    from paper_2009_10400_b300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    P = args.sur_grid ** 3
+    sur = surrogate.Surrogate(n_out=2 * P, width=512, depth=6, members=args.sur_members, max_batch=4096)
+    rng = np.random.default_rng(0)
+    for net in sur.members:
+        net.set_params(surrogate.he_init(sur.dims, rng))
+    dev = "cuda:0"
+    sur._scale = torch.ones(2 * P, device=dev)
+    sur._shift = torch.zeros(2 * P, device=dev)
+    sur._offset = torch.zeros(2 * P, device=dev)
+    Xd = torch.tensor(W.sample_scenarios(4096, seed=7), dtype=torch.float32, device=dev)
+    for _ in range(max(args.warmup, 3)):
+        sur.predict_device(Xd, P, args.sur_tol)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sur.predict_device(Xd, P, args.sur_tol)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sec = ev0.elapsed_time(ev1) * 1e-3 / args.steps
+    flop = 2.0 * 4096 * args.sur_members * sum(k * m for k, m in zip(sur.dims[:-1], sur.dims[1:]))
+    try:
+        peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        psrc = "measured"
+    except Exception:
+        peak, psrc = 1800.0, "fallback"
+    line = {"metric": "surrogate scenario-solves/s", "value": 4096 / sec, "unit": "scenario-solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * sec, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"surrogate inference: MLP {sur.dims}, {args.sur_members} members, batch 4096, "
+                                   "seeded He-initialised weights"},
+            "roofline": {"bound": "tensor", "achieved": flop / sec / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flop / sec / 1e12 / peak, "traffic": None, "peak_source": psrc,
+                         "kernel": "umma_gemm_kernel (tcgen05) forward passes + ensemble_kernel"},
+            "gpu_launches": args.steps * (args.sur_members * (1 + len(sur.dims) - 1) + 1)}
+    print(json.dumps(line))
+    return 0
+
 def run_liver(args):
     """The paper's liver heating case (25 s of heating with three uniform
     spherical sources, temperature-dependent c and k, CEM43 tracked) from rest,
@@ -644,6 +695,8 @@ def main():
         return run_surrogate(args)
     if args.workload == "liver_f2":
         return run_liver(args)
+    if args.workload == "surrogate_inference":
+        return run_surrogate_inference(args)
     return run_gpu(args)
 
 
