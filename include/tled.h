@@ -67,6 +67,10 @@ extern "C" {
 #define TLED_TEMP_DEP (1u << 1)    /* c(T), k(T) linear in T (Table 5) */
 #define TLED_COMPENSATED (1u << 2) /* float-float accumulation of u and T */
 #define TLED_CEM43 (1u << 3)       /* accumulate the CEM43 thermal dose per node (single problems only) */
+#define TLED_GENERAL_H8 (1u << 4)  /* keep the general H8 kernel for brick meshes (every element an H8 whose
+                                      reference hourglass projections vanish in float, e.g. voxels), which
+                                      otherwise take a kernel without those zero terms; the two agree up to
+                                      the compiler's multiply-add fusion (a few ulps) */
 
 /* boundary mask bits (per node) */
 #define TLED_FIX_X 1u

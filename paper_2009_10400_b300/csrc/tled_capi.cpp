@@ -862,6 +862,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         std::fill(scn_of_elem.begin() + c->sc[si].elem_off, scn_of_elem.begin() + c->sc[si].elem_off + c->sc[si].ne, si);
     std::vector<char> rec((size_t)p.n_tiles * rb, 0);
     std::vector<double> Mn(nn, 0.0), Cn(nn, 0.0), Vn(nn, 0.0), Kb(nn, 0.0);
+    bool brick = true;  // every element an H8 brick (vanishing reference hourglass projections)
     for (int64_t e = 0; e < nep; e++) {
         const int64_t eo = p.elem_old[e];
         if (eo < 0) continue;  // padding slot
@@ -871,6 +872,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         const int32_t *cn = s.conn.data() + el * ke;
         double Ji[9], V;
         tled::element_geometry(ke, s.X.data(), cn, Ji, &V);
+        if (brick) brick = ke == 8 && tled::hourglass_projections_vanish(s.X.data(), cn);
         char *r = rec.data() + (size_t)(e / kT) * rb;
         const int ei = (int)(e % kT);
         std::memcpy(r + (size_t)ei * ke * 2, &p.conn_local[(size_t)e * p.npe], (size_t)ke * 2);
@@ -997,6 +999,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.ani_alpha = (float)fibre_ratio(m.alpha_fibre_ratio);
     A.ani_k = (float)fibre_ratio(m.k_fibre_ratio);
     A.ani = fibre_ratio(m.alpha_fibre_ratio) != 1.0 || fibre_ratio(m.k_fibre_ratio) != 1.0;
+    A.brick = brick && !(s0.prm.flags & TLED_GENERAL_H8);
     A.T0 = m.T0;
     A.n_tiles = p.n_tiles;
     tled::tile_smem_layout(A, npe);

@@ -22,6 +22,31 @@ static inline double nat_deriv(int npe, int a, int k) {
     return npe == 8 ? kH8Sign[a][k] * 0.125 : kT4Deriv[a][k];
 }
 
+// True when the hourglass projections (the Walsh-Hadamard coefficients xi eta,
+// eta zeta, xi zeta and xi eta zeta) of the H8 element's reference corner
+// coordinates, rounded to float and transformed in the tile kernel's butterfly
+// order, are exactly zero -- axis-aligned bricks such as voxel meshes.  The
+// kernel then drops every term these coefficients multiply (exact zeros; only
+// the compiler's multiply-add fusion around them can differ, by an ulp).
+bool hourglass_projections_vanish(const double *X, const int32_t *cn) {
+    for (int d = 0; d < 3; d++) {
+        float w[8];
+        for (int i = 0; i < 8; i++) {
+            const int a = i == 2 ? 3 : i == 3 ? 2 : i == 6 ? 7 : i == 7 ? 6 : i;  // transform index -> VTK corner
+            w[i] = (float)X[3 * (int64_t)cn[a] + d];
+        }
+        for (int h = 1; h < 8; h <<= 1)
+            for (int i = 0; i < 8; i++)
+                if ((i & h) == 0) {
+                    const float x = w[i], y = w[i + h];
+                    w[i] = x + y;
+                    w[i + h] = x - y;
+                }
+        if (w[3] != 0.f || w[5] != 0.f || w[6] != 0.f || w[7] != 0.f) return false;
+    }
+    return true;
+}
+
 // Reference Jacobian J0 = sum_a X_a (x) dN_a/dxi, its inverse, and the element
 // volume (8 det J0 for H8, det J0 / 6 for T4).  Returns false if det J0 <= 0.
 bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V) {
@@ -332,6 +357,11 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
             return TLED_E_MESH;
         }
         ti[4] = nl;
+        // each tile's shared-node lists start on a 16-byte boundary (bulk-copied to shared memory)
+        while (p.tile_shared.size() % 4) {
+            p.tile_shared.push_back(-1);
+            p.part_pos.push_back(0);
+        }
         ti[5] = (int32_t)p.tile_shared.size();
         ti[6] = (int32_t)part;
         const int kt = nc(p.elem_old[e0]);
@@ -371,10 +401,15 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
                 rec_codes[cur[l]++] = (uint16_t)(a * kTile + (int)(i - e0));
             }
     }
+    while (p.tile_shared.size() % 4) {  // the last tile's padded copy stays inside the arrays
+        p.tile_shared.push_back(-1);
+        p.part_pos.push_back(0);
+    }
     p.n_partials = part;
     p.sh_rowptr.assign(p.n_shared + 1, 0);
     for (int64_t s = 0; s < p.n_shared; s++) p.sh_rowptr[s + 1] = p.sh_rowptr[s] + sh_n[s];
-    for (size_t j = 0; j < p.tile_shared.size(); j++) p.part_pos[j] += p.sh_rowptr[p.tile_shared[j] - p.n_interior];
+    for (size_t j = 0; j < p.tile_shared.size(); j++)
+        if (p.tile_shared[j] >= 0) p.part_pos[j] += p.sh_rowptr[p.tile_shared[j] - p.n_interior];
     return TLED_OK;
 }
 

@@ -42,7 +42,7 @@ struct Plan {
     int n_tiles = 0;
     std::vector<int32_t> tile_info;     // [n_tiles][8]: e0 (= tile * kTile), ne, int_begin, n_int,
                                         //   n_local, sh_off, part_off, element type (4 or 8)
-    std::vector<int32_t> tile_shared;   // per tile: new ids of its shared nodes (ascending)
+    std::vector<int32_t> tile_shared;   // per tile (from a multiple of 4, -1 padded): new ids of its shared nodes (ascending)
     std::vector<uint16_t> conn_local;   // [ne_pad][npe] tile-local node index
     std::vector<uint16_t> csr;          // [n_tiles][csr_rec_u16]: slot offsets corner * kTile + element, grouped
                                         //   by local node (ascending element, corner), then the n_local + 1 row offsets
@@ -103,7 +103,7 @@ struct StepArgs {
     // dynamic shared-memory layout of the tile kernel (bytes)
     int sm_in;             // bytes of a tile's staged element inputs (record + Prony state)
     int sm_buf;            // max(sm_in, slot buffer bytes), 128-aligned; two such buffers
-    int sm_ns, sm_csr, sm_xu, sm_X, sm_bar, sm_total;
+    int sm_ns, sm_csr, sm_sh, sm_xu, sm_X, sm_bar, sm_total;  // sm_sh: shared-node index lists
     int n_tiles;
     int csr_stride;        // uint16 entries between consecutive tiles' gather records
     int n_comp;            // staged float components per element (J0^-1 9, V0, [mat 6], [fibre 3], Prony 6 n)
@@ -117,6 +117,7 @@ struct StepArgs {
     float lnA, Ea_R, T0_K;                // T0 + 273.15
     float khg, khgT;                      // kappa_hg, kappa_hgT
     int ani;                              // anisotropic thermal physics (the ratios below differ from 1)
+    int brick;                            // every element an H8 whose reference hourglass projections vanish
     float ani_alpha, ani_k;               // fibre / transverse expansion and conductivity
     double ramp_time;
 };
@@ -154,6 +155,7 @@ cudaError_t noalloc_scratch(int device, double **ptr);
 
 // host geometry and planning (tled_host.cpp)
 bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V);
+bool hourglass_projections_vanish(const double *X, const int32_t *cn);  // H8 brick test
 // fib: per-element fibres [ne][3] or NULL (m.a0); the conduction bound uses the anisotropic
 // conductivity at F = I when m.k_fibre_ratio is not 0 or 1
 void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const tled_material &m,

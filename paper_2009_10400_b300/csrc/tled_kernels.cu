@@ -124,6 +124,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// 16-byte asynchronous global -> shared copy (L2 only); completion by cp_async_wait_all
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -292,7 +297,9 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, i
 // chunk's slot buffer at [corner][ec] (conflict-free).
 // ANI: transversely isotropic thermal expansion about the fibre (Eq. 11) and
 // conductivity along the current fibre; otherwise isotropic (F_th = lambda I).
-template <int NPE, int NPR, bool ANI>
+// BRICK (H8): the reference hourglass projections c_al vanish exactly for every
+// element, so the terms they multiply (and the corner coordinates) are dropped.
+template <int NPE, int NPR, bool ANI, bool BRICK>
 __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &SP, int64_t e, int ec, const int *cl,
                                              ElemIn<NPR> &E, const float4 *__restrict__ s_xu,
                                              const float4 *__restrict__ s_X, float4 *__restrict__ slot,
@@ -310,11 +317,16 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
         for (int i = 0; i < 8; i++) {
             const int a = cl[wht_corner(i)];
             const float4 q = s_xu[a];
-            const float4 x = s_X[a];
             wx[i] = q.x; wy[i] = q.y; wz[i] = q.z; wt[i] = q.w;
-            px[i] = x.x; py[i] = x.y; pz[i] = x.z;
+            if constexpr (!BRICK) {
+                const float4 x = s_X[a];
+                px[i] = x.x; py[i] = x.y; pz[i] = x.z;
+            }
         }
-        wht8(wx); wht8(wy); wht8(wz); wht8(wt); wht8(px); wht8(py); wht8(pz);
+        wht8(wx); wht8(wy); wht8(wz); wht8(wt);
+        if constexpr (!BRICK) {
+            wht8(px); wht8(py); wht8(pz);
+        }
         G[0][0] = -wx[1]; G[0][1] = -wx[2]; G[0][2] = -wx[4];
         G[1][0] = -wy[1]; G[1][1] = -wy[2]; G[1][2] = -wy[4];
         G[2][0] = -wz[1]; G[2][1] = -wz[2]; G[2][2] = -wz[4];
@@ -325,9 +337,11 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
         hu[0][1] = wy[3]; hu[1][1] = wy[6]; hu[2][1] = wy[5]; hu[3][1] = -wy[7];
         hu[0][2] = wz[3]; hu[1][2] = wz[6]; hu[2][2] = wz[5]; hu[3][2] = -wz[7];
         ht[0] = wt[3]; ht[1] = wt[6]; ht[2] = wt[5]; ht[3] = -wt[7];
-        cX[0][0] = px[3]; cX[1][0] = px[6]; cX[2][0] = px[5]; cX[3][0] = -px[7];
-        cX[0][1] = py[3]; cX[1][1] = py[6]; cX[2][1] = py[5]; cX[3][1] = -py[7];
-        cX[0][2] = pz[3]; cX[1][2] = pz[6]; cX[2][2] = pz[5]; cX[3][2] = -pz[7];
+        if constexpr (!BRICK) {
+            cX[0][0] = px[3]; cX[1][0] = px[6]; cX[2][0] = px[5]; cX[3][0] = -px[7];
+            cX[0][1] = py[3]; cX[1][1] = py[6]; cX[2][1] = py[5]; cX[3][1] = -py[7];
+            cX[0][2] = pz[3]; cX[1][2] = pz[6]; cX[2][2] = pz[5]; cX[3][2] = -pz[7];
+        }
     } else {
         float ux[4], uy[4], uz[4], th[4];
 #pragma unroll
@@ -538,28 +552,36 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
         const float khg = A.khg * (kap + (4.f / 3.f) * mu) * V * jn2 * (1.f / 64.f);
         const float khgT = A.khgT * kT * V * jn2 * (1.f / 64.f);
         float qa[4][3], qT[4];
-        float Wm[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        float wT[3] = {0.f, 0.f, 0.f};
+        if constexpr (BRICK) {  // c_al = 0: gamma_a,al = h_a,al and q_al = sum_b h_b,al u_b
 #pragma unroll
-        for (int l = 0; l < 4; l++) {
-#pragma unroll
-            for (int i = 0; i < 3; i++) {
-                qa[l][i] = hu[l][i] - (H[i][0] * cX[l][0] + H[i][1] * cX[l][1] + H[i][2] * cX[l][2]);
-#pragma unroll
-                for (int j = 0; j < 3; j++) Wm[i][j] += qa[l][i] * cX[l][j];
+            for (int l = 0; l < 4; l++) {
+                qa[l][0] = hu[l][0]; qa[l][1] = hu[l][1]; qa[l][2] = hu[l][2];
+                qT[l] = ht[l];
             }
-            qT[l] = ht[l] - (cX[l][0] * gth[0] + cX[l][1] * gth[1] + cX[l][2] * gth[2]);
-            wT[0] += qT[l] * cX[l][0]; wT[1] += qT[l] * cX[l][1]; wT[2] += qT[l] * cX[l][2];
+        } else {
+            float Wm[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+            float wT[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    qa[l][i] = hu[l][i] - (H[i][0] * cX[l][0] + H[i][1] * cX[l][1] + H[i][2] * cX[l][2]);
+#pragma unroll
+                    for (int j = 0; j < 3; j++) Wm[i][j] += qa[l][i] * cX[l][j];
+                }
+                qT[l] = ht[l] - (cX[l][0] * gth[0] + cX[l][1] * gth[1] + cX[l][2] * gth[2]);
+                wT[0] += qT[l] * cX[l][0]; wT[1] += qT[l] * cX[l][1]; wT[2] += qT[l] * cX[l][2];
+            }
+            // fold the -k_hg W dh_a/dX part into Q and r
+            const float kh8 = 0.125f * khg, kT8 = 0.125f * khgT;
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    Qm[i][k] -= kh8 * (Wm[i][0] * Ji[3 * k] + Wm[i][1] * Ji[3 * k + 1] + Wm[i][2] * Ji[3 * k + 2]);
+#pragma unroll
+            for (int k = 0; k < 3; k++) r[k] -= kT8 * (Ji[3 * k] * wT[0] + Ji[3 * k + 1] * wT[1] + Ji[3 * k + 2] * wT[2]);
         }
-        // fold the -k_hg W dh_a/dX part into Q and r
-        const float kh8 = 0.125f * khg, kT8 = 0.125f * khgT;
-#pragma unroll
-        for (int i = 0; i < 3; i++)
-#pragma unroll
-            for (int k = 0; k < 3; k++)
-                Qm[i][k] -= kh8 * (Wm[i][0] * Ji[3 * k] + Wm[i][1] * Ji[3 * k + 1] + Wm[i][2] * Ji[3 * k + 2]);
-#pragma unroll
-        for (int k = 0; k < 3; k++) r[k] -= kT8 * (Ji[3 * k] * wT[0] + Ji[3 * k + 1] * wT[1] + Ji[3 * k + 2] * wT[2]);
         // corner values by the inverse transform of the sign-vector coefficients
         float fx[8], fy[8], fz[8], ft[8];
         fx[0] = 0.f; fx[1] = -Qm[0][0]; fx[2] = -Qm[0][1]; fx[4] = -Qm[0][2];
@@ -597,12 +619,6 @@ __device__ __forceinline__ TileInfo tile_info(const StepArgs &A, int t) {
     const int4 b = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t + 1);
     return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 }
-// element type of tile t: the kernel's own, or the tile's in a mixed batch (NPE = 0)
-template <int NPE>
-__device__ __forceinline__ int tile_npe(const StepArgs &A, int t) {
-    if constexpr (NPE != 0) return NPE;
-    return __ldg(A.tile_info + kTileInfo * t + 7);
-}
 // bytes of a tile's element record for its element type (the stride is rec_bytes)
 __device__ __forceinline__ uint32_t rec_len(const StepArgs &A, int npe) {
     return (uint32_t)(kTile * npe * 2 + (A.n_comp - 6 * A.n_prony) * kTile * 4);
@@ -617,21 +633,26 @@ __device__ __forceinline__ void stage_elem(const StepArgs &A, int t, int npe, ch
     bulk_g2s(buf, A.elem_rec + (int64_t)t * A.rec_bytes, rb, bar);
     if (vb) bulk_g2s(buf + rb, A.visc + (int64_t)t * (vb / 4), vb, bar);
 }
-// gather record and interior (u, theta, X0) of tile T
+// gather record, interior (u, theta, X0) and shared-node lists (global index, partial
+// position; the lists start on 16-byte boundaries, the copy is rounded up to 4 entries) of tile T
 template <int NPE>
 __device__ __forceinline__ void stage_nodes(const StepArgs &A, int t, const TileInfo &T, char *smem, uint64_t *bar) {
     const uint32_t cb = (uint32_t)csr_rec_u16(NPE ? NPE : T.npe) * 2;
-    mbar_expect_tx(bar, cb + 32u * T.n_int);
+    const uint32_t sb = 4u * (uint32_t)((T.nl - T.n_int + 3) & ~3);
+    mbar_expect_tx(bar, cb + 32u * T.n_int + 2u * sb);
     bulk_g2s(smem + A.sm_csr, A.csr + (int64_t)t * A.csr_stride, cb, bar);
     if (T.n_int > 0) {
         bulk_g2s(smem + A.sm_xu, A.xu + T.ib, 16u * T.n_int, bar);
         bulk_g2s(smem + A.sm_X, A.X0 + T.ib, 16u * T.n_int, bar);
     }
+    if (sb) {
+        bulk_g2s(smem + A.sm_sh, A.tile_shared + T.sh_off, sb, bar);
+        bulk_g2s(smem + A.sm_sh + 4 * kMaxLocal, A.part_pos + T.sh_off, sb, bar);
+    }
 }
 // warm L2 with tile t's streams
 template <int NPE>
-__device__ void prefetch_tile(const StepArgs &A, int t) {
-    const TileInfo T = tile_info(A, t);
+__device__ void prefetch_tile(const StepArgs &A, int t, const TileInfo &T) {
     const int npe = NPE ? NPE : T.npe;
     prefetch_l2(A.elem_rec + (int64_t)t * A.rec_bytes, rec_len(A, npe));
     const uint32_t vb = visc_tile_bytes(A);
@@ -645,54 +666,76 @@ __device__ void prefetch_tile(const StepArgs &A, int t) {
         prefetch_l2(A.vel + T.ib, nb);
         prefetch_l2(A.nodec + T.ib, nb);
     }
+    const uint32_t sb = 4u * (uint32_t)((T.nl - T.n_int + 3) & ~3);
+    if (sb) {
+        prefetch_l2(A.tile_shared + T.sh_off, sb);
+        prefetch_l2(A.part_pos + T.sh_off, sb);
+    }
 }
 
-template <int NPE, int NPR, bool ANI>
+template <int NPE, int NPR, bool ANI, bool BRICK>
 __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
     __shared__ ScenStep S;
     __shared__ int s_abort;
-    __shared__ int s_ppos[kMaxLocal];  // partial-sum positions of the tile's shared nodes
     const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_csr);
+    const int *s_shg = reinterpret_cast<const int *>(smem + A.sm_sh);  // shared node -> global index
+    const int *s_ppos = s_shg + kMaxLocal;                             // shared node -> partial position
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
     float4 *s_X = reinterpret_cast<float4 *>(smem + A.sm_X);
     float4 *ns = reinterpret_cast<float4 *>(smem + A.sm_ns);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);  // [0,1] element buffers, [2] nodes, [3] node state
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);  // [0] element buffer, [2] nodes, [3] node state
     const int G = gridDim.x;
 
     const int n_tiles = *A.n_active;  // tiles of unfinished scenarios form a prefix
+    TileInfo T{};
+    int scn = 0;
+    if ((int)blockIdx.x < n_tiles) {
+        T = tile_info(A, blockIdx.x);
+        scn = __ldg(A.tile_scn + blockIdx.x);
+    }
     if (threadIdx.x == 0) {
         for (int b = 0; b < 4; b++) mbar_init(&bar[b], 1);
         fence_barrier_init();
         s_abort = 0;
         if ((int)blockIdx.x < n_tiles) {
-            stage_elem(A, blockIdx.x, tile_npe<NPE>(A, blockIdx.x), smem, &bar[0]);
-            stage_nodes<NPE>(A, blockIdx.x, tile_info(A, blockIdx.x), smem, &bar[2]);
+            stage_elem(A, blockIdx.x, NPE ? NPE : T.npe, smem, &bar[0]);
+            stage_nodes<NPE>(A, blockIdx.x, T, smem, &bar[2]);
         }
     }
     __syncthreads();  // barrier init visible to all
     uint32_t ph_s = 0;
     int i = 0, cur_scn = -1;
     for (int t = blockIdx.x; t < n_tiles; t += G, i++) {
-        const TileInfo T = tile_info(A, t);
+        // the records of the next tile (and, for the L2 prefetch, of the one after), loaded
+        // here so that their latency hides behind this tile
+        const bool has_next = t + G < n_tiles;
+        TileInfo Tn = T;
+        int scn_n = scn;
+        if (has_next) {
+            Tn = tile_info(A, t + G);
+            scn_n = __ldg(A.tile_scn + t + G);
+        }
+        const bool has_pf = threadIdx.x == 0 && t + 2 * G < n_tiles;
+        TileInfo Tp = T;
+        if (has_pf) Tp = tile_info(A, t + 2 * G);
         const int npe = NPE ? NPE : T.npe;
         const uint16_t *s_row = s_code + kTile * npe;
         char *buf = smem;  // element inputs, then this tile's corner slots
         float4 *slot = reinterpret_cast<float4 *>(buf);
         const bool ns_smem = T.n_int > 0 && T.n_int <= kNsMax;
-        const int scn = __ldg(A.tile_scn + t);
         if (scn != cur_scn) {  // published by the barrier after the element inputs are read
             prepare_scen(A, scn, k, S, threadIdx.x, kBlock);
             cur_scn = scn;
         }
-        // ---- 1. shared nodes of the tile: ordinary loads (mostly L2 hits)
-        for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
-            const int64_t g = __ldg(A.tile_shared + T.sh_off + l - T.n_int);
-            s_ppos[l - T.n_int] = __ldg(A.part_pos + T.sh_off + l - T.n_int);
-            s_xu[l] = A.xu[g];
-            s_X[l] = __ldg(&A.X0[g]);
-        }
+        // ---- 1. gather record, interior nodes and shared-node lists (bulk copies); then the
+        //         shared nodes' (u, theta, X0) by 16-byte asynchronous copies (mostly L2 hits)
         bool ok = mbar_wait(&bar[2], i & 1);
+        for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
+            const int64_t g = s_shg[l - T.n_int];
+            cp_async16(&s_xu[l], &A.xu[g]);
+            if constexpr (!BRICK) cp_async16(&s_X[l], &A.X0[g]);  // bricks: only interior X0 is read
+        }
         ok = mbar_wait(&bar[0], i & 1) && ok;
         if (!ok) {
             atomicOr(A.status, kStatusTimeout);
@@ -708,6 +751,7 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
             else if (npe == 8) load_elem<8, NPR>(A, buf, ec, cl, E);
             else load_elem<4, NPR>(A, buf, ec, cl, E);
         }
+        cp_async_wait_all();
         __syncthreads();
         if (s_abort) return;
         if (threadIdx.x == 0) {
@@ -718,18 +762,17 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
                 bulk_g2s(ns + T.n_int, A.vel + T.ib, 16u * T.n_int, &bar[3]);
                 bulk_g2s(ns + 2 * T.n_int, A.nodec + T.ib, 16u * T.n_int, &bar[3]);
             }
-            if (t + 2 * G < n_tiles) prefetch_tile<NPE>(A, t + 2 * G);
+            if (has_pf) prefetch_tile<NPE>(A, t + 2 * G, Tp);
         }
         // ---- 3. element pass
         if (active) {
             float *gv = A.visc + (int64_t)t * A.n_prony * 6 * kTile + ec;
-            if constexpr (NPE != 0) element_step<NPE, NPR, ANI>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
-            else if (npe == 8) element_step<8, NPR, ANI>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
-            else element_step<4, NPR, ANI>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            if constexpr (NPE != 0) element_step<NPE, NPR, ANI, BRICK>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else if (npe == 8) element_step<8, NPR, ANI, false>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
+            else element_step<4, NPR, ANI, false>(A, S, (int64_t)t * kTile + ec, ec, cl, E, s_xu, s_X, slot, gv);
         }
         __syncthreads();
-        // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum,
-        //         and the last of the node's tiles to arrive sums the partials in tile order
+        // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum
         if (ns_smem) {
             if (!mbar_wait(&bar[3], ph_s)) atomicOr(A.status, kStatusTimeout);
             ph_s ^= 1;
@@ -764,12 +807,14 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         }
         __syncthreads();
         // ---- 5. stage the next tile's element record (into the consumed slot buffer),
-        //         gather record and interior nodes
-        if (threadIdx.x == 0 && t + G < n_tiles) {
+        //         gather record, interior nodes and shared-node lists
+        if (threadIdx.x == 0 && has_next) {
             fence_proxy_async();
-            stage_elem(A, t + G, tile_npe<NPE>(A, t + G), smem, &bar[0]);
-            stage_nodes<NPE>(A, t + G, tile_info(A, t + G), smem, &bar[2]);
+            stage_elem(A, t + G, NPE ? NPE : Tn.npe, smem, &bar[0]);
+            stage_nodes<NPE>(A, t + G, Tn, smem, &bar[2]);
         }
+        T = Tn;
+        scn = scn_n;
     }
 }
 
@@ -1099,6 +1144,8 @@ void tile_smem_layout(StepArgs &a, int npe) {
     off = align128(off + kNsMax * 48);
     a.sm_csr = off;
     off = align128(off + csr_rec_u16(npe) * 2);
+    a.sm_sh = off;
+    off = align128(off + 2 * kMaxLocal * 4);
     a.sm_xu = off;
     off = align128(off + kMaxLocal * 16);
     a.sm_X = off;
@@ -1116,24 +1163,25 @@ static cudaError_t set_smem(K kern, int bytes) {
 // the tile kernel instance for (element type, Prony terms, anisotropic thermal physics):
 // npe 8, 4 or 0 (mixed), n_prony 0..4, ani
 using TileKernel = void (*)(const StepArgs, const int);
-template <int NPE, bool ANI>
+template <int NPE, bool ANI, bool BRICK = false>
 static TileKernel tile_kernel_npr(int n_prony) {
     switch (n_prony) {
-        case 0: return tile_step_kernel<NPE, 0, ANI>;
-        case 1: return tile_step_kernel<NPE, 1, ANI>;
-        case 2: return tile_step_kernel<NPE, 2, ANI>;
-        case 3: return tile_step_kernel<NPE, 3, ANI>;
-        default: return tile_step_kernel<NPE, 4, ANI>;
+        case 0: return tile_step_kernel<NPE, 0, ANI, BRICK>;
+        case 1: return tile_step_kernel<NPE, 1, ANI, BRICK>;
+        case 2: return tile_step_kernel<NPE, 2, ANI, BRICK>;
+        case 3: return tile_step_kernel<NPE, 3, ANI, BRICK>;
+        default: return tile_step_kernel<NPE, 4, ANI, BRICK>;
     }
 }
 template <bool ANI>
-static TileKernel tile_kernel_ani(int npe, int n_prony) {
-    return npe == 8 ? tile_kernel_npr<8, ANI>(n_prony)
+static TileKernel tile_kernel_ani(int npe, bool brick, int n_prony) {
+    return npe == 8 ? (brick ? tile_kernel_npr<8, ANI, true>(n_prony) : tile_kernel_npr<8, ANI>(n_prony))
          : npe == 4 ? tile_kernel_npr<4, ANI>(n_prony)
                     : tile_kernel_npr<0, ANI>(n_prony);
 }
 static TileKernel tile_kernel(const StepArgs &a, int npe) {
-    return a.ani ? tile_kernel_ani<true>(npe, a.n_prony) : tile_kernel_ani<false>(npe, a.n_prony);
+    const bool brick = a.brick != 0;
+    return a.ani ? tile_kernel_ani<true>(npe, brick, a.n_prony) : tile_kernel_ani<false>(npe, brick, a.n_prony);
 }
 
 cudaError_t tile_kernel_setup(const StepArgs &a, int npe) { return set_smem(tile_kernel(a, npe), a.sm_total); }

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtled.so")
 OK, E_ARG, E_MESH, E_STATE, E_CUDA, E_UNSTABLE, E_INVERTED, E_TIMEOUT, E_NOMEM, E_FORMAT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 T4, H8 = 4, 8
 HOST, DEVICE = 0, 1
-EXPANSION, TEMP_DEP, COMPENSATED, CEM43 = 1, 2, 4, 8
+EXPANSION, TEMP_DEP, COMPENSATED, CEM43, GENERAL_H8 = 1, 2, 4, 8, 16
 SRC_GAUSSIAN, SRC_SPHERE = 0, 1
 FIX_X, FIX_Y, FIX_Z, FIX_T = 1, 2, 4, 8
 
