@@ -37,7 +37,7 @@ constexpr int kSingleSources = tled::kMaxSources;
 
 struct Layout {
     size_t xu, lo, vel, X0, nodec, ubar, elem_rec, visc;
-    size_t tile_info, tile_shared, part_pos, csr, partials, sh_rowptr;
+    size_t tile_info, tile_shared, part_pos, pattern, partials, sh_rowptr;
     size_t scn, src, scn_time, scn_step, tile_scn, shared_scn, n_active, status;
     size_t node_new, probe_node, probe_w, probe_out, stat_part, stat_out, staging, cem;
     size_t total;
@@ -143,10 +143,10 @@ uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ULL) {
 Scenario &single(tled_ctx *c) { return c->sc[0]; }
 int n_prony(const tled_ctx *c) { return c->sc.empty() ? 0 : c->sc[0].mat.n_prony; }
 
-// element record bytes of a tile of npe-node elements; the tile stride is rec_bytes(c, c->npe_max)
-size_t rec_bytes(const tled_ctx *c, int npe) {
+// element record bytes of a tile (float components; the connectivity is in the structure record)
+size_t rec_bytes(const tled_ctx *c) {
     const int ncomp = 10 + (c->has_mat ? 6 : 0) + (c->has_fib ? 3 : 0);
-    return (size_t)tled::kTile * npe * 2 + (size_t)ncomp * tled::kTile * 4;
+    return (size_t)ncomp * tled::kTile * 4;
 }
 // Prony state index of element slot e, component q (tile-blocked [t][6 n_prony][kTile])
 inline size_t visc_index(int np, int64_t e, int q) {
@@ -185,11 +185,11 @@ Layout make_layout(const tled_ctx *c) {
     L.X0 = take(16 * nn);
     L.nodec = take(16 * nn);
     L.ubar = take(any_ubar ? 16 * nn : 0);
-    L.elem_rec = take((size_t)p.n_tiles * rec_bytes(c, c->npe_max));
+    L.elem_rec = take((size_t)p.n_tiles * rec_bytes(c));
     L.visc = take(4 * 6 * (size_t)std::max(n_prony(c), 0) * ne);
     L.tile_info = take(4 * p.tile_info.size());
     L.tile_shared = take(4 * p.tile_shared.size());
-    L.csr = take(2 * p.csr.size());
+    L.pattern = take(2 * p.patterns.size());
     L.partials = take(16 * (size_t)p.n_partials);
     L.sh_rowptr = take(4 * p.sh_rowptr.size());
     L.part_pos = take(4 * p.part_pos.size());
@@ -855,7 +855,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     }
     // --- element records (tile-blocked), lumped masses, nodal constants
     const int64_t nep = p.ne_pad;
-    const size_t rb = rec_bytes(c, c->npe_max);  // tile stride
+    const size_t rb = rec_bytes(c);  // tile stride
     const int kT = tled::kTile;
     std::vector<int32_t> scn_of_elem(c->ne);
     for (int si = 0; si < ns; si++)
@@ -875,8 +875,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         if (brick) brick = ke == 8 && tled::hourglass_projections_vanish(s.X.data(), cn);
         char *r = rec.data() + (size_t)(e / kT) * rb;
         const int ei = (int)(e % kT);
-        std::memcpy(r + (size_t)ei * ke * 2, &p.conn_local[(size_t)e * p.npe], (size_t)ke * 2);
-        float *cf = reinterpret_cast<float *>(r + (size_t)kT * ke * 2) + ei;
+        float *cf = reinterpret_cast<float *>(r) + ei;
         int q = 0;
         for (int j = 0; j < 9; j++) cf[(q++) * kT] = (float)Ji[j];
         cf[(q++) * kT] = (float)V;
@@ -933,7 +932,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     CUDA_TRY(c, up(L.elem_rec, rec.data(), rec.size()));
     CUDA_TRY(c, up(L.tile_info, p.tile_info.data(), 4 * p.tile_info.size()));
     CUDA_TRY(c, up(L.tile_shared, p.tile_shared.data(), 4 * p.tile_shared.size()));
-    CUDA_TRY(c, up(L.csr, p.csr.data(), 2 * p.csr.size()));
+    CUDA_TRY(c, up(L.pattern, p.patterns.data(), 2 * p.patterns.size()));
     CUDA_TRY(c, up(L.sh_rowptr, p.sh_rowptr.data(), 4 * p.sh_rowptr.size()));
     CUDA_TRY(c, up(L.part_pos, p.part_pos.data(), 4 * p.part_pos.size()));
     CUDA_TRY(c, up(L.node_new, node_new.data(), 4 * nn));
@@ -965,7 +964,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.ne = nep;
     A.tile_info = dptr<int>(c, L.tile_info);
     A.tile_shared = dptr<int>(c, L.tile_shared);
-    A.csr = dptr<uint16_t>(c, L.csr);
+    A.pattern = dptr<uint16_t>(c, L.pattern);
     A.partials = dptr<float4>(c, L.partials);
     A.part_pos = dptr<int>(c, L.part_pos);
     A.sh_rowptr = dptr<int>(c, L.sh_rowptr);
@@ -1002,6 +1001,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.brick = brick && !(s0.prm.flags & TLED_GENERAL_H8);
     A.T0 = m.T0;
     A.n_tiles = p.n_tiles;
+    A.pat_stride = p.pat_stride;
     tled::tile_smem_layout(A, npe);
     CUDA_TRY(c, tled::tile_kernel_setup(A, npe));
     int n_sm = 0;

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <unordered_map>
 
 #include "tled_internal.h"
 
@@ -330,9 +331,11 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     p.elem_old.assign(p.ne_pad, -1);
     for (int tt = 0; tt < p.n_tiles; tt++)
         for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) p.elem_old[tile_pad[tt] + (i - tile_begin[tt])] = sorted_old[i];
-    p.conn_local.assign((size_t)p.ne_pad * npe, 0);
-    const int rec = csr_rec_u16(npe);
-    p.csr.assign((size_t)p.n_tiles * rec, 0);
+    std::vector<uint16_t> conn_local((size_t)p.ne_pad * npe, 0);  // [slot][npe] tile-local node index
+    p.pat_stride = pattern_u16(npe);
+    p.patterns.clear();
+    std::unordered_map<uint64_t, std::vector<int32_t>> pat_by_hash;  // content hash -> pattern ids
+    std::vector<uint16_t> pat(p.pat_stride);
     std::vector<int32_t> local(nn, -1);
     std::vector<int32_t> sh_n(p.n_shared, 0);  // tiles touching each shared node so far
     int64_t part = 0;
@@ -350,7 +353,8 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
                 }
             }
         }
-        std::sort(shared.begin(), shared.end());
+        // shared nodes keep their first-appearance order in the tile, so that tiles of
+        // the same shape and position class get identical local structures
         const int nl = n_int + (int)shared.size();
         if (nl > kMaxLocal) {
             err = "internal: tile exceeds the local node limit";
@@ -363,7 +367,6 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
             p.part_pos.push_back(0);
         }
         ti[5] = (int32_t)p.tile_shared.size();
-        ti[6] = (int32_t)part;
         const int kt = nc(p.elem_old[e0]);
         ti[7] = kt;  // element type of the tile (4 or 8)
         for (size_t j = 0; j < shared.size(); j++) {
@@ -371,35 +374,51 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
             p.part_pos.push_back(sh_n[shared[j] - p.n_interior]++);  // rank; made absolute below
         }
         part += (int64_t)shared.size();
+        for (size_t j = 0; j < shared.size(); j++) local[shared[j]] = n_int + (int32_t)j;
         // local index of every node of the tile
         for (int64_t i = e0; i < e0 + ne_t; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
             for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++) {
-                int32_t g = p.node_new[cn[a]];
-                int l;
-                if (g < p.n_interior) {
-                    l = g - int_begin;
-                } else {
-                    l = n_int + (int)(std::lower_bound(shared.begin(), shared.end(), g) - shared.begin());
-                }
-                p.conn_local[(size_t)i * npe + a] = (uint16_t)l;
+                const int32_t g = p.node_new[cn[a]];
+                conn_local[(size_t)i * npe + a] = (uint16_t)(g < p.n_interior ? g - int_begin : local[g]);
             }
         }
-        // gather list: for every local node the slot offsets (corner * kTile +
-        // element) of its incident corners, ascending element then corner
-        uint16_t *rec_codes = &p.csr[(size_t)tt * rec];
+        // the tile's structure record: local connectivity [kTile][kt], then the gather
+        // list -- for every local node the slot offsets (corner * kTile + element) of its
+        // incident corners, ascending element then corner -- and the nl + 1 row offsets
+        std::fill(pat.begin(), pat.end(), (uint16_t)0);
+        uint16_t *rec_conn = pat.data();
+        uint16_t *rec_codes = rec_conn + kTile * kt;
         uint16_t *rec_row = rec_codes + kTile * kt;
+        for (int64_t i = e0; i < e0 + ne_t; i++)
+            for (int a = 0; a < kt; a++) rec_conn[(i - e0) * kt + a] = conn_local[(size_t)i * npe + a];
         std::vector<int32_t> cnt(nl + 1, 0);
         for (int64_t i = e0; i < e0 + ne_t; i++)
-            for (int a = 0; a < kt; a++) cnt[p.conn_local[(size_t)i * npe + a] + 1]++;
+            for (int a = 0; a < kt; a++) cnt[conn_local[(size_t)i * npe + a] + 1]++;
         for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
         for (int l = 0; l <= nl; l++) rec_row[l] = (uint16_t)cnt[l];
         std::vector<int32_t> cur(cnt.begin(), cnt.end() - 1);
         for (int64_t i = e0; i < e0 + ne_t; i++)
             for (int a = 0; a < kt; a++) {
-                int l = p.conn_local[(size_t)i * npe + a];
+                int l = conn_local[(size_t)i * npe + a];
                 rec_codes[cur[l]++] = (uint16_t)(a * kTile + (int)(i - e0));
             }
+        // tiles with the same structure share one record (FNV-1a hash, then a full compare)
+        uint64_t h = 1469598103934665603ull;
+        for (uint16_t v : pat) h = (h ^ v) * 1099511628211ull;
+        int32_t id = -1;
+        auto &cand = pat_by_hash[h];
+        for (int32_t c : cand)
+            if (std::equal(pat.begin(), pat.end(), p.patterns.begin() + (size_t)c * p.pat_stride)) {
+                id = c;
+                break;
+            }
+        if (id < 0) {
+            id = (int32_t)(p.patterns.size() / p.pat_stride);
+            p.patterns.insert(p.patterns.end(), pat.begin(), pat.end());
+            cand.push_back(id);
+        }
+        ti[6] = id;
     }
     while (p.tile_shared.size() % 4) {  // the last tile's padded copy stays inside the arrays
         p.tile_shared.push_back(-1);

@@ -16,8 +16,9 @@ constexpr int kTile = 256;         // elements per tile (one per thread); every 
 constexpr int kTileCtasPerSm = 3; // tile kernel CTAs resident per SM (register budget 85 per thread)
 constexpr int kMaxLocal = 448;     // max nodes touched by one tile (shared memory)
 constexpr int kNsMax = 256;        // interior nodes whose state is staged in shared memory
-// per-tile gather record (uint16): slot offsets [kTile * npe], then row offsets [kMaxLocal + 8]
-constexpr int csr_rec_u16(int npe) { return kTile * npe + kMaxLocal + 8; }
+// per-tile structure record (uint16): local connectivity [kTile * npe], gather slot
+// offsets [kTile * npe], row offsets [kMaxLocal + 8]; tiles of equal structure share one
+constexpr int pattern_u16(int npe) { return 2 * kTile * npe + kMaxLocal + 8; }
 constexpr int kMaxSources = 16;
 constexpr int kSrcRow = 11;        // doubles per source in the device table: c0, vel, sigma, P, t_on, t_off, shape
 constexpr int kTileInfo = 8;       // ints per tile record
@@ -41,11 +42,12 @@ struct Plan {
     int64_t n_interior = 0, n_shared = 0;
     int n_tiles = 0;
     std::vector<int32_t> tile_info;     // [n_tiles][8]: e0 (= tile * kTile), ne, int_begin, n_int,
-                                        //   n_local, sh_off, part_off, element type (4 or 8)
+                                        //   n_local, sh_off, structure record id, element type (4 or 8)
     std::vector<int32_t> tile_shared;   // per tile (from a multiple of 4, -1 padded): new ids of its shared nodes (ascending)
-    std::vector<uint16_t> conn_local;   // [ne_pad][npe] tile-local node index
-    std::vector<uint16_t> csr;          // [n_tiles][csr_rec_u16]: slot offsets corner * kTile + element, grouped
-                                        //   by local node (ascending element, corner), then the n_local + 1 row offsets
+    std::vector<uint16_t> patterns;     // [n_patterns][pat_stride] distinct structure records: local connectivity
+                                        //   [kTile][npe], slot offsets corner * kTile + element grouped by local
+                                        //   node (ascending element, corner), then the n_local + 1 row offsets
+    int pat_stride = 0;                 // pattern_u16(npe)
     std::vector<int32_t> sh_rowptr;     // [n_shared + 1]: node-major partial positions, tile order within a node
     std::vector<int32_t> part_pos;      // parallel to tile_shared: partial position of that (tile, node)
     int64_t n_partials = 0;
@@ -71,10 +73,10 @@ struct StepArgs {
     const float4 *X0;      // X.xyz, lumped volume V_i
     const float4 *nodec;   // m_i, Cth_i, mask bits (as float bits), 0
     const float4 *ubar;    // prescribed displacement or nullptr
-    // element data, tile-blocked: tile t's record at elem_rec + t * rec_bytes holds the local
-    // connectivity [kTile][npe] (uint16, npe = the tile's element type) then float components
-    // [q][kTile]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz]; the Prony state lives in
-    // visc [t][6 n_prony][kTile].  rec_bytes is the stride (the largest element type's record).
+    // element data, tile-blocked: tile t's record at elem_rec + t * rec_bytes holds float
+    // components [q][kTile]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz]; the Prony
+    // state lives in visc [t][6 n_prony][kTile]; the local connectivity is in the tile's
+    // structure record (pattern).
     const char *elem_rec;
     int64_t rec_bytes;
     int has_mat, has_fib;
@@ -83,7 +85,7 @@ struct StepArgs {
     // tiles
     const int *tile_info;
     const int *tile_shared;
-    const uint16_t *csr;   // [n_tiles][csr_stride]: csr_rec_u16(npe of the tile) entries used
+    const uint16_t *pattern;  // [n_patterns][pat_stride]: pattern_u16(npe of the tile) entries used
     float4 *partials;      // node-major: shared node s owns [sh_rowptr[s], sh_rowptr[s+1]), one per touching tile
     const int *part_pos;   // per (tile, shared node) entry of tile_shared: its partial's position
     const int *sh_rowptr;
@@ -103,9 +105,9 @@ struct StepArgs {
     // dynamic shared-memory layout of the tile kernel (bytes)
     int sm_in;             // bytes of a tile's staged element inputs (record + Prony state)
     int sm_buf;            // max(sm_in, slot buffer bytes), 128-aligned; two such buffers
-    int sm_ns, sm_csr, sm_sh, sm_xu, sm_X, sm_bar, sm_total;  // sm_sh: shared-node index lists
+    int sm_ns, sm_pat, sm_sh, sm_xu, sm_X, sm_bar, sm_total;  // sm_pat: structure record, sm_sh: shared-node lists
     int n_tiles;
-    int csr_stride;        // uint16 entries between consecutive tiles' gather records
+    int pat_stride;        // uint16 entries between consecutive structure records
     int n_comp;            // staged float components per element (J0^-1 9, V0, [mat 6], [fibre 3], Prony 6 n)
     // batch-wide scalars
     float mu, kappa, k1, k2, kc, alpha;   // uniform material (used when has_mat == 0)
@@ -139,7 +141,7 @@ cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w
 // read-back in caller order: mode 0 displacement [nn][3], 1 temperature, 2 damage fraction, 3 CEM43
 cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t nn, double T0, int mode, double *out,
                             cudaStream_t s);
-void tile_smem_layout(StepArgs &a, int npe);  // fills the sm_* fields and csr_stride
+void tile_smem_layout(StepArgs &a, int npe);  // fills the sm_* fields and pat_stride
 cudaError_t tile_kernel_setup(const StepArgs &a, int npe);
 // FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
 // damaged volume, out[6..7] = stored (hyperelastic) energy and hourglass energy; deterministic

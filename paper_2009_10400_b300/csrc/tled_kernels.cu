@@ -244,6 +244,28 @@ __device__ __forceinline__ void wht8(float *x) {
                 x[i + h] = a - b;
             }
 }
+// Paired form: two independent transforms (the two lanes of a float2) with
+// one packed f32x2 add or subtract per butterfly (sm_100+); same roundings.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ void wht8x2(float2 *x) {
+#pragma unroll
+    for (int h = 1; h < 8; h <<= 1)
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+            if ((i & h) == 0) {
+                const float2 a = x[i], b = x[i + h];
+                x[i] = add2(a, b);
+                x[i + h] = sub2(a, b);
+            }
+}
 // WHT index -> VTK corner (an involution)
 __device__ __forceinline__ constexpr int wht_corner(int i) { return i == 2 ? 3 : i == 3 ? 2 : i == 6 ? 7 : i == 7 ? 6 : i; }
 
@@ -257,20 +279,21 @@ struct ElemIn {
     float vs[NPR > 0 ? NPR : 1][6];
 };
 
-// Element inputs staged in shared memory for one tile: local connectivity
-// [kTile][NPE] (uint16), then float components [q][kTile]: J0^-1 (9), V0,
-// [mu kappa k1 k2 k alpha], [fibre xyz], Prony state (6 per term).
+// Element inputs staged in shared memory for one tile: the local connectivity
+// [kTile][NPE] (uint16, head of the structure record) and the float components
+// [q][kTile]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz], Prony state (6 per term).
 template <int NPE, int NPR>
-__device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, int ec, int *cl, ElemIn<NPR> &E) {
+__device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, const uint16_t *conn, int ec, int *cl,
+                                          ElemIn<NPR> &E) {
     if constexpr (NPE == 8) {
-        const uint4 c = reinterpret_cast<const uint4 *>(base)[ec];
+        const uint4 c = reinterpret_cast<const uint4 *>(conn)[ec];
         cl[0] = c.x & 0xffff; cl[1] = c.x >> 16; cl[2] = c.y & 0xffff; cl[3] = c.y >> 16;
         cl[4] = c.z & 0xffff; cl[5] = c.z >> 16; cl[6] = c.w & 0xffff; cl[7] = c.w >> 16;
     } else {
-        const uint2 c = reinterpret_cast<const uint2 *>(base)[ec];
+        const uint2 c = reinterpret_cast<const uint2 *>(conn)[ec];
         cl[0] = c.x & 0xffff; cl[1] = c.x >> 16; cl[2] = c.y & 0xffff; cl[3] = c.y >> 16;
     }
-    const float *cp = reinterpret_cast<const float *>(base + kTile * NPE * 2) + ec;
+    const float *cp = reinterpret_cast<const float *>(base) + ec;
     int q = 0;
 #pragma unroll
     for (int k = 0; k < 9; k++) E.Ji[k] = cp[(q++) * kTile];
@@ -312,20 +335,32 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     float G[3][3], gt[3], the;
     float hu[4][3], ht[4], cX[4][3];  // H8 hourglass projections
     if constexpr (NPE == 8) {
-        float wx[8], wy[8], wz[8], wt[8], px[8], py[8], pz[8];
+        // (u_x, u_y), (u_z, theta) and (X, Y) transformed in pairs, Z alone
+        float2 uxy[8], uzt[8], pxy[8];
+        float pz[8];
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             const int a = cl[wht_corner(i)];
             const float4 q = s_xu[a];
-            wx[i] = q.x; wy[i] = q.y; wz[i] = q.z; wt[i] = q.w;
+            uxy[i] = make_float2(q.x, q.y);
+            uzt[i] = make_float2(q.z, q.w);
             if constexpr (!BRICK) {
                 const float4 x = s_X[a];
-                px[i] = x.x; py[i] = x.y; pz[i] = x.z;
+                pxy[i] = make_float2(x.x, x.y);
+                pz[i] = x.z;
             }
         }
-        wht8(wx); wht8(wy); wht8(wz); wht8(wt);
+        wht8x2(uxy); wht8x2(uzt);
         if constexpr (!BRICK) {
-            wht8(px); wht8(py); wht8(pz);
+            wht8x2(pxy); wht8(pz);
+        }
+        float wx[8], wy[8], wz[8], wt[8], px[8], py[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            wx[i] = uxy[i].x; wy[i] = uxy[i].y; wz[i] = uzt[i].x; wt[i] = uzt[i].y;
+            if constexpr (!BRICK) {
+                px[i] = pxy[i].x; py[i] = pxy[i].y;
+            }
         }
         G[0][0] = -wx[1]; G[0][1] = -wx[2]; G[0][2] = -wx[4];
         G[1][0] = -wy[1]; G[1][1] = -wy[2]; G[1][2] = -wy[4];
@@ -592,9 +627,16 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
         fz[3] = khg * qa[0][2]; fz[6] = khg * qa[1][2]; fz[5] = khg * qa[2][2]; fz[7] = -khg * qa[3][2];
         ft[0] = 0.f; ft[1] = -r[0]; ft[2] = -r[1]; ft[4] = -r[2];
         ft[3] = khgT * qT[0]; ft[6] = khgT * qT[1]; ft[5] = khgT * qT[2]; ft[7] = -khgT * qT[3];
-        wht8(fx); wht8(fy); wht8(fz); wht8(ft);
+        float2 fxy[8], fzt[8];
 #pragma unroll
-        for (int i = 0; i < 8; i++) slot[wht_corner(i) * kTile + ec] = make_float4(fx[i], fy[i], fz[i], ft[i]);
+        for (int i = 0; i < 8; i++) {
+            fxy[i] = make_float2(fx[i], fy[i]);
+            fzt[i] = make_float2(fz[i], ft[i]);
+        }
+        wht8x2(fxy); wht8x2(fzt);
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+            slot[wht_corner(i) * kTile + ec] = make_float4(fxy[i].x, fxy[i].y, fzt[i].x, fzt[i].y);
     } else {
         // T4: dh_0 = -(dh_1 + dh_2 + dh_3), dh_{j+1} = row j of J0^-1
         slot[ec] = make_float4(-(Qm[0][0] + Qm[0][1] + Qm[0][2]), -(Qm[1][0] + Qm[1][1] + Qm[1][2]),
@@ -612,35 +654,33 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 }
 
 struct TileInfo {
-    int e0, ne_t, ib, n_int, nl, sh_off, part_off, npe;
+    int e0, ne_t, ib, n_int, nl, sh_off, pat, npe;  // pat: structure record id
 };
 __device__ __forceinline__ TileInfo tile_info(const StepArgs &A, int t) {
     const int4 a = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t);
     const int4 b = __ldg(reinterpret_cast<const int4 *>(A.tile_info) + 2 * t + 1);
     return TileInfo{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 }
-// bytes of a tile's element record for its element type (the stride is rec_bytes)
-__device__ __forceinline__ uint32_t rec_len(const StepArgs &A, int npe) {
-    return (uint32_t)(kTile * npe * 2 + (A.n_comp - 6 * A.n_prony) * kTile * 4);
-}
+// bytes of a tile's element record (float components; the stride is rec_bytes)
+__device__ __forceinline__ uint32_t rec_len(const StepArgs &A) { return (uint32_t)((A.n_comp - 6 * A.n_prony) * kTile * 4); }
 
 __device__ __forceinline__ uint32_t visc_tile_bytes(const StepArgs &A) { return (uint32_t)(A.n_prony * 6 * kTile * 4); }
 
-// element record + Prony state of tile t (element type npe) -> buf
-__device__ __forceinline__ void stage_elem(const StepArgs &A, int t, int npe, char *buf, uint64_t *bar) {
-    const uint32_t rb = rec_len(A, npe), vb = visc_tile_bytes(A);
+// element record + Prony state of tile t -> buf
+__device__ __forceinline__ void stage_elem(const StepArgs &A, int t, char *buf, uint64_t *bar) {
+    const uint32_t rb = rec_len(A), vb = visc_tile_bytes(A);
     mbar_expect_tx(bar, rb + vb);
     bulk_g2s(buf, A.elem_rec + (int64_t)t * A.rec_bytes, rb, bar);
     if (vb) bulk_g2s(buf + rb, A.visc + (int64_t)t * (vb / 4), vb, bar);
 }
-// gather record, interior (u, theta, X0) and shared-node lists (global index, partial
+// structure record, interior (u, theta, X0) and shared-node lists (global index, partial
 // position; the lists start on 16-byte boundaries, the copy is rounded up to 4 entries) of tile T
 template <int NPE>
-__device__ __forceinline__ void stage_nodes(const StepArgs &A, int t, const TileInfo &T, char *smem, uint64_t *bar) {
-    const uint32_t cb = (uint32_t)csr_rec_u16(NPE ? NPE : T.npe) * 2;
+__device__ __forceinline__ void stage_nodes(const StepArgs &A, const TileInfo &T, char *smem, uint64_t *bar) {
+    const uint32_t cb = (uint32_t)pattern_u16(NPE ? NPE : T.npe) * 2;
     const uint32_t sb = 4u * (uint32_t)((T.nl - T.n_int + 3) & ~3);
     mbar_expect_tx(bar, cb + 32u * T.n_int + 2u * sb);
-    bulk_g2s(smem + A.sm_csr, A.csr + (int64_t)t * A.csr_stride, cb, bar);
+    bulk_g2s(smem + A.sm_pat, A.pattern + (int64_t)T.pat * A.pat_stride, cb, bar);
     if (T.n_int > 0) {
         bulk_g2s(smem + A.sm_xu, A.xu + T.ib, 16u * T.n_int, bar);
         bulk_g2s(smem + A.sm_X, A.X0 + T.ib, 16u * T.n_int, bar);
@@ -654,10 +694,10 @@ __device__ __forceinline__ void stage_nodes(const StepArgs &A, int t, const Tile
 template <int NPE>
 __device__ void prefetch_tile(const StepArgs &A, int t, const TileInfo &T) {
     const int npe = NPE ? NPE : T.npe;
-    prefetch_l2(A.elem_rec + (int64_t)t * A.rec_bytes, rec_len(A, npe));
+    prefetch_l2(A.elem_rec + (int64_t)t * A.rec_bytes, rec_len(A));
     const uint32_t vb = visc_tile_bytes(A);
     if (vb) prefetch_l2(A.visc + (int64_t)t * (vb / 4), vb);
-    prefetch_l2(A.csr + (int64_t)t * A.csr_stride, (uint32_t)csr_rec_u16(npe) * 2);
+    prefetch_l2(A.pattern + (int64_t)T.pat * A.pat_stride, (uint32_t)pattern_u16(npe) * 2);
     if (T.n_int > 0) {
         const uint32_t nb = 16u * T.n_int;
         prefetch_l2(A.xu + T.ib, nb);
@@ -678,7 +718,7 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
     extern __shared__ __align__(128) char smem[];
     __shared__ ScenStep S;
     __shared__ int s_abort;
-    const uint16_t *s_code = reinterpret_cast<const uint16_t *>(smem + A.sm_csr);
+    const uint16_t *s_pat = reinterpret_cast<const uint16_t *>(smem + A.sm_pat);  // structure record
     const int *s_shg = reinterpret_cast<const int *>(smem + A.sm_sh);  // shared node -> global index
     const int *s_ppos = s_shg + kMaxLocal;                             // shared node -> partial position
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
@@ -699,8 +739,8 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         fence_barrier_init();
         s_abort = 0;
         if ((int)blockIdx.x < n_tiles) {
-            stage_elem(A, blockIdx.x, NPE ? NPE : T.npe, smem, &bar[0]);
-            stage_nodes<NPE>(A, blockIdx.x, T, smem, &bar[2]);
+            stage_elem(A, blockIdx.x, smem, &bar[0]);
+            stage_nodes<NPE>(A, T, smem, &bar[2]);
         }
     }
     __syncthreads();  // barrier init visible to all
@@ -720,7 +760,8 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         TileInfo Tp = T;
         if (has_pf) Tp = tile_info(A, t + 2 * G);
         const int npe = NPE ? NPE : T.npe;
-        const uint16_t *s_row = s_code + kTile * npe;
+        const uint16_t *s_code = s_pat + kTile * npe;  // gather slot offsets
+        const uint16_t *s_row = s_code + kTile * npe;   // and their row offsets
         char *buf = smem;  // element inputs, then this tile's corner slots
         float4 *slot = reinterpret_cast<float4 *>(buf);
         const bool ns_smem = T.n_int > 0 && T.n_int <= kNsMax;
@@ -728,7 +769,7 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
             prepare_scen(A, scn, k, S, threadIdx.x, kBlock);
             cur_scn = scn;
         }
-        // ---- 1. gather record, interior nodes and shared-node lists (bulk copies); then the
+        // ---- 1. structure record, interior nodes and shared-node lists (bulk copies); then the
         //         shared nodes' (u, theta, X0) by 16-byte asynchronous copies (mostly L2 hits)
         bool ok = mbar_wait(&bar[2], i & 1);
         for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
@@ -747,9 +788,9 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         int cl[NPE ? NPE : 8];
         ElemIn<NPR> E;
         if (active) {
-            if constexpr (NPE != 0) load_elem<NPE, NPR>(A, buf, ec, cl, E);
-            else if (npe == 8) load_elem<8, NPR>(A, buf, ec, cl, E);
-            else load_elem<4, NPR>(A, buf, ec, cl, E);
+            if constexpr (NPE != 0) load_elem<NPE, NPR>(A, buf, s_pat, ec, cl, E);
+            else if (npe == 8) load_elem<8, NPR>(A, buf, s_pat, ec, cl, E);
+            else load_elem<4, NPR>(A, buf, s_pat, ec, cl, E);
         }
         cp_async_wait_all();
         __syncthreads();
@@ -780,18 +821,20 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         for (int l = threadIdx.x; l < T.nl; l += kBlock) {
             int r = s_row[l];
             const int r1 = s_row[l + 1];
-            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+            // two running sums (even and odd entries), each as (x, y) and (z, w) pairs
+            float2 a0 = make_float2(0.f, 0.f), b0 = a0, a1 = a0, b1 = a0;
             for (; r + 1 < r1; r += 2) {
                 const float4 v0 = slot[s_code[r]];
                 const float4 v1 = slot[s_code[r + 1]];
-                a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
-                a1.x += v1.x; a1.y += v1.y; a1.z += v1.z; a1.w += v1.w;
+                a0 = add2(a0, make_float2(v0.x, v0.y)); b0 = add2(b0, make_float2(v0.z, v0.w));
+                a1 = add2(a1, make_float2(v1.x, v1.y)); b1 = add2(b1, make_float2(v1.z, v1.w));
             }
             if (r < r1) {
                 const float4 v0 = slot[s_code[r]];
-                a0.x += v0.x; a0.y += v0.y; a0.z += v0.z; a0.w += v0.w;
+                a0 = add2(a0, make_float2(v0.x, v0.y)); b0 = add2(b0, make_float2(v0.z, v0.w));
             }
-            const float4 acc = make_float4(a0.x + a1.x, a0.y + a1.y, a0.z + a1.z, a0.w + a1.w);
+            const float2 sxy = add2(a0, a1), szw = add2(b0, b1);
+            const float4 acc = make_float4(sxy.x, sxy.y, szw.x, szw.y);
             if (l < T.n_int) {
                 const int64_t g = (int64_t)T.ib + l;
                 float4 lo, vo, nc;
@@ -807,11 +850,11 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
         }
         __syncthreads();
         // ---- 5. stage the next tile's element record (into the consumed slot buffer),
-        //         gather record, interior nodes and shared-node lists
+        //         structure record, interior nodes and shared-node lists
         if (threadIdx.x == 0 && has_next) {
             fence_proxy_async();
-            stage_elem(A, t + G, NPE ? NPE : Tn.npe, smem, &bar[0]);
-            stage_nodes<NPE>(A, t + G, Tn, smem, &bar[2]);
+            stage_elem(A, t + G, smem, &bar[0]);
+            stage_nodes<NPE>(A, Tn, smem, &bar[2]);
         }
         T = Tn;
         scn = scn_n;
@@ -1012,8 +1055,8 @@ __global__ void __launch_bounds__(256) energy_partial_kernel(const StepArgs A, d
         const int ec = threadIdx.x;
         if (ec >= T.ne_t) continue;
         const char *base = A.elem_rec + (int64_t)t * A.rec_bytes;
-        const uint16_t *cl = reinterpret_cast<const uint16_t *>(base) + ec * npe;
-        const float *cp = reinterpret_cast<const float *>(base + kTile * npe * 2) + ec;
+        const uint16_t *cl = A.pattern + (int64_t)T.pat * A.pat_stride + ec * npe;
+        const float *cp = reinterpret_cast<const float *>(base) + ec;
         double Ji[9];
         int q = 0;
         for (int k = 0; k < 9; k++) Ji[k] = cp[(q++) * kTile];
@@ -1135,15 +1178,14 @@ static int align128(int x) { return (x + 127) & ~127; }
 
 void tile_smem_layout(StepArgs &a, int npe) {
     if (npe == 0) npe = 8;  // a mixed batch sizes everything for the larger element
-    a.csr_stride = csr_rec_u16(npe);
     a.n_comp = 10 + (a.has_mat ? 6 : 0) + (a.has_fib ? 3 : 0) + 6 * a.n_prony;
-    a.sm_in = align128(kTile * npe * 2 + a.n_comp * kTile * 4);
+    a.sm_in = align128(a.n_comp * kTile * 4);
     a.sm_buf = std::max(a.sm_in, kTile * npe * 16);
     int off = a.sm_buf;  // element inputs; once read into registers, the corner slot buffer
     a.sm_ns = off;
     off = align128(off + kNsMax * 48);
-    a.sm_csr = off;
-    off = align128(off + csr_rec_u16(npe) * 2);
+    a.sm_pat = off;
+    off = align128(off + pattern_u16(npe) * 2);
     a.sm_sh = off;
     off = align128(off + 2 * kMaxLocal * 4);
     a.sm_xu = off;
