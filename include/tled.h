@@ -71,6 +71,9 @@ extern "C" {
                                       reference hourglass projections vanish in float, e.g. voxels), which
                                       otherwise take a kernel without those zero terms; the two agree up to
                                       the compiler's multiply-add fusion (a few ulps) */
+#define TLED_STREAMED (1u << 5)    /* keep the streamed step (tile kernel + shared-node kernel per step) when
+                                      the problem would fit the resident mode (every scenario in one CTA's
+                                      shared memory, K steps per launch; same arithmetic, same results) */
 
 /* boundary mask bits (per node) */
 #define TLED_FIX_X 1u
@@ -310,13 +313,17 @@ int tled_scenario_dt(tled_ctx *ctx, int32_t index, double *dt);
 
 /* ---- autotuner ----
  * Time the candidate tilings (elements per tile 256 / 192 / 128, persistent
- * grid of one or two CTAs per SM) for `trial_steps` steps each in the
+ * grid of one or two CTAs per SM; and the resident mode when every scenario
+ * fits one CTA's shared memory) for `trial_steps` steps each in the
  * caller's workspace (bytes of it), keep the fastest, and leave the context
  * initialised with it at t = 0 (state reset).  The choice is cached in the
  * process per element type, size (log2 of the element count), material
  * layout and scenario count; a cached choice is applied without timing.
  * choice[0] elements per tile, [1] CTAs, [2] 1 if it came from the cache. */
 int tled_autotune(tled_ctx *ctx, void *dev_workspace, int64_t bytes, int32_t trial_steps, int32_t *choice);
+/* Step mode after init: *resident = 1 when the steps run in the resident mode (each
+ * scenario held by one CTA in shared memory for K steps per launch), 0 when streamed. */
+int tled_get_mode(tled_ctx *ctx, int32_t *resident);
 
 /* Scalar diagnostics, reduced on the device in FP64 in a fixed order
  * (deterministic).  With no damping, no viscous terms, fixed or free

@@ -38,7 +38,7 @@ constexpr int kSingleSources = tled::kMaxSources;
 struct Layout {
     size_t xu, lo, vel, X0, nodec, ubar, elem_rec, visc;
     size_t tile_info, tile_shared, part_pos, pattern, partials, sh_rowptr;
-    size_t scn, src, scn_time, scn_step, tile_scn, shared_scn, n_active, status;
+    size_t scn, src, scn_time, scn_step, tile_scn, shared_scn, n_active, status, res;
     size_t node_new, probe_node, probe_w, probe_out, stat_part, stat_out, staging, cem;
     size_t total;
 };
@@ -98,6 +98,7 @@ struct tled_ctx {
     std::vector<int32_t> probe_node;               // [n_probes][8] new node ids
     std::vector<float> probe_w;                    // [n_probes][8]
     int tile_override = 0, grid_override = 0;      // set by the autotuner
+    int mode_override = 0;                         // autotuner: 1 streamed, 2 resident (if it fits), 0 default
     // plan and device
     bool planned = false;
     Plan plan;
@@ -112,6 +113,8 @@ struct tled_ctx {
     int tile_ctas = 1;
     int shared_blocks = 1;         // persistent grid of the shared-node kernel
     int active_host[2] = {0, 0};   // last uploaded active prefix lengths
+    bool res_ok = false;           // every scenario fits one CTA's shared memory (resident mode possible)
+    bool resident = false;         // steps run by the resident kernel
 };
 
 namespace {
@@ -200,6 +203,7 @@ Layout make_layout(const tled_ctx *c) {
     L.tile_scn = take(4 * (size_t)p.n_tiles);
     L.shared_scn = take(4 * (size_t)p.n_shared);
     L.n_active = take(8);
+    L.res = take(sizeof(tled::ResDesc) * ns);
     L.status = take(16);
     L.node_new = take(4 * nn);
     L.probe_node = take(4 * 8 * (size_t)c->n_probes);
@@ -1009,6 +1013,40 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     c->tile_ctas = tled::tile_grid(A, npe, n_sm);
     c->shared_blocks = tled::shared_grid(A, n_sm);
     if (c->grid_override > 0) c->tile_ctas = std::min(c->tile_ctas, c->grid_override);
+    // resident mode: possible when every scenario (one element type, no dose field) fits one
+    // CTA's shared memory; one descriptor per rank (CTA b runs the scenario of rank b)
+    c->res_ok = c->resident = false;
+    if (npe != 0 && !cem_on(c)) {
+        std::vector<tled::ResDesc> rd(ns);
+        int nn_max = 0, nt_max = 0, np_max = 0, nsh_max = 0;
+        for (int r = 0; r < ns; r++) {
+            tled::ResDesc d{};
+            d.scn = c->scn_of_rank[r];
+            d.t0 = (int)c->tiles_upto[r];
+            d.n_t = (int)(c->tiles_upto[r + 1] - c->tiles_upto[r]);
+            d.i0 = d.n_t ? p.tile_info[(size_t)d.t0 * tled::kTileInfo + 2] : 0;
+            for (int t = d.t0; t < d.t0 + d.n_t; t++) d.n_int += p.tile_info[(size_t)t * tled::kTileInfo + 3];
+            d.s0 = (int)c->shared_upto[r];
+            d.n_sh = (int)(c->shared_upto[r + 1] - c->shared_upto[r]);
+            d.p0 = p.sh_rowptr[d.s0];
+            d.n_part = p.sh_rowptr[d.s0 + d.n_sh] - d.p0;
+            rd[r] = d;
+            nn_max = std::max(nn_max, d.n_int + d.n_sh);
+            nt_max = std::max(nt_max, d.n_t);
+            np_max = std::max(np_max, d.n_part);
+            nsh_max = std::max(nsh_max, d.n_sh);
+        }
+        const int need = tled::resident_smem_layout(A, npe, nn_max, nt_max, np_max, nsh_max);
+        if (need <= tled::resident_smem_limit() && nn_max < 65536) {
+            CUDA_TRY(c, cudaMemcpyAsync(c->ws + L.res, rd.data(), sizeof(tled::ResDesc) * ns, cudaMemcpyHostToDevice,
+                                        c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            A.res = dptr<tled::ResDesc>(c, L.res);
+            CUDA_TRY(c, tled::resident_kernel_setup(A, npe));
+            c->res_ok = true;
+            c->resident = c->mode_override == 2 || (c->mode_override == 0 && !(s0.prm.flags & TLED_STREAMED));
+        }
+    }
     // set-up hash for checkpoints
     uint64_t h = 1469598103934665603ULL;
     for (auto &s : c->sc) {
@@ -1057,10 +1095,14 @@ static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     }
     CUDA_TRY(c, cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < K && e == cudaSuccess; k++) {
-        if (c->A.cem) e = tled::launch_cem43(c->A, c->nn, k, c->cap);  // dose at T(t), before the update
-        if (e == cudaSuccess) e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
-        if (e == cudaSuccess) e = tled::launch_shared_step(c->A, c->shared_blocks, k, c->cap);
+    if (c->resident) {  // K steps in one launch, one CTA per scenario (finished ones return at once)
+        e = tled::launch_resident_step(c->A, (int)c->sc.size(), c->npe, K, c->cap);
+    } else {
+        for (int k = 0; k < K && e == cudaSuccess; k++) {
+            if (c->A.cem) e = tled::launch_cem43(c->A, c->nn, k, c->cap);  // dose at T(t), before the update
+            if (e == cudaSuccess) e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
+            if (e == cudaSuccess) e = tled::launch_shared_step(c->A, c->shared_blocks, k, c->cap);
+        }
     }
     if (e == cudaSuccess) e = tled::launch_bump(c->A, K, c->cap);
     cudaGraph_t graph = nullptr;
@@ -1251,9 +1293,11 @@ int tled_step_timed(tled_ctx *c, int64_t n, double *ms) {
     for (int64_t i = 0; i < n && err == cudaSuccess; i++) {
         if (c->A.cem) err = tled::launch_cem43(c->A, c->nn, 0, c->stream);
         cudaEventRecord(ev[3 * i], c->stream);
-        if (err == cudaSuccess) err = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
+        if (err == cudaSuccess)
+            err = c->resident ? tled::launch_resident_step(c->A, (int)c->sc.size(), c->npe, 1, c->stream)
+                              : tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
         cudaEventRecord(ev[3 * i + 1], c->stream);
-        if (err == cudaSuccess) err = tled::launch_shared_step(c->A, c->shared_blocks, 0, c->stream);
+        if (err == cudaSuccess && !c->resident) err = tled::launch_shared_step(c->A, c->shared_blocks, 0, c->stream);
         cudaEventRecord(ev[3 * i + 2], c->stream);
         if (err == cudaSuccess) err = tled::launch_bump(c->A, 1, c->stream);
     }
@@ -1338,7 +1382,10 @@ int tled_get_stats_noalloc(tled_ctx *c, int32_t n_blocks, double *out) {
 // layout), and the context is left initialised with it at t = 0.
 namespace {
 std::mutex g_tune_mu;
-std::map<uint64_t, std::pair<int, int>> g_tune_cache;
+struct TuneChoice {
+    int tile_elems, grid, mode;  // mode: 1 streamed, 2 resident
+};
+std::map<uint64_t, TuneChoice> g_tune_cache;
 }  // namespace
 
 int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial_steps, int32_t *choice) {
@@ -1351,7 +1398,7 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
     const int bucket = (int)std::floor(std::log2((double)std::max<int64_t>(ne, 1)));
     const uint64_t key = ((uint64_t)c->npe << 56) ^ ((uint64_t)bucket << 40) ^ ((uint64_t)c->has_mat << 36) ^
                          ((uint64_t)c->has_fib << 35) ^ ((uint64_t)n_prony(c) << 32) ^ (uint64_t)c->sc.size();
-    std::pair<int, int> best{0, 0};
+    TuneChoice best{0, 0, 1};
     bool cached = false;
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);
@@ -1365,15 +1412,23 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
         double best_ms = INFINITY;
         int n_sm = 0;
         CUDA_TRY(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
-        const int tiles[] = {256, 192, 128};
-        for (int te : tiles)
-            for (int gscale = 0; gscale < 2; gscale++) {
+        // candidates: (elements per tile, grid scale, mode); the resident candidate is
+        // skipped when the problem does not fit it
+        struct Cand {
+            int te, gscale, mode;
+        };
+        const Cand cands[] = {{256, 0, 2}, {256, 0, 1}, {256, 1, 1}, {192, 0, 1}, {192, 1, 1}, {128, 0, 1}, {128, 1, 1}};
+        for (const Cand &cd : cands) {
+            const int te = cd.te;
+            {
                 invalidate(c);
                 c->tile_override = te;
-                c->grid_override = gscale == 1 ? n_sm : 0;
+                c->grid_override = cd.gscale == 1 ? n_sm : 0;
+                c->mode_override = cd.mode;
                 if (int rc = ensure_plan(c)) return rc;
                 if ((int64_t)c->L.total > bytes) continue;  // does not fit the caller's workspace
                 if (int rc = tled_init(c, dev_workspace, bytes)) return rc;
+                if (cd.mode == 2 && !c->resident) continue;  // no resident mode for this problem
                 if (int rc = run_steps(c, 3, nullptr)) return rc;  // graphs captured, caches warm
                 cudaEvent_t e0, e1;
                 CUDA_TRY(c, cudaEventCreate(&e0));
@@ -1389,23 +1444,32 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
                 if (rc) return rc;
                 if (ms < best_ms) {
                     best_ms = ms;
-                    best = {te, c->grid_override};
+                    best = {te, c->grid_override, cd.mode};
                 }
             }
+        }
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = best;
     }
     invalidate(c);
-    c->tile_override = best.first;
-    c->grid_override = best.second;
+    c->tile_override = best.tile_elems;
+    c->grid_override = best.grid;
+    c->mode_override = best.mode;
     if (int rc = ensure_plan(c)) return rc;
     if ((int64_t)c->L.total > bytes) return fail(c, TLED_E_NOMEM, "workspace too small for the tuned plan");
     if (int rc = tled_init(c, dev_workspace, bytes)) return rc;
     if (choice) {
-        choice[0] = best.first;
+        choice[0] = best.tile_elems;
         choice[1] = c->tile_ctas;
         choice[2] = cached;
     }
+    return TLED_OK;
+}
+
+int tled_get_mode(tled_ctx *c, int32_t *resident) {
+    if (!c || !resident) return fail(c, TLED_E_ARG, "NULL argument");
+    if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
+    *resident = c->resident ? 1 : 0;
     return TLED_OK;
 }
 

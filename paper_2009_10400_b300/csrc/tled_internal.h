@@ -16,6 +16,8 @@ constexpr int kTile = 256;         // elements per tile (one per thread); every 
 constexpr int kTileCtasPerSm = 3; // tile kernel CTAs resident per SM (register budget 85 per thread)
 constexpr int kMaxLocal = 448;     // max nodes touched by one tile (shared memory)
 constexpr int kNsMax = 256;        // interior nodes whose state is staged in shared memory
+constexpr int kResLanes = 2;       // resident mode: tiles processed side by side in one CTA
+constexpr int kResBlock = kResLanes * kBlock;
 // per-tile structure record (uint16): local connectivity [kTile * npe], gather slot
 // offsets [kTile * npe], row offsets [kMaxLocal + 8]; tiles of equal structure share one
 constexpr int pattern_u16(int npe) { return 2 * kTile * npe + kMaxLocal + 8; }
@@ -51,6 +53,19 @@ struct Plan {
     std::vector<int32_t> sh_rowptr;     // [n_shared + 1]: node-major partial positions, tile order within a node
     std::vector<int32_t> part_pos;      // parallel to tile_shared: partial position of that (tile, node)
     int64_t n_partials = 0;
+};
+
+// Resident mode: one CTA holds a whole scenario (its tiles' element data, structure
+// records, node state and partial sums) in shared memory and runs many steps in one
+// launch, one block barrier between phases instead of a kernel boundary.  One
+// descriptor per CTA, in rank order.
+struct ResDesc {
+    int scn;          // scenario
+    int t0, n_t;      // tiles [t0, t0 + n_t)
+    int i0, n_int;    // interior nodes [i0, i0 + n_int)
+    int s0, n_sh;     // shared nodes [n_interior + s0, n_interior + s0 + n_sh)
+    int p0, n_part;   // their node-major partial sums [p0, p0 + n_part)
+    int pad[3];
 };
 
 // Constant per-scenario parameters (device table).
@@ -122,6 +137,11 @@ struct StepArgs {
     int brick;                            // every element an H8 whose reference hourglass projections vanish
     float ani_alpha, ani_k;               // fibre / transverse expansion and conductivity
     double ramp_time;
+    // resident mode (shared-memory byte offsets; rs_tile is the per-tile block stride and
+    // rt_* are offsets inside a tile block)
+    const ResDesc *res;
+    int rs_xu, rs_lo, rs_vel, rs_X, rs_nc, rs_rowptr, rs_part, rs_slot, rs_tiles, rs_tile, rs_total;
+    int rt_conn, rt_codes, rt_ppos, rt_info;
 };
 
 // kernel launchers (tled_kernels.cu); npe 4 or 8, or 0 for a batch mixing both element types
@@ -143,6 +163,12 @@ cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t 
                             cudaStream_t s);
 void tile_smem_layout(StepArgs &a, int npe);  // fills the sm_* fields and pat_stride
 cudaError_t tile_kernel_setup(const StepArgs &a, int npe);
+// resident mode: shared-memory layout for the largest scenario (returns the bytes), the
+// kernel's attribute set-up, and a launch of K steps for the first n_ctas descriptors
+int resident_smem_layout(StepArgs &a, int npe, int nn_max, int nt_max, int npart_max, int nsh_max);
+int resident_smem_limit();
+cudaError_t resident_kernel_setup(const StepArgs &a, int npe);
+cudaError_t launch_resident_step(const StepArgs &a, int n_ctas, int npe, int K, cudaStream_t s);
 // FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
 // damaged volume, out[6..7] = stored (hyperelastic) energy and hourglass energy; deterministic
 // two-stage reduction through `partials` [kStatBlocks][8].

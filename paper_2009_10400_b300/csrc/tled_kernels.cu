@@ -154,8 +154,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // xu: (u_hi, theta_hi); X: (X0, V_i); lo: (u_lo, theta_lo); vo: (v, Omega);
 // nc: (1/m_i, 1/C_i, mask bits, K_b,i); f: (internal force, thermal load).
 // nc.w: perfusion conductance w_b c_b V_i of the node.
-__device__ __forceinline__ void node_update(const StepArgs &A, const ScenStep &S, int64_t g, float4 f, float4 xu,
-                                            float4 X, float4 lo, float4 vo, float4 nc) {
+// The new state goes to xo (u_hi, theta_hi), lo_o (u_lo, theta_lo), vo_o (v, Omega).
+__device__ __forceinline__ void node_advance(const StepArgs &A, const ScenStep &S, int64_t g, float4 f, float4 xu,
+                                             float4 X, float4 lo, float4 vo, float4 nc, float4 &xo, float4 &lo_o,
+                                             float4 &vo_o) {
     const unsigned mask = __float_as_uint(nc.z);
     const bool comp = (A.flags & TLED_COMPENSATED) != 0;
     const float dt = S.dtf;
@@ -219,9 +221,18 @@ __device__ __forceinline__ void node_update(const StepArgs &A, const ScenStep &S
         atomicOr(A.status, kStatusNaN);
         atomicMin(A.status + 2, (unsigned)g);
     }
-    A.xu[g] = make_float4(u[0], u[1], u[2], th);
-    A.lo[g] = make_float4(ul[0], ul[1], ul[2], tl);
-    A.vel[g] = make_float4(v[0], v[1], v[2], Om);
+    xo = make_float4(u[0], u[1], u[2], th);
+    lo_o = make_float4(ul[0], ul[1], ul[2], tl);
+    vo_o = make_float4(v[0], v[1], v[2], Om);
+}
+// ... stored to node g's state in global memory
+__device__ __forceinline__ void node_update(const StepArgs &A, const ScenStep &S, int64_t g, float4 f, float4 xu,
+                                            float4 X, float4 lo, float4 vo, float4 nc) {
+    float4 a, b, c;
+    node_advance(A, S, g, f, xu, X, lo, vo, nc, a, b, c);
+    A.xu[g] = a;
+    A.lo[g] = b;
+    A.vel[g] = c;
 }
 
 // ---------------------------------------------------------------------------
@@ -713,6 +724,26 @@ __device__ void prefetch_tile(const StepArgs &A, int t, const TileInfo &T) {
     }
 }
 
+// fixed-order sum of local node l's corner slots (ascending element, corner): two
+// running sums (even and odd entries), each as (x, y) and (z, w) pairs
+__device__ __forceinline__ float4 gather_node(const float4 *slot, const uint16_t *s_code, const uint16_t *s_row, int l) {
+    int r = s_row[l];
+    const int r1 = s_row[l + 1];
+    float2 a0 = make_float2(0.f, 0.f), b0 = a0, a1 = a0, b1 = a0;
+    for (; r + 1 < r1; r += 2) {
+        const float4 v0 = slot[s_code[r]];
+        const float4 v1 = slot[s_code[r + 1]];
+        a0 = add2(a0, make_float2(v0.x, v0.y)); b0 = add2(b0, make_float2(v0.z, v0.w));
+        a1 = add2(a1, make_float2(v1.x, v1.y)); b1 = add2(b1, make_float2(v1.z, v1.w));
+    }
+    if (r < r1) {
+        const float4 v0 = slot[s_code[r]];
+        a0 = add2(a0, make_float2(v0.x, v0.y)); b0 = add2(b0, make_float2(v0.z, v0.w));
+    }
+    const float2 sxy = add2(a0, a1), szw = add2(b0, b1);
+    return make_float4(sxy.x, sxy.y, szw.x, szw.y);
+}
+
 template <int NPE, int NPR, bool ANI, bool BRICK>
 __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
@@ -819,22 +850,7 @@ __global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const
             ph_s ^= 1;
         }
         for (int l = threadIdx.x; l < T.nl; l += kBlock) {
-            int r = s_row[l];
-            const int r1 = s_row[l + 1];
-            // two running sums (even and odd entries), each as (x, y) and (z, w) pairs
-            float2 a0 = make_float2(0.f, 0.f), b0 = a0, a1 = a0, b1 = a0;
-            for (; r + 1 < r1; r += 2) {
-                const float4 v0 = slot[s_code[r]];
-                const float4 v1 = slot[s_code[r + 1]];
-                a0 = add2(a0, make_float2(v0.x, v0.y)); b0 = add2(b0, make_float2(v0.z, v0.w));
-                a1 = add2(a1, make_float2(v1.x, v1.y)); b1 = add2(b1, make_float2(v1.z, v1.w));
-            }
-            if (r < r1) {
-                const float4 v0 = slot[s_code[r]];
-                a0 = add2(a0, make_float2(v0.x, v0.y)); b0 = add2(b0, make_float2(v0.z, v0.w));
-            }
-            const float2 sxy = add2(a0, a1), szw = add2(b0, b1);
-            const float4 acc = make_float4(sxy.x, sxy.y, szw.x, szw.y);
+            const float4 acc = gather_node(slot, s_code, s_row, l);
             if (l < T.n_int) {
                 const int64_t g = (int64_t)T.ib + l;
                 float4 lo, vo, nc;
@@ -906,6 +922,138 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
             prepare_scen(A, scn, k, L, 0, 1);
             node_update(A, L, g, acc, xu, X, lo, vo, nc);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// resident mode: one CTA per scenario holds the whole scenario in shared memory
+// and runs K steps.  Per step, the scenario's tiles two at a time (two lanes of
+// 256 threads: element pass, fixed-order gather, interior node updates, partial
+// sums of shared nodes -- two tiles share no interior node), then its shared
+// nodes (partials in tile order): the arithmetic and its order are those of the
+// tile and shared-node kernels.
+// ---------------------------------------------------------------------------
+template <int NPE, int NPR, bool ANI, bool BRICK>
+__global__ void __launch_bounds__(kResBlock, 1) resident_step_kernel(const StepArgs A, const int K) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ ScenStep S;
+    const ResDesc D = A.res[blockIdx.x];
+    if (D.t0 >= *A.n_active) return;  // a finished scenario (active tiles form a prefix)
+    float4 *r_xu = reinterpret_cast<float4 *>(smem + A.rs_xu);
+    float4 *r_lo = reinterpret_cast<float4 *>(smem + A.rs_lo);
+    float4 *r_vel = reinterpret_cast<float4 *>(smem + A.rs_vel);
+    float4 *r_X = reinterpret_cast<float4 *>(smem + A.rs_X);
+    float4 *r_nc = reinterpret_cast<float4 *>(smem + A.rs_nc);
+    int *r_rowptr = reinterpret_cast<int *>(smem + A.rs_rowptr);
+    float4 *r_part = reinterpret_cast<float4 *>(smem + A.rs_part);
+    const int tid = threadIdx.x;
+    const int lane = tid / kBlock, lt = tid % kBlock;  // tile lane, thread within it
+    float4 *slot = reinterpret_cast<float4 *>(smem + A.rs_slot) + lane * kTile * NPE;
+    const int nn_s = D.n_int + D.n_sh;
+    const int nfix = A.n_comp - 6 * A.n_prony;  // record floats before the Prony state
+    // scenario-local node q: interior nodes first, then shared nodes
+    auto gnode = [&](int q) -> int64_t { return q < D.n_int ? (int64_t)D.i0 + q : A.n_interior + D.s0 + (q - D.n_int); };
+
+    // ---- the scenario into shared memory: node state, and per tile its element record and
+    //      Prony state, its connectivity in scenario-local node numbers, gather lists and
+    //      shared-node partial positions
+    for (int q = tid; q < nn_s; q += kResBlock) {
+        const int64_t g = gnode(q);
+        r_xu[q] = A.xu[g];
+        r_lo[q] = A.lo[g];
+        r_vel[q] = A.vel[g];
+        r_X[q] = __ldg(&A.X0[g]);
+        r_nc[q] = __ldg(&A.nodec[g]);
+    }
+    for (int q = tid; q <= D.n_sh; q += kResBlock) r_rowptr[q] = __ldg(A.sh_rowptr + D.s0 + q) - D.p0;
+    for (int j = 0; j < D.n_t; j++) {
+        const int t = D.t0 + j;
+        const TileInfo T = tile_info(A, t);
+        char *blk = smem + A.rs_tiles + j * A.rs_tile;
+        float *rec = reinterpret_cast<float *>(blk);
+        const float *grec = reinterpret_cast<const float *>(A.elem_rec + (int64_t)t * A.rec_bytes);
+        for (int i = tid; i < nfix * kTile; i += kResBlock) rec[i] = __ldg(grec + i);
+        const float *gvs = A.visc + (int64_t)t * A.n_prony * 6 * kTile;
+        for (int i = tid; i < 6 * A.n_prony * kTile; i += kResBlock) rec[nfix * kTile + i] = gvs[i];
+        const uint16_t *pat = A.pattern + (int64_t)T.pat * A.pat_stride;
+        uint16_t *conn = reinterpret_cast<uint16_t *>(blk + A.rt_conn);
+        for (int i = tid; i < kTile * NPE; i += kResBlock) {
+            int q = 0;
+            if (i < T.ne_t * NPE) {
+                const int l = pat[i];
+                q = l < T.n_int ? (T.ib - D.i0) + l
+                                : D.n_int + (__ldg(A.tile_shared + T.sh_off + l - T.n_int) - (int)A.n_interior - D.s0);
+            }
+            conn[i] = (uint16_t)q;
+        }
+        uint16_t *codes = reinterpret_cast<uint16_t *>(blk + A.rt_codes);
+        for (int i = tid; i < kTile * NPE + kMaxLocal + 8; i += kResBlock) codes[i] = pat[kTile * NPE + i];
+        int *ppos = reinterpret_cast<int *>(blk + A.rt_ppos);
+        for (int m = tid; m < T.nl - T.n_int; m += kResBlock) ppos[m] = __ldg(A.part_pos + T.sh_off + m) - D.p0;
+        if (tid == 0) {
+            int *ti = reinterpret_cast<int *>(blk + A.rt_info);
+            ti[0] = T.ne_t; ti[1] = T.ib - D.i0; ti[2] = T.n_int; ti[3] = T.nl;
+        }
+    }
+    __syncthreads();
+
+    // ---- K steps
+    for (int k = 0; k < K; k++) {
+        prepare_scen(A, D.scn, k, S, tid, kResBlock);
+        __syncthreads();
+        for (int j0 = 0; j0 < D.n_t; j0 += kResLanes) {
+            const int j = j0 + lane;
+            const bool on = j < D.n_t;  // this lane has a tile in this round
+            char *blk = smem + A.rs_tiles + (on ? j : j0) * A.rs_tile;
+            const int *ti = reinterpret_cast<const int *>(blk + A.rt_info);
+            const int ne_t = on ? ti[0] : 0, q0 = on ? ti[1] : 0, n_int = on ? ti[2] : 0, nl = on ? ti[3] : 0;
+            const uint16_t *codes = reinterpret_cast<const uint16_t *>(blk + A.rt_codes);
+            const uint16_t *rows = codes + kTile * NPE;
+            const int *ppos = reinterpret_cast<const int *>(blk + A.rt_ppos);
+            if (lt < ne_t) {
+                int cl[NPE];
+                ElemIn<NPR> E;
+                load_elem<NPE, NPR>(A, blk, reinterpret_cast<const uint16_t *>(blk + A.rt_conn), lt, cl, E);
+                element_step<NPE, NPR, ANI, BRICK>(A, S, (int64_t)(D.t0 + j) * kTile + lt, lt, cl, E, r_xu, r_X, slot,
+                                                   reinterpret_cast<float *>(blk) + nfix * kTile + lt);
+            }
+            __syncthreads();
+            for (int l = lt; l < nl; l += kBlock) {
+                const float4 acc = gather_node(slot, codes, rows, l);
+                if (l < n_int) {
+                    const int q = q0 + l;
+                    node_advance(A, S, (int64_t)D.i0 + q, acc, r_xu[q], r_X[q], r_lo[q], r_vel[q], r_nc[q], r_xu[q], r_lo[q],
+                                 r_vel[q]);
+                } else {
+                    r_part[ppos[l - n_int]] = acc;
+                }
+            }
+            __syncthreads();
+        }
+        for (int q = tid; q < D.n_sh; q += kResBlock) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int r = r_rowptr[q]; r < r_rowptr[q + 1]; r++) {
+                const float4 d = r_part[r];
+                acc.x += d.x; acc.y += d.y; acc.z += d.z; acc.w += d.w;
+            }
+            const int qq = D.n_int + q;
+            node_advance(A, S, A.n_interior + D.s0 + q, acc, r_xu[qq], r_X[qq], r_lo[qq], r_vel[qq], r_nc[qq], r_xu[qq],
+                         r_lo[qq], r_vel[qq]);
+        }
+        __syncthreads();
+    }
+
+    // ---- state back to global memory
+    for (int q = tid; q < nn_s; q += kResBlock) {
+        const int64_t g = gnode(q);
+        A.xu[g] = r_xu[q];
+        A.lo[g] = r_lo[q];
+        A.vel[g] = r_vel[q];
+    }
+    for (int j = 0; j < D.n_t; j++) {
+        const float *rec = reinterpret_cast<const float *>(smem + A.rs_tiles + j * A.rs_tile);
+        float *gvs = A.visc + (int64_t)(D.t0 + j) * A.n_prony * 6 * kTile;
+        for (int i = tid; i < 6 * A.n_prony * kTile; i += kResBlock) gvs[i] = rec[nfix * kTile + i];
     }
 }
 
@@ -1227,6 +1375,74 @@ static TileKernel tile_kernel(const StepArgs &a, int npe) {
 }
 
 cudaError_t tile_kernel_setup(const StepArgs &a, int npe) { return set_smem(tile_kernel(a, npe), a.sm_total); }
+
+// resident kernel instance (element type 4 or 8, Prony terms, anisotropic, brick)
+template <int NPE, bool ANI, bool BRICK = false>
+static TileKernel resident_kernel_npr(int n_prony) {
+    switch (n_prony) {
+        case 0: return resident_step_kernel<NPE, 0, ANI, BRICK>;
+        case 1: return resident_step_kernel<NPE, 1, ANI, BRICK>;
+        case 2: return resident_step_kernel<NPE, 2, ANI, BRICK>;
+        case 3: return resident_step_kernel<NPE, 3, ANI, BRICK>;
+        default: return resident_step_kernel<NPE, 4, ANI, BRICK>;
+    }
+}
+template <bool ANI>
+static TileKernel resident_kernel_ani(int npe, bool brick, int n_prony) {
+    return npe == 8 ? (brick ? resident_kernel_npr<8, ANI, true>(n_prony) : resident_kernel_npr<8, ANI>(n_prony))
+                    : resident_kernel_npr<4, ANI>(n_prony);
+}
+static TileKernel resident_kernel(const StepArgs &a, int npe) {
+    const bool brick = a.brick != 0;
+    return a.ani ? resident_kernel_ani<true>(npe, brick, a.n_prony) : resident_kernel_ani<false>(npe, brick, a.n_prony);
+}
+
+static int align16(int x) { return (x + 15) & ~15; }
+
+int resident_smem_layout(StepArgs &a, int npe, int nn_max, int nt_max, int npart_max, int nsh_max) {
+    int off = 0;
+    auto take = [&](int bytes) {
+        const int o = off;
+        off = align128(off + bytes);
+        return o;
+    };
+    a.rs_xu = take(16 * nn_max);
+    a.rs_lo = take(16 * nn_max);
+    a.rs_vel = take(16 * nn_max);
+    a.rs_X = take(16 * nn_max);
+    a.rs_nc = take(16 * nn_max);
+    a.rs_rowptr = take(4 * (nsh_max + 1));
+    a.rs_part = take(16 * npart_max);
+    a.rs_slot = take(kResLanes * kTile * npe * 16);  // one corner slot buffer per tile lane
+    int to = align128(a.n_comp * kTile * 4);  // element record and Prony state
+    a.rt_conn = to;
+    to = align16(to + kTile * npe * 2);
+    a.rt_codes = to;
+    to = align16(to + (kTile * npe + kMaxLocal + 8) * 2);
+    a.rt_ppos = to;
+    to = align16(to + kMaxLocal * 4);
+    a.rt_info = to;
+    a.rs_tile = align128(to + 16);
+    a.rs_tiles = take(nt_max * a.rs_tile);
+    a.rs_total = off;
+    return off;
+}
+
+// dynamic shared memory a resident CTA may use (the opt-in limit less the static part)
+int resident_smem_limit() {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    return optin - 1024;
+}
+
+cudaError_t resident_kernel_setup(const StepArgs &a, int npe) { return set_smem(resident_kernel(a, npe), a.rs_total); }
+
+cudaError_t launch_resident_step(const StepArgs &a, int n_ctas, int npe, int K, cudaStream_t s) {
+    if (n_ctas <= 0) return cudaSuccess;
+    resident_kernel(a, npe)<<<n_ctas, kResBlock, (size_t)a.rs_total, s>>>(a, K);
+    return cudaGetLastError();
+}
 
 int tile_grid(const StepArgs &a, int npe, int n_sm) {
     int per_sm = 0;

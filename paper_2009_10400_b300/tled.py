@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libtled.so")
 OK, E_ARG, E_MESH, E_STATE, E_CUDA, E_UNSTABLE, E_INVERTED, E_TIMEOUT, E_NOMEM, E_FORMAT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 T4, H8 = 4, 8
 HOST, DEVICE = 0, 1
-EXPANSION, TEMP_DEP, COMPENSATED, CEM43, GENERAL_H8 = 1, 2, 4, 8, 16
+EXPANSION, TEMP_DEP, COMPENSATED, CEM43, GENERAL_H8, STREAMED = 1, 2, 4, 8, 16, 32
 SRC_GAUSSIAN, SRC_SPHERE = 0, 1
 FIX_X, FIX_Y, FIX_Z, FIX_T = 1, 2, 4, 8
 
@@ -102,6 +102,7 @@ _SIGS = {
     "tled_scenario_dt": ([C.c_void_p, C.c_int32, _dp], C.c_int),
     "tled_stable_dt": ([C.c_void_p, _dp, _dp], C.c_int),
     "tled_autotune": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "tled_get_mode": ([C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
     "tled_save_state": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_load_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
 }
@@ -352,6 +353,13 @@ class Solver:
 
     def plan_info(self) -> dict:
         return plan_info(self.h, self._check)
+
+    @property
+    def resident(self) -> bool:
+        """True when the steps run in the resident mode (each scenario held by one CTA)."""
+        m = C.c_int32()
+        self._check(lib().tled_get_mode(self.h, C.byref(m)))
+        return bool(m.value)
 
     # -- read-back ---------------------------------------------------------
     def _read(self, fn, shape, out=None):

@@ -150,3 +150,47 @@ def test_autotune_then_parity():
     s.sync()
     c = compare(s.displacement(), s.temperature(), s.damage(), o.u, o.T, o.Omega)
     assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E
+
+
+def _flags(p, tled, extra=0):
+    return tled.COMPENSATED | (tled.EXPANSION if p.expansion else 0) | (tled.TEMP_DEP if p.temp_dep else 0) | extra
+
+
+@pytest.mark.parametrize("kind", ["brick", "h8", "t4"])
+def test_resident_mode_equals_streamed(kind):
+    """A problem that fits one CTA's shared memory runs in the resident mode (K steps per
+    launch, one CTA) by default; the streamed tile + shared-node kernels give the same
+    numbers (same arithmetic in the same order)."""
+    tled = _tled()
+    prob = {"brick": lambda: W.cube_h8(n=8), "h8": lambda: W.cube_h8(n=6, jitter=0.15, seed=91),
+            "t4": lambda: W.cube_t4(n=4, seed=92)}[kind]()
+    outs = []
+    for extra in (0, tled.STREAMED):
+        s = tled.Solver.from_problem(prob, flags=_flags(prob, tled, extra))
+        assert s.resident == (extra == 0)
+        s.step(250)  # 7 full graph chunks and a partial one
+        s.sync()
+        outs.append((s.displacement(), s.temperature(), s.damage(), s.get_state()["v"]))
+    assert np.abs(outs[0][0]).max() > 0 and outs[0][1].max() > prob.T0 + 0.01
+    for a, b in zip(*outs):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-6 * np.abs(b).max() + 1e-30)
+
+
+def test_resident_batch_scenarios_stop_at_their_own_step_count():
+    """Three small H8 scenarios of different step counts in the resident mode (one CTA
+    each, finished scenarios' CTAs return at once) against the streamed batch."""
+    tled = _tled()
+    scen = _scenarios_h8()
+    n_steps = [300, 120, 210]
+    res = []
+    for extra in (0, tled.STREAMED):
+        b = tled.Batch()
+        for p, n in zip(scen, n_steps):
+            b.add(p, n, flags=_flags(p, tled, extra))
+        b.init()
+        assert b.resident == (extra == 0)
+        assert b.run() == max(n_steps)
+        b.sync()
+        res.append((b.displacement(), b.temperature(), b.damage()))
+    for a, c in zip(*res):
+        np.testing.assert_allclose(a, c, rtol=0, atol=1e-6 * np.abs(c).max() + 1e-30)
