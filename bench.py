@@ -554,6 +554,9 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     probes = probe_lattice(prob, args.probes)
     s = tled.Solver.from_problem(prob, device=local, stream=stream, probes=probes)
+    kernel_desc = ("resident (one CTA, K steps per launch)" if s.resident else "streamed (tile + shared-node kernels)") + \
+        ("; H8 brick instance: every element an axis-aligned brick, reference hourglass projections exactly zero"
+         if s.brick else "")
     info = s.plan_info()
     dt = s.get_dt()[0]
     n_prony = len(prob.prony_g)
@@ -632,7 +635,8 @@ def run_gpu(args):
                        "element": "H8" if prob.npe == 8 else "T4", "dt_s": dt,
                        "tiles": info["n_tiles"], "shared_nodes": info["n_shared"],
                        "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (layout_bytes(prob, n_prony) / 1e6),
-                       "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}"},
+                       "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}",
+                       "kernels": kernel_desc},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "tile_step_kernel + shared_step_kernel (one step)",

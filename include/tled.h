@@ -321,9 +321,12 @@ int tled_scenario_dt(tled_ctx *ctx, int32_t index, double *dt);
  * layout and scenario count; a cached choice is applied without timing.
  * choice[0] elements per tile, [1] CTAs, [2] 1 if it came from the cache. */
 int tled_autotune(tled_ctx *ctx, void *dev_workspace, int64_t bytes, int32_t trial_steps, int32_t *choice);
-/* Step mode after init: *resident = 1 when the steps run in the resident mode (each
- * scenario held by one CTA in shared memory for K steps per launch), 0 when streamed. */
-int tled_get_mode(tled_ctx *ctx, int32_t *resident);
+/* Kernel choice after init, as bits of *mode: bit 0 (TLED_MODE_RESIDENT) when the steps
+ * run in the resident mode (each scenario held by one CTA in shared memory for K steps
+ * per launch; else streamed), bit 1 (TLED_MODE_BRICK) when the H8 brick instance runs. */
+#define TLED_MODE_RESIDENT 1
+#define TLED_MODE_BRICK 2
+int tled_get_mode(tled_ctx *ctx, int32_t *mode);
 
 /* Scalar diagnostics, reduced on the device in FP64 in a fixed order
  * (deterministic).  With no damping, no viscous terms, fixed or free

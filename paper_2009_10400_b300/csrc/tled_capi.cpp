@@ -1466,10 +1466,10 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
     return TLED_OK;
 }
 
-int tled_get_mode(tled_ctx *c, int32_t *resident) {
-    if (!c || !resident) return fail(c, TLED_E_ARG, "NULL argument");
+int tled_get_mode(tled_ctx *c, int32_t *mode) {
+    if (!c || !mode) return fail(c, TLED_E_ARG, "NULL argument");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
-    *resident = c->resident ? 1 : 0;
+    *mode = (c->resident ? TLED_MODE_RESIDENT : 0) | (c->A.brick ? TLED_MODE_BRICK : 0);
     return TLED_OK;
 }
 

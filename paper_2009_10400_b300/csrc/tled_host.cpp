@@ -336,6 +336,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     p.patterns.clear();
     std::unordered_map<uint64_t, std::vector<int32_t>> pat_by_hash;  // content hash -> pattern ids
     std::vector<uint16_t> pat(p.pat_stride);
+    std::vector<int> pat_type;  // element type of each distinct record
     std::vector<int32_t> local(nn, -1);
     std::vector<int32_t> sh_n(p.n_shared, 0);  // tiles touching each shared node so far
     int64_t part = 0;
@@ -403,19 +404,21 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
                 int l = conn_local[(size_t)i * npe + a];
                 rec_codes[cur[l]++] = (uint16_t)(a * kTile + (int)(i - e0));
             }
-        // tiles with the same structure share one record (FNV-1a hash, then a full compare)
-        uint64_t h = 1469598103934665603ull;
+        // tiles with the same element type and structure share one record (FNV-1a hash,
+        // then a full compare)
+        uint64_t h = 1469598103934665603ull ^ (uint64_t)kt;
         for (uint16_t v : pat) h = (h ^ v) * 1099511628211ull;
         int32_t id = -1;
         auto &cand = pat_by_hash[h];
         for (int32_t c : cand)
-            if (std::equal(pat.begin(), pat.end(), p.patterns.begin() + (size_t)c * p.pat_stride)) {
+            if (pat_type[c] == kt && std::equal(pat.begin(), pat.end(), p.patterns.begin() + (size_t)c * p.pat_stride)) {
                 id = c;
                 break;
             }
         if (id < 0) {
-            id = (int32_t)(p.patterns.size() / p.pat_stride);
+            id = (int32_t)pat_type.size();
             p.patterns.insert(p.patterns.end(), pat.begin(), pat.end());
+            pat_type.push_back(kt);
             cand.push_back(id);
         }
         ti[6] = id;

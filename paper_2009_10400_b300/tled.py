@@ -354,12 +354,20 @@ class Solver:
     def plan_info(self) -> dict:
         return plan_info(self.h, self._check)
 
+    def _mode(self) -> int:
+        m = C.c_int32()
+        self._check(lib().tled_get_mode(self.h, C.byref(m)))
+        return m.value
+
     @property
     def resident(self) -> bool:
         """True when the steps run in the resident mode (each scenario held by one CTA)."""
-        m = C.c_int32()
-        self._check(lib().tled_get_mode(self.h, C.byref(m)))
-        return bool(m.value)
+        return bool(self._mode() & 1)
+
+    @property
+    def brick(self) -> bool:
+        """True when the H8 brick instance (no reference hourglass projections) runs."""
+        return bool(self._mode() & 2)
 
     # -- read-back ---------------------------------------------------------
     def _read(self, fn, shape, out=None):

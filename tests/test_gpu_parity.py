@@ -220,6 +220,7 @@ def test_brick_kernel_matches_general_h8():
     outs = []
     for flags in (base, base | tled.GENERAL_H8):
         s = tled.Solver.from_problem(prob, flags=flags)
+        assert s.brick == (flags == base)
         s.step(400)
         s.sync()
         outs.append((s.displacement(), s.temperature() - prob.T0, s.damage()))
