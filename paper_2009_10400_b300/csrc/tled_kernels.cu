@@ -16,6 +16,12 @@
 //         their partial sums instead.
 //  * shared-node kernel: each node touched by several tiles sums its partials
 //    in tile order and applies the same nodal update.
+//  * resident kernel (problems, or batch scenarios, that fit one CTA's shared
+//    memory): one CTA per scenario runs the same phases for K steps with block
+//    barriers in place of kernel boundaries.
+// Instances: element type (H8, T4 or a mixed batch), Prony term count,
+// transversely isotropic thermal physics, and for H8 meshes of axis-aligned
+// bricks an instance without the (exactly zero) reference hourglass projections.
 //
 // Floating point: FP32 throughout; kinematics are written in H = du/dX so
 // that J - 1, E and I4b - 1 never cancel; nodal u and theta accumulate in
