@@ -474,9 +474,10 @@ int upload_scenarios(tled_ctx *c) {
             r[6] = s.sigma; r[7] = s.power; r[8] = s.t_on; r[9] = s.t_off; r[10] = (double)s.shape;
         }
     }
+    // stream-ordered after the steps already enqueued; the sources are pageable host
+    // memory, which the runtime stages before these calls return (no stream sync needed)
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.scn, d.data(), sizeof(ScenDev) * d.size(), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.src, src.data(), 8 * src.size(), cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // host staging buffers are local
     return TLED_OK;
 }
 

@@ -1106,18 +1106,29 @@ __global__ void bump_kernel(const StepArgs A, int K) {
 __global__ void probe_kernel(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
                              const float4 *__restrict__ vel, const int32_t *__restrict__ node,
                              const float *__restrict__ w, int64_t n, double T0, double *__restrict__ out) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
+    // eight lanes per probe, one per weight; the eight terms are summed by a fixed
+    // butterfly (pairs, then quads, then the two halves)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t p = i >> 3;
+    const int a = (int)(i & 7);
     double th = 0.0, dmg = 0.0;
-    for (int a = 0; a < 8; a++) {
+    if (p < n) {
         const double wa = w[8 * p + a];
-        if (wa == 0.0) continue;
-        const int64_t g = node[8 * p + a];
-        th += wa * ((double)hi[g].w + (double)lo[g].w);
-        dmg += wa * -expm1(-(double)vel[g].w);
+        if (wa != 0.0) {
+            const int64_t g = node[8 * p + a];
+            th = wa * ((double)hi[g].w + (double)lo[g].w);
+            dmg = wa * -expm1(-(double)vel[g].w);
+        }
     }
-    out[p] = T0 + th;
-    out[n + p] = dmg;
+#pragma unroll
+    for (int m = 1; m < 8; m <<= 1) {
+        th += __shfl_xor_sync(0xffffffffu, th, m);
+        dmg += __shfl_xor_sync(0xffffffffu, dmg, m);
+    }
+    if (p < n && a == 0) {
+        out[p] = T0 + th;
+        out[n + p] = dmg;
+    }
 }
 
 __global__ void readback_kernel(const float4 *__restrict__ hi, const float4 *__restrict__ lo,
@@ -1503,7 +1514,7 @@ cudaError_t launch_readback(const StepArgs &a, const int32_t *node_new, int64_t 
 
 cudaError_t launch_probes(const StepArgs &a, const int32_t *node, const float *w, int64_t n, double T0, double *out,
                           cudaStream_t s) {
-    probe_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(a.xu, a.lo, a.vel, node, w, n, T0, out);
+    probe_kernel<<<(int)((8 * n + 255) / 256), 256, 0, s>>>(a.xu, a.lo, a.vel, node, w, n, T0, out);
     return cudaGetLastError();
 }
 
