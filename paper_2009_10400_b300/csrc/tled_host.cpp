@@ -242,8 +242,9 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         return ga != gb ? ga < gb : key[a] < key[b];
     });
 
-    // --- cut tiles: at most tile_elems elements and kMaxLocal distinct nodes; a tile
+    // --- cut tiles: at most tile_elems elements and cap distinct nodes; a tile
     //     holds one group and one element type
+    const int cap = etype ? kMaxLocal : max_local(npe);  // local nodes per tile (the kernel's layout)
     std::vector<int32_t> mark(nn, -1);
     std::vector<int32_t> tile_begin;
     int n_local = 0, n_in = 0, t = -1;
@@ -256,7 +257,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         int fresh = 0;
         if (t >= 0)
             for (int a = 0; a < ki; a++) fresh += (mark[cn[a]] != t);
-        if (t < 0 || n_in == tile_elems || n_local + fresh > kMaxLocal || gi != prev_group || ki != prev_type) {
+        if (t < 0 || n_in == tile_elems || n_local + fresh > cap || gi != prev_group || ki != prev_type) {
             prev_group = gi;
             prev_type = ki;
             t++;
@@ -357,7 +358,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         // shared nodes keep their first-appearance order in the tile, so that tiles of
         // the same shape and position class get identical local structures
         const int nl = n_int + (int)shared.size();
-        if (nl > kMaxLocal) {
+        if (nl > cap) {
             err = "internal: tile exceeds the local node limit";
             return TLED_E_MESH;
         }

@@ -15,6 +15,9 @@ constexpr int kBlock = 256;        // threads per CTA of the tile kernel
 constexpr int kTile = 256;         // elements per tile (one per thread); every tile owns kTile element slots
 constexpr int kTileCtasPerSm = 3; // tile kernel CTAs resident per SM (register budget 85 per thread)
 constexpr int kMaxLocal = 448;     // max nodes touched by one tile (shared memory)
+constexpr int kMaxLocalT4 = 256;   // ... by a tile of a T4-only problem (smaller layout: 4 CTAs per SM)
+constexpr int max_local(int npe) { return npe == 4 ? kMaxLocalT4 : kMaxLocal; }
+constexpr int tile_ctas_per_sm(int npe) { return npe == 4 ? 4 : kTileCtasPerSm; }
 constexpr int kNsMax = 256;        // interior nodes whose state is staged in shared memory
 constexpr int kResLanes = 2;       // resident mode: tiles processed side by side in one CTA
 constexpr int kResBlock = kResLanes * kBlock;

@@ -704,7 +704,7 @@ __device__ __forceinline__ void stage_nodes(const StepArgs &A, const TileInfo &T
     }
     if (sb) {
         bulk_g2s(smem + A.sm_sh, A.tile_shared + T.sh_off, sb, bar);
-        bulk_g2s(smem + A.sm_sh + 4 * kMaxLocal, A.part_pos + T.sh_off, sb, bar);
+        bulk_g2s(smem + A.sm_sh + 4 * max_local(NPE), A.part_pos + T.sh_off, sb, bar);
     }
 }
 // warm L2 with tile t's streams
@@ -751,13 +751,13 @@ __device__ __forceinline__ float4 gather_node(const float4 *slot, const uint16_t
 }
 
 template <int NPE, int NPR, bool ANI, bool BRICK>
-__global__ void __launch_bounds__(kBlock, kTileCtasPerSm) tile_step_kernel(const StepArgs A, const int k) {
+__global__ void __launch_bounds__(kBlock, tile_ctas_per_sm(NPE)) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
     __shared__ ScenStep S;
     __shared__ int s_abort;
     const uint16_t *s_pat = reinterpret_cast<const uint16_t *>(smem + A.sm_pat);  // structure record
     const int *s_shg = reinterpret_cast<const int *>(smem + A.sm_sh);  // shared node -> global index
-    const int *s_ppos = s_shg + kMaxLocal;                             // shared node -> partial position
+    const int *s_ppos = s_shg + max_local(NPE);                        // shared node -> partial position
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
     float4 *s_X = reinterpret_cast<float4 *>(smem + A.sm_X);
     float4 *ns = reinterpret_cast<float4 *>(smem + A.sm_ns);
@@ -1352,11 +1352,11 @@ void tile_smem_layout(StepArgs &a, int npe) {
     a.sm_pat = off;
     off = align128(off + pattern_u16(npe) * 2);
     a.sm_sh = off;
-    off = align128(off + 2 * kMaxLocal * 4);
+    off = align128(off + 2 * max_local(npe) * 4);
     a.sm_xu = off;
-    off = align128(off + kMaxLocal * 16);
+    off = align128(off + max_local(npe) * 16);
     a.sm_X = off;
-    off = align128(off + kMaxLocal * 16);
+    off = align128(off + max_local(npe) * 16);
     a.sm_bar = off;
     off = align128(off + 32);
     a.sm_total = off;
