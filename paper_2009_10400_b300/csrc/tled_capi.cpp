@@ -1007,17 +1007,18 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.T0 = m.T0;
     A.n_tiles = p.n_tiles;
     A.pat_stride = p.pat_stride;
-    tled::tile_smem_layout(A, npe);
-    CUDA_TRY(c, tled::tile_kernel_setup(A, npe));
     int n_sm = 0;
     CUDA_TRY(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    A.wide = npe == 4 && p.n_tiles > tled::kTileCtasPerSm * n_sm;
+    tled::tile_smem_layout(A, npe);
+    CUDA_TRY(c, tled::tile_kernel_setup(A, npe));
     c->tile_ctas = tled::tile_grid(A, npe, n_sm);
     c->shared_blocks = tled::shared_grid(A, n_sm);
     if (c->grid_override > 0) c->tile_ctas = std::min(c->tile_ctas, c->grid_override);
-    // resident mode: possible when every scenario (one element type, no dose field) fits one
+    // resident mode: possible when every scenario (one element type) fits one
     // CTA's shared memory; one descriptor per rank (CTA b runs the scenario of rank b)
     c->res_ok = c->resident = false;
-    if (npe != 0 && !cem_on(c)) {
+    if (npe != 0) {
         std::vector<tled::ResDesc> rd(ns);
         int nn_max = 0, nt_max = 0, np_max = 0, nsh_max = 0;
         for (int r = 0; r < ns; r++) {
@@ -1100,8 +1101,7 @@ static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
         e = tled::launch_resident_step(c->A, (int)c->sc.size(), c->npe, K, c->cap);
     } else {
         for (int k = 0; k < K && e == cudaSuccess; k++) {
-            if (c->A.cem) e = tled::launch_cem43(c->A, c->nn, k, c->cap);  // dose at T(t), before the update
-            if (e == cudaSuccess) e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
+            e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
             if (e == cudaSuccess) e = tled::launch_shared_step(c->A, c->shared_blocks, k, c->cap);
         }
     }
@@ -1292,7 +1292,6 @@ int tled_step_timed(tled_ctx *c, int64_t n, double *ms) {
     for (auto &e : ev) CUDA_TRY(c, cudaEventCreate(&e));
     cudaError_t err = cudaSuccess;
     for (int64_t i = 0; i < n && err == cudaSuccess; i++) {
-        if (c->A.cem) err = tled::launch_cem43(c->A, c->nn, 0, c->stream);
         cudaEventRecord(ev[3 * i], c->stream);
         if (err == cudaSuccess)
             err = c->resident ? tled::launch_resident_step(c->A, (int)c->sc.size(), c->npe, 1, c->stream)

@@ -15,9 +15,9 @@ constexpr int kBlock = 256;        // threads per CTA of the tile kernel
 constexpr int kTile = 256;         // elements per tile (one per thread); every tile owns kTile element slots
 constexpr int kTileCtasPerSm = 3; // tile kernel CTAs resident per SM (register budget 85 per thread)
 constexpr int kMaxLocal = 448;     // max nodes touched by one tile (shared memory)
-constexpr int kMaxLocalT4 = 256;   // ... by a tile of a T4-only problem (smaller layout: 4 CTAs per SM)
+constexpr int kMaxLocalT4 = 256;   // ... by a tile of a T4-only problem (smaller layout: fits 4 CTAs per SM)
 constexpr int max_local(int npe) { return npe == 4 ? kMaxLocalT4 : kMaxLocal; }
-constexpr int tile_ctas_per_sm(int npe) { return npe == 4 ? 4 : kTileCtasPerSm; }
+constexpr int kTileCtasPerSmT4 = 4; // T4 problems with more tiles than 3 CTAs per SM cover (64 registers)
 constexpr int kNsMax = 256;        // interior nodes whose state is staged in shared memory
 constexpr int kResLanes = 2;       // resident mode: tiles processed side by side in one CTA
 constexpr int kResBlock = kResLanes * kBlock;
@@ -138,6 +138,7 @@ struct StepArgs {
     float khg, khgT;                      // kappa_hg, kappa_hgT
     int ani;                              // anisotropic thermal physics (the ratios below differ from 1)
     int brick;                            // every element an H8 whose reference hourglass projections vanish
+    int wide;                             // T4 problem with more tiles than 3 CTAs per SM: the 4-CTA instance
     float ani_alpha, ani_k;               // fibre / transverse expansion and conductivity
     double ramp_time;
     // resident mode (shared-memory byte offsets; rs_tile is the per-tile block stride and
@@ -152,7 +153,6 @@ cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cuda
 int tile_grid(const StepArgs &a, int npe, int n_sm);  // persistent grid size
 int shared_grid(const StepArgs &a, int n_sm);  // persistent grid of the shared-node kernel
 // CEM43 dose += dt R^(43 - T) / 60 at every node (single problems; before the step's update)
-cudaError_t launch_cem43(const StepArgs &a, int64_t nn, int k, cudaStream_t s);
 // sum of the lumped volumes of the nodes with theta >= theta_iso, FP64, fixed order: out[0]
 cudaError_t launch_isotherm(const StepArgs &a, int64_t nn, double theta_iso, double *partials, double *out,
                             cudaStream_t s);

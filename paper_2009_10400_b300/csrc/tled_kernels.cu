@@ -167,6 +167,12 @@ __device__ __forceinline__ void node_advance(const StepArgs &A, const ScenStep &
     const unsigned mask = __float_as_uint(nc.z);
     const bool comp = (A.flags & TLED_COMPENSATED) != 0;
     const float dt = S.dtf;
+    if (A.cem) {  // CEM43 dose (Sapareto-Dewey) at T(t): dt R^(43 - T) / 60 minutes, R = 0.5 at or
+                  // above 43 C, 0.25 below; FP64 (single problems)
+        const double T = A.T0 + ((double)xu.w + (double)lo.w);
+        const double x = T - 43.0;  // R^(43 - T) = 2^(x) or 4^(x)
+        A.cem[g] += S.dt * exp2(T >= 43.0 ? x : 2.0 * x) / 60.0;
+    }
     // current position for the heat source (state at t)
     const float px = X.x + (xu.x + lo.x), py = X.y + (xu.y + lo.y), pz = X.z + (xu.z + lo.z);
 
@@ -750,8 +756,9 @@ __device__ __forceinline__ float4 gather_node(const float4 *slot, const uint16_t
     return make_float4(sxy.x, sxy.y, szw.x, szw.y);
 }
 
-template <int NPE, int NPR, bool ANI, bool BRICK>
-__global__ void __launch_bounds__(kBlock, tile_ctas_per_sm(NPE)) tile_step_kernel(const StepArgs A, const int k) {
+// CPS: resident CTAs per SM the instance is built for (its register budget)
+template <int NPE, int NPR, bool ANI, bool BRICK, int CPS>
+__global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A, const int k) {
     extern __shared__ __align__(128) char smem[];
     __shared__ ScenStep S;
     __shared__ int s_abort;
@@ -1063,17 +1070,6 @@ __global__ void __launch_bounds__(kResBlock, 1) resident_step_kernel(const StepA
     }
 }
 
-// CEM43 thermal dose (Sapareto-Dewey), explicit in T(t): dose += dt R^(43 - T) / 60
-// minutes, R = 0.5 at or above 43 C, 0.25 below; FP64 per node, single problems
-__global__ void cem43_kernel(const StepArgs A, int64_t nn) {
-    const double dt = A.scn[0].dt;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nn; g += (int64_t)gridDim.x * blockDim.x) {
-        const double T = A.T0 + ((double)A.xu[g].w + (double)A.lo[g].w);
-        const double x = T - 43.0;  // R^(43 - T) = 2^(x) or 4^(x)
-        A.cem[g] += dt * exp2(T >= 43.0 ? x : 2.0 * x) / 60.0;
-    }
-}
-
 // volume at or above an isotherm: sum of V_i over theta_i >= theta_iso (fixed grid, fixed tree)
 __global__ void __launch_bounds__(256) isotherm_partial_kernel(const StepArgs A, int64_t nn, double th_iso,
                                                                double *partials) {
@@ -1367,28 +1363,29 @@ static cudaError_t set_smem(K kern, int bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
-// the tile kernel instance for (element type, Prony terms, anisotropic thermal physics):
-// npe 8, 4 or 0 (mixed), n_prony 0..4, ani
+// the tile kernel instance for (element type, Prony terms, anisotropic thermal physics,
+// brick H8, CTAs per SM): npe 8, 4 or 0 (mixed), n_prony 0..4; T4 problems with more
+// tiles than three CTAs per SM cover take the 4-CTA (64-register) instance
 using TileKernel = void (*)(const StepArgs, const int);
-template <int NPE, bool ANI, bool BRICK = false>
+template <int NPE, bool ANI, bool BRICK = false, int CPS = kTileCtasPerSm>
 static TileKernel tile_kernel_npr(int n_prony) {
     switch (n_prony) {
-        case 0: return tile_step_kernel<NPE, 0, ANI, BRICK>;
-        case 1: return tile_step_kernel<NPE, 1, ANI, BRICK>;
-        case 2: return tile_step_kernel<NPE, 2, ANI, BRICK>;
-        case 3: return tile_step_kernel<NPE, 3, ANI, BRICK>;
-        default: return tile_step_kernel<NPE, 4, ANI, BRICK>;
+        case 0: return tile_step_kernel<NPE, 0, ANI, BRICK, CPS>;
+        case 1: return tile_step_kernel<NPE, 1, ANI, BRICK, CPS>;
+        case 2: return tile_step_kernel<NPE, 2, ANI, BRICK, CPS>;
+        case 3: return tile_step_kernel<NPE, 3, ANI, BRICK, CPS>;
+        default: return tile_step_kernel<NPE, 4, ANI, BRICK, CPS>;
     }
 }
 template <bool ANI>
-static TileKernel tile_kernel_ani(int npe, bool brick, int n_prony) {
+static TileKernel tile_kernel_ani(int npe, bool brick, bool wide, int n_prony) {
     return npe == 8 ? (brick ? tile_kernel_npr<8, ANI, true>(n_prony) : tile_kernel_npr<8, ANI>(n_prony))
-         : npe == 4 ? tile_kernel_npr<4, ANI>(n_prony)
+         : npe == 4 ? (wide ? tile_kernel_npr<4, ANI, false, kTileCtasPerSmT4>(n_prony) : tile_kernel_npr<4, ANI>(n_prony))
                     : tile_kernel_npr<0, ANI>(n_prony);
 }
 static TileKernel tile_kernel(const StepArgs &a, int npe) {
-    const bool brick = a.brick != 0;
-    return a.ani ? tile_kernel_ani<true>(npe, brick, a.n_prony) : tile_kernel_ani<false>(npe, brick, a.n_prony);
+    const bool brick = a.brick != 0, wide = a.wide != 0;
+    return a.ani ? tile_kernel_ani<true>(npe, brick, wide, a.n_prony) : tile_kernel_ani<false>(npe, brick, wide, a.n_prony);
 }
 
 cudaError_t tile_kernel_setup(const StepArgs &a, int npe) { return set_smem(tile_kernel(a, npe), a.sm_total); }
@@ -1484,12 +1481,6 @@ int shared_grid(const StepArgs &a, int n_sm) {
 cudaError_t launch_shared_step(const StepArgs &a, int n_blocks, int k, cudaStream_t s) {
     if (a.n_shared <= 0) return cudaSuccess;
     shared_step_kernel<<<n_blocks, 256, 0, s>>>(a, k);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cem43(const StepArgs &a, int64_t nn, int k, cudaStream_t s) {
-    (void)k;  // the dose uses the state at t; the step within a graph does not enter
-    cem43_kernel<<<(int)std::min<int64_t>((nn + 255) / 256, 4 * kStatBlocks), 256, 0, s>>>(a, nn);
     return cudaGetLastError();
 }
 
