@@ -898,6 +898,7 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
 __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, const int k) {
     __shared__ ScenStep S;
     const int64_t n_sh = A.n_active[1];  // shared nodes of unfinished scenarios form a prefix
+    const bool multi = A.n_scn > 1;      // a batch: nodes carry their scenario
     int cur = -1;
     for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < n_sh; c0 += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = c0 + threadIdx.x;
@@ -907,11 +908,11 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
         const int64_t g = A.n_interior + (live ? s : c0);
         const float4 xu = A.xu[g], X = __ldg(&A.X0[g]), lo = A.lo[g], vo = A.vel[g], nc = __ldg(&A.nodec[g]);
         const int r0 = live ? __ldg(A.sh_rowptr + s) : 0, r1 = live ? __ldg(A.sh_rowptr + s + 1) : 0;
-        const int scn = live ? __ldg(A.shared_scn + s) : -1;
+        const int scn = !multi ? 0 : live ? __ldg(A.shared_scn + s) : -1;
         float4 c[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) c[j] = r0 + j < r1 ? A.partials[r0 + j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int scn0 = __ldg(A.shared_scn + c0);  // the chunk's first node's scenario (block-uniform)
+        const int scn0 = multi ? __ldg(A.shared_scn + c0) : 0;  // the chunk's first node's scenario (block-uniform)
         if (scn0 != cur) {
             __syncthreads();  // nobody still reads the previous step values
             prepare_scen(A, scn0, k, S, threadIdx.x, blockDim.x);
