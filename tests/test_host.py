@@ -196,3 +196,23 @@ def test_cem43_is_refused_in_a_batch():
     one.set_params(flags=tled.EXPANSION | tled.COMPENSATED | tled.CEM43)
     assert tled.lib().tled_batch_add(h, one.h, 10, None) == tled.E_ARG
     tled.lib().tled_destroy(h)
+
+
+def test_binding_constants_match_the_header():
+    """Flag, status and mode values of the Python binding are the C header's."""
+    hdr = open(os.path.join(ROOT, "include", "tled.h")).read()
+
+    def val(name):
+        m = re.search(r"#define %s \((\d+)u << (\d+)\)" % name, hdr)
+        if m:
+            return int(m.group(1)) << int(m.group(2))
+        m = re.search(r"#define %s \(?(-?\d+)u?\)?(?:\s|/|$)" % name, hdr, re.M)
+        assert m, name
+        return int(m.group(1))
+
+    for py, c in (("EXPANSION", "TLED_EXPANSION"), ("TEMP_DEP", "TLED_TEMP_DEP"), ("COMPENSATED", "TLED_COMPENSATED"),
+                  ("CEM43", "TLED_CEM43"), ("GENERAL_H8", "TLED_GENERAL_H8"), ("STREAMED", "TLED_STREAMED"),
+                  ("E_FORMAT", "TLED_E_FORMAT"), ("E_MESH", "TLED_E_MESH"), ("E_ARG", "TLED_E_ARG")):
+        assert getattr(tled, py) == val(c), (py, c)
+    assert val("TLED_MODE_RESIDENT") == 1 and val("TLED_MODE_BRICK") == 2
+
