@@ -73,7 +73,8 @@ extern "C" {
                                       the compiler's multiply-add fusion (a few ulps) */
 #define TLED_STREAMED (1u << 5)    /* keep the streamed step (tile kernel + shared-node kernel per step) when
                                       the problem would fit the resident mode (every scenario in one CTA's
-                                      shared memory, K steps per launch; same arithmetic, same results) */
+                                      shared memory) or the grid-resident one (a single problem's tiles in
+                                      co-resident CTAs); K steps per launch there, same arithmetic and results */
 
 /* boundary mask bits (per node) */
 #define TLED_FIX_X 1u
@@ -313,8 +314,8 @@ int tled_scenario_dt(tled_ctx *ctx, int32_t index, double *dt);
 
 /* ---- autotuner ----
  * Time the candidate tilings (elements per tile 256 / 192 / 128, persistent
- * grid of one or two CTAs per SM; and the resident mode when every scenario
- * fits one CTA's shared memory) for `trial_steps` steps each in the
+ * grid of one or two CTAs per SM; and the resident and grid-resident modes
+ * where the problem fits them) for `trial_steps` steps each in the
  * caller's workspace (bytes of it), keep the fastest, and leave the context
  * initialised with it at t = 0 (state reset).  The choice is cached in the
  * process per element type, size (log2 of the element count), material
@@ -323,9 +324,13 @@ int tled_scenario_dt(tled_ctx *ctx, int32_t index, double *dt);
 int tled_autotune(tled_ctx *ctx, void *dev_workspace, int64_t bytes, int32_t trial_steps, int32_t *choice);
 /* Kernel choice after init, as bits of *mode: bit 0 (TLED_MODE_RESIDENT) when the steps
  * run in the resident mode (each scenario held by one CTA in shared memory for K steps
- * per launch; else streamed), bit 1 (TLED_MODE_BRICK) when the H8 brick instance runs. */
+ * per launch), bit 2 (TLED_MODE_GRID) in the grid-resident mode (a single problem's tiles
+ * held by the CTAs of one cooperative launch for K steps, grid barriers between the
+ * phases), neither when streamed (tile and shared-node kernels per step); bit 1
+ * (TLED_MODE_BRICK) when the H8 brick instance runs. */
 #define TLED_MODE_RESIDENT 1
 #define TLED_MODE_BRICK 2
+#define TLED_MODE_GRID 4
 int tled_get_mode(tled_ctx *ctx, int32_t *mode);
 
 /* Scalar diagnostics, reduced on the device in FP64 in a fixed order

@@ -38,7 +38,7 @@ constexpr int kSingleSources = tled::kMaxSources;
 struct Layout {
     size_t xu, lo, vel, X0, nodec, ubar, elem_rec, visc;
     size_t tile_info, tile_shared, part_pos, pattern, partials, sh_rowptr;
-    size_t scn, src, scn_time, scn_step, tile_scn, shared_scn, n_active, status, res;
+    size_t scn, src, scn_time, scn_step, tile_scn, shared_scn, n_active, status, res, gbar;
     size_t node_new, probe_node, probe_w, probe_out, stat_part, stat_out, staging, cem;
     size_t total;
 };
@@ -98,7 +98,7 @@ struct tled_ctx {
     std::vector<int32_t> probe_node;               // [n_probes][8] new node ids
     std::vector<float> probe_w;                    // [n_probes][8]
     int tile_override = 0, grid_override = 0;      // set by the autotuner
-    int mode_override = 0;                         // autotuner: 1 streamed, 2 resident (if it fits), 0 default
+    int mode_override = 0;  // autotuner: 1 streamed, 2 resident, 3 grid-resident (if it fits), 0 default
     // plan and device
     bool planned = false;
     Plan plan;
@@ -115,6 +115,8 @@ struct tled_ctx {
     int active_host[2] = {0, 0};   // last uploaded active prefix lengths
     bool res_ok = false;           // every scenario fits one CTA's shared memory (resident mode possible)
     bool resident = false;         // steps run by the resident kernel
+    bool coop_ok = false;          // a single problem whose tiles fit co-resident CTAs (grid-resident mode)
+    bool coop = false;             // steps run by the grid-resident (cooperative) kernel
 };
 
 namespace {
@@ -204,6 +206,7 @@ Layout make_layout(const tled_ctx *c) {
     L.shared_scn = take(4 * (size_t)p.n_shared);
     L.n_active = take(8);
     L.res = take(sizeof(tled::ResDesc) * ns);
+    L.gbar = take(8);
     L.status = take(16);
     L.node_new = take(4 * nn);
     L.probe_node = take(4 * 8 * (size_t)c->n_probes);
@@ -1049,6 +1052,24 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
             c->resident = c->mode_override == 2 || (c->mode_override == 0 && !(s0.prm.flags & TLED_STREAMED));
         }
     }
+    // grid-resident mode: a single problem whose tiles (one CTA each) all fit co-resident CTAs of
+    // a cooperative launch
+    c->coop_ok = c->coop = false;
+    int coop_dev = 0;
+    CUDA_TRY(c, cudaDeviceGetAttribute(&coop_dev, cudaDevAttrCooperativeLaunch, c->device));
+    if (npe != 0 && ns == 1 && !c->resident && coop_dev && p.n_tiles > 0) {
+        tled::coop_smem_layout(A, npe);
+        if (A.cs_total <= tled::resident_smem_limit()) {
+            CUDA_TRY(c, tled::coop_kernel_setup(A, npe));
+            const int per_sm = tled::coop_ctas_per_sm(A, npe);
+            if ((int64_t)per_sm * n_sm >= p.n_tiles) {
+                c->coop_ok = true;
+                A.coop_chunk = (int)((p.n_shared + p.n_tiles - 1) / p.n_tiles);
+                A.gbar = dptr<unsigned>(c, L.gbar);
+                c->coop = c->mode_override == 3 || (c->mode_override == 0 && !(s0.prm.flags & TLED_STREAMED));
+            }
+        }
+    }
     // set-up hash for checkpoints
     uint64_t h = 1469598103934665603ULL;
     for (auto &s : c->sc) {
@@ -1099,6 +1120,8 @@ static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     cudaError_t e = cudaSuccess;
     if (c->resident) {  // K steps in one launch, one CTA per scenario (finished ones return at once)
         e = tled::launch_resident_step(c->A, (int)c->sc.size(), c->npe, K, c->cap);
+    } else if (c->coop) {  // K steps in one cooperative launch, one CTA per tile
+        e = tled::launch_coop_step(c->A, c->npe, K, c->cap);
     } else {
         for (int k = 0; k < K && e == cudaSuccess; k++) {
             e = tled::launch_tile_step(c->A, c->tile_ctas, c->npe, k, c->cap);
@@ -1295,9 +1318,11 @@ int tled_step_timed(tled_ctx *c, int64_t n, double *ms) {
         cudaEventRecord(ev[3 * i], c->stream);
         if (err == cudaSuccess)
             err = c->resident ? tled::launch_resident_step(c->A, (int)c->sc.size(), c->npe, 1, c->stream)
+                : c->coop     ? tled::launch_coop_step(c->A, c->npe, 1, c->stream)
                               : tled::launch_tile_step(c->A, c->tile_ctas, c->npe, 0, c->stream);
         cudaEventRecord(ev[3 * i + 1], c->stream);
-        if (err == cudaSuccess && !c->resident) err = tled::launch_shared_step(c->A, c->shared_blocks, 0, c->stream);
+        if (err == cudaSuccess && !c->resident && !c->coop)
+            err = tled::launch_shared_step(c->A, c->shared_blocks, 0, c->stream);
         cudaEventRecord(ev[3 * i + 2], c->stream);
         if (err == cudaSuccess) err = tled::launch_bump(c->A, 1, c->stream);
     }
@@ -1417,7 +1442,8 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
         struct Cand {
             int te, gscale, mode;
         };
-        const Cand cands[] = {{256, 0, 2}, {256, 0, 1}, {256, 1, 1}, {192, 0, 1}, {192, 1, 1}, {128, 0, 1}, {128, 1, 1}};
+        const Cand cands[] = {{256, 0, 2}, {256, 0, 3}, {256, 0, 1}, {256, 1, 1}, {192, 0, 1}, {192, 1, 1}, {128, 0, 1},
+                              {128, 1, 1}};
         for (const Cand &cd : cands) {
             const int te = cd.te;
             {
@@ -1428,7 +1454,7 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
                 if (int rc = ensure_plan(c)) return rc;
                 if ((int64_t)c->L.total > bytes) continue;  // does not fit the caller's workspace
                 if (int rc = tled_init(c, dev_workspace, bytes)) return rc;
-                if (cd.mode == 2 && !c->resident) continue;  // no resident mode for this problem
+                if ((cd.mode == 2 && !c->resident) || (cd.mode == 3 && !c->coop)) continue;  // mode not available
                 if (int rc = run_steps(c, 3, nullptr)) return rc;  // graphs captured, caches warm
                 cudaEvent_t e0, e1;
                 CUDA_TRY(c, cudaEventCreate(&e0));
@@ -1469,7 +1495,7 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
 int tled_get_mode(tled_ctx *c, int32_t *mode) {
     if (!c || !mode) return fail(c, TLED_E_ARG, "NULL argument");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
-    *mode = (c->resident ? TLED_MODE_RESIDENT : 0) | (c->A.brick ? TLED_MODE_BRICK : 0);
+    *mode = (c->resident ? TLED_MODE_RESIDENT : 0) | (c->A.brick ? TLED_MODE_BRICK : 0) | (c->coop ? TLED_MODE_GRID : 0);
     return TLED_OK;
 }
 

@@ -146,6 +146,11 @@ struct StepArgs {
     const ResDesc *res;
     int rs_xu, rs_lo, rs_vel, rs_X, rs_nc, rs_rowptr, rs_part, rs_slot, rs_tiles, rs_tile, rs_total;
     int rt_conn, rt_codes, rt_ppos, rt_info;
+    // grid-resident mode (cooperative launch, one CTA per tile): shared-memory offsets, the
+    // shared nodes each CTA updates, and the grid barrier words (arrivals, generation)
+    int cs_rec, cs_pat, cs_sh, cs_xu, cs_X, cs_lo, cs_vo, cs_nc, cs_slot, cs_total;
+    int coop_chunk;
+    unsigned int *gbar;
 };
 
 // kernel launchers (tled_kernels.cu); npe 4 or 8, or 0 for a batch mixing both element types
@@ -172,6 +177,12 @@ int resident_smem_layout(StepArgs &a, int npe, int nn_max, int nt_max, int npart
 int resident_smem_limit();
 cudaError_t resident_kernel_setup(const StepArgs &a, int npe);
 cudaError_t launch_resident_step(const StepArgs &a, int n_ctas, int npe, int K, cudaStream_t s);
+// grid-resident mode: layout (returns the bytes), co-resident CTAs per SM for it, set-up,
+// and a cooperative launch of K steps (one CTA per tile)
+int coop_smem_layout(StepArgs &a, int npe);
+int coop_ctas_per_sm(const StepArgs &a, int npe);
+cudaError_t coop_kernel_setup(const StepArgs &a, int npe);
+cudaError_t launch_coop_step(const StepArgs &a, int npe, int K, cudaStream_t s);
 // FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
 // damaged volume, out[6..7] = stored (hyperelastic) energy and hourglass energy; deterministic
 // two-stage reduction through `partials` [kStatBlocks][8].

@@ -1071,6 +1071,148 @@ __global__ void __launch_bounds__(kResBlock, 1) resident_step_kernel(const StepA
     }
 }
 
+// ---------------------------------------------------------------------------
+// grid-resident mode (single problems whose tiles all fit co-resident CTAs): a
+// cooperative launch of one CTA per tile runs K steps.  The tile's element record,
+// Prony state, structure record, shared-node lists, reference coordinates and the
+// state of its interior nodes stay in the CTA's shared memory; per step the CTA
+// gathers its shared nodes' u, theta, runs the element pass and the node phase
+// (interior nodes updated in shared memory, partial sums to global memory), then
+// after a grid barrier each CTA updates its share of the shared nodes, and a
+// second barrier closes the step.  Same functions and order as the tile and
+// shared-node kernels.
+// ---------------------------------------------------------------------------
+// Grid barrier over all CTAs of a cooperative launch: a monotonic arrival count in
+// global memory (zeroed before the launch); barrier j opens when it reaches
+// j * gridDim.x.  Arrival with release semantics (the CTA's writes, ordered by the
+// block barrier, before it), acquire on the wait; the wait is bounded (about a
+// second), after which the CTA flags the device status and reports failure.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ bool grid_barrier(const StepArgs &A, unsigned &target) {
+    __shared__ int s_ok;
+    target += gridDim.x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_ok = 1;
+        red_release_add(&A.gbar[0], 1u);
+        const long long t0 = clock64();
+        while (ld_acquire_u32(&A.gbar[0]) < target) {
+            if (clock64() - t0 > (1ll << 31)) {
+                atomicOr(A.status, kStatusTimeout);
+                s_ok = 0;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int NPE, int NPR, bool ANI, bool BRICK>
+__global__ void __launch_bounds__(kBlock, 2) coop_step_kernel(const StepArgs A, const int K) {
+    extern __shared__ __align__(128) char smem[];
+    __shared__ ScenStep S;
+    const int t = blockIdx.x, tid = threadIdx.x;
+    const TileInfo T = tile_info(A, t);
+    char *rec = smem + A.cs_rec;
+    const uint16_t *s_pat = reinterpret_cast<const uint16_t *>(smem + A.cs_pat);
+    const uint16_t *s_code = s_pat + kTile * NPE, *s_row = s_code + kTile * NPE;
+    int *s_shg = reinterpret_cast<int *>(smem + A.cs_sh);
+    int *s_ppos = s_shg + max_local(NPE);
+    float4 *s_xu = reinterpret_cast<float4 *>(smem + A.cs_xu);
+    float4 *s_X = reinterpret_cast<float4 *>(smem + A.cs_X);
+    float4 *s_lo = reinterpret_cast<float4 *>(smem + A.cs_lo);
+    float4 *s_vo = reinterpret_cast<float4 *>(smem + A.cs_vo);
+    float4 *s_nc = reinterpret_cast<float4 *>(smem + A.cs_nc);
+    float4 *slot = reinterpret_cast<float4 *>(smem + A.cs_slot);
+    const int nfix = A.n_comp - 6 * A.n_prony;
+    const int n_sh = T.nl - T.n_int;
+    unsigned target = 0;  // arrivals that open the next grid barrier
+
+    // ---- the tile into shared memory
+    {
+        const float *grec = reinterpret_cast<const float *>(A.elem_rec + (int64_t)t * A.rec_bytes);
+        float *r = reinterpret_cast<float *>(rec);
+        for (int i = tid; i < nfix * kTile; i += kBlock) r[i] = __ldg(grec + i);
+        const float *gvs = A.visc + (int64_t)t * A.n_prony * 6 * kTile;
+        for (int i = tid; i < 6 * A.n_prony * kTile; i += kBlock) r[nfix * kTile + i] = gvs[i];
+        const uint16_t *pat = A.pattern + (int64_t)T.pat * A.pat_stride;
+        uint16_t *sp = reinterpret_cast<uint16_t *>(smem + A.cs_pat);
+        for (int i = tid; i < pattern_u16(NPE); i += kBlock) sp[i] = pat[i];
+        for (int m = tid; m < n_sh; m += kBlock) {
+            s_shg[m] = __ldg(A.tile_shared + T.sh_off + m);
+            s_ppos[m] = __ldg(A.part_pos + T.sh_off + m);
+        }
+        for (int l = tid; l < T.nl; l += kBlock) {
+            const int64_t g = l < T.n_int ? (int64_t)T.ib + l : (int64_t)__ldg(A.tile_shared + T.sh_off + l - T.n_int);
+            s_X[l] = __ldg(&A.X0[g]);
+            if (l < T.n_int) {
+                s_xu[l] = A.xu[g];
+                s_lo[l] = A.lo[g];
+                s_vo[l] = A.vel[g];
+                s_nc[l] = __ldg(&A.nodec[g]);
+            }
+        }
+    }
+    __syncthreads();
+
+    for (int k = 0; k < K; k++) {
+        prepare_scen(A, 0, k, S, tid, kBlock);
+        // the shared nodes' u, theta as the previous step's second phase left them (L2)
+        for (int m = tid; m < n_sh; m += kBlock) s_xu[T.n_int + m] = __ldcg(&A.xu[s_shg[m]]);
+        __syncthreads();
+        if (tid < T.ne_t) {
+            int cl[NPE];
+            ElemIn<NPR> E;
+            load_elem<NPE, NPR>(A, rec, s_pat, tid, cl, E);
+            element_step<NPE, NPR, ANI, BRICK>(A, S, (int64_t)t * kTile + tid, tid, cl, E, s_xu, s_X, slot,
+                                               reinterpret_cast<float *>(rec) + nfix * kTile + tid);
+        }
+        __syncthreads();
+        for (int l = tid; l < T.nl; l += kBlock) {
+            const float4 acc = gather_node(slot, s_code, s_row, l);
+            if (l < T.n_int)
+                node_advance(A, S, (int64_t)T.ib + l, acc, s_xu[l], s_X[l], s_lo[l], s_vo[l], s_nc[l], s_xu[l], s_lo[l],
+                             s_vo[l]);
+            else
+                A.partials[s_ppos[l - T.n_int]] = acc;
+        }
+        if (!grid_barrier(A, target)) return;  // every tile's partial sums are in memory
+        // this CTA's share of the shared nodes: partial sums in tile order, then the update
+        const int64_t s0 = (int64_t)t * A.coop_chunk, s1 = min(s0 + A.coop_chunk, A.n_shared);
+        for (int64_t s = s0 + tid; s < s1; s += kBlock) {
+            const int r0 = __ldg(A.sh_rowptr + s), r1 = __ldg(A.sh_rowptr + s + 1);
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int r = r0; r < r1; r++) {
+                const float4 d = __ldcg(&A.partials[r]);
+                acc.x += d.x; acc.y += d.y; acc.z += d.z; acc.w += d.w;
+            }
+            const int64_t g = A.n_interior + s;
+            node_update(A, S, g, acc, __ldcg(&A.xu[g]), __ldg(&A.X0[g]), __ldcg(&A.lo[g]), __ldcg(&A.vel[g]),
+                        __ldg(&A.nodec[g]));
+        }
+        if (!grid_barrier(A, target)) return;  // the shared nodes' new state is in memory
+    }
+
+    // ---- interior state and Prony state back to global memory
+    for (int l = tid; l < T.n_int; l += kBlock) {
+        const int64_t g = (int64_t)T.ib + l;
+        A.xu[g] = s_xu[l];
+        A.lo[g] = s_lo[l];
+        A.vel[g] = s_vo[l];
+    }
+    float *gvs = A.visc + (int64_t)t * A.n_prony * 6 * kTile;
+    const float *r = reinterpret_cast<const float *>(rec);
+    for (int i = tid; i < 6 * A.n_prony * kTile; i += kBlock) gvs[i] = r[nfix * kTile + i];
+}
+
 // volume at or above an isotherm: sum of V_i over theta_i >= theta_iso (fixed grid, fixed tree)
 __global__ void __launch_bounds__(256) isotherm_partial_kernel(const StepArgs A, int64_t nn, double th_iso,
                                                                double *partials) {
@@ -1452,6 +1594,73 @@ int resident_smem_limit() {
 }
 
 cudaError_t resident_kernel_setup(const StepArgs &a, int npe) { return set_smem(resident_kernel(a, npe), a.rs_total); }
+
+// grid-resident kernel instance (element type 4 or 8, Prony terms, anisotropic, brick)
+template <int NPE, bool ANI, bool BRICK = false>
+static TileKernel coop_kernel_npr(int n_prony) {
+    switch (n_prony) {
+        case 0: return coop_step_kernel<NPE, 0, ANI, BRICK>;
+        case 1: return coop_step_kernel<NPE, 1, ANI, BRICK>;
+        case 2: return coop_step_kernel<NPE, 2, ANI, BRICK>;
+        case 3: return coop_step_kernel<NPE, 3, ANI, BRICK>;
+        default: return coop_step_kernel<NPE, 4, ANI, BRICK>;
+    }
+}
+template <bool ANI>
+static TileKernel coop_kernel_ani(int npe, bool brick, int n_prony) {
+    return npe == 8 ? (brick ? coop_kernel_npr<8, ANI, true>(n_prony) : coop_kernel_npr<8, ANI>(n_prony))
+                    : coop_kernel_npr<4, ANI>(n_prony);
+}
+static TileKernel coop_kernel(const StepArgs &a, int npe) {
+    const bool brick = a.brick != 0;
+    return a.ani ? coop_kernel_ani<true>(npe, brick, a.n_prony) : coop_kernel_ani<false>(npe, brick, a.n_prony);
+}
+
+int coop_smem_layout(StepArgs &a, int npe) {
+    const int ml = max_local(npe);
+    int off = 0;
+    auto take = [&](int bytes) {
+        const int o = off;
+        off = align128(off + bytes);
+        return o;
+    };
+    a.cs_rec = take(a.n_comp * kTile * 4);
+    a.cs_pat = take(pattern_u16(npe) * 2);
+    a.cs_sh = take(2 * ml * 4);
+    a.cs_xu = take(ml * 16);
+    a.cs_X = take(ml * 16);
+    a.cs_lo = take(ml * 16);  // interior node state: up to every local node
+    a.cs_vo = take(ml * 16);
+    a.cs_nc = take(ml * 16);
+    a.cs_slot = take(kTile * npe * 16);
+    a.cs_total = off;
+    return off;
+}
+
+int coop_ctas_per_sm(const StepArgs &a, int npe) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coop_kernel(a, npe), kBlock, a.cs_total) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+cudaError_t coop_kernel_setup(const StepArgs &a, int npe) { return set_smem(coop_kernel(a, npe), a.cs_total); }
+
+cudaError_t launch_coop_step(const StepArgs &a, int npe, int K, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.gbar, 0, sizeof(unsigned), s);  // arrivals start at zero
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)a.n_tiles);
+    cfg.blockDim = dim3(kBlock);
+    cfg.dynamicSmemBytes = (size_t)a.cs_total;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, coop_kernel(a, npe), a, K);
+}
 
 cudaError_t launch_resident_step(const StepArgs &a, int n_ctas, int npe, int K, cudaStream_t s) {
     if (n_ctas <= 0) return cudaSuccess;

@@ -365,6 +365,11 @@ class Solver:
         return bool(self._mode() & 1)
 
     @property
+    def grid_resident(self) -> bool:
+        """True when the steps run in the grid-resident mode (one cooperative launch per chunk)."""
+        return bool(self._mode() & 4)
+
+    @property
     def brick(self) -> bool:
         """True when the H8 brick instance (no reference hourglass projections) runs."""
         return bool(self._mode() & 2)

@@ -194,3 +194,31 @@ def test_resident_batch_scenarios_stop_at_their_own_step_count():
         res.append((b.displacement(), b.temperature(), b.damage()))
     for a, c in zip(*res):
         np.testing.assert_allclose(a, c, rtol=0, atol=1e-6 * np.abs(c).max() + 1e-30)
+
+
+@pytest.mark.parametrize("kind", ["brick", "h8", "t4_cem"])
+def test_grid_resident_mode_equals_streamed(kind):
+    """A single problem too large for one CTA but whose tiles all fit co-resident CTAs runs
+    in the grid-resident mode (one cooperative launch per graph chunk, grid barriers between
+    the phases) by default; the streamed kernels give the same numbers."""
+    tled = _tled()
+    if kind == "brick":
+        prob = W.block_h8(n=16, h=3e-3)
+    elif kind == "h8":
+        prob = W.cube_h8(n=12, jitter=0.15, seed=93)
+    else:
+        prob = W.liver_f2()
+    outs = []
+    for extra in (0, tled.STREAMED):
+        f = _flags(prob, tled, extra) | (tled.CEM43 if getattr(prob, "cem43", False) else 0)
+        s = tled.Solver.from_problem(prob, flags=f, dt=0.0 if kind == "t4_cem" else None)
+        assert s.grid_resident == (extra == 0) and not s.resident
+        s.step(100)  # 3 full graph chunks and a partial one
+        s.sync()
+        o = [s.displacement(), s.temperature(), s.damage(), s.get_state()["v"]]
+        if kind == "t4_cem":
+            o.append(s.cem43())
+        outs.append(o)
+    assert np.abs(outs[0][0]).max() > 0
+    for a, b in zip(*outs):
+        np.testing.assert_allclose(a, b, rtol=0, atol=1e-6 * np.abs(b).max() + 1e-30)
