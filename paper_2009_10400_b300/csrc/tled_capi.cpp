@@ -33,6 +33,7 @@ using tled::StepArgs;
 namespace {
 
 constexpr int kGraphChunk = 32;  // steps per captured graph
+constexpr int kCoopTilesMax = 512;  // tiles of a grid-resident candidate (its partial sums are double-buffered)
 constexpr int kSingleSources = tled::kMaxSources;
 
 struct Layout {
@@ -195,7 +196,8 @@ Layout make_layout(const tled_ctx *c) {
     L.tile_info = take(4 * p.tile_info.size());
     L.tile_shared = take(4 * p.tile_shared.size());
     L.pattern = take(2 * p.patterns.size());
-    L.partials = take(16 * (size_t)p.n_partials);
+    // small problems (grid-resident candidates) get a second buffer of partial sums
+    L.partials = take(16 * (size_t)p.n_partials * (p.n_tiles <= kCoopTilesMax ? 2 : 1));
     L.sh_rowptr = take(4 * p.sh_rowptr.size());
     L.part_pos = take(4 * p.part_pos.size());
     L.scn = take(sizeof(ScenDev) * ns);
@@ -974,6 +976,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.tile_shared = dptr<int>(c, L.tile_shared);
     A.pattern = dptr<uint16_t>(c, L.pattern);
     A.partials = dptr<float4>(c, L.partials);
+    A.n_partials = p.n_partials;
     A.part_pos = dptr<int>(c, L.part_pos);
     A.sh_rowptr = dptr<int>(c, L.sh_rowptr);
     A.n_interior = p.n_interior;
@@ -1059,12 +1062,11 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     CUDA_TRY(c, cudaDeviceGetAttribute(&coop_dev, cudaDevAttrCooperativeLaunch, c->device));
     if (npe != 0 && ns == 1 && !c->resident && coop_dev && p.n_tiles > 0) {
         tled::coop_smem_layout(A, npe);
-        if (A.cs_total <= tled::resident_smem_limit()) {
+        if (A.cs_total <= tled::resident_smem_limit() && p.n_tiles <= kCoopTilesMax) {
             CUDA_TRY(c, tled::coop_kernel_setup(A, npe));
             const int per_sm = tled::coop_ctas_per_sm(A, npe);
             if ((int64_t)per_sm * n_sm >= p.n_tiles) {
                 c->coop_ok = true;
-                A.coop_chunk = (int)((p.n_shared + p.n_tiles - 1) / p.n_tiles);
                 A.gbar = dptr<unsigned>(c, L.gbar);
                 c->coop = c->mode_override == 3 || (c->mode_override == 0 && !(s0.prm.flags & TLED_STREAMED));
             }

@@ -146,10 +146,10 @@ struct StepArgs {
     const ResDesc *res;
     int rs_xu, rs_lo, rs_vel, rs_X, rs_nc, rs_rowptr, rs_part, rs_slot, rs_tiles, rs_tile, rs_total;
     int rt_conn, rt_codes, rt_ppos, rt_info;
-    // grid-resident mode (cooperative launch, one CTA per tile): shared-memory offsets, the
-    // shared nodes each CTA updates, and the grid barrier words (arrivals, generation)
+    // grid-resident mode (cooperative launch, one CTA per tile): shared-memory offsets, and
+    // the grid barrier's arrival count
     int cs_rec, cs_pat, cs_sh, cs_xu, cs_X, cs_lo, cs_vo, cs_nc, cs_slot, cs_total;
-    int coop_chunk;
+    int64_t n_partials;     // partial sums per buffer (the grid-resident mode double-buffers them)
     unsigned int *gbar;
 };
 

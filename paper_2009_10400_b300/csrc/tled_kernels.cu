@@ -161,13 +161,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 // nc: (1/m_i, 1/C_i, mask bits, K_b,i); f: (internal force, thermal load).
 // nc.w: perfusion conductance w_b c_b V_i of the node.
 // The new state goes to xo (u_hi, theta_hi), lo_o (u_lo, theta_lo), vo_o (v, Omega).
+// dose: accumulate the CEM43 dose (off for the redundant copies of a shared node's update)
 __device__ __forceinline__ void node_advance(const StepArgs &A, const ScenStep &S, int64_t g, float4 f, float4 xu,
                                              float4 X, float4 lo, float4 vo, float4 nc, float4 &xo, float4 &lo_o,
-                                             float4 &vo_o) {
+                                             float4 &vo_o, bool dose = true) {
     const unsigned mask = __float_as_uint(nc.z);
     const bool comp = (A.flags & TLED_COMPENSATED) != 0;
     const float dt = S.dtf;
-    if (A.cem) {  // CEM43 dose (Sapareto-Dewey) at T(t): dt R^(43 - T) / 60 minutes, R = 0.5 at or
+    if (A.cem && dose) {  // CEM43 dose (Sapareto-Dewey) at T(t): dt R^(43 - T) / 60 minutes, R = 0.5 at or
                   // above 43 C, 0.25 below; FP64 (single problems)
         const double T = A.T0 + ((double)xu.w + (double)lo.w);
         const double x = T - 43.0;  // R^(43 - T) = 2^(x) or 4^(x)
@@ -1075,12 +1076,14 @@ __global__ void __launch_bounds__(kResBlock, 1) resident_step_kernel(const StepA
 // grid-resident mode (single problems whose tiles all fit co-resident CTAs): a
 // cooperative launch of one CTA per tile runs K steps.  The tile's element record,
 // Prony state, structure record, shared-node lists, reference coordinates and the
-// state of its interior nodes stay in the CTA's shared memory; per step the CTA
-// gathers its shared nodes' u, theta, runs the element pass and the node phase
-// (interior nodes updated in shared memory, partial sums to global memory), then
-// after a grid barrier each CTA updates its share of the shared nodes, and a
-// second barrier closes the step.  Same functions and order as the tile and
-// shared-node kernels.
+// state of all its nodes stay in the CTA's shared memory.  Per step the CTA runs
+// the element pass and the node phase (interior nodes updated in shared memory,
+// shared nodes' partial sums to global memory, double-buffered by step parity);
+// after one grid barrier every CTA updates its own copy of each of its shared
+// nodes from all the node's partial sums in tile order -- the copies of a node
+// in different CTAs are computed from the same values in the same order and stay
+// identical, and only the node's first tile writes it back and adds its dose.
+// Same functions and order as the tile and shared-node kernels.
 // ---------------------------------------------------------------------------
 // Grid barrier over all CTAs of a cooperative launch: a monotonic arrival count in
 // global memory (zeroed before the launch); barrier j opens when it reaches
@@ -1121,11 +1124,14 @@ __global__ void __launch_bounds__(kBlock, 2) coop_step_kernel(const StepArgs A, 
     __shared__ ScenStep S;
     const int t = blockIdx.x, tid = threadIdx.x;
     const TileInfo T = tile_info(A, t);
+    constexpr int ML = max_local(NPE);
     char *rec = smem + A.cs_rec;
     const uint16_t *s_pat = reinterpret_cast<const uint16_t *>(smem + A.cs_pat);
     const uint16_t *s_code = s_pat + kTile * NPE, *s_row = s_code + kTile * NPE;
-    int *s_shg = reinterpret_cast<int *>(smem + A.cs_sh);
-    int *s_ppos = s_shg + max_local(NPE);
+    int *s_shg = reinterpret_cast<int *>(smem + A.cs_sh);  // per shared node: global index,
+    int *s_ppos = s_shg + ML;                               // this tile's partial position,
+    int *s_r0 = s_shg + 2 * ML;                             // the node's first partial,
+    int *s_cnt = s_shg + 3 * ML;                            // and its tile count
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.cs_xu);
     float4 *s_X = reinterpret_cast<float4 *>(smem + A.cs_X);
     float4 *s_lo = reinterpret_cast<float4 *>(smem + A.cs_lo);
@@ -1147,26 +1153,27 @@ __global__ void __launch_bounds__(kBlock, 2) coop_step_kernel(const StepArgs A, 
         uint16_t *sp = reinterpret_cast<uint16_t *>(smem + A.cs_pat);
         for (int i = tid; i < pattern_u16(NPE); i += kBlock) sp[i] = pat[i];
         for (int m = tid; m < n_sh; m += kBlock) {
-            s_shg[m] = __ldg(A.tile_shared + T.sh_off + m);
+            const int g = __ldg(A.tile_shared + T.sh_off + m);
+            const int64_t s = g - A.n_interior;
+            s_shg[m] = g;
             s_ppos[m] = __ldg(A.part_pos + T.sh_off + m);
+            s_r0[m] = __ldg(A.sh_rowptr + s);
+            s_cnt[m] = __ldg(A.sh_rowptr + s + 1) - s_r0[m];
         }
         for (int l = tid; l < T.nl; l += kBlock) {
             const int64_t g = l < T.n_int ? (int64_t)T.ib + l : (int64_t)__ldg(A.tile_shared + T.sh_off + l - T.n_int);
             s_X[l] = __ldg(&A.X0[g]);
-            if (l < T.n_int) {
-                s_xu[l] = A.xu[g];
-                s_lo[l] = A.lo[g];
-                s_vo[l] = A.vel[g];
-                s_nc[l] = __ldg(&A.nodec[g]);
-            }
+            s_xu[l] = A.xu[g];
+            s_lo[l] = A.lo[g];
+            s_vo[l] = A.vel[g];
+            s_nc[l] = __ldg(&A.nodec[g]);
         }
     }
     __syncthreads();
 
     for (int k = 0; k < K; k++) {
+        float4 *part = A.partials + (k & 1) * A.n_partials;  // this step's partial sums
         prepare_scen(A, 0, k, S, tid, kBlock);
-        // the shared nodes' u, theta as the previous step's second phase left them (L2)
-        for (int m = tid; m < n_sh; m += kBlock) s_xu[T.n_int + m] = __ldcg(&A.xu[s_shg[m]]);
         __syncthreads();
         if (tid < T.ne_t) {
             int cl[NPE];
@@ -1182,28 +1189,30 @@ __global__ void __launch_bounds__(kBlock, 2) coop_step_kernel(const StepArgs A, 
                 node_advance(A, S, (int64_t)T.ib + l, acc, s_xu[l], s_X[l], s_lo[l], s_vo[l], s_nc[l], s_xu[l], s_lo[l],
                              s_vo[l]);
             else
-                A.partials[s_ppos[l - T.n_int]] = acc;
+                part[s_ppos[l - T.n_int]] = acc;
         }
-        if (!grid_barrier(A, target)) return;  // every tile's partial sums are in memory
-        // this CTA's share of the shared nodes: partial sums in tile order, then the update
-        const int64_t s0 = (int64_t)t * A.coop_chunk, s1 = min(s0 + A.coop_chunk, A.n_shared);
-        for (int64_t s = s0 + tid; s < s1; s += kBlock) {
-            const int r0 = __ldg(A.sh_rowptr + s), r1 = __ldg(A.sh_rowptr + s + 1);
+        if (!grid_barrier(A, target)) return;  // every tile's partial sums of this step are in memory
+        // this CTA's copy of each of its shared nodes: all the node's partial sums in tile order
+        for (int m = tid; m < n_sh; m += kBlock) {
+            const int r0 = s_r0[m], cnt = s_cnt[m];
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int r = r0; r < r1; r++) {
-                const float4 d = __ldcg(&A.partials[r]);
+            for (int r = 0; r < cnt; r++) {
+                const float4 d = __ldcg(&part[r0 + r]);
                 acc.x += d.x; acc.y += d.y; acc.z += d.z; acc.w += d.w;
             }
-            const int64_t g = A.n_interior + s;
-            node_update(A, S, g, acc, __ldcg(&A.xu[g]), __ldg(&A.X0[g]), __ldcg(&A.lo[g]), __ldcg(&A.vel[g]),
-                        __ldg(&A.nodec[g]));
+            const int l = T.n_int + m;
+            node_advance(A, S, (int64_t)s_shg[m], acc, s_xu[l], s_X[l], s_lo[l], s_vo[l], s_nc[l], s_xu[l], s_lo[l],
+                         s_vo[l], s_ppos[m] == r0);
         }
-        if (!grid_barrier(A, target)) return;  // the shared nodes' new state is in memory
+        __syncthreads();
     }
 
-    // ---- interior state and Prony state back to global memory
-    for (int l = tid; l < T.n_int; l += kBlock) {
-        const int64_t g = (int64_t)T.ib + l;
+    // ---- node state (interior nodes, and the shared nodes this tile is the first of) and
+    //      Prony state back to global memory
+    for (int l = tid; l < T.nl; l += kBlock) {
+        const bool own = l < T.n_int || s_ppos[l - T.n_int] == s_r0[l - T.n_int];
+        if (!own) continue;
+        const int64_t g = l < T.n_int ? (int64_t)T.ib + l : (int64_t)s_shg[l - T.n_int];
         A.xu[g] = s_xu[l];
         A.lo[g] = s_lo[l];
         A.vel[g] = s_vo[l];
@@ -1626,7 +1635,7 @@ int coop_smem_layout(StepArgs &a, int npe) {
     };
     a.cs_rec = take(a.n_comp * kTile * 4);
     a.cs_pat = take(pattern_u16(npe) * 2);
-    a.cs_sh = take(2 * ml * 4);
+    a.cs_sh = take(4 * ml * 4);
     a.cs_xu = take(ml * 16);
     a.cs_X = take(ml * 16);
     a.cs_lo = take(ml * 16);  // interior node state: up to every local node
