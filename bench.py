@@ -511,6 +511,9 @@ def run_liver(args):
     s = tled.Solver.from_problem(prob, stream=stream)
     dt = s.get_dt()[0]
     n = int(round(prob.duration / dt))
+    if args.liver_steps > 0:  # a shorter run (profiling)
+        n = min(n, args.liver_steps)
+    mode = "grid-resident" if s.grid_resident else "resident" if s.resident else "streamed"
     s.step(max(args.warmup, 3) * 32)  # graphs captured, caches warm
     s.sync()
     z3, z = np.zeros((prob.nn, 3)), np.zeros(prob.nn)
@@ -531,11 +534,14 @@ def run_liver(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"liver_f2: synthetic ellipsoid, {prob.ne} T4, {prob.nn} nodes, 3 uniform "
                                    f"spheres D = 1 cm at 9.70536 MW/m^3, c(T), k(T), Q_m 33.8 kW/m^3, "
-                                   f"{prob.duration:g} s of heating at dt {dt:.3e} s", "cem43": True},
+                                   f"{n * dt:g} s of heating at dt {dt:.3e} s", "cem43": True, "mode": mode},
             "simulated_s_per_wall_s": prob.duration / sec, "wall_s": sec,
             "T_max_C": st["T_max"], "ablation_volume_60C_cm3": 1e6 * s.isotherm_volume(60.0),
             "damaged_volume_cm3": 1e6 * st["damage_volume"], "cem43_max_min": float(cem.max()),
-            "clocks": clk.summary(), "gpu_launches": n * 3 + (n + 31) // 32}
+            "clocks": clk.summary(),
+            # per graph chunk of 32 steps: one step kernel (resident modes) or a tile and a
+            # shared-node kernel per step (streamed), and the clock bump
+            "gpu_launches": (n + 31) // 32 * 2 if mode != "streamed" else n * 2 + (n + 31) // 32}
     print(json.dumps(line))
     return 0
 
@@ -579,8 +585,10 @@ def run_gpu(args):
     ms = ev0.elapsed_time(ev1)
     ms = reduce_max(ms, ws, f"cuda:{local}")
     value = ws * prob.ne * args.steps / (ms * 1e-3)
-    launches_per_step = 1 + (1 if info["n_shared"] > 0 else 0)
-    gpu_launches = args.steps * launches_per_step + (args.steps + 31) // 32  # + one clock bump per graph
+    if s.resident or s.grid_resident:  # one step kernel per graph chunk of 32 steps, and the clock bump
+        gpu_launches = (args.steps + 31) // 32 * 2
+    else:  # a tile kernel and a shared-node kernel per step, and one clock bump per graph chunk
+        gpu_launches = args.steps * (1 + (1 if info["n_shared"] > 0 else 0)) + (args.steps + 31) // 32
 
     # ---- live per-kernel timing for the roofline (CUDA events on the launching stream)
     k_tile, k_sh = s.step_timed(args.roofline_steps)
@@ -688,6 +696,7 @@ def main():
     ap.add_argument("--workload", default="block_h8")
     ap.add_argument("--roofline-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=500)
+    ap.add_argument("--liver-steps", type=int, default=0, help="liver_f2: stop after this many steps (0: 25 s)")
     ap.add_argument("--probes", type=int, default=16)
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--ref-seconds", type=float, default=30.0)
