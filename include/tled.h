@@ -333,6 +333,13 @@ int tled_autotune(tled_ctx *ctx, void *dev_workspace, int64_t bytes, int32_t tri
 #define TLED_MODE_GRID 4
 int tled_get_mode(tled_ctx *ctx, int32_t *mode);
 
+/* Self-test of the bounded device waits (after init): runs a one-CTA kernel whose wait
+ * can never complete -- which = 0 an mbarrier wait (as the tile kernel's copies use),
+ * 1 a grid-barrier wait (as the grid-resident mode uses) -- and returns what a step
+ * would report: TLED_E_TIMEOUT after about a second.  The status is cleared again
+ * afterwards, so the context stays usable.  Nothing faults or hangs. */
+int tled_selftest_wait(tled_ctx *ctx, int32_t which);
+
 /* Scalar diagnostics, reduced on the device in FP64 in a fixed order
  * (deterministic).  With no damping, no viscous terms, fixed or free
  * boundaries and no thermal load, kinetic_energy + strain_energy +

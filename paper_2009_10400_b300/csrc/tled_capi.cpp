@@ -1494,6 +1494,25 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
     return TLED_OK;
 }
 
+int tled_selftest_wait(tled_ctx *c, int32_t which) {
+    if (!c) return TLED_E_ARG;
+    if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
+    if (which != 0 && which != 1) return fail(c, TLED_E_ARG, "which must be 0 (mbarrier) or 1 (grid barrier)");
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    if (int rc = check_status(c)) return rc;  // start from a clean status
+    tled::StepArgs a = c->A;
+    a.gbar = dptr<unsigned>(c, c->L.gbar);
+    CUDA_TRY(c, cudaMemsetAsync(a.gbar, 0, 4, c->stream));
+    CUDA_TRY(c, tled::launch_wait_selftest(a, which, c->stream));
+    const int rc = check_status(c);  // the timed-out wait's status, as a step would report it
+    // clear it again: the context stays usable
+    const unsigned st[4] = {0u, 0xffffffffu, 0xffffffffu, 0u};
+    CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.status, st, 16, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(a.gbar, 0, 4, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
 int tled_get_mode(tled_ctx *c, int32_t *mode) {
     if (!c || !mode) return fail(c, TLED_E_ARG, "NULL argument");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");

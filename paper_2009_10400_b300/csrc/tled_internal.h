@@ -183,6 +183,7 @@ int coop_smem_layout(StepArgs &a, int npe);
 int coop_ctas_per_sm(const StepArgs &a, int npe);
 cudaError_t coop_kernel_setup(const StepArgs &a, int npe);
 cudaError_t launch_coop_step(const StepArgs &a, int npe, int K, cudaStream_t s);
+cudaError_t launch_wait_selftest(const StepArgs &a, int which, cudaStream_t s);
 // FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
 // damaged volume, out[6..7] = stored (hyperelastic) energy and hourglass energy; deterministic
 // two-stage reduction through `partials` [kStatBlocks][8].

@@ -1118,6 +1118,24 @@ __device__ bool grid_barrier(const StepArgs &A, unsigned &target) {
     return s_ok != 0;
 }
 
+// Self-test of the bounded device waits: which = 0 waits on an mbarrier nothing
+// arrives at, which = 1 on a grid barrier whose arrival count is never reached.
+// Either wait gives up after about a second and sets the timeout status bit.
+__global__ void wait_selftest_kernel(const StepArgs A, int which) {
+    __shared__ __align__(8) uint64_t bar;
+    if (which == 0) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_barrier_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && !mbar_wait(&bar, 0)) atomicOr(A.status, kStatusTimeout);
+    } else {
+        unsigned target = 1u << 30;  // far beyond the arrivals of this one-CTA launch
+        grid_barrier(A, target);
+    }
+}
+
 template <int NPE, int NPR, bool ANI, bool BRICK>
 __global__ void __launch_bounds__(kBlock, 2) coop_step_kernel(const StepArgs A, const int K) {
     extern __shared__ __align__(128) char smem[];
@@ -1654,6 +1672,11 @@ int coop_ctas_per_sm(const StepArgs &a, int npe) {
 }
 
 cudaError_t coop_kernel_setup(const StepArgs &a, int npe) { return set_smem(coop_kernel(a, npe), a.cs_total); }
+
+cudaError_t launch_wait_selftest(const StepArgs &a, int which, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(a, which);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_coop_step(const StepArgs &a, int npe, int K, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.gbar, 0, sizeof(unsigned), s);  // arrivals start at zero

@@ -103,6 +103,7 @@ _SIGS = {
     "tled_stable_dt": ([C.c_void_p, _dp, _dp], C.c_int),
     "tled_autotune": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "tled_get_mode": ([C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
+    "tled_selftest_wait": ([C.c_void_p, C.c_int32], C.c_int),
     "tled_save_state": ([C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_load_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
 }
@@ -353,6 +354,11 @@ class Solver:
 
     def plan_info(self) -> dict:
         return plan_info(self.h, self._check)
+
+    def selftest_wait(self, which: int) -> int:
+        """Run the bounded-wait self-test (0: mbarrier, 1: grid barrier); returns the
+        library status code (E_TIMEOUT expected)."""
+        return lib().tled_selftest_wait(self.h, int(which))
 
     def _mode(self) -> int:
         m = C.c_int32()
