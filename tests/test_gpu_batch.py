@@ -143,6 +143,8 @@ def test_autotune_then_parity():
     assert ch["tile_elems"] in (256, 192, 128) and ch["ctas"] >= 1 and not ch["cached"]
     s2 = tled.Solver.from_problem(p)
     assert s2.autotune(trial_steps=10)["cached"]
+    # the cached choice includes the step mode (streamed, resident or grid-resident)
+    assert (s2.resident, s2.grid_resident) == (s.resident, s.grid_resident)
     m = oracle.OracleModel(p, dt=s.get_dt()[0])
     o = m.init_state()
     m.step(o, 200)
