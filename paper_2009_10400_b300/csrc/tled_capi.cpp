@@ -479,8 +479,16 @@ int upload_scenarios(tled_ctx *c) {
             r[6] = s.sigma; r[7] = s.power; r[8] = s.t_on; r[9] = s.t_off; r[10] = (double)s.shape;
         }
     }
-    // stream-ordered after the steps already enqueued; the sources are pageable host
-    // memory, which the runtime stages before these calls return (no stream sync needed)
+    // stream-ordered after the steps already enqueued, without a host wait: a single
+    // problem's tables travel as the parameters of a one-block kernel; a batch's (larger)
+    // tables are pageable host memory, which the runtime stages before the copies return
+    if (!c->batch && src.size() == (size_t)tled::kMaxSources * tled::kSrcRow) {
+        tled::SingleScenUpload u{};
+        u.d = d[0];
+        std::copy(src.begin(), src.end(), u.src);
+        CUDA_TRY(c, tled::launch_single_upload(u, dptr<ScenDev>(c, c->L.scn), dptr<double>(c, c->L.src), c->stream));
+        return TLED_OK;
+    }
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.scn, d.data(), sizeof(ScenDev) * d.size(), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->ws + c->L.src, src.data(), 8 * src.size(), cudaMemcpyHostToDevice, c->stream));
     return TLED_OK;

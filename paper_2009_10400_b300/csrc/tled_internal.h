@@ -82,6 +82,13 @@ struct ScenDev {
     int pad;
 };
 
+// A single problem's scenario table and source rows, passed by value to a one-block
+// upload kernel so that a source change is stream-ordered without a host wait.
+struct SingleScenUpload {
+    ScenDev d;
+    double src[kMaxSources * kSrcRow];
+};
+
 // Arguments of the step kernels (passed by value).
 struct StepArgs {
     // node arrays (new numbering)
@@ -184,6 +191,7 @@ int coop_ctas_per_sm(const StepArgs &a, int npe);
 cudaError_t coop_kernel_setup(const StepArgs &a, int npe);
 cudaError_t launch_coop_step(const StepArgs &a, int npe, int K, cudaStream_t s);
 cudaError_t launch_wait_selftest(const StepArgs &a, int which, cudaStream_t s);
+cudaError_t launch_single_upload(const SingleScenUpload &u, ScenDev *scn, double *src, cudaStream_t s);
 // FP64 diagnostics: out[0..5] = kinetic energy, heat content, T max (rel), T min (rel), max |u|^2,
 // damaged volume, out[6..7] = stored (hyperelastic) energy and hourglass energy; deterministic
 // two-stage reduction through `partials` [kStatBlocks][8].

@@ -1673,6 +1673,17 @@ int coop_ctas_per_sm(const StepArgs &a, int npe) {
 
 cudaError_t coop_kernel_setup(const StepArgs &a, int npe) { return set_smem(coop_kernel(a, npe), a.cs_total); }
 
+// single problem: its scenario table and source rows from the kernel's parameters
+__global__ void single_upload_kernel(const SingleScenUpload u, ScenDev *scn, double *src) {
+    if (threadIdx.x == 0) *scn = u.d;
+    for (int i = threadIdx.x; i < kMaxSources * kSrcRow; i += blockDim.x) src[i] = u.src[i];
+}
+
+cudaError_t launch_single_upload(const SingleScenUpload &u, ScenDev *scn, double *src, cudaStream_t s) {
+    single_upload_kernel<<<1, 64, 0, s>>>(u, scn, src);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wait_selftest(const StepArgs &a, int which, cudaStream_t s) {
     wait_selftest_kernel<<<1, 32, 0, s>>>(a, which);
     return cudaGetLastError();
