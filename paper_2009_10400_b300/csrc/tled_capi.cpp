@@ -1120,7 +1120,27 @@ int tled_scenario_dt(tled_ctx *c, int32_t idx, double *dt) {
     return TLED_OK;
 }
 
+static int capture_graph(tled_ctx *c, int K, cudaGraphExec_t *out);
+// The step graph of K steps (cached per K).  Should the grid-resident launch be refused
+// (a cooperative launch needs every CTA placed at once), the context falls back to the
+// streamed kernels, which compute the same numbers.
 static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
+    auto it = c->graphs.find(K);
+    if (it != c->graphs.end()) {
+        *out = it->second;
+        return TLED_OK;
+    }
+    int rc = capture_graph(c, K, out);
+    if (rc && c->coop) {
+        cudaGetLastError();  // clear the refused launch's error
+        drop_graphs(c);
+        c->coop = false;
+        c->coop_ok = false;
+        rc = capture_graph(c, K, out);
+    }
+    return rc;
+}
+static int capture_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     auto it = c->graphs.find(K);
     if (it != c->graphs.end()) {
         *out = it->second;
