@@ -1467,24 +1467,35 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
         double best_ms = INFINITY;
         int n_sm = 0;
         CUDA_TRY(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
-        // candidates: (elements per tile, grid scale, mode); the resident candidate is
-        // skipped when the problem does not fit it
+        // candidates: (elements per tile, grid scale, mode); candidates of one tile size share
+        // the plan (only the set-up is redone), and the resident modes are tried only when the
+        // streamed set-up of that plan found the problem fits them
         struct Cand {
             int te, gscale, mode;
         };
-        const Cand cands[] = {{256, 0, 2}, {256, 0, 3}, {256, 0, 1}, {256, 1, 1}, {192, 0, 1}, {192, 1, 1}, {128, 0, 1},
+        const Cand cands[] = {{256, 0, 1}, {256, 0, 2}, {256, 0, 3}, {256, 1, 1}, {192, 0, 1}, {192, 1, 1}, {128, 0, 1},
                               {128, 1, 1}};
+        bool res_ok = false, coop_ok = false;
         for (const Cand &cd : cands) {
             const int te = cd.te;
             {
-                invalidate(c);
-                c->tile_override = te;
+                if ((cd.mode == 2 && !res_ok) || (cd.mode == 3 && !coop_ok)) continue;  // mode not available
+                if (!c->planned || c->tile_override != te) {
+                    invalidate(c);
+                    c->tile_override = te;
+                } else {
+                    drop_graphs(c);
+                    c->inited = false;
+                }
                 c->grid_override = cd.gscale == 1 ? n_sm : 0;
                 c->mode_override = cd.mode;
                 if (int rc = ensure_plan(c)) return rc;
                 if ((int64_t)c->L.total > bytes) continue;  // does not fit the caller's workspace
                 if (int rc = tled_init(c, dev_workspace, bytes)) return rc;
-                if ((cd.mode == 2 && !c->resident) || (cd.mode == 3 && !c->coop)) continue;  // mode not available
+                if (cd.mode == 1) {
+                    res_ok = c->res_ok;
+                    coop_ok = c->coop_ok;
+                }
                 if (int rc = run_steps(c, 3, nullptr)) return rc;  // graphs captured, caches warm
                 cudaEvent_t e0, e1;
                 CUDA_TRY(c, cudaEventCreate(&e0));
@@ -1507,8 +1518,13 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
         std::lock_guard<std::mutex> lock(g_tune_mu);
         g_tune_cache[key] = best;
     }
-    invalidate(c);
-    c->tile_override = best.tile_elems;
+    if (!c->planned || c->tile_override != best.tile_elems) {
+        invalidate(c);
+        c->tile_override = best.tile_elems;
+    } else {
+        drop_graphs(c);
+        c->inited = false;
+    }
     c->grid_override = best.grid;
     c->mode_override = best.mode;
     if (int rc = ensure_plan(c)) return rc;
