@@ -61,8 +61,9 @@ struct Scenario {
     tled_params prm{};
     std::vector<double> probes;  // [n][3]
     int64_t n_steps = INT64_MAX;
-    // derived at init
+    // derived at init (the stable-step bounds once per set-up: dt_valid)
     double dt = 0, dt_mech = 0, dt_th = 0;
+    bool dt_valid = false;
     int64_t node_off = 0, elem_off = 0, probe_off = 0;
     int src_off = 0;
 };
@@ -723,6 +724,7 @@ int tled_set_mesh(tled_ctx *c, int elem_type, int64_t n_nodes, const double *X0,
     s.mat6.clear();
     s.fib.clear();
     s.probes.clear();
+    s.dt_valid = false;
     return TLED_OK;
 }
 
@@ -737,6 +739,7 @@ int tled_set_material(tled_ctx *c, const tled_material *m, const double *per_ele
     s.mat6.assign(per_elem ? per_elem : nullptr, per_elem ? per_elem + 6 * s.ne : nullptr);
     s.fib.assign(fibre ? fibre : nullptr, fibre ? fibre + 3 * s.ne : nullptr);
     s.have_mat = true;
+    s.dt_valid = false;
     return TLED_OK;
 }
 
@@ -779,6 +782,7 @@ int tled_set_params(tled_ctx *c, const tled_params *p) {
         return fail(c, TLED_E_ARG, "invalid solver parameters");
     invalidate(c);
     single(c).prm = q;
+    single(c).dt_valid = false;
     return TLED_OK;
 }
 
@@ -865,8 +869,11 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     // --- per-scenario time steps and source offsets
     int src_off = 0;
     for (auto &s : c->sc) {
-        tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
-                        s.fib.empty() ? nullptr : s.fib.data(), s.prm, &s.dt_mech, &s.dt_th);
+        if (!s.dt_valid) {  // mesh, material and parameters unchanged since: the bounds stand
+            tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
+                            s.fib.empty() ? nullptr : s.fib.data(), s.prm, &s.dt_mech, &s.dt_th);
+            s.dt_valid = true;
+        }
         s.dt = s.prm.dt > 0 ? s.prm.dt : s.prm.dt_safety * std::min(s.dt_mech, s.dt_th);
         s.src_off = src_off;
         src_off += c->batch ? (int)s.src.size() : kSingleSources;
