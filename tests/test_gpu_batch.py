@@ -224,3 +224,27 @@ def test_grid_resident_mode_equals_streamed(kind):
     assert np.abs(outs[0][0]).max() > 0
     for a, b in zip(*outs):
         np.testing.assert_allclose(a, b, rtol=0, atol=1e-6 * np.abs(b).max() + 1e-30)
+
+
+def test_grid_resident_checkpoint_and_source_change_match_streamed():
+    """Grid-resident mode across a checkpoint/restore and a heat-source change between
+    steps (stream-ordered upload), against the streamed kernels doing the same."""
+    tled = _tled()
+    prob = W.block_h8(n=16, h=3e-3)
+    moved = np.array(prob.sources)
+    moved[:, 0] += 2e-3
+    outs = []
+    for extra in (0, tled.STREAMED):
+        f = _flags(prob, tled, extra)
+        a = tled.Solver.from_problem(prob, flags=f)
+        assert a.grid_resident == (extra == 0)
+        a.step(45)
+        blob = a.save_state()
+        b = tled.Solver.from_problem(prob, flags=f)
+        b.load_state(blob)
+        b.set_heat_sources(moved)
+        b.step(37)
+        b.sync()
+        outs.append((b.displacement(), b.temperature(), b.damage()))
+    for x, y in zip(*outs):
+        np.testing.assert_allclose(x, y, rtol=0, atol=1e-6 * np.abs(y).max() + 1e-30)
