@@ -2,11 +2,12 @@
 // FP32 accumulation in tensor memory, GELU activations, MSE loss, Adam.
 //
 // GEMM: D[M][N] = A[M][K] * B[N][K]^T with both operands K-major BF16 in
-// global memory.  One CTA computes a 128 x BN tile: warp 0 streams 128 x 64 and
-// BN x 64 operand boxes with TMA (128-byte swizzle) through a 4-stage
-// mbarrier pipeline, one thread of warp 1 issues tcgen05.mma (K = 16 each)
-// into a TMEM accumulator and commits stage releases, and warps 2-5 read the
-// accumulator with tcgen05.ld (one row per thread) and apply the epilogue:
+// global memory.  Persistent CTAs (two per SM) take 128 x BN tiles in turn: warp
+// 0 streams 128 x 64 and BN x 64 operand boxes with TMA (128-byte swizzle)
+// through a 2-stage mbarrier pipeline, one thread of warp 1 issues tcgen05.mma
+// (K = 16 each) into one of two TMEM accumulators and commits stage releases,
+// and warps 2-5 read the other accumulator with tcgen05.ld (one row per thread)
+// and apply the epilogue:
 //   kEpiBiasF32   Y = D + b                        (float output)
 //   kEpiGelu      Z = D + b, A = GELU(Z)           (Z float; A bf16 and its transpose)
 //   kEpiGeluGrad  dZ = D * GELU'(Zprev)            (bf16 and its transpose)
@@ -17,6 +18,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "mlp_internal.h"
@@ -101,11 +103,83 @@ constexpr int gemm_smem_bytes() {
     return STAGES * (kBM + BN) * kBK * 2 + 1024 + 4 * 32 * kEpiLd * 4;
 }
 
+// Epilogue of one 128 x BN tile for the calling warp (rows row0 .. row0 + 31 = TMEM lanes
+// 32 lg .. + 31, one row per lane), from TMEM columns tcol .. tcol + BN - 1.  Row-major
+// traffic goes through a per-warp 32 x 33 transpose buffer so that a warp's loads and
+// stores cover 32 consecutive columns of one row.
+template <int BN, int MODE>
+__device__ __forceinline__ void epilogue_tile(const GemmArgs &g, uint32_t tmem, uint32_t tcol, int lg, int lane,
+                                              float *buf, int m0, int n0) {
+    const int row0 = m0 + lg * 32;
+    const int row = row0 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + tcol + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+              "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+              "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+              "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int col0 = n0 + c0;
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
+        if constexpr (MODE == kEpiGeluGrad) {  // Z of the previous layer: coalesced rows in, transposed
+#pragma unroll 4
+            for (int rr = 0; rr < 32; rr++) buf[rr * kEpiLd + lane] = g.z_in[(int64_t)(row0 + rr) * g.ld_z + col0 + lane];
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] *= gelu_grad(buf[lane * kEpiLd + j]);
+            __syncwarp();
+        } else if constexpr (MODE == kEpiBiasF32 || MODE == kEpiGelu) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) v[j] += g.bias[col0 + j];
+        }
+        // row-major float output (Y, Z or G): stage and write rows
+        float *out_rm = MODE == kEpiGelu ? g.z_out : g.out_f32;
+        const int ld_rm = MODE == kEpiGelu ? g.ld_z : g.ld_f32;
+        if constexpr (MODE != kEpiGeluGrad) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) buf[lane * kEpiLd + j] = v[j];
+            __syncwarp();
+#pragma unroll 4
+            for (int rr = 0; rr < 32; rr++) out_rm[(int64_t)(row0 + rr) * ld_rm + col0 + lane] = buf[rr * kEpiLd + lane];
+            __syncwarp();
+        }
+        if constexpr (MODE == kEpiGelu || MODE == kEpiGeluGrad) {
+            // bf16 activation (or gradient): transposed copy straight from registers
+            // (consecutive lanes = consecutive rows), row-major copy through the buffer
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(MODE == kEpiGelu ? gelu(v[j]) : v[j]);
+                g.out_bfT[(int64_t)(col0 + j) * g.ld_bfT + row] = h;
+                buf[lane * kEpiLd + j] = __bfloat162float(h);
+            }
+            __syncwarp();
+#pragma unroll 4
+            for (int rr = 0; rr < 32; rr++)
+                g.out_bf[(int64_t)(row0 + rr) * g.ld_bf + col0 + lane] = __float2bfloat16_rn(buf[rr * kEpiLd + lane]);
+            __syncwarp();
+        }
+    }
+}
+
+// Persistent GEMM: CTA b takes the 128 x BN tiles b, b + gridDim.x, ... (M-major order, so
+// that neighbouring CTAs share the weight tile).  The accumulator is double-buffered in
+// TMEM (2 BN columns): the MMA warp fills one buffer while the epilogue warps drain the
+// other; tfull[a] (MMA -> epilogue, a tcgen05 commit) and tempty[a] (epilogue -> MMA, one
+// arrival per epilogue warp) hand the buffers over.
 template <int BN, int MODE, int kStages>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(192, 2)
     umma_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const GemmArgs g) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t full[kStages], empty[kStages], accum;
+    __shared__ uint64_t full[kStages], empty[kStages], tfull[2], tempty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail;
     uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -113,7 +187,7 @@ __global__ void __launch_bounds__(192, 1)
     uint8_t *sA = smem, *sB = smem + kStages * kABytes;
     float *sEpi = reinterpret_cast<float *>(sB + kStages * kBBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int n_mt = g.M / kBM, n_tiles = n_mt * (g.N / BN);
     const int KB = g.K / kBK;
 
     if (threadIdx.x == 0) {
@@ -121,119 +195,94 @@ __global__ void __launch_bounds__(192, 1)
             bar_init(&full[s], 1);
             bar_init(&empty[s], 1);
         }
-        bar_init(&accum, 1);
+        for (int a = 0; a < 2; a++) {
+            bar_init(&tfull[a], 1);
+            bar_init(&tempty[a], 4);  // one arrival per epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
-                     "r"((uint32_t)BN));
+                     "r"((uint32_t)(2 * BN)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    int issued = 0;  // producer: k-blocks whose loads were issued
+    int issued = 0, consumed = 0;  // producer: k-blocks whose loads were issued / known to have landed
 
     if (warp == 0 && lane == 0) {
-        // ---- TMA producer
-        for (int kb = 0; kb < KB; kb++) {
-            const int s = kb % kStages;
-            if (kb >= kStages && !bar_wait(&empty[s], ((kb / kStages) - 1) & 1)) {
-                s_fail = 1;
-                break;
+        // ---- TMA producer over all the CTA's tiles
+        int it = 0;
+        bool dead = false;
+        for (int t = blockIdx.x; t < n_tiles && !dead; t += gridDim.x) {
+            const int m0 = (t % n_mt) * kBM, n0 = (t / n_mt) * BN;
+            for (int kb = 0; kb < KB; kb++, it++) {
+                const int s = it % kStages;
+                if (it >= kStages) {
+                    if (!bar_wait(&empty[s], ((it / kStages) - 1) & 1)) {
+                        s_fail = 1;
+                        dead = true;
+                        break;
+                    }
+                    consumed = it - kStages + 1;
+                }
+                bar_expect(&full[s], kABytes + kBBytes);
+                tma_load_2d(sA + s * kABytes, &tmA, kb * kBK, m0, &full[s]);
+                tma_load_2d(sB + s * kBBytes, &tmB, kb * kBK, n0, &full[s]);
+                issued = it + 1;
             }
-            bar_expect(&full[s], kABytes + kBBytes);
-            tma_load_2d(sA + s * kABytes, &tmA, kb * kBK, m0, &full[s]);
-            tma_load_2d(sB + s * kBBytes, &tmB, kb * kBK, n0, &full[s]);
-            issued++;
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer
         constexpr uint32_t idesc = idesc_bf16<BN>();
-        for (int kb = 0; kb < KB; kb++) {
-            const int s = kb % kStages;
-            if (!bar_wait(&full[s], (kb / kStages) & 1)) {
+        int it = 0, i = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, i++) {
+            const int a = i & 1;
+            if (i >= 2 && !bar_wait(&tempty[a], ((i >> 1) - 1) & 1)) {  // the epilogue drained buffer a
                 s_fail = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = su32(sA + s * kABytes), b0 = su32(sB + s * kBBytes);
-#pragma unroll
-            for (int kk = 0; kk < kBK / 16; kk++)  // advance 16 elements = 32 bytes along K inside the swizzle row
-                umma(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (kb | kk) != 0);
-            umma_commit(&empty[s]);  // stage reusable once these MMAs completed
-        }
-        umma_commit(&accum);
-    } else if (warp >= 2) {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows (lane = row);
-        //      row-major traffic goes through a per-warp 32 x 33 transpose buffer so that a
-        //      warp's loads and stores cover 32 consecutive columns of one row
-        const int lg = warp & 3;
-        const int row0 = m0 + lg * 32;
-        const int row = row0 + lane;
-        float *buf = sEpi + (warp - 2) * 32 * kEpiLd;
-        const bool ok = bar_wait(&accum, 0);
-        if (!ok) s_fail = 1;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) {
-#pragma unroll 1
-            for (int c0 = 0; c0 < BN; c0 += 32) {
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                      "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                      "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                      "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                      "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int col0 = n0 + c0;
-                float v[32];
-#pragma unroll
-                for (int j = 0; j < 32; j++) v[j] = __uint_as_float(r[j]);
-                if constexpr (MODE == kEpiGeluGrad) {  // Z of the previous layer: coalesced rows in, transposed
-#pragma unroll 4
-                    for (int rr = 0; rr < 32; rr++) buf[rr * kEpiLd + lane] = g.z_in[(int64_t)(row0 + rr) * g.ld_z + col0 + lane];
-                    __syncwarp();
-#pragma unroll
-                    for (int j = 0; j < 32; j++) v[j] *= gelu_grad(buf[lane * kEpiLd + j]);
-                    __syncwarp();
-                } else if constexpr (MODE == kEpiBiasF32 || MODE == kEpiGelu) {
-#pragma unroll
-                    for (int j = 0; j < 32; j++) v[j] += g.bias[col0 + j];
+            const uint32_t acc_t = tmem + (uint32_t)(a * BN);
+            bool ok = true;
+            for (int kb = 0; kb < KB; kb++, it++) {
+                const int s = it % kStages;
+                if (!bar_wait(&full[s], (it / kStages) & 1)) {
+                    ok = false;
+                    break;
                 }
-                // row-major float output (Y, Z or G): stage and write rows
-                float *out_rm = MODE == kEpiGelu ? g.z_out : g.out_f32;
-                const int ld_rm = MODE == kEpiGelu ? g.ld_z : g.ld_f32;
-                if constexpr (MODE != kEpiGeluGrad) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = su32(sA + s * kABytes), b0 = su32(sB + s * kBBytes);
 #pragma unroll
-                    for (int j = 0; j < 32; j++) buf[lane * kEpiLd + j] = v[j];
-                    __syncwarp();
-#pragma unroll 4
-                    for (int rr = 0; rr < 32; rr++) out_rm[(int64_t)(row0 + rr) * ld_rm + col0 + lane] = buf[rr * kEpiLd + lane];
-                    __syncwarp();
-                }
-                if constexpr (MODE == kEpiGelu || MODE == kEpiGeluGrad) {
-                    // bf16 activation (or gradient): transposed copy straight from registers
-                    // (consecutive lanes = consecutive rows), row-major copy through the buffer
-#pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const __nv_bfloat16 h = __float2bfloat16_rn(MODE == kEpiGelu ? gelu(v[j]) : v[j]);
-                        g.out_bfT[(int64_t)(col0 + j) * g.ld_bfT + row] = h;
-                        buf[lane * kEpiLd + j] = __bfloat162float(h);
-                    }
-                    __syncwarp();
-#pragma unroll 4
-                    for (int rr = 0; rr < 32; rr++)
-                        g.out_bf[(int64_t)(row0 + rr) * g.ld_bf + col0 + lane] = __float2bfloat16_rn(buf[rr * kEpiLd + lane]);
-                    __syncwarp();
-                }
+                for (int kk = 0; kk < kBK / 16; kk++)  // advance 16 elements = 32 bytes along K inside the swizzle row
+                    umma(acc_t, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (kb | kk) != 0);
+                umma_commit(&empty[s]);  // stage reusable once these MMAs completed
             }
+            if (!ok) {
+                s_fail = 1;
+                break;
+            }
+            umma_commit(&tfull[a]);  // buffer a complete once every MMA of the tile has
+        }
+    } else if (warp >= 2) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31
+        const int lg = warp & 3;
+        float *buf = sEpi + (warp - 2) * 32 * kEpiLd;
+        int i = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, i++) {
+            const int a = i & 1;
+            if (!bar_wait(&tfull[a], (i >> 1) & 1)) {
+                s_fail = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            epilogue_tile<BN, MODE>(g, tmem, (uint32_t)(a * BN), lg, lane, buf, (t % n_mt) * kBM, (t / n_mt) * BN);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(&tempty[a])) : "memory");
         }
     }
     __syncthreads();
@@ -241,12 +290,12 @@ __global__ void __launch_bounds__(192, 1)
         if (threadIdx.x == 0) {
             atomicOr(g.status, 1u);
             // let this CTA's issued copies land before its shared memory is released
-            for (int kb = 0; kb < issued; kb++) bar_wait(&full[kb % kStages], (kb / kStages) & 1);
+            for (int it = consumed; it < issued; it++) bar_wait(&full[it % kStages], (it / kStages) & 1);
         }
         __syncthreads();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * BN)));
 }
 
 // ---------------------------------------------------------------------------
@@ -410,21 +459,22 @@ __global__ void __launch_bounds__(256) ensemble_kernel(const EnsembleArgs E) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-constexpr int kGemmStages = 2;  // two CTAs per SM: one's epilogue overlaps the other's MMAs
+constexpr int kGemmStages = 2;  // two persistent CTAs per SM, each overlapping its epilogue with its next MMAs
 template <int BN, int MODE>
 static cudaError_t launch_one(const CUtensorMap &a, const CUtensorMap &b, const GemmArgs &g, cudaStream_t s) {
     const int smem = gemm_smem_bytes<BN, kGemmStages>();
     auto kern = umma_gemm_kernel<BN, MODE, kGemmStages>;
-    static int set_device = -1;  // the attribute is per device: set it on first use there
+    static int set_device = -1, n_sm = 0;  // the attribute is per device: set it on first use there
     int dev = 0;
     cudaGetDevice(&dev);
     if (set_device != dev) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         set_device = dev;
     }
-    dim3 grid(g.M / kBM, g.N / BN);
-    kern<<<grid, 192, smem, s>>>(a, b, g);
+    const int n_tiles = (g.M / kBM) * (g.N / BN);
+    kern<<<std::min(n_tiles, 2 * n_sm), 192, smem, s>>>(a, b, g);
     return cudaGetLastError();
 }
 
