@@ -86,6 +86,10 @@ int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *
                       float *mean, float *std, float *spread, uint8_t *fallback);
 /* wait for the stream; E_TIMEOUT if a bounded pipeline wait gave up */
 int tled_mlp_sync(tled_mlp *m);
+/* enqueue the network's later work on another stream of its device (e.g. to run the
+ * members of an ensemble side by side); ordering against the previous stream is the
+ * caller's.  Errors: E_ARG for a NULL network. */
+int tled_mlp_set_stream(tled_mlp *m, void *cuda_stream);
 
 #ifdef __cplusplus
 }

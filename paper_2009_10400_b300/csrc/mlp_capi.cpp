@@ -325,6 +325,12 @@ int tled_mlp_set_input_scaling(tled_mlp *m, const float *shift, const float *sca
     return TLED_OK;
 }
 
+int tled_mlp_set_stream(tled_mlp *m, void *stream) {
+    if (!m) return TLED_E_ARG;
+    m->stream = (cudaStream_t)stream;
+    return TLED_OK;
+}
+
 int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *const *y, int32_t B, int32_t n_out,
                       const float *out_scale, const float *out_shift, const float *row_src, int32_t row_stride,
                       float row_mult, int32_t n_row_scaled, const float *out_offset, int32_t n_spread, float tol,

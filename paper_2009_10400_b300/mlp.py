@@ -25,6 +25,7 @@ _SIGS = {
     "tled_mlp_gradients": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "tled_mlp_train_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p], C.c_int),
     "tled_mlp_sync": ([C.c_void_p], C.c_int),
+    "tled_mlp_set_stream": ([C.c_void_p, C.c_void_p], C.c_int),
     "tled_mlp_set_input_scaling": ([C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
     "tled_mlp_train_step_rows": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_void_p],
                                  C.c_int),
@@ -145,6 +146,11 @@ class MLP:
 
     def sync(self):
         self._check(lib().tled_mlp_sync(self.h))
+
+    def set_stream(self, stream):
+        """Enqueue later work on `stream` (a torch.cuda.Stream of the same device)."""
+        self.stream = stream
+        self._check(lib().tled_mlp_set_stream(self.h, C.c_void_p(stream.cuda_stream)))
 
 
 def ensemble(ys, out_scale=None, out_shift=None, n_spread=0, tol=0.0, device=0, stream=None, want_std=True,

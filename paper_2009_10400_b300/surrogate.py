@@ -121,6 +121,7 @@ class Surrogate:
             net.set_input_scaling(0.5 * (lo + hi), 2.0 / (hi - lo))
         self.y_mean = self.y_std = None
         self._ys = None
+        self._side = None  # one stream per member for side-by-side inference
 
     def _dev(self):
         return f"cuda:{self.device}"
@@ -177,9 +178,19 @@ class Surrogate:
             self._ys = [torch.empty(mp, self.dims[-1], dtype=torch.float32, device=Xd.device)
                         for _ in self.members]
         ys = [y[:mp] for y in self._ys]
-        for net, y in zip(self.members, ys):
+        # the members' forward passes side by side, one stream each, joined before the
+        # ensemble statistics (the outputs live across calls, the inputs outlive the join)
+        main = torch.cuda.current_stream(self.device)
+        if self._side is None:
+            self._side = [torch.cuda.Stream(device=self.device) for _ in self.members]
+        ready = main.record_event()
+        for net, y, side in zip(self.members, ys, self._side):
+            side.wait_event(ready)
+            net.set_stream(side)
             for b0 in range(0, mp, self.max_batch):
                 net.forward(Xd[b0:b0 + self.max_batch], out=y[b0:b0 + self.max_batch])
+            net.set_stream(main)
+            main.wait_stream(side)
         if self.per_power:
             mean, std, spread, fb = ensemble(ys, self._scale, self._shift, n_spread, tol, device=self.device,
                                              want_std=want_std, row_src=Xd, row_mult=1.0 / P_REF,
