@@ -190,10 +190,11 @@ def barrier(ws):
         dist.barrier()
 
 
-def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1):
+def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1, warmup_seconds=10.0):
     """Time the FP64 oracle as it stands on a bounded sample of the workload:
-    `warmup` untimed steps, then as many full steps as fit in about `seconds`
-    (at least 1, at most max_steps)."""
+    up to `warmup` untimed steps (at least one, stopping after about
+    `warmup_seconds`), then as many full steps as fit in about `seconds` (at
+    least 1, at most max_steps)."""
     import oracle
 
     t0 = time.perf_counter()
@@ -201,15 +202,20 @@ def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1):
     setup = time.perf_counter() - t0
     s = m.init_state()
     t0 = time.perf_counter()
-    m.step(s, max(1, warmup))
-    one = (time.perf_counter() - t0) / max(1, warmup)
+    n_warm = 0
+    while n_warm < max(1, warmup):
+        m.step(s, 1)
+        n_warm += 1
+        if time.perf_counter() - t0 > warmup_seconds:
+            break
+    one = (time.perf_counter() - t0) / n_warm
     steps = int(max(1, min(max_steps, seconds // max(one, 1e-9))))
     t0 = time.perf_counter()
     m.step(s, steps)
     el = time.perf_counter() - t0
     return {"value": prob.ne * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{prob.name}: {steps} full steps after {max(1, warmup)} warm-up step(s) ({el:.1f} s, "
-                      f"set-up {setup:.1f} s), FP64 C oracle, single-threaded", "steps": steps}
+            "sample": f"{prob.name}: {steps} full steps after {n_warm} warm-up step(s) ({el:.1f} s, "
+                      f"set-up {setup:.1f} s), FP64 C oracle, single-threaded", "steps": steps, "warmup": n_warm}
 
 
 def run_reference(args):
@@ -220,9 +226,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     prob = make_problem(args.workload if args.workload != "surrogate" else "block_h8")
-    r = cpu_oracle_sample(prob, args.steps, seconds=args.ref_seconds, warmup=min(args.warmup, 1))
-    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 0, "steps": r["steps"],
-            "warmup": 1, "ms_per_step": 1e3 * prob.ne / r["value"], "higher_is_better": True,
+    r = cpu_oracle_sample(prob, args.steps, seconds=args.ref_seconds, warmup=args.warmup)
+    # run on the host cores of the launch's box (n_gpus = the launch's world size, for bookkeeping)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": r["steps"],
+            "warmup": r["warmup"], "ms_per_step": 1e3 * prob.ne / r["value"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn},
             "cpu_baseline": r, "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
