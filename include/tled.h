@@ -27,6 +27,12 @@
  *    tled_create() (NULL = the legacy default stream).  Calls that return
  *    host data synchronise that stream.
  *  - A context is not thread-safe; distinct contexts are independent.
+ *  - Step modes (chosen at init, reported by tled_get_mode, all computing the
+ *    same numbers): streamed (a tile kernel and a shared-node kernel per step,
+ *    captured in CUDA graphs of 32 steps), resident (a problem -- or each
+ *    scenario of a batch -- that fits one CTA's shared memory runs 32 steps
+ *    per launch in one CTA) and grid-resident (a single problem whose tiles fit
+ *    co-resident CTAs runs 32 steps per cooperative launch).
  *
  * Call order:  create -> set_mesh -> set_material -> [set_bcs] ->
  *   [set_heat_sources] -> [set_params] -> workspace_size -> init ->
