@@ -386,8 +386,8 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
             }
         }
         // the tile's structure record: local connectivity [kTile][kt], then the gather
-        // list -- for every local node the slot offsets (corner * kTile + element) of its
-        // incident corners, ascending element then corner -- and the nl + 1 row offsets
+        // list -- for every local node the slot offsets slot_pos(element, corner) of its
+        // incident corners, ascending corner then element -- and the nl + 1 row offsets
         std::fill(pat.begin(), pat.end(), (uint16_t)0);
         uint16_t *rec_conn = pat.data();
         uint16_t *rec_codes = rec_conn + kTile * kt;
@@ -400,10 +400,10 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         for (int l = 0; l < nl; l++) cnt[l + 1] += cnt[l];
         for (int l = 0; l <= nl; l++) rec_row[l] = (uint16_t)cnt[l];
         std::vector<int32_t> cur(cnt.begin(), cnt.end() - 1);
-        for (int64_t i = e0; i < e0 + ne_t; i++)
-            for (int a = 0; a < kt; a++) {
+        for (int a = 0; a < kt; a++)
+            for (int64_t i = e0; i < e0 + ne_t; i++) {
                 int l = conn_local[(size_t)i * npe + a];
-                rec_codes[cur[l]++] = (uint16_t)(a * kTile + (int)(i - e0));
+                rec_codes[cur[l]++] = (uint16_t)slot_pos((int)(i - e0), a);
             }
         // tiles with the same element type and structure share one record (FNV-1a hash,
         // then a full compare)

@@ -24,6 +24,15 @@ constexpr int kResBlock = kResLanes * kBlock;
 // per-tile structure record (uint16): local connectivity [kTile * npe], gather slot
 // offsets [kTile * npe], row offsets [kMaxLocal + 8]; tiles of equal structure share one
 constexpr int pattern_u16(int npe) { return 2 * kTile * npe + kMaxLocal + 8; }
+// Position of element e's corner c in a tile's corner-slot buffer ([corner][kTile] float4).
+// The low three bits of e are XOR-ed with a linear function of bits 3-5 of e and of c: for
+// a fixed corner this permutes each aligned group of 8 elements (the element pass's stores
+// stay conflict-free), and a warp gathering one node per thread, entry by entry in corner
+// order, spreads its reads over more shared-memory banks (on 8x8x4 Morton blocks of bricks
+// about half the excess wavefronts of the plain [corner][element] layout).
+constexpr int slot_swz_e(int h) { return ((h >> 1 ^ h >> 2) & 1) | ((h ^ h >> 2) & 1) << 1 | (h & 1) << 2; }
+constexpr int slot_swz_c(int c) { return (c & 1) << 1 | ((c ^ c >> 1 ^ c >> 2) & 1) << 2; }
+constexpr int slot_pos(int e, int c) { return c * kTile + (e ^ slot_swz_e((e >> 3) & 7) ^ slot_swz_c(c)); }
 constexpr int kMaxSources = 16;
 constexpr int kSrcRow = 11;        // doubles per source in the device table: c0, vel, sigma, P, t_on, t_off, shape
 constexpr int kTileInfo = 8;       // ints per tile record
@@ -50,8 +59,8 @@ struct Plan {
                                         //   n_local, sh_off, structure record id, element type (4 or 8)
     std::vector<int32_t> tile_shared;   // per tile (from a multiple of 4, -1 padded): new ids of its shared nodes (ascending)
     std::vector<uint16_t> patterns;     // [n_patterns][pat_stride] distinct structure records: local connectivity
-                                        //   [kTile][npe], slot offsets corner * kTile + element grouped by local
-                                        //   node (ascending element, corner), then the n_local + 1 row offsets
+                                        //   [kTile][npe], slot offsets slot_pos(element, corner) grouped by local
+                                        //   node (ascending corner, element), then the n_local + 1 row offsets
     int pat_stride = 0;                 // pattern_u16(npe)
     std::vector<int32_t> sh_rowptr;     // [n_shared + 1]: node-major partial positions, tile order within a node
     std::vector<int32_t> part_pos;      // parallel to tile_shared: partial position of that (tile, node)

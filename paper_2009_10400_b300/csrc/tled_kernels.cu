@@ -660,13 +660,13 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
         wht8x2(fxy); wht8x2(fzt);
 #pragma unroll
         for (int i = 0; i < 8; i++)
-            slot[wht_corner(i) * kTile + ec] = make_float4(fxy[i].x, fxy[i].y, fzt[i].x, fzt[i].y);
+            slot[slot_pos(ec, wht_corner(i))] = make_float4(fxy[i].x, fxy[i].y, fzt[i].x, fzt[i].y);
     } else {
         // T4: dh_0 = -(dh_1 + dh_2 + dh_3), dh_{j+1} = row j of J0^-1
-        slot[ec] = make_float4(-(Qm[0][0] + Qm[0][1] + Qm[0][2]), -(Qm[1][0] + Qm[1][1] + Qm[1][2]),
+        slot[slot_pos(ec, 0)] = make_float4(-(Qm[0][0] + Qm[0][1] + Qm[0][2]), -(Qm[1][0] + Qm[1][1] + Qm[1][2]),
                                -(Qm[2][0] + Qm[2][1] + Qm[2][2]), -(r[0] + r[1] + r[2]));
 #pragma unroll
-        for (int j = 0; j < 3; j++) slot[(1 + j) * kTile + ec] = make_float4(Qm[0][j], Qm[1][j], Qm[2][j], r[j]);
+        for (int j = 0; j < 3; j++) slot[slot_pos(ec, 1 + j)] = make_float4(Qm[0][j], Qm[1][j], Qm[2][j], r[j]);
     }
 }
 
@@ -737,7 +737,7 @@ __device__ void prefetch_tile(const StepArgs &A, int t, const TileInfo &T) {
     }
 }
 
-// fixed-order sum of local node l's corner slots (ascending element, corner): two
+// fixed-order sum of local node l's corner slots (ascending corner, element): two
 // running sums (even and odd entries), each as (x, y) and (z, w) pairs
 __device__ __forceinline__ float4 gather_node(const float4 *slot, const uint16_t *s_code, const uint16_t *s_row, int l) {
     int r = s_row[l];
