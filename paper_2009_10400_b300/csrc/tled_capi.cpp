@@ -887,7 +887,15 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         std::fill(scn_of_elem.begin() + c->sc[si].elem_off, scn_of_elem.begin() + c->sc[si].elem_off + c->sc[si].ne, si);
     std::vector<char> rec((size_t)p.n_tiles * rb, 0);
     std::vector<double> Mn(nn, 0.0), Cn(nn, 0.0), Vn(nn, 0.0), Kb(nn, 0.0);
-    bool brick = true;  // every element an H8 brick (vanishing reference hourglass projections)
+    // every element an H8 axis-aligned box: the brick instance, whose records hold the
+    // diagonal of J0^-1 only
+    bool brick = !(c->sc[0].prm.flags & TLED_GENERAL_H8);
+    for (int64_t e = 0; e < nep && brick; e++) {
+        const int64_t eo = p.elem_old[e];
+        if (eo < 0) continue;
+        const Scenario &s = c->sc[scn_of_elem[eo]];
+        brick = s.npe == 8 && tled::brick_element(s.X.data(), s.conn.data() + (eo - s.elem_off) * 8);
+    }
     for (int64_t e = 0; e < nep; e++) {
         const int64_t eo = p.elem_old[e];
         if (eo < 0) continue;  // padding slot
@@ -897,12 +905,11 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         const int32_t *cn = s.conn.data() + el * ke;
         double Ji[9], V;
         tled::element_geometry(ke, s.X.data(), cn, Ji, &V);
-        if (brick) brick = ke == 8 && tled::hourglass_projections_vanish(s.X.data(), cn);
         char *r = rec.data() + (size_t)(e / kT) * rb;
         const int ei = (int)(e % kT);
         float *cf = reinterpret_cast<float *>(r) + ei;
         int q = 0;
-        for (int j = 0; j < 9; j++) cf[(q++) * kT] = (float)Ji[j];
+        for (int j = 0; j < 9; j += brick ? 4 : 1) cf[(q++) * kT] = (float)Ji[j];
         cf[(q++) * kT] = (float)V;
         if (c->has_mat) {
             if (!s.mat6.empty()) {
@@ -1024,7 +1031,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.ani_alpha = (float)fibre_ratio(m.alpha_fibre_ratio);
     A.ani_k = (float)fibre_ratio(m.k_fibre_ratio);
     A.ani = fibre_ratio(m.alpha_fibre_ratio) != 1.0 || fibre_ratio(m.k_fibre_ratio) != 1.0;
-    A.brick = brick && !(s0.prm.flags & TLED_GENERAL_H8);
+    A.brick = brick;  // (TLED_GENERAL_H8 excluded above)
     A.T0 = m.T0;
     A.n_tiles = p.n_tiles;
     A.pat_stride = p.pat_stride;

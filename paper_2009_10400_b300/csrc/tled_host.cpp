@@ -23,13 +23,15 @@ static inline double nat_deriv(int npe, int a, int k) {
     return npe == 8 ? kH8Sign[a][k] * 0.125 : kT4Deriv[a][k];
 }
 
-// True when the hourglass projections (the Walsh-Hadamard coefficients xi eta,
-// eta zeta, xi zeta and xi eta zeta) of the H8 element's reference corner
-// coordinates, rounded to float and transformed in the tile kernel's butterfly
-// order, are exactly zero -- axis-aligned bricks such as voxel meshes.  The
-// kernel then drops every term these coefficients multiply (exact zeros; only
-// the compiler's multiply-add fusion around them can differ, by an ulp).
-bool hourglass_projections_vanish(const double *X, const int32_t *cn) {
+// True for an axis-aligned box: the H8 element's reference corner coordinates,
+// rounded to float and transformed in the tile kernel's butterfly order, have
+// exactly zero hourglass projections (the Walsh-Hadamard coefficients xi eta,
+// eta zeta, xi zeta and xi eta zeta), and each coordinate has zero first-order
+// coefficients along the other two reference directions (J0 diagonal) -- voxel
+// and block meshes.  The kernel then drops every term these coefficients multiply
+// and stores only the diagonal of J0^-1 (the off-diagonal entries computed in
+// double are round-off, some 1e-14 of the diagonal).
+bool brick_element(const double *X, const int32_t *cn) {
     for (int d = 0; d < 3; d++) {
         float w[8];
         for (int i = 0; i < 8; i++) {
@@ -44,6 +46,8 @@ bool hourglass_projections_vanish(const double *X, const int32_t *cn) {
                     w[i + h] = x - y;
                 }
         if (w[3] != 0.f || w[5] != 0.f || w[6] != 0.f || w[7] != 0.f) return false;
+        for (int j = 0; j < 3; j++)  // first-order coefficients: xi (1), eta (2), zeta (4)
+            if (j != d && w[1 << j] != 0.f) return false;
     }
     return true;
 }

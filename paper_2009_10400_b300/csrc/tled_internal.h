@@ -108,7 +108,8 @@ struct StepArgs {
     const float4 *nodec;   // m_i, Cth_i, mask bits (as float bits), 0
     const float4 *ubar;    // prescribed displacement or nullptr
     // element data, tile-blocked: tile t's record at elem_rec + t * rec_bytes holds float
-    // components [q][kTile]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz]; the Prony
+    // components [q][kTile]: J0^-1 (9; bricks: its diagonal, 3), V0, [mu kappa k1 k2 k alpha],
+    // [fibre xyz] (rec_bytes is sized for 9); the Prony
     // state lives in visc [t][6 n_prony][kTile]; the local connectivity is in the tile's
     // structure record (pattern).
     const char *elem_rec;
@@ -142,7 +143,8 @@ struct StepArgs {
     int sm_ns, sm_pat, sm_sh, sm_xu, sm_X, sm_bar, sm_total;  // sm_pat: structure record, sm_sh: shared-node lists
     int n_tiles;
     int pat_stride;        // uint16 entries between consecutive structure records
-    int n_comp;            // staged float components per element (J0^-1 9, V0, [mat 6], [fibre 3], Prony 6 n)
+    int n_comp;            // staged float components per element (J0^-1 9 or, bricks, its diagonal 3, V0,
+                           //   [mat 6], [fibre 3], Prony 6 n)
     // batch-wide scalars
     float mu, kappa, k1, k2, kc, alpha;   // uniform material (used when has_mat == 0)
     float a0x, a0y, a0z;                  // uniform fibre (used when has_fib == 0)
@@ -215,7 +217,7 @@ cudaError_t noalloc_scratch(int device, double **ptr);
 
 // host geometry and planning (tled_host.cpp)
 bool element_geometry(int npe, const double *X, const int32_t *cn, double Jinv[9], double *V);
-bool hourglass_projections_vanish(const double *X, const int32_t *cn);  // H8 brick test
+bool brick_element(const double *X, const int32_t *cn);  // H8 axis-aligned box test
 // fib: per-element fibres [ne][3] or NULL (m.a0); the conduction bound uses the anisotropic
 // conductivity at F = I when m.k_fibre_ratio is not 0 or 1
 void stable_dt(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *conn, const tled_material &m,

@@ -305,8 +305,9 @@ struct ElemIn {
 
 // Element inputs staged in shared memory for one tile: the local connectivity
 // [kTile][NPE] (uint16, head of the structure record) and the float components
-// [q][kTile]: J0^-1 (9), V0, [mu kappa k1 k2 k alpha], [fibre xyz], Prony state (6 per term).
-template <int NPE, int NPR>
+// [q][kTile]: J0^-1 (9; bricks: its diagonal, 3), V0, [mu kappa k1 k2 k alpha], [fibre xyz],
+// Prony state (6 per term).
+template <int NPE, int NPR, bool BRICK = false>
 __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, const uint16_t *conn, int ec, int *cl,
                                           ElemIn<NPR> &E) {
     if constexpr (NPE == 8) {
@@ -319,8 +320,14 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, c
     }
     const float *cp = reinterpret_cast<const float *>(base) + ec;
     int q = 0;
+    if constexpr (BRICK) {
 #pragma unroll
-    for (int k = 0; k < 9; k++) E.Ji[k] = cp[(q++) * kTile];
+        for (int k = 0; k < 9; k++) E.Ji[k] = 0.f;
+        E.Ji[0] = cp[(q++) * kTile]; E.Ji[4] = cp[(q++) * kTile]; E.Ji[8] = cp[(q++) * kTile];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; k++) E.Ji[k] = cp[(q++) * kTile];
+    }
     E.V = cp[(q++) * kTile];
     if (A.has_mat) {
         E.mu = cp[(q++) * kTile]; E.kap = cp[(q++) * kTile]; E.k1 = cp[(q++) * kTile];
@@ -344,8 +351,9 @@ __device__ __forceinline__ void load_elem(const StepArgs &A, const char *base, c
 // chunk's slot buffer at [corner][ec] (conflict-free).
 // ANI: transversely isotropic thermal expansion about the fibre (Eq. 11) and
 // conductivity along the current fibre; otherwise isotropic (F_th = lambda I).
-// BRICK (H8): the reference hourglass projections c_al vanish exactly for every
-// element, so the terms they multiply (and the corner coordinates) are dropped.
+// BRICK (H8): every element an axis-aligned box: J0^-1 is diagonal (its off-diagonal
+// products are dropped) and the reference hourglass projections c_al vanish exactly,
+// so the terms they multiply (and the corner coordinates) are dropped too.
 template <int NPE, int NPR, bool ANI, bool BRICK>
 __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &SP, int64_t e, int ec, const int *cl,
                                              ElemIn<NPR> &E, const float4 *__restrict__ s_xu,
@@ -420,9 +428,15 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     float H[3][3], gth[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
+        if constexpr (BRICK) {
 #pragma unroll
-        for (int i = 0; i < 3; i++) H[i][j] = sc * (G[i][0] * Ji[j] + G[i][1] * Ji[3 + j] + G[i][2] * Ji[6 + j]);
-        gth[j] = sc * (gt[0] * Ji[j] + gt[1] * Ji[3 + j] + gt[2] * Ji[6 + j]);
+            for (int i = 0; i < 3; i++) H[i][j] = sc * (G[i][j] * Ji[4 * j]);
+            gth[j] = sc * (gt[j] * Ji[4 * j]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; i++) H[i][j] = sc * (G[i][0] * Ji[j] + G[i][1] * Ji[3 + j] + G[i][2] * Ji[6 + j]);
+            gth[j] = sc * (gt[0] * Ji[j] + gt[1] * Ji[3 + j] + gt[2] * Ji[6 + j]);
+        }
     }
 
     // ---- thermal split (Eqs. 7-11, isotropic): lambda = 1 + delta, delta = alpha theta_e
@@ -572,7 +586,8 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int k = 0; k < 3; k++)
-            Qm[i][k] = sV * (P[i][0] * Ji[3 * k] + P[i][1] * Ji[3 * k + 1] + P[i][2] * Ji[3 * k + 2]);
+            Qm[i][k] = BRICK ? sV * (P[i][k] * Ji[4 * k])
+                             : sV * (P[i][0] * Ji[3 * k] + P[i][1] * Ji[3 * k + 1] + P[i][2] * Ji[3 * k + 2]);
     // thermal: q = k J C^-1 grad0 theta = k lambda J_el C_el^-1 grad0 theta (Eq. 16);
     // fT_a = V dh_a/dX . q = r . Xi_a with r = s V J0^-1 q
     float kT = kc;
@@ -599,15 +614,20 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
         q2 = kq * (Ci[5] * gth[0] + Ci[4] * gth[1] + Ci[2] * gth[2]);
     }
     float r[3];
+    if constexpr (BRICK) {
+        r[0] = sV * (Ji[0] * q0); r[1] = sV * (Ji[4] * q1); r[2] = sV * (Ji[8] * q2);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 3; k++) r[k] = sV * (Ji[3 * k] * q0 + Ji[3 * k + 1] * q1 + Ji[3 * k + 2] * q2);
+        for (int k = 0; k < 3; k++) r[k] = sV * (Ji[3 * k] * q0 + Ji[3 * k + 1] * q1 + Ji[3 * k + 2] * q2);
+    }
 
     if constexpr (NPE == 8) {
         // hourglass control: gamma_a,al = h_a,al - c_al . dh_a/dX with c_al = sum_b h_b,al X_b;
         // f_a += k_hg sum_al gamma_a,al q_al with q_al = sum_b h_b,al u_b - H c_al (thermal alike)
         float jn2 = 0.f;
 #pragma unroll
-        for (int q = 0; q < 9; q++) jn2 += Ji[q] * Ji[q];
+        for (int q = 0; q < 9; q++)
+            if (!BRICK || q % 4 == 0) jn2 += Ji[q] * Ji[q];
         const float khg = A.khg * (kap + (4.f / 3.f) * mu) * V * jn2 * (1.f / 64.f);
         const float khgT = A.khgT * kT * V * jn2 * (1.f / 64.f);
         float qa[4][3], qT[4];
@@ -833,7 +853,7 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
         int cl[NPE ? NPE : 8];
         ElemIn<NPR> E;
         if (active) {
-            if constexpr (NPE != 0) load_elem<NPE, NPR>(A, buf, s_pat, ec, cl, E);
+            if constexpr (NPE != 0) load_elem<NPE, NPR, BRICK>(A, buf, s_pat, ec, cl, E);
             else if (npe == 8) load_elem<8, NPR>(A, buf, s_pat, ec, cl, E);
             else load_elem<4, NPR>(A, buf, s_pat, ec, cl, E);
         }
@@ -1028,7 +1048,7 @@ __global__ void __launch_bounds__(kResBlock, 1) resident_step_kernel(const StepA
             if (lt < ne_t) {
                 int cl[NPE];
                 ElemIn<NPR> E;
-                load_elem<NPE, NPR>(A, blk, reinterpret_cast<const uint16_t *>(blk + A.rt_conn), lt, cl, E);
+                load_elem<NPE, NPR, BRICK>(A, blk, reinterpret_cast<const uint16_t *>(blk + A.rt_conn), lt, cl, E);
                 element_step<NPE, NPR, ANI, BRICK>(A, S, (int64_t)(D.t0 + j) * kTile + lt, lt, cl, E, r_xu, r_X, slot,
                                                    reinterpret_cast<float *>(blk) + nfix * kTile + lt);
             }
@@ -1196,7 +1216,7 @@ __global__ void __launch_bounds__(kBlock, 2) coop_step_kernel(const StepArgs A, 
         if (tid < T.ne_t) {
             int cl[NPE];
             ElemIn<NPR> E;
-            load_elem<NPE, NPR>(A, rec, s_pat, tid, cl, E);
+            load_elem<NPE, NPR, BRICK>(A, rec, s_pat, tid, cl, E);
             element_step<NPE, NPR, ANI, BRICK>(A, S, (int64_t)t * kTile + tid, tid, cl, E, s_xu, s_X, slot,
                                                reinterpret_cast<float *>(rec) + nfix * kTile + tid);
         }
@@ -1388,9 +1408,13 @@ __global__ void __launch_bounds__(256) energy_partial_kernel(const StepArgs A, d
         const char *base = A.elem_rec + (int64_t)t * A.rec_bytes;
         const uint16_t *cl = A.pattern + (int64_t)T.pat * A.pat_stride + ec * npe;
         const float *cp = reinterpret_cast<const float *>(base) + ec;
-        double Ji[9];
+        double Ji[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         int q = 0;
-        for (int k = 0; k < 9; k++) Ji[k] = cp[(q++) * kTile];
+        if (A.brick) {  // diagonal of J0^-1
+            for (int k = 0; k < 9; k += 4) Ji[k] = cp[(q++) * kTile];
+        } else {
+            for (int k = 0; k < 9; k++) Ji[k] = cp[(q++) * kTile];
+        }
         const double V = cp[(q++) * kTile];
         double mu = A.mu, kap = A.kappa, k1 = A.k1, k2 = A.k2, al = A.alpha;
         if (A.has_mat) {
@@ -1509,7 +1533,7 @@ static int align128(int x) { return (x + 127) & ~127; }
 
 void tile_smem_layout(StepArgs &a, int npe) {
     if (npe == 0) npe = 8;  // a mixed batch sizes everything for the larger element
-    a.n_comp = 10 + (a.has_mat ? 6 : 0) + (a.has_fib ? 3 : 0) + 6 * a.n_prony;
+    a.n_comp = (a.brick ? 4 : 10) + (a.has_mat ? 6 : 0) + (a.has_fib ? 3 : 0) + 6 * a.n_prony;
     a.sm_in = align128(a.n_comp * kTile * 4);
     a.sm_buf = std::max(a.sm_in, kTile * npe * 16);
     int off = a.sm_buf;  // element inputs; once read into registers, the corner slot buffer

@@ -81,6 +81,29 @@ def test_block_h8_noise_many_tiles_matches_oracle():
     print("block_h8_16", w)
 
 
+@pytest.mark.parametrize("shape", ["graded", "rotated"])
+def test_graded_and_rotated_h8_blocks_match_oracle(shape):
+    """Axis-aligned boxes of graded size (every element its own diagonal J0^-1)
+    take the brick kernel; the same block rotated by 30 degrees about z (still
+    parallelepipeds, J0 no longer diagonal) keeps the general H8 kernel.  Both
+    against the oracle."""
+    import dataclasses
+    tled = _tled()
+    prob = W.block_h8(n=12, h=3e-3)
+    X = prob.X.copy()
+    L = X.max(axis=0)
+    if shape == "graded":  # x -> L (x / L)^1.4 per axis: monotone, every spacing different
+        X = L * (X / L) ** 1.4
+    else:
+        c, s_ = np.cos(np.pi / 6), np.sin(np.pi / 6)
+        X = np.stack([c * X[:, 0] - s_ * X[:, 1], s_ * X[:, 0] + c * X[:, 1], X[:, 2]], axis=1)
+    prob = dataclasses.replace(prob, X=X)
+    s = tled.Solver.from_problem(prob)
+    assert s.brick == (shape == "graded")
+    w = _check_trajectory(prob, 400, 200)
+    print(shape, w)
+
+
 def test_small_tiles_exercise_shared_nodes():
     """Tiny tiles (37 elements) make most nodes shared between tiles: the
     second-pass gather must give the same answer."""
