@@ -80,12 +80,14 @@ def algorithmic_bytes(prob, n_prony):
     return elem * prob.ne + 136 * prob.nn
 
 
-def layout_bytes(prob, n_prony):
+def layout_bytes(prob, n_prony, brick=False):
     """Bytes the same step moves in this library's layout (uint16 local
-    connectivity, J0^-1 instead of dh/dX, float4 nodal records): element record
-    2 npe + 40 B (+24 material, +12 fibre) and the Prony state, 128 B per node."""
+    connectivity -- an upper bound: tiles of equal structure share one record --,
+    J0^-1 instead of dh/dX, its diagonal for axis-aligned bricks, float4 nodal
+    records): element record 2 npe + 40 B (bricks 2 npe + 16 B; +24 material,
+    +12 fibre) and the Prony state, 128 B per node."""
     npe = prob.npe
-    elem = 2 * npe + 9 * 4 + 4 + 2 * 4 * 6 * n_prony
+    elem = 2 * npe + (3 if brick else 9) * 4 + 4 + 2 * 4 * 6 * n_prony
     if prob.per_element:
         elem += 6 * 4
         if not np.allclose(prob.a0, prob.a0[0]):
@@ -668,7 +670,7 @@ def run_gpu(args):
             "config": {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn,
                        "element": "H8" if prob.npe == 8 else "T4", "dt_s": dt,
                        "tiles": info["n_tiles"], "shared_nodes": info["n_shared"],
-                       "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (layout_bytes(prob, n_prony) / 1e6),
+                       "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (layout_bytes(prob, n_prony, s.brick) / 1e6),
                        "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}",
                        "kernels": kernel_desc},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -676,7 +678,7 @@ def run_gpu(args):
                          "kernel": "tile_step_kernel + shared_step_kernel (one step)",
                          "algorithmic_bytes_per_step": alg,
                          "algorithmic_bytes_per_element_step": alg / prob.ne,
-                         "layout_bytes_per_step": layout_bytes(prob, n_prony),
+                         "layout_bytes_per_step": layout_bytes(prob, n_prony, s.brick),
                          "kernel_ms_per_step": per_step_kernel_ms,
                          "tile_kernel_ms": k_tile / args.roofline_steps,
                          "shared_kernel_ms": k_sh / args.roofline_steps, "peak_source": src},

@@ -73,10 +73,11 @@ extern "C" {
 #define TLED_TEMP_DEP (1u << 1)    /* c(T), k(T) linear in T (Table 5) */
 #define TLED_COMPENSATED (1u << 2) /* float-float accumulation of u and T */
 #define TLED_CEM43 (1u << 3)       /* accumulate the CEM43 thermal dose per node (single problems only) */
-#define TLED_GENERAL_H8 (1u << 4)  /* keep the general H8 kernel for brick meshes (every element an H8 whose
-                                      reference hourglass projections vanish in float, e.g. voxels), which
-                                      otherwise take a kernel without those zero terms; the two agree up to
-                                      the compiler's multiply-add fusion (a few ulps) */
+#define TLED_GENERAL_H8 (1u << 4)  /* keep the general H8 kernel for brick meshes (every element an
+                                      axis-aligned box: reference hourglass projections and off-diagonal
+                                      reference Jacobian entries zero in float, e.g. voxels), which otherwise
+                                      take a kernel without those zero terms that stores only the diagonal
+                                      of J0^-1; the two agree to ~1e-7 relative */
 #define TLED_STREAMED (1u << 5)    /* keep the streamed step (tile kernel + shared-node kernel per step) when
                                       the problem would fit the resident mode (every scenario in one CTA's
                                       shared memory) or the grid-resident one (a single problem's tiles in

@@ -377,7 +377,8 @@ class Solver:
 
     @property
     def brick(self) -> bool:
-        """True when the H8 brick instance (no reference hourglass projections) runs."""
+        """True when the H8 brick instance (axis-aligned boxes: no reference hourglass
+        projections, diagonal J0^-1) runs."""
         return bool(self._mode() & 2)
 
     # -- read-back ---------------------------------------------------------
