@@ -569,6 +569,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     probes = probe_lattice(prob, args.probes)
     s = tled.Solver.from_problem(prob, device=local, stream=stream, probes=probes)
+    brick = s.brick
     kernel_desc = ("resident (one CTA, K steps per launch)" if s.resident else "streamed (tile + shared-node kernels)") + \
         ("; H8 brick instance: every element an axis-aligned brick, reference hourglass projections exactly zero"
          if s.brick else "")
@@ -670,7 +671,7 @@ def run_gpu(args):
             "config": {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn,
                        "element": "H8" if prob.npe == 8 else "T4", "dt_s": dt,
                        "tiles": info["n_tiles"], "shared_nodes": info["n_shared"],
-                       "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (layout_bytes(prob, n_prony, s.brick) / 1e6),
+                       "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (layout_bytes(prob, n_prony, brick) / 1e6),
                        "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}",
                        "kernels": kernel_desc},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -678,7 +679,7 @@ def run_gpu(args):
                          "kernel": "tile_step_kernel + shared_step_kernel (one step)",
                          "algorithmic_bytes_per_step": alg,
                          "algorithmic_bytes_per_element_step": alg / prob.ne,
-                         "layout_bytes_per_step": layout_bytes(prob, n_prony, s.brick),
+                         "layout_bytes_per_step": layout_bytes(prob, n_prony, brick),
                          "kernel_ms_per_step": per_step_kernel_ms,
                          "tile_kernel_ms": k_tile / args.roofline_steps,
                          "shared_kernel_ms": k_sh / args.roofline_steps, "peak_source": src},

@@ -297,11 +297,15 @@ def test_stats_match_state():
 def test_energy_reduction_matches_oracle():
     """The FP64 stored and hourglass energies of tled_get_stats against the
     oracle's element energies on random mid-run states with strains of order
-    0.1-0.3 (H8 with hourglass energy, T4 with per-element fibres)."""
+    0.1-0.3 (jittered H8 with hourglass energy, a brick H8 cube -- its records
+    hold the diagonal of J0^-1 --, T4 with per-element fibres)."""
     tled = _tled()
-    for prob in (W.cube_h8(n=6, jitter=0.1, seed=8), W.cube_t4(n=5, seed=9)):
+    cases = ((W.cube_h8(n=6, jitter=0.1, seed=8), False), (W.cube_h8(n=6, seed=8), True),
+             (W.cube_t4(n=5, seed=9), False))
+    for prob, brick in cases:
         st = W.random_state(prob, seed=3, u_scale=2e-3)
         s = tled.Solver.from_problem(prob)
+        assert s.brick == brick
         s.set_state(st["u"], st["v"], st["T"], st["Omega"], st["visc"])
         r = s.stats()
         m = oracle.OracleModel(prob)
