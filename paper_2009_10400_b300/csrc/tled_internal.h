@@ -29,7 +29,8 @@ constexpr int pattern_u16(int npe) { return 2 * kTile * npe + kMaxLocal + 8; }
 // a fixed corner this permutes each aligned group of 8 elements (the element pass's stores
 // stay conflict-free), and a warp gathering one node per thread, entry by entry in corner
 // order, spreads its reads over more shared-memory banks (on 8x8x4 Morton blocks of bricks
-// about half the excess wavefronts of the plain [corner][element] layout).
+// about 30 % fewer excess wavefronts than the plain [corner][element] layout, by a model of
+// 128-bit loads served eight threads at a time that matches the profiler's counts).
 constexpr int slot_swz_e(int h) { return ((h >> 1 ^ h >> 2) & 1) | ((h ^ h >> 2) & 1) << 1 | (h & 1) << 2; }
 constexpr int slot_swz_c(int c) { return (c & 1) << 1 | ((c ^ c >> 1 ^ c >> 2) & 1) << 2; }
 constexpr int slot_pos(int e, int c) { return c * kTile + (e ^ slot_swz_e((e >> 3) & 7) ^ slot_swz_c(c)); }
