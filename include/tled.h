@@ -77,7 +77,7 @@ extern "C" {
                                       axis-aligned box: reference hourglass projections and off-diagonal
                                       reference Jacobian entries zero in float, e.g. voxels), which otherwise
                                       take a kernel without those zero terms that stores only the diagonal
-                                      of J0^-1; the two agree to ~1e-7 relative */
+                                      of J0^-1; the two agree within 1e-6 relative */
 #define TLED_STREAMED (1u << 5)    /* keep the streamed step (tile kernel + shared-node kernel per step) when
                                       the problem would fit the resident mode (every scenario in one CTA's
                                       shared memory) or the grid-resident one (a single problem's tiles in

@@ -156,7 +156,8 @@ struct StepArgs {
     float lnA, Ea_R, T0_K;                // T0 + 273.15
     float khg, khgT;                      // kappa_hg, kappa_hgT
     int ani;                              // anisotropic thermal physics (the ratios below differ from 1)
-    int brick;                            // every element an H8 whose reference hourglass projections vanish
+    int brick;                            // every element an axis-aligned H8 box (no reference hourglass
+                                          //   projections, diagonal J0^-1; records hold its diagonal)
     int wide;                             // T4 problem with more tiles than 3 CTAs per SM: the 4-CTA instance
     float ani_alpha, ani_k;               // fibre / transverse expansion and conductivity
     double ramp_time;
