@@ -920,15 +920,30 @@ __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, cons
     __shared__ ScenStep S;
     const int64_t n_sh = A.n_active[1];  // shared nodes of unfinished scenarios form a prefix
     const bool multi = A.n_scn > 1;      // a batch: nodes carry their scenario
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int cur = -1;
-    for (int64_t c0 = (int64_t)blockIdx.x * blockDim.x; c0 < n_sh; c0 += (int64_t)gridDim.x * blockDim.x) {
+    // the node's partial-sum range, loaded one chunk ahead so that the partial sums
+    // themselves can be requested as soon as a chunk starts
+    int64_t c0 = (int64_t)blockIdx.x * blockDim.x;
+    int rn0 = 0, rn1 = 0;
+    if (c0 + threadIdx.x < n_sh) {
+        rn0 = __ldg(A.sh_rowptr + c0 + threadIdx.x);
+        rn1 = __ldg(A.sh_rowptr + c0 + threadIdx.x + 1);
+    }
+    for (; c0 < n_sh; c0 += stride) {
         const int64_t s = c0 + threadIdx.x;
         const bool live = s < n_sh;
+        const int r0 = rn0, r1 = rn1;
+        rn0 = 0;
+        rn1 = 0;
+        if (s + stride < n_sh) {
+            rn0 = __ldg(A.sh_rowptr + s + stride);
+            rn1 = __ldg(A.sh_rowptr + s + stride + 1);
+        }
         // every load of the node issued up front: its state, then its first four partial
         // sums (a node of a tile-boundary face has 2, of an edge 4); more follow in order
         const int64_t g = A.n_interior + (live ? s : c0);
         const float4 xu = A.xu[g], X = __ldg(&A.X0[g]), lo = A.lo[g], vo = A.vel[g], nc = __ldg(&A.nodec[g]);
-        const int r0 = live ? __ldg(A.sh_rowptr + s) : 0, r1 = live ? __ldg(A.sh_rowptr + s + 1) : 0;
         const int scn = !multi ? 0 : live ? __ldg(A.shared_scn + s) : -1;
         float4 c[4];
 #pragma unroll
