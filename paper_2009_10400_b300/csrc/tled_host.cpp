@@ -225,11 +225,13 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         }
     double ext = std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
     std::vector<uint64_t> key(ne);
+    std::vector<double> cen(3 * (size_t)ne);  // element centroids
     for (int64_t e = 0; e < ne; e++) {
         double c[3] = {0, 0, 0};
         const int ke = nc(e);
         for (int a = 0; a < ke; a++)
             for (int j = 0; j < 3; j++) c[j] += X[3 * (int64_t)conn[e * npe + a] + j];
+        for (int j = 0; j < 3; j++) cen[3 * e + j] = c[j] / ke;
         uint64_t k = 0;
         for (int j = 0; j < 3; j++) {
             double q = (c[j] / ke - lo[j]) / ext;
@@ -278,6 +280,18 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
     }
     p.n_tiles = (int)tile_begin.size();
     tile_begin.push_back((int32_t)ne);
+    // inside a tile, elements in (z, y, x) order of their centroids and (below) nodes in
+    // (z, y, x) order of their coordinates: in a block of bricks, eight consecutive
+    // elements are then a row, and the corner nodes they read, like the element slots a
+    // row of nodes reads, sit at consecutive local positions -- distinct shared-memory
+    // banks for the eight threads a 16-byte load serves at a time
+    auto zyx_less = [](const double *a, const double *b) {
+        return a[2] != b[2] ? a[2] < b[2] : a[1] != b[1] ? a[1] < b[1] : a[0] < b[0];
+    };
+    for (int tt = 0; tt < p.n_tiles; tt++)
+        std::stable_sort(p.elem_old.begin() + tile_begin[tt], p.elem_old.begin() + tile_begin[tt + 1],
+                         [&](int32_t a, int32_t b) { return zyx_less(&cen[3 * (size_t)a], &cen[3 * (size_t)b]); });
+    auto node_less = [&](int32_t a, int32_t b) { return zyx_less(X + 3 * (int64_t)a, X + 3 * (int64_t)b); };
 
     // --- how many tiles touch each node
     std::vector<int32_t> ntouch(nn, 0), last(nn, -1);
@@ -308,16 +322,23 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
         return TLED_E_MESH;
     }
     int32_t next = 0;
+    std::vector<int32_t> own;
     for (int tt = 0; tt < p.n_tiles; tt++) {
         int32_t *ti = &p.tile_info[(size_t)tt * kTileInfo];
         ti[0] = (int32_t)tile_pad[tt];
         ti[1] = tile_begin[tt + 1] - tile_begin[tt];
         ti[2] = next;
+        own.clear();
         for (int64_t i = tile_begin[tt]; i < tile_begin[tt + 1]; i++) {
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
             for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++)
-                if (ntouch[cn[a]] == 1 && p.node_new[cn[a]] < 0) p.node_new[cn[a]] = next++;
+                if (ntouch[cn[a]] == 1 && p.node_new[cn[a]] < 0) {
+                    p.node_new[cn[a]] = 0;  // seen
+                    own.push_back(cn[a]);
+                }
         }
+        std::stable_sort(own.begin(), own.end(), node_less);
+        for (int32_t n : own) p.node_new[n] = next++;
         ti[3] = next - ti[2];
     }
     p.n_interior = next;
@@ -359,8 +380,10 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
                 }
             }
         }
-        // shared nodes keep their first-appearance order in the tile, so that tiles of
-        // the same shape and position class get identical local structures
+        // shared nodes in (z, y, x) order inside the tile (tiles of the same shape and
+        // position class get identical local structures)
+        std::stable_sort(shared.begin(), shared.end(),
+                         [&](int32_t a, int32_t b) { return node_less(p.node_old[a], p.node_old[b]); });
         const int nl = n_int + (int)shared.size();
         if (nl > cap) {
             err = "internal: tile exceeds the local node limit";
