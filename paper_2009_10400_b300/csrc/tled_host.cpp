@@ -333,7 +333,7 @@ int build_plan(int npe, int64_t nn, const double *X, int64_t ne, const int32_t *
             const int32_t *cn = conn + (int64_t)p.elem_old[i] * npe;
             for (int a = 0, ka = nc(p.elem_old[i]); a < ka; a++)
                 if (ntouch[cn[a]] == 1 && p.node_new[cn[a]] < 0) {
-                    p.node_new[cn[a]] = 0;  // seen
+                    p.node_new[cn[a]] = 0;  // collected; numbered below, in coordinate order
                     own.push_back(cn[a]);
                 }
         }
