@@ -568,11 +568,12 @@ def run_gpu(args):
     prob = make_problem(args.workload)
     stream = torch.cuda.current_stream()
     probes = probe_lattice(prob, args.probes)
-    s = tled.Solver.from_problem(prob, device=local, stream=stream, probes=probes)
+    flags = tled.default_flags(prob) | (tled.GENERAL_H8 if args.general_h8 else 0)
+    s = tled.Solver.from_problem(prob, device=local, stream=stream, probes=probes, flags=flags)
     brick = s.brick
     kernel_desc = ("resident (one CTA, K steps per launch)" if s.resident else "streamed (tile + shared-node kernels)") + \
         ("; H8 brick instance: every element an axis-aligned brick, reference hourglass projections exactly zero"
-         if s.brick else "")
+         if s.brick else "; general H8 instance (TLED_GENERAL_H8)" if args.general_h8 else "")
     info = s.plan_info()
     dt = s.get_dt()[0]
     n_prony = len(prob.prony_g)
@@ -607,7 +608,7 @@ def run_gpu(args):
     alg = algorithmic_bytes(prob, n_prony)
     hbm, src = peaks()
     achieved = alg / (per_step_kernel_ms * 1e-3) / 1e9
-    traffic = kernel_traffic(prob.name)
+    traffic = None if args.general_h8 else kernel_traffic(prob.name)  # the capture is of the brick instance
 
     # ---- end to end through the C ABI with host buffers, every step: the step's
     #      source settings from pinned host memory, one step, and the step's result
@@ -719,6 +720,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-planning", action="store_true")
+    ap.add_argument("--general-h8", action="store_true", help="keep the general H8 kernel on brick meshes")
     ap.add_argument("--plan-scenarios", type=int, default=256)
     ap.add_argument("--plan-subset", type=int, default=32)
     ap.add_argument("--sur-grid", type=int, default=16)

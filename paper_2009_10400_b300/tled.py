@@ -20,6 +20,13 @@ OK, E_ARG, E_MESH, E_STATE, E_CUDA, E_UNSTABLE, E_INVERTED, E_TIMEOUT, E_NOMEM, 
 T4, H8 = 4, 8
 HOST, DEVICE = 0, 1
 EXPANSION, TEMP_DEP, COMPENSATED, CEM43, GENERAL_H8, STREAMED = 1, 2, 4, 8, 16, 32
+
+
+def default_flags(prob):
+    """Step flags a workloads.Problem asks for: compensated accumulation, and
+    thermal expansion, temperature-dependent c and k, CEM43 as it sets them."""
+    return (COMPENSATED | (EXPANSION if prob.expansion else 0) | (TEMP_DEP if prob.temp_dep else 0) |
+            (CEM43 if getattr(prob, "cem43", False) else 0))
 SRC_GAUSSIAN, SRC_SPHERE = 0, 1
 FIX_X, FIX_Y, FIX_Z, FIX_T = 1, 2, 4, 8
 
@@ -325,8 +332,7 @@ class Solver:
         s.set_bcs(prob.mask, prob.ubar, prob.ramp_time)
         s.set_heat_sources(prob.sources)
         if flags is None:
-            flags = (COMPENSATED | (EXPANSION if prob.expansion else 0) | (TEMP_DEP if prob.temp_dep else 0) |
-                     (CEM43 if getattr(prob, "cem43", False) else 0))
+            flags = default_flags(prob)
         s.set_params(dt=float(prob.dt if dt is None else dt), dt_safety=prob.dt_safety, gamma=prob.gamma,
                      mass_scale=prob.mass_scale, kappa_hg=prob.kappa_hg, kappa_hgT=prob.kappa_hgT, flags=flags,
                      tile_elems=tile_elems)
