@@ -112,59 +112,99 @@ def kernel_traffic(workload):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """SM clock and throttle-reason sampling during the timed region, in
+    process through NVML (the driver's libnvidia-ml, read-only queries) every
+    ~1 ms from a background thread, so that even a few-millisecond region gets
+    samples and no nvidia-smi process competes with the timed work.  Use
+    mark_start()/mark_end() around the region; summary() reports the samples
+    inside it (or the nearest ones, stated, if the region was shorter than one
+    sampling interval)."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    # NVML clock-event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, index):
+    def __init__(self, index, interval=1e-3):
         self.index = index
-        self.proc = None
-        self.lines = []
+        self.interval = interval
+        self.samples = []  # (host time, sm MHz, reasons bitmask)
+        self.max_mhz = None
+        self.t_start = self.t_end = None
+        self._stop = threading.Event()
+        self._nvml = None
+
+    def _open(self):
+        import ctypes as C
+
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                L = C.CDLL(name)
+                break
+            except OSError:
+                L = None
+        if L is None or L.nvmlInit_v2() != 0:
+            return None
+        h = C.c_void_p()
+        if L.nvmlDeviceGetHandleByIndex_v2(C.c_uint(self.index), C.byref(h)) != 0:
+            return None
+        mx = C.c_uint()
+        if L.nvmlDeviceGetMaxClockInfo(h, C.c_int(1), C.byref(mx)) == 0:  # NVML_CLOCK_SM = 1
+            self.max_mhz = float(mx.value)
+        return L, h
+
+    def _run(self):
+        import ctypes as C
+
+        L, h = self._nvml
+        clk, rs = C.c_uint(), C.c_ulonglong()
+        get_reasons = getattr(L, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            L.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            if L.nvmlDeviceGetClockInfo(h, C.c_int(1), C.byref(clk)) == 0 and get_reasons(h, C.byref(rs)) == 0:
+                self.samples.append((t, float(clk.value), int(rs.value)))
+            self._stop.wait(self.interval)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            self._nvml = self._open()
         except Exception:
-            self.proc = None
+            self._nvml = None
+        if self._nvml:
+            self._thread = threading.Thread(target=self._run, daemon=True)
+            self._thread.start()
+            time.sleep(0.02)  # a few samples before the region
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+    def mark_start(self):
+        self.t_start = time.perf_counter()
+
+    def mark_end(self):
+        self.t_end = time.perf_counter()
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except Exception:
-                self.proc.kill()
+        if self._nvml:
+            time.sleep(0.005)
+            self._stop.set()
+            self._thread.join(timeout=2)
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            p = [x.strip() for x in ln.split(",")]
-            if len(p) < 8:
-                continue
-            try:
-                sm.append(float(p[0]))
-                mx.append(float(p[1]))
-            except ValueError:
-                continue
-            for n, v in zip(names, p[4:8]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0,
+                    "source": "nvml"}
+        t0 = self.t_start if self.t_start is not None else self.samples[0][0]
+        t1 = self.t_end if self.t_end is not None else self.samples[-1][0]
+        inside = [x for x in self.samples if t0 <= x[0] <= t1]
+        where = "inside the timed region"
+        if not inside:  # region shorter than a sampling interval: the samples around it
+            inside = sorted(self.samples, key=lambda x: min(abs(x[0] - t0), abs(x[0] - t1)))[:2]
+            where = "nearest to the timed region (shorter than one sampling interval)"
+        mask = 0
+        for x in inside:
+            mask |= x[2]
+        reasons = sorted(n for b, n in self.REASONS.items() if mask & b)
+        return {"sm_mhz": float(np.median([x[1] for x in inside])), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(inside), "source": "nvml", "where": where}
 
 
 def dist_setup():
@@ -192,50 +232,110 @@ def barrier(ws):
         dist.barrier()
 
 
-def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1, warmup_seconds=10.0):
+def cpu_model():
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1, warmup_seconds=10.0, parallel=False):
     """Time the FP64 oracle as it stands on a bounded sample of the workload:
     up to `warmup` untimed steps (at least one, stopping after about
     `warmup_seconds`), then as many full steps as fit in about `seconds` (at
-    least 1, at most max_steps)."""
+    least 1, at most max_steps).  parallel: the oracle's OpenMP step on every
+    host core (elements in parallel, fixed-order node gather; bitwise the
+    single-threaded result)."""
     import oracle
 
     t0 = time.perf_counter()
     m = oracle.OracleModel(prob)
     setup = time.perf_counter() - t0
     s = m.init_state()
+    step = m.step_parallel if parallel else m.step
+    cores = oracle.threads() if parallel else 1
     t0 = time.perf_counter()
     n_warm = 0
     while n_warm < max(1, warmup):
-        m.step(s, 1)
+        step(s, 1)
         n_warm += 1
         if time.perf_counter() - t0 > warmup_seconds:
             break
     one = (time.perf_counter() - t0) / n_warm
     steps = int(max(1, min(max_steps, seconds // max(one, 1e-9))))
     t0 = time.perf_counter()
-    m.step(s, steps)
+    step(s, steps)
     el = time.perf_counter() - t0
-    return {"value": prob.ne * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+    how = f"OpenMP on {cores} host cores, fixed-order node gather" if parallel else "single-threaded"
+    return {"value": prob.ne * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{prob.name}: {steps} full steps after {n_warm} warm-up step(s) ({el:.1f} s, "
-                      f"set-up {setup:.1f} s), FP64 C oracle, single-threaded", "steps": steps, "warmup": n_warm}
+                      f"set-up {setup:.1f} s), FP64 C oracle, {how}", "steps": steps, "warmup": n_warm,
+            "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+
+
+def workload_config(prob):
+    """The `config` object of a bench line: what the workload is (the same for
+    both arms)."""
+    return {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn,
+            "element": "H8" if prob.npe == 8 else "T4",
+            "floor_bytes_per_step": algorithmic_bytes(prob, len(prob.prony_g)),
+            "l2": "inputs larger than L2 (no flush needed)" if algorithmic_bytes(prob, len(prob.prony_g)) > 126e6
+            else "L2-resident working set"}
 
 
 def run_reference(args):
-    """The reference arm: the FP64 oracle on the host cores, same workload,
-    metric and unit; each step a full oracle step, as many as fit in about
-    --ref-seconds (at most --steps)."""
+    """The reference arm: the FP64 oracle on all host cores (OpenMP, bitwise
+    the single-threaded oracle), same workload, metric and unit.  Exactly
+    --warmup untimed and --steps timed steps; each step is one oracle step of
+    the whole workload, or -- when W + K full steps would not fit in about
+    --ref-seconds -- of a smaller block of the same generator (stated)."""
     ws, rank, _ = dist_setup()
     if rank != 0:
         return 0
+    import oracle
+
     prob = make_problem(args.workload if args.workload != "surrogate" else "block_h8")
-    r = cpu_oracle_sample(prob, args.steps, seconds=args.ref_seconds, warmup=args.warmup)
+    sample = prob
+    t0 = time.perf_counter()
+    m = oracle.OracleModel(sample)
+    s = m.init_state()
+    m.step_parallel(s, 1)
+    one = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    m.step_parallel(s, 1)
+    one = time.perf_counter() - t0
+    n_total = args.warmup + args.steps
+    if prob.name.startswith("block_h8") and n_total * one > args.ref_seconds:
+        # a smaller block of the same generator: element count scaled to fit the budget
+        from paper_2009_10400_b300 import workloads as W
+
+        n_side = round(prob.ne ** (1 / 3))
+        k = max(8, int(n_side * (args.ref_seconds / (n_total * one)) ** (1 / 3)))
+        sample = W.block_h8(n=k)
+        m = oracle.OracleModel(sample)
+        s = m.init_state()
+    m.step_parallel(s, args.warmup)
+    t0 = time.perf_counter()
+    m.step_parallel(s, args.steps)
+    el = time.perf_counter() - t0
+    value = sample.ne * args.steps / el
+    cores = oracle.threads()
+    what = "every step one step of the whole workload" if sample is prob else \
+        f"every step one step of the same generator's {sample.name} ({sample.ne} elements; {prob.ne} would not fit)"
+    cpu = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{what}: {args.steps} timed steps after {args.warmup} warm-up steps ({el:.1f} s), FP64 C "
+                     f"oracle, OpenMP on {cores} host cores with a fixed-order node gather (bitwise the "
+                     f"single-threaded oracle)", "cpu_model": cpu_model(), "nproc": os.cpu_count()}
     # run on the host cores of the launch's box (n_gpus = the launch's world size, for bookkeeping)
-    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": r["steps"],
-            "warmup": r["warmup"], "ms_per_step": 1e3 * prob.ne / r["value"], "higher_is_better": True,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference", "config": {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn},
-            "cpu_baseline": r, "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
-                                       "d2h_bytes_per_step": 0}}
+            "impl": "reference", "config": workload_config(prob),
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -277,11 +377,11 @@ def planning_bench(args, device, stream):
     results are compared with the batch's to show both are the same solve."""
     import torch
 
-    from paper_2009_10400_b300 import surrogate, tled
+    from paper_2009_10400_b300 import tled
     from paper_2009_10400_b300 import workloads as W
 
     t_setup = time.perf_counter()
-    scen = [surrogate.mass_scaled(p) for p in W.planning_scenarios(args.plan_scenarios)]
+    scen = W.planning_scenarios(args.plan_scenarios)  # R17 mass scaling chosen by the library
     b = tled.Batch(device=device, stream=stream)
     for p in scen:
         b.add(p, p.n_steps)
@@ -578,19 +678,20 @@ def run_gpu(args):
     dt = s.get_dt()[0]
     n_prony = len(prob.prony_g)
 
-    # ---- warm-up (graphs captured here)
-    s.step(args.warmup)
-    s.sync()
-
-    # ---- device-timed region: K steps, inputs resident in HBM (larger than L2)
+    # ---- warm-up (graphs captured here) and the device-timed region: K steps,
+    #      inputs resident in HBM (larger than L2); clocks sampled throughout
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(ws)
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        s.step(args.warmup)
+        s.sync()
+        barrier(ws)
+        torch.cuda.synchronize()
+        clk.mark_start()
         ev0.record(stream)
         s.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     barrier(ws)
     s.sync()
     ms = ev0.elapsed_time(ev1)
@@ -616,24 +717,15 @@ def run_gpu(args):
     #      The read-back is pipelined: step i's probe values are copied into one of two
     #      pinned buffers behind step i + 1's launch, and the host waits for (and reads)
     #      step i's copy before it enqueues step i + 2's into the same buffer.
-    n_e2e = min(args.steps, args.e2e_steps)
+    n_e2e = args.e2e_steps
     src_host = torch.tensor(np.array(prob.sources), dtype=torch.float64).pin_memory()
     P_dev = torch.empty((2, len(probes)), dtype=torch.float64, device=f"cuda:{local}")
     P_host = [torch.empty((2, len(probes)), dtype=torch.float64).pin_memory() for _ in range(2)]
     ev = [torch.cuda.Event() for _ in range(2)]
-    t_probe = 0.0
-    with torch.cuda.stream(stream):  # untimed warm-up of the same loop (single-step graph, copies)
-        for i in range(max(args.warmup, 3)):
-            s.set_heat_sources(src_host.numpy())
-            s.step(1)
-            s.probes(out=P_dev)
-            P_host[0].copy_(P_dev, non_blocking=True)
-    barrier(ws)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for i in range(n_e2e + 1):
-            if i < n_e2e:
+    def e2e_loop(n):
+        t_probe = 0.0
+        for i in range(n + 1):
+            if i < n:
                 s.set_heat_sources(src_host.numpy())  # H2D: this step's source settings
                 s.step(1)
                 s.probes(out=P_dev)                   # probe temperatures and damage, on the device
@@ -642,6 +734,15 @@ def run_gpu(args):
             if i >= 1:
                 ev[(i - 1) % 2].synchronize()         # step i - 1's result is on the host
                 t_probe += float(P_host[(i - 1) % 2][0, 0])
+        return t_probe
+
+    with torch.cuda.stream(stream):  # untimed warm-up of the same loop (single-step graph, copies, events)
+        e2e_loop(max(args.warmup, 3))
+    barrier(ws)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        e2e_loop(n_e2e)
     torch.cuda.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, ws, f"cuda:{local}")
     e2e_value = ws * prob.ne * n_e2e / e2e_s
@@ -661,20 +762,19 @@ def run_gpu(args):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
-            from paper_2009_10400_b300 import workloads as W
-
-            cpu = cpu_oracle_sample(prob, args.cpu_steps, seconds=args.cpu_seconds)
+            # the oracle on every host core (the headline baseline) and on one core
+            cpu = cpu_oracle_sample(prob, args.cpu_steps, seconds=args.cpu_seconds, parallel=True)
+            cpu["single_core"] = cpu_oracle_sample(prob, args.cpu_steps, seconds=args.cpu_seconds)
         clocks = clk.summary()
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn,
-                       "element": "H8" if prob.npe == 8 else "T4", "dt_s": dt,
-                       "tiles": info["n_tiles"], "shared_nodes": info["n_shared"],
-                       "l2": "inputs larger than L2 (state + element data ~%.0f MB per step)" % (layout_bytes(prob, n_prony, brick) / 1e6),
-                       "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}",
-                       "kernels": kernel_desc},
+            "config": workload_config(prob),
+            "plan": {"dt_s": dt, "tiles": info["n_tiles"], "shared_nodes": info["n_shared"],
+                     "layout_bytes_per_step": layout_bytes(prob, n_prony, brick),
+                     "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}",
+                     "kernels": kernel_desc},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "tile_step_kernel + shared_step_kernel (one step)",
@@ -716,7 +816,7 @@ def main():
     ap.add_argument("--liver-steps", type=int, default=0, help="liver_f2: stop after this many steps (0: 25 s)")
     ap.add_argument("--probes", type=int, default=16)
     ap.add_argument("--cpu-steps", type=int, default=8)
-    ap.add_argument("--ref-seconds", type=float, default=30.0)
+    ap.add_argument("--ref-seconds", type=float, default=90.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-planning", action="store_true")

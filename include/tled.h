@@ -144,7 +144,12 @@ typedef struct tled_params {
     double dt;          /* time step, s; 0 = dt_safety * stable step */
     double dt_safety;   /* fraction of the stable step used when dt = 0 (default 0.8) */
     double gamma;       /* mass-proportional damping D = gamma M, 1/s (Eq. 21) */
-    double mass_scale;  /* mechanical mass multiplier >= 1 (1 = none) */
+    double mass_scale;  /* mechanical mass multiplier >= 1 (1 = none); < 0 = automatic (needs dt > 0):
+                           s_m = max(1, (dt / (dt_safety dt_mech))^2) with dt_mech the CFL bound of the
+                           unscaled mesh, which makes dt the safe mechanical step (mass scaling for
+                           long heating runs, where inertia barely affects temperature); init and
+                           tled_stable_dt then fail with E_ARG if dt exceeds dt_safety x the thermal
+                           bound */
     double kappa_hg;    /* H8 hourglass coefficient (default 0.1) */
     double kappa_hgT;   /* H8 thermal hourglass coefficient (default 0.1) */
     uint32_t flags;     /* TLED_EXPANSION | TLED_TEMP_DEP | TLED_COMPENSATED */
@@ -230,6 +235,12 @@ int tled_get_dt(tled_ctx *ctx, double *dt, double *dt_mech, double *dt_thermal);
  * mechanical CFL bound (with the set mass scale) and the thermal Gershgorin
  * bound, before the safety factor. */
 int tled_stable_dt(tled_ctx *ctx, double *dt_mech, double *dt_thermal);
+
+/* Mechanical mass multiplier in use for scenario `index` (0 for a single
+ * problem): tled_params.mass_scale, or the automatic choice described there.
+ * No GPU needed.  Errors: E_ARG (index, or dt above the thermal bound with the
+ * automatic choice), E_STATE (no mesh or material). */
+int tled_get_mass_scale(tled_ctx *ctx, int32_t index, double *mass_scale);
 
 /* Enqueue n explicit coupled steps (element pass, deterministic node gather,
  * nodal updates of u, T and damage).  Asynchronous: device faults such as

@@ -54,7 +54,8 @@ class _State(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with the system C compiler (plain IEEE FP64, no fast-math)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", _LIB_PATH, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", _LIB_PATH, _SRC,
+                               "-lm"])
     return _LIB_PATH
 
 
@@ -78,6 +79,11 @@ def lib():
                                      _dp, _dp, _dp]
         L.ora_stable_dt.argtypes = [C.POINTER(_Model), C.c_double, _dp, _dp]
         L.ora_stable_dt.restype = C.c_double
+        _i64p = C.POINTER(C.c_int64)
+        L.ora_probe.argtypes = [C.POINTER(_Model), C.POINTER(_State), _dp, C.c_int64, _dp, _dp]
+        L.ora_incidence.argtypes = [C.POINTER(_Model), _i64p, _i64p]
+        L.ora_step_parallel.argtypes = [C.POINTER(_Model), C.POINTER(_State), _i64p, _i64p, _dp, _dp, _dp]
+        L.ora_threads.restype = C.c_int
         _lib = L
     return _lib
 
@@ -147,6 +153,9 @@ class OracleModel:
         for f in ("c_heat", "beta_c", "beta_k", "T_ref", "wbcb", "Qm", "T0", "Ta", "lnA", "Ea", "gamma",
                   "mass_scale", "kappa_hg", "kappa_hgT", "ramp_time", "aniso_alpha", "aniso_k"):
             setattr(m, f, float(getattr(prob, f)))
+        if prob.mass_scale < 0:  # R17: scaled so that the fixed dt is the safe mechanical step
+            m.mass_scale = mass_scale_for(prob, prob.dt, prob.dt_safety)
+        self.mass_scale = m.mass_scale
         m.expansion = int(bool(prob.expansion))
         m.temp_dep = int(bool(prob.temp_dep))
         m.n_src = self._src.shape[0]
@@ -195,6 +204,39 @@ class OracleModel:
             s.t, s.step = cs.t, cs.step
         return s
 
+    def step_parallel(self, s: OracleState, n=1):
+        """The same steps on all host cores (OpenMP threads, OMP_NUM_THREADS):
+        bitwise the result of step()."""
+        L = lib()
+        if not hasattr(self, "_inc_off"):
+            npe = self.prob.npe
+            self._inc_off = np.zeros(self.prob.nn + 1, np.int64)
+            self._inc_slot = np.zeros(self.prob.ne * npe, np.int64)
+            self._elem_out = np.zeros((self.prob.ne, npe, 4))
+            ip = C.POINTER(C.c_int64)
+            if L.ora_incidence(C.byref(self._m), self._inc_off.ctypes.data_as(ip), self._inc_slot.ctypes.data_as(ip)):
+                raise MemoryError("oracle: allocation failed")
+        ip = C.POINTER(C.c_int64)
+        for _ in range(n):
+            cs = s._c()
+            L.ora_step_parallel(C.byref(self._m), C.byref(cs), self._inc_off.ctypes.data_as(ip),
+                                self._inc_slot.ctypes.data_as(ip), _p(self._elem_out), _p(self._f), _p(self._fT))
+            s.t, s.step = cs.t, cs.step
+        return s
+
+    def probe(self, s: OracleState, xyz):
+        """Temperature (C) and damage fraction at points xyz [k][3] (reference
+        coordinates), interpolated with the shape functions of the element
+        that contains each point."""
+        xyz = np.ascontiguousarray(xyz, float).reshape(-1, 3)
+        k = xyz.shape[0]
+        T, d = np.zeros(k), np.zeros(k)
+        cs = s._c()
+        rc = lib().ora_probe(C.byref(self._m), C.byref(cs), _p(xyz), k, _p(T), _p(d))
+        if rc:
+            raise ValueError(f"oracle: probe {-rc - 1} lies outside the mesh")
+        return T, d
+
     def forces(self):
         """Assembled nodal forces and thermal loads from the last step."""
         return self._f.copy(), self._fT.copy()
@@ -230,6 +272,24 @@ class OracleModel:
         if rc:
             raise MemoryError("oracle: allocation failed")
         return ou, oT, oO
+
+
+def threads() -> int:
+    """Threads the oracle's parallel step uses on this host."""
+    return int(lib().ora_threads())
+
+
+def mass_scale_for(prob, dt, safety=0.8):
+    """R17 mass scaling: the mechanical mass multiplier s_m >= 1 that makes dt
+    the safe mechanical step, s_m = (dt / (safety dt_mech))^2, with dt_mech the
+    oracle's own CFL bound of the unscaled mesh (R16)."""
+    import copy
+
+    q = copy.copy(prob)
+    q.mass_scale = 1.0
+    m = OracleModel(q, dt=dt)
+    m.stable_dt(safety)
+    return max(1.0, (dt / (safety * m.dt_mech)) ** 2)
 
 
 def damage_fraction(Omega):

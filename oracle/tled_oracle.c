@@ -37,6 +37,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define R_GAS 8.314
 #define KELVIN 273.15
@@ -646,4 +649,186 @@ double ora_stable_dt(const ora_model *m, double safety, double *dt_mech, double 
     if (dt_mech) *dt_mech = dtm;
     if (dt_th) *dt_th = dtt;
     return safety * fmin(dtm, dtt);
+}
+
+/* ------------------------------------------------------------------ */
+/* point probes: temperature and damage fraction at arbitrary points   */
+/* ------------------------------------------------------------------ */
+/* Shape functions N_a at natural coordinates xi: T4 barycentric (N0 = 1 - xi - eta
+ * - zeta, N1 = xi, N2 = eta, N3 = zeta), H8 trilinear (1/8) prod_j (1 + s_aj xi_j)
+ * -- the interpolation behind Eqs. (18)-(19). */
+static void shape_values(int npe, const double xi[3], double N[8]) {
+    if (npe == 4) {
+        N[0] = 1.0 - xi[0] - xi[1] - xi[2];
+        N[1] = xi[0];
+        N[2] = xi[1];
+        N[3] = xi[2];
+        return;
+    }
+    for (int a = 0; a < 8; a++)
+        N[a] = (1.0 + H8_NAT[a][0] * xi[0]) * (1.0 + H8_NAT[a][1] * xi[1]) * (1.0 + H8_NAT[a][2] * xi[2]) / 8.0;
+}
+
+/* Natural coordinates of point x in element e, if it lies in the element.
+ * T4: the map is affine, solved once.  H8: Newton iteration on the trilinear
+ * isoparametric map x(xi) = sum_a N_a(xi) X_a from the centroid.  Returns 1 if
+ * the point is inside (tolerance 1e-9 in natural coordinates). */
+static int point_in_element(const ora_model *m, int64_t e, const double x[3], double xi[3]) {
+    const int npe = m->npe;
+    const int32_t *cn = m->conn + e * npe;
+    const double *P[8];
+    for (int a = 0; a < npe; a++) P[a] = m->X + 3 * (int64_t)cn[a];
+    /* quick reject: outside the element's bounding box (with a margin) */
+    for (int j = 0; j < 3; j++) {
+        double lo = P[0][j], hi = P[0][j];
+        for (int a = 1; a < npe; a++) {
+            lo = fmin(lo, P[a][j]);
+            hi = fmax(hi, P[a][j]);
+        }
+        double pad = 1e-9 * (hi - lo);
+        if (x[j] < lo - pad || x[j] > hi + pad) return 0;
+    }
+    if (npe == 4) {
+        double J[3][3], Ji[3][3];
+        for (int i = 0; i < 3; i++)
+            for (int k = 0; k < 3; k++) J[i][k] = P[k + 1][i] - P[0][i];
+        if (m_det(J) == 0.0) return 0;
+        m_inv(J, Ji);
+        for (int k = 0; k < 3; k++) {
+            xi[k] = 0;
+            for (int i = 0; i < 3; i++) xi[k] += Ji[k][i] * (x[i] - P[0][i]);
+        }
+        const double tol = 1e-9;
+        return xi[0] >= -tol && xi[1] >= -tol && xi[2] >= -tol && xi[0] + xi[1] + xi[2] <= 1.0 + tol;
+    }
+    xi[0] = xi[1] = xi[2] = 0.0;
+    for (int it = 0; it < 60; it++) {
+        double N[8], r[3], J[3][3], Ji[3][3];
+        shape_values(8, xi, N);
+        m_zero(J);
+        for (int i = 0; i < 3; i++) r[i] = -x[i];
+        for (int a = 0; a < 8; a++) {
+            double dN[3];
+            for (int k = 0; k < 3; k++) {
+                dN[k] = H8_NAT[a][k] / 8.0;
+                for (int l = 0; l < 3; l++)
+                    if (l != k) dN[k] *= 1.0 + H8_NAT[a][l] * xi[l];
+            }
+            for (int i = 0; i < 3; i++) {
+                r[i] += N[a] * P[a][i];
+                for (int k = 0; k < 3; k++) J[i][k] += P[a][i] * dN[k];
+            }
+        }
+        if (!(m_det(J) > 0)) return 0;
+        m_inv(J, Ji);
+        double step = 0;
+        for (int k = 0; k < 3; k++) {
+            double d = 0;
+            for (int i = 0; i < 3; i++) d += Ji[k][i] * r[i];
+            xi[k] -= d;
+            step += fabs(d);
+        }
+        if (fabs(xi[0]) > 4 || fabs(xi[1]) > 4 || fabs(xi[2]) > 4) return 0;
+        if (step < 1e-15) break;
+    }
+    const double tol = 1e-9;
+    return fabs(xi[0]) <= 1 + tol && fabs(xi[1]) <= 1 + tol && fabs(xi[2]) <= 1 + tol;
+}
+
+int ora_probe(const ora_model *m, const ora_state *s, const double *xyz, int64_t k, double *T_out,
+              double *d_out) {
+    const int npe = m->npe;
+    for (int64_t q = 0; q < k; q++) {
+        int64_t found = -1;
+        double xi[3];
+        for (int64_t e = 0; e < m->ne && found < 0; e++)
+            if (point_in_element(m, e, xyz + 3 * q, xi)) found = e;
+        if (found < 0) return -(int)(1 + q);
+        double N[8];
+        shape_values(npe, xi, N);
+        const int32_t *cn = m->conn + found * npe;
+        double T = 0, d = 0;
+        for (int a = 0; a < npe; a++) {
+            T += N[a] * s->T[cn[a]];
+            d += N[a] * (1.0 - exp(-s->Omega[cn[a]])); /* nodal damage fraction, interpolated */
+        }
+        T_out[q] = T;
+        d_out[q] = d;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* the same step on all host cores                                     */
+/* ------------------------------------------------------------------ */
+int ora_incidence(const ora_model *m, int64_t *offsets, int64_t *slots) {
+    const int npe = m->npe;
+    memset(offsets, 0, (m->nn + 1) * sizeof(int64_t));
+    for (int64_t e = 0; e < m->ne; e++)
+        for (int a = 0; a < npe; a++) offsets[m->conn[e * npe + a] + 1]++;
+    for (int64_t i = 0; i < m->nn; i++) offsets[i + 1] += offsets[i];
+    int64_t *fill = (int64_t *)malloc(m->nn * sizeof(int64_t));
+    if (!fill) return -1;
+    memcpy(fill, offsets, m->nn * sizeof(int64_t));
+    for (int64_t e = 0; e < m->ne; e++) /* ascending element id within every node's list */
+        for (int a = 0; a < npe; a++) slots[fill[m->conn[e * npe + a]]++] = e * npe + a;
+    free(fill);
+    return 0;
+}
+
+int ora_step_parallel(const ora_model *m, ora_state *s, const int64_t *offsets, const int64_t *slots,
+                      double *elem_out, double *f, double *fT) {
+    const int npe = m->npe;
+    const int64_t ne = m->ne, nn = m->nn;
+    /* element loop: every element independent; results kept per (element, corner) */
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < ne; e++) {
+        double fe[24], fTe[8];
+        double *vs = m->n_prony ? s->visc + e * m->n_prony * 6 : NULL;
+        ora_element(m, e, s->u, s->T, vs, vs, fe, fTe);
+        for (int a = 0; a < npe; a++) {
+            double *o = elem_out + 4 * (e * npe + a);
+            o[0] = fe[3 * a];
+            o[1] = fe[3 * a + 1];
+            o[2] = fe[3 * a + 2];
+            o[3] = fTe[a];
+        }
+    }
+    /* node gather in ascending element order from zero: the additions of
+     * ora_step's element-order assembly, in the same order */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nn; i++) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int64_t r = offsets[i]; r < offsets[i + 1]; r++) {
+            const double *o = elem_out + 4 * slots[r];
+            for (int d = 0; d < 4; d++) acc[d] += o[d];
+        }
+        f[3 * i] = acc[0];
+        f[3 * i + 1] = acc[1];
+        f[3 * i + 2] = acc[2];
+        fT[i] = acc[3];
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < nn; i++) {
+        double un[3], Tn, On;
+        node_update(m, s, i, f + 3 * i, fT[i], un, &Tn, &On);
+        if (s->cem) s->cem[i] += m->dt * cem43_rate(s->T[i]);
+        for (int d = 0; d < 3; d++) {
+            s->u_prev[3 * i + d] = s->u[3 * i + d];
+            s->u[3 * i + d] = un[d];
+        }
+        s->T[i] = Tn;
+        s->Omega[i] = On;
+    }
+    s->t += m->dt;
+    s->step += 1;
+    return 0;
+}
+
+int ora_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -117,6 +117,31 @@ int ora_step_nodes(const ora_model *m, const ora_state *s, const int64_t *nodes,
 
 /* Critical time step reading: safety * min(mechanical CFL, thermal Gershgorin). */
 double ora_stable_dt(const ora_model *m, double safety, double *dt_mech, double *dt_th);
+
+/* Temperature and damage fraction at k points xyz [k][3] (reference
+ * coordinates) from the state s: the point is located in the first element (in
+ * id order) that contains it -- T4 by its affine map, H8 by a Newton solve of
+ * the trilinear isoparametric map -- and the nodal temperatures and nodal
+ * damage fractions 1 - exp(-Omega) are interpolated with that element's shape
+ * functions (the interpolation behind Eqs. 18-19).  Returns 0, or -(1+q) for
+ * the first point q that lies in no element. */
+int ora_probe(const ora_model *m, const ora_state *s, const double *xyz, int64_t k, double *T_out,
+              double *d_out);
+
+/* Node-to-element incidence for ora_step_parallel: offsets [nn + 1] and
+ * slots [ne * npe] (entries e * npe + corner, ascending element id within a
+ * node).  Returns 0, or -1 if a work allocation failed. */
+int ora_incidence(const ora_model *m, int64_t *offsets, int64_t *slots);
+
+/* ora_step on all host cores (OpenMP): elements in parallel into elem_out
+ * [ne][npe][4], then every node sums its incident elements' entries in
+ * ascending element id from zero -- the additions ora_step makes, in the same
+ * order -- so the result is bitwise that of ora_step.  Returns 0. */
+int ora_step_parallel(const ora_model *m, ora_state *s, const int64_t *offsets, const int64_t *slots,
+                      double *elem_out, double *f, double *fT);
+
+/* Threads ora_step_parallel uses (1 without OpenMP). */
+int ora_threads(void);
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,7 @@ struct Scenario {
     int64_t n_steps = INT64_MAX;
     // derived at init (the stable-step bounds once per set-up: dt_valid)
     double dt = 0, dt_mech = 0, dt_th = 0;
+    double mass_scale = 1.0;  // mechanical mass multiplier in use (prm.mass_scale, or the automatic choice)
     bool dt_valid = false;
     int64_t node_off = 0, elem_off = 0, probe_off = 0;
     int src_off = 0;
@@ -618,6 +619,31 @@ int require_single(tled_ctx *c) {
     return TLED_OK;
 }
 
+// The two stable-step bounds of a scenario (R16) and the mass scale in use.  With
+// mass_scale < 0 (automatic, R17) the mechanical mass is scaled by
+// s_m = max(1, (dt / (dt_safety dt_mech))^2), dt_mech the CFL bound of the unscaled
+// mesh, which makes the fixed dt the safe mechanical step; the scaled mesh's bound
+// is then dt_mech sqrt(s_m).  E_ARG if dt exceeds the thermal step's safe fraction.
+int resolve_bounds(tled_ctx *c, Scenario &s) {
+    if (s.dt_valid) return TLED_OK;  // mesh, material and parameters unchanged since: the bounds stand
+    tled_params q = s.prm;
+    const bool automatic = q.mass_scale < 0;
+    if (automatic) q.mass_scale = 1.0;
+    tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
+                    s.fib.empty() ? nullptr : s.fib.data(), q, &s.dt_mech, &s.dt_th);
+    s.mass_scale = q.mass_scale;
+    if (automatic) {
+        if (s.prm.dt > s.prm.dt_safety * s.dt_th)
+            return fail(c, TLED_E_ARG, "dt " + std::to_string(s.prm.dt) + " exceeds the thermal stable step " +
+                                           std::to_string(s.prm.dt_safety * s.dt_th));
+        const double r = s.prm.dt / (s.prm.dt_safety * s.dt_mech);
+        s.mass_scale = std::max(1.0, r * r);
+        s.dt_mech *= std::sqrt(s.mass_scale);
+    }
+    s.dt_valid = true;
+    return TLED_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -777,9 +803,10 @@ int tled_set_params(tled_ctx *c, const tled_params *p) {
     if (!c) return TLED_E_ARG;
     if (int rc = require_single(c)) return rc;
     tled_params q = p ? *p : default_params();
-    if (q.dt < 0 || !(q.dt_safety > 0) || q.gamma < 0 || !(q.mass_scale >= 1.0) || q.kappa_hg < 0 || q.kappa_hgT < 0 ||
-        q.tile_elems < 0)
+    if (q.dt < 0 || !(q.dt_safety > 0) || q.gamma < 0 || q.kappa_hg < 0 || q.kappa_hgT < 0 || q.tile_elems < 0)
         return fail(c, TLED_E_ARG, "invalid solver parameters");
+    if (q.mass_scale < 0 ? !(q.dt > 0) : !(q.mass_scale >= 1.0))
+        return fail(c, TLED_E_ARG, "mass_scale must be >= 1, or < 0 (automatic) with a fixed dt > 0");
     invalidate(c);
     single(c).prm = q;
     single(c).dt_valid = false;
@@ -869,11 +896,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     // --- per-scenario time steps and source offsets
     int src_off = 0;
     for (auto &s : c->sc) {
-        if (!s.dt_valid) {  // mesh, material and parameters unchanged since: the bounds stand
-            tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
-                            s.fib.empty() ? nullptr : s.fib.data(), s.prm, &s.dt_mech, &s.dt_th);
-            s.dt_valid = true;
-        }
+        if ((rc = resolve_bounds(c, s))) return rc;
         s.dt = s.prm.dt > 0 ? s.prm.dt : s.prm.dt_safety * std::min(s.dt_mech, s.dt_th);
         s.src_off = src_off;
         src_off += c->batch ? (int)s.src.size() : kSingleSources;
@@ -923,7 +946,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
             for (int j = 0; j < 3; j++) cf[(q++) * kT] = (float)(s.fib.empty() ? s.mat.a0[j] : s.fib[3 * el + j]);
         for (int a = 0; a < ke; a++) {
             const int64_t i = cn[a] + s.node_off;
-            Mn[i] += s.prm.mass_scale * s.mat.rho * V / ke;
+            Mn[i] += s.mass_scale * s.mat.rho * V / ke;
             Cn[i] += s.mat.rho * s.mat.c * V / ke;
             Vn[i] += V / ke;
             Kb[i] += s.mat.wb_cb * V / ke;
@@ -1119,10 +1142,21 @@ int tled_get_dt(tled_ctx *c, double *dt, double *dt_mech, double *dt_thermal) {
 int tled_stable_dt(tled_ctx *c, double *dt_mech, double *dt_thermal) {
     if (!c || !dt_mech || !dt_thermal) return fail(c, TLED_E_ARG, "NULL argument");
     if (int rc = require_single(c)) return rc;
-    const Scenario &s = single(c);
+    Scenario &s = single(c);
     if (s.npe == 0 || !s.have_mat) return fail(c, TLED_E_STATE, "set the mesh and the material first");
-    tled::stable_dt(s.npe, s.nn, s.X.data(), s.ne, s.conn.data(), s.mat, s.mat6.empty() ? nullptr : s.mat6.data(),
-                    s.fib.empty() ? nullptr : s.fib.data(), s.prm, dt_mech, dt_thermal);
+    if (int rc = resolve_bounds(c, s)) return rc;
+    *dt_mech = s.dt_mech;
+    *dt_thermal = s.dt_th;
+    return TLED_OK;
+}
+
+int tled_get_mass_scale(tled_ctx *c, int32_t idx, double *mass_scale) {
+    if (!c || !mass_scale) return fail(c, TLED_E_ARG, "NULL argument");
+    if (idx < 0 || idx >= (int32_t)c->sc.size()) return fail(c, TLED_E_ARG, "scenario index out of range");
+    Scenario &s = c->sc[idx];
+    if (s.npe == 0 || !s.have_mat) return fail(c, TLED_E_STATE, "set the mesh and the material first");
+    if (int rc = resolve_bounds(c, s)) return rc;
+    *mass_scale = s.mass_scale;
     return TLED_OK;
 }
 

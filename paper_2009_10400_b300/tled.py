@@ -108,6 +108,7 @@ _SIGS = {
     "tled_scenario_info": ([C.c_void_p, C.c_int32, C.POINTER(C.c_int64)], C.c_int),
     "tled_scenario_dt": ([C.c_void_p, C.c_int32, _dp], C.c_int),
     "tled_stable_dt": ([C.c_void_p, _dp, _dp], C.c_int),
+    "tled_get_mass_scale": ([C.c_void_p, C.c_int32, _dp], C.c_int),
     "tled_autotune": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int32)], C.c_int),
     "tled_get_mode": ([C.c_void_p, C.POINTER(C.c_int32)], C.c_int),
     "tled_selftest_wait": ([C.c_void_p, C.c_int32], C.c_int),
@@ -227,6 +228,9 @@ class HostPlanner:
     def init(self, ptr=1 << 20, n=1 << 30):
         self._check(lib().tled_init(self.h, C.c_void_p(ptr), n))
 
+    def mass_scale(self, index=0):
+        return Solver.mass_scale(self, index)
+
 
 class Solver:
     """One coupled TLED problem on one GPU (a libtled context + its workspace)."""
@@ -339,6 +343,13 @@ class Solver:
         if probes is not None:
             s.set_probes(probes)
         return s
+
+    def mass_scale(self, index=0) -> float:
+        """Mechanical mass multiplier in use for scenario `index` (the automatic
+        R17 choice when the set-up asked for mass_scale < 0)."""
+        a = C.c_double()
+        self._check(lib().tled_get_mass_scale(self.h, int(index), C.byref(a)))
+        return a.value
 
     # -- stepping ----------------------------------------------------------
     def get_dt(self):

@@ -71,7 +71,8 @@ class Problem:
     aniso_alpha: float = 1.0      # thermal expansion along the fibre / transverse (Eq. 11)
     aniso_k: float = 1.0          # conductivity along the current fibre / transverse
     gamma: float = 0.0
-    mass_scale: float = 1.0
+    mass_scale: float = 1.0       # mechanical mass multiplier >= 1; < 0: chosen so that dt is the safe
+                                  # mechanical step (R17 mass scaling, needs a fixed dt)
     kappa_hg: float = 0.1
     kappa_hgT: float = 0.1
     dt: float = 0.0               # 0 = use the stable step
@@ -361,8 +362,9 @@ def sample_scenarios(n, seed=5, side=0.05, duration=None):
 
 def scenario_problem(q, n=16, side=0.05, dt=0.01, gamma=5.0, sigma=5e-3):
     """Problem of one scenario row q (see SURROGATE_INPUTS) on an n^3 H8 cube,
-    bottom fixed, fixed time step dt and damping gamma (mass scaling is chosen
-    by the solver driver); its probes are the n^3 element centroids."""
+    bottom fixed, fixed time step dt and damping gamma, with the mechanical
+    mass scaled so that dt is the safe mechanical step (R17); its probes are
+    the n^3 element centroids."""
     X, conn = hex_grid((n, n, n), (side, side, side))
     ne = conn.shape[0]
     ang = q[11]
@@ -372,7 +374,7 @@ def scenario_problem(q, n=16, side=0.05, dt=0.01, gamma=5.0, sigma=5e-3):
     mask = np.where(np.isclose(X[:, 2], 0.0), MASK_U, 0).astype(np.uint8)
     p = Problem(name=f"scenario_h8_{n}", npe=8, X=X, conn=conn, **mat, c_heat=q[8],
                 wbcb=BLOOD_RHO * q[9] * BLOOD_CB, sources=[source(q[1:4], q[0], sigma=sigma)], mask=mask,
-                dt=dt, gamma=gamma, n_steps=int(round(q[4] / dt)))
+                dt=dt, gamma=gamma, mass_scale=-1.0, n_steps=int(round(q[4] / dt)))
     return p
 
 
@@ -386,8 +388,9 @@ def planning_scenarios(n=256, seed=4, side=0.05, dt=0.01, gamma=5.0, ne_range=(2
     H8) or tetrahedral (Kuhn-split jittered grid) mesh of the 5 cm cube with a
     log-uniform element count, one Gaussian source of U(1, 10) MW/m^3 in the
     inner half, heating time U(60, 600) s at a fixed dt, shear modulus and
-    conductivity x U(0.8, 1.2), bottom fixed.  Returns a list of Problems
-    (n_steps = heating time / dt)."""
+    conductivity x U(0.8, 1.2), bottom fixed, mechanical mass scaled so that dt
+    is the safe mechanical step (R17).  Returns a list of Problems (n_steps =
+    heating time / dt)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -408,7 +411,8 @@ def planning_scenarios(n=256, seed=4, side=0.05, dt=0.01, gamma=5.0, ne_range=(2
         T = rng.uniform(*duration)
         src = [source(rng.uniform(side / 4, 3 * side / 4, 3), rng.uniform(1e6, 1e7))]
         out.append(Problem(name=f"plan_{'h8' if hexa else 't4'}_{i}", npe=8 if hexa else 4, X=X, conn=conn, **mat,
-                           sources=src, mask=mask, dt=dt, gamma=gamma, n_steps=int(round(T / dt))))
+                           sources=src, mask=mask, dt=dt, gamma=gamma, mass_scale=-1.0,
+                           n_steps=int(round(T / dt))))
     return out
 
 

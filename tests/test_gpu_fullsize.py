@@ -85,8 +85,7 @@ def test_planning_batch_256_single_step_sampled():
     the benchmark runs it: one step from random per-scenario states; 12
     scenarios' sampled nodes against each scenario's own oracle model."""
     tled = _tled()
-    from paper_2009_10400_b300 import surrogate
-    scen = [surrogate.mass_scaled(p) for p in W.planning_scenarios(256)]
+    scen = W.planning_scenarios(256)  # R17 mass scale: the library's and the oracle's own choice
     b = tled.Batch()
     for p in scen:
         b.add(p, p.n_steps)

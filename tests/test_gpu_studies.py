@@ -16,14 +16,18 @@ def test_mass_scaling_effect_on_temperature_over_2s():
     mechanical inertia's effect on theta, which only enters through the source
     position x = X + u and the deformed-configuration conduction); and that
     mass scale at dt = 0.01 s (adds the explicit Euler time-step effect)."""
-    from paper_2009_10400_b300 import surrogate, tled
+    import oracle
+    from paper_2009_10400_b300 import tled
     q = W.sample_scenarios(1, seed=41)[0]
     q[0], q[4] = 8e6, 2.0
     base = W.scenario_problem(q, n=16, dt=0.01)
-    base.dt = 0.0  # the stable step of the unscaled problem
-    scaled = surrogate.mass_scaled(W.scenario_problem(q, n=16, dt=0.01))
-    s_m = scaled.mass_scale
+    base.dt, base.mass_scale = 0.0, 1.0  # the stable step of the unscaled problem
+    pl = tled.HostPlanner()
+    pl.setup_from(W.scenario_problem(q, n=16, dt=0.01))  # automatic mass scale for dt = 0.01 s
+    s_m = pl.mass_scale()
+    pl.close()
     assert s_m > 100.0
+    np.testing.assert_allclose(s_m, oracle.mass_scale_for(base, 0.01), rtol=1e-12)
 
     def run(mass_scale, dt):
         p = W.scenario_problem(q, n=16, dt=0.01)

@@ -536,3 +536,218 @@ def test_stable_dt_uniform_cube():
     np.testing.assert_allclose(m.dt_mech, h / cd, rtol=1e-12)
     np.testing.assert_allclose(m.dt, 0.8 * h / cd, rtol=1e-12)
     assert m.dt_th > 100 * m.dt_mech
+
+
+# ---------------------------------------------------------------------------
+# P6 continued: a moving Gaussian source at t > 0 (R14: c(t) = c0 + v t)
+# ---------------------------------------------------------------------------
+def test_p6_moving_source_heat_balance_at_later_time():
+    """One step from a mid-run state at t1 > 0 with a moving source (and one
+    already switched off): the heat content rises by dt sum_i V_i (Q_r(x_i, t1)
+    - perfusion), with Q_r centred at c0 + v t1 and x_i = X_i + u_i; the element
+    conduction loads sum to zero.  Centring the source at c0 - v t1 or at c0
+    would miss by far more than the tolerance (checked)."""
+    p = W.cube_h8(n=6, jitter=0.1, seed=11)
+    c0, v, sig, P = np.array([0.012, 0.02, 0.03]), np.array([0.02, 0.01, -0.015]), 4e-3, 6e6
+    p.sources = np.array([W.source(c0, P, sigma=sig, vel=v),
+                          W.source((0.025, 0.025, 0.025), 9e6, sigma=sig, t_on=0.0, t_off=0.3)])
+    p.dt = 1e-4
+    m = oracle.OracleModel(p)
+    st = W.random_state(p, 4, u_scale=1e-3)
+    t1 = 0.6
+    s = m.state_from(**st, t=t1, step=6000)
+    T_old = s.T.copy()
+    m.step(s, 1)
+    heat = (m.Cth * (s.T - T_old)).sum()
+    fixedT = (p.mask & W.MASK_T) != 0
+    x = p.X + st["u"]
+
+    def expected(centre):
+        Qr = P * np.exp(-((x - centre) ** 2).sum(1) / (2 * sig * sig))
+        return p.dt * (m.Vn * (-p.wbcb * (T_old - p.Ta) + p.Qm + Qr))[~fixedT].sum()
+
+    np.testing.assert_allclose(heat, expected(c0 + v * t1), rtol=1e-9)
+    for wrong in (c0 - v * t1, c0, c0 + v * (t1 + p.dt)):
+        assert abs(expected(wrong) - heat) > 1e-6 * abs(heat), wrong
+    assert s.t == pytest.approx(t1 + p.dt, abs=0, rel=1e-15)
+
+
+# ---------------------------------------------------------------------------
+# P3 continued: prescribed displacement ramp, applied at t_{n+1} (R19)
+# ---------------------------------------------------------------------------
+def test_p3_prescribed_displacement_ramp_mid_ramp():
+    """u_bar ramps linearly over ramp_time; after step n the prescribed
+    components hold (n dt / ramp_time) u_bar exactly (u_{n+1} at t_{n+1}), and
+    u_bar itself once the ramp is over.  A ramp evaluated at t_n, or a wrong
+    slope, fails at the first step."""
+    p = W.cube_h8(n=3)
+    p.sources = np.zeros((0, 10))
+    top = np.isclose(p.X[:, 2], 0.05)
+    p.mask[top] = W.MASK_U
+    p.ubar = np.zeros((p.nn, 3))
+    p.ubar[top, 2] = 4e-3
+    p.ubar[top, 0] = -1e-3
+    p.dt = 1e-4
+    p.ramp_time = 10 * p.dt
+    m = oracle.OracleModel(p)
+    s = m.init_state()
+    held = p.mask.astype(bool)
+    for n in range(1, 15):
+        m.step(s, 1)
+        frac = min(1.0, n * p.dt / p.ramp_time)
+        np.testing.assert_allclose(s.u[top], frac * p.ubar[top], rtol=1e-14, atol=0)
+        np.testing.assert_array_equal(s.u[held & ~top], 0.0)
+    # the free nodes have moved (the ramp drives the body)
+    assert np.abs(s.u[~held]).max() > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# R16 thermal Gershgorin bound on a uniform cube, in closed form
+# ---------------------------------------------------------------------------
+def _uniform_cube_row_sum(kappa_t, r_k):
+    """Sum over b of |K_ab| of one cube element of side h, in units of h k / 16,
+    for conduction along a0 = x scaled by r_k and the thermal hourglass of
+    coefficient kappa_t.  Corner a = (sx, sy, sz) in {-1, 1}^3: grad h_a =
+    s_a / (4 h), V = h^3, so V grad h_a . D grad h_b = (h k / 16)(p + q + r +
+    (r_k - 1) p) with p = sx_a sx_b etc.; the hourglass vectors of a brick are
+    the base vectors h_alpha (their projections vanish), BB = 3 / (2 h^2), so
+    k_hgT = kappa_t V BB / 8 = 3 kappa_t h / 16 and K^hg_ab = k k_hgT (pq + qr +
+    pr + pqr)."""
+    a = (1, 1, 1)
+    total = 0.0
+    for b in [(x, y, z) for x in (-1, 1) for y in (-1, 1) for z in (-1, 1)]:
+        p, q, r = a[0] * b[0], a[1] * b[1], a[2] * b[2]
+        total += abs(p + q + r + (r_k - 1) * p + 3 * kappa_t * (p * q + q * r + p * r + p * q * r))
+    return total
+
+
+@pytest.mark.parametrize("kappa_t,r_k,expect_R", [(0.1, 1.0, 10.8), (0.0, 1.0, 12.0), (0.1, 2.5, None)])
+def test_stable_dt_thermal_gershgorin_closed_form(kappa_t, r_k, expect_R):
+    """R16's thermal bound dt_th = min_i 2 C_i / (sum_j |K_ij| + w_b c_b V_i) on a
+    uniform n^3 cube: every node, interior or boundary, gets
+    2 rho c h^3 / (8 (h k / 16) R + w_b c_b h^3) with R the element's absolute
+    row sum worked out by hand (10.8 for the default hourglass coefficient 0.1:
+    4.2 + 3 x 0.4 + 3 x 1 + 2.4)."""
+    n, side = 4, 0.05
+    h = side / n
+    p = W.cube_h8(n=n)
+    p.kappa_hgT = kappa_t
+    p.aniso_k = r_k
+    p.a0 = np.tile([1.0, 0.0, 0.0], (p.ne, 1))
+    m = oracle.OracleModel(p)
+    R = _uniform_cube_row_sum(kappa_t, r_k)
+    if expect_R is not None:
+        assert R == pytest.approx(expect_R, rel=1e-14)
+    rho, c, k = 1000.0, p.c_heat, 0.5
+    dt_th = 2 * rho * c * h ** 3 / (8 * h * k / 16 * R + p.wbcb * h ** 3)
+    np.testing.assert_allclose(m.dt_th, dt_th, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# P10 continued: the Arrhenius integral's exact value with R18's constants
+# ---------------------------------------------------------------------------
+def test_p10_arrhenius_exact_value():
+    """At a held temperature Omega(t) = t A exp(-E_a / (R (T + 273.15))) with
+    A = 7.39e39 1/s, E_a = 2.577e5 J/mol, R = 8.314 J/(mol K) (R18); the rates at
+    37, 60 and 90 C are about 2.92e-4, 0.290 and 631 1/s."""
+    p = W.cube_h8(n=1)
+    p.sources = np.zeros((0, 10))
+    p.mask = p.mask | W.MASK_T  # hold every temperature
+    m = oracle.OracleModel(p, dt=0.01)
+    A, Ea, R = 7.39e39, 2.577e5, 8.314
+    for Tc, rate in ((37.0, 2.92e-4), (60.0, 0.290), (90.0, 631.0)):
+        s = m.init_state()
+        s.T[:] = Tc
+        m.step(s, 250)
+        k = A * np.exp(-Ea / (R * (Tc + 273.15)))
+        np.testing.assert_allclose(s.Omega, 250 * 0.01 * k, rtol=1e-12)
+        assert k == pytest.approx(rate, rel=3e-3)
+
+
+# ---------------------------------------------------------------------------
+# probes: shape-function interpolation at arbitrary points
+# ---------------------------------------------------------------------------
+def _probe_points(p, k, seed):
+    rng = np.random.default_rng(seed)
+    lo, hi = p.X.min(0), p.X.max(0)
+    return lo + (hi - lo) * rng.uniform(0.12, 0.88, (k, 3))
+
+
+@pytest.mark.parametrize("kind", ["h8_jittered", "t4"])
+def test_probe_reproduces_linear_fields(kind):
+    """Linear fields are interpolated exactly by T4 barycentric and by
+    isoparametric H8 shape functions, on distorted elements too, provided the
+    point is located correctly (x(xi) = x): T = a + b . x and a damage fraction
+    linear in x come back exactly at arbitrary (off-centroid) points."""
+    p = W.cube_h8(n=5, jitter=0.25, seed=4) if kind == "h8_jittered" else W.cube_t4(n=4, jitter=0.15)
+    m = oracle.OracleModel(p)
+    s = m.init_state()
+    b, g = np.array([300.0, -200.0, 150.0]), np.array([4.0, 2.0, -3.0])
+    s.T[:] = 40.0 + p.X @ b
+    d_nodes = 0.4 + p.X @ g
+    s.Omega[:] = -np.log1p(-d_nodes)
+    x = _probe_points(p, 300, 3)
+    T, d = m.probe(s, x)
+    np.testing.assert_allclose(T, 40.0 + x @ b, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(d, 0.4 + x @ g, rtol=0, atol=1e-12)
+
+
+def test_probe_trilinear_on_bricks_and_nodes():
+    """On axis-aligned bricks the trilinear shape functions reproduce x y z
+    exactly (x, y, z are affine in the natural coordinates), which pins the
+    H8 interpolation itself, not only partition of unity; a probe on a node
+    returns that node's value (any field)."""
+    X, conn = W.hex_grid((3, 4, 2), (0.03, 0.05, 0.02))
+    mat = W._material(conn.shape[0])
+    p = W.Problem(name="bricks", npe=8, X=X, conn=conn, **mat)
+    m = oracle.OracleModel(p)
+    s = m.init_state()
+    s.T[:] = 1e5 * X[:, 0] * X[:, 1] * X[:, 2]
+    x = _probe_points(p, 200, 8)
+    T, _ = m.probe(s, x)
+    np.testing.assert_allclose(T, 1e5 * x[:, 0] * x[:, 1] * x[:, 2], rtol=1e-12, atol=1e-15)
+    rng = np.random.default_rng(1)
+    s.T[:] = 37 + rng.uniform(0, 20, p.nn)
+    s.Omega[:] = rng.uniform(0, 3, p.nn)
+    T, d = m.probe(s, X[::5])
+    np.testing.assert_allclose(T, s.T[::5], rtol=1e-13)
+    np.testing.assert_allclose(d, oracle.damage_fraction(s.Omega[::5]), rtol=1e-13)
+    with pytest.raises(ValueError, match="outside"):
+        m.probe(s, [[0.5, 0.5, 0.5]])
+
+
+# ---------------------------------------------------------------------------
+# the oracle on all host cores is the same computation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["h8", "t4"])
+def test_parallel_oracle_is_bitwise_serial(kind):
+    """ora_step_parallel (elements in parallel, fixed-order node gather) gives
+    bitwise the state of the plain element-order ora_step."""
+    p = W.cube_h8(n=6, jitter=0.2, seed=9) if kind == "h8" else W.cube_t4(n=4)
+    p.sources = np.array([W.source((0.02, 0.025, 0.03), 8e6, sigma=6e-3, vel=(0.01, 0, 0))])
+    m = oracle.OracleModel(p)
+    st = W.random_state(p, 2, u_scale=1e-3)
+    a, b = m.state_from(**st), m.state_from(**st)
+    m.step(a, 30)
+    m.step_parallel(b, 30)
+    for f in ("u", "u_prev", "T", "Omega", "visc", "cem"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    assert a.t == b.t and a.step == b.step
+
+
+# ---------------------------------------------------------------------------
+# R17 mass scaling from the oracle's own CFL bound
+# ---------------------------------------------------------------------------
+def test_mass_scale_for_fixed_step():
+    """s_m = (dt / (0.8 dt_mech))^2 with dt_mech = h / c_d, c_d = sqrt((kappa +
+    4 mu / 3 + 4 k1) / rho) on a uniform cube; with that scale the safe
+    mechanical step is dt itself."""
+    p = W.cube_h8(n=8)
+    h, dt = 0.05 / 8, 0.01
+    cd = np.sqrt((3e5 + 4 * 3e3 / 3 + 4 * 1e3) / 1000.0)
+    s_m = oracle.mass_scale_for(p, dt)
+    np.testing.assert_allclose(s_m, (dt * cd / (0.8 * h)) ** 2, rtol=1e-12)
+    p.mass_scale = s_m
+    m = oracle.OracleModel(p, dt=dt)
+    m.stable_dt(0.8)
+    np.testing.assert_allclose(0.8 * m.dt_mech, dt, rtol=1e-12)
