@@ -47,8 +47,10 @@ def make_problem(workload):
         return W.block_h8(n=128)
     if workload == "ellipsoid_t4":
         return W.ellipsoid_t4()
-    if workload.startswith("block_h8_"):
-        return W.block_h8(n=int(workload.split("_")[-1]))
+    if workload.startswith("block_h8_"):  # block_h8_N (h = 1 mm) or block_h8_N_hXmm
+        parts = workload.split("_")
+        h = float(parts[3][1:-2]) * 1e-3 if len(parts) > 3 else 1e-3
+        return W.block_h8(n=int(parts[2]), h=h)
     raise SystemExit(f"unknown workload {workload}")
 
 
@@ -274,6 +276,84 @@ def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1, warmup_seconds=10
             "sample": f"{prob.name}: {steps} full steps after {n_warm} warm-up step(s) ({el:.1f} s, "
                       f"set-up {setup:.1f} s), FP64 C oracle, {how}", "steps": steps, "warmup": n_warm,
             "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+
+
+def cpu_sample_subprocess(args, parallel):
+    """cpu_oracle_sample of the bench's workload in a fresh Python process."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", args.workload,
+           "--cpu-steps", str(args.cpu_steps), "--cpu-seconds", str(args.cpu_seconds)]
+    if parallel:
+        cmd.append("--cpu-parallel")
+    r = subprocess.run(cmd, capture_output=True, text=True, check=True)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_trajectory_child(workload, n_steps, every, dt, path):
+    """Child process of the precision leg: the FP64 oracle's trajectory of the
+    workload on all host cores, snapshots (u, T, Omega) every `every` steps to
+    an .npz file."""
+    import oracle
+
+    prob = make_problem(workload)
+    m = oracle.OracleModel(prob, dt=dt)
+    s = m.init_state()
+    snaps = {}
+    for k in range(every, n_steps + 1, every):
+        m.step_parallel(s, every)
+        snaps[f"u{k}"], snaps[f"T{k}"], snaps[f"O{k}"] = s.u, s.T, s.Omega
+    np.savez(path, **snaps)
+
+
+def rel_l2(a, b):
+    """The paper's error indicator e = ||a - b||_2 / ||b||_2 (Section 6.1)."""
+    a, b = np.ravel(a), np.ravel(b)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def nre_max(a, b):
+    """Maximum normalised relative error |a - b| / (max b - min b) (Section 6.1)."""
+    a, b = np.ravel(a), np.ravel(b)
+    return float(np.abs(a - b).max() / np.ptp(b))
+
+
+def precision_leg(args, device, stream, n=32, n_steps=5000, every=1000):
+    """Per-result error against the FP64 oracle for the 128^3 block's generator
+    at n^3 (h = 4 mm): n_steps steps, compared every `every` steps, with the
+    float-float accumulation of u and T on (the product setting) and off."""
+    import tempfile
+
+    from paper_2009_10400_b300 import tled
+
+    workload = f"block_h8_{n}_h4mm"
+    prob = make_problem(workload)
+    base = tled.default_flags(prob)
+    runs = {"compensated": base, "plain_fp32": base & ~tled.COMPENSATED}
+    gs = {k: tled.Solver.from_problem(prob, device=device, stream=stream, flags=f) for k, f in runs.items()}
+    dt = gs["compensated"].get_dt()[0]
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "oracle.npz")
+        t0 = time.perf_counter()
+        subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-trajectory", path, "--workload", workload,
+                        "--steps", str(n_steps), "--oracle-every", str(every), "--oracle-dt", repr(dt)], check=True)
+        oracle_s = time.perf_counter() - t0
+        ref = dict(np.load(path))
+    out = {"workload": f"{workload}: the 128^3 block's generator at {n}^3, h = 4 mm, {prob.ne} H8, {n_steps} "
+                       f"steps at dt {dt:.4e} s", "every": every, "oracle": "FP64 C oracle, OpenMP on all host cores",
+           "oracle_s": oracle_s, "tolerance": {"e_u": 1e-4, "e_theta": 1e-4, "damage_abs": 1e-3}}
+    for name, g in gs.items():
+        rows = []
+        for k in range(every, n_steps + 1, every):
+            g.step(every)
+            g.sync()
+            u, T, d = g.displacement(), g.temperature(), g.damage()
+            uo, To, Oo = ref[f"u{k}"], ref[f"T{k}"], ref[f"O{k}"]
+            rows.append({"step": k, "e_u": rel_l2(u, uo), "e_theta": rel_l2(T - prob.T0, To - prob.T0),
+                         "nre_u": nre_max(u, uo), "nre_T": nre_max(T, To),
+                         "damage_abs": float(np.abs(d + np.expm1(-Oo)).max())})
+        out[name] = rows
+        g.close()
+    out["peak_rise_K"] = float(ref[f"T{n_steps}"].max() - prob.T0)
+    return out
 
 
 def workload_config(prob):
@@ -753,6 +833,9 @@ def run_gpu(args):
     del s
     torch.cuda.empty_cache()
     smalls = None if args.no_planning else small_configs(local, stream)
+    precision = None
+    if not args.no_precision and rank == 0 and prob.name.startswith("block_h8"):
+        precision = precision_leg(args, local, stream)
     plan = None
     if not args.no_planning and prob.name.startswith("block_h8"):
         plan = planning_bench(args, local, stream)
@@ -762,9 +845,10 @@ def run_gpu(args):
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
-            # the oracle on every host core (the headline baseline) and on one core
-            cpu = cpu_oracle_sample(prob, args.cpu_steps, seconds=args.cpu_seconds, parallel=True)
-            cpu["single_core"] = cpu_oracle_sample(prob, args.cpu_steps, seconds=args.cpu_seconds)
+            # the oracle on every host core (the headline baseline) and on one core, each in a
+            # child process without torch (whose own OpenMP threads would compete for the cores)
+            cpu = cpu_sample_subprocess(args, parallel=True)
+            cpu["single_core"] = cpu_sample_subprocess(args, parallel=False)
         clocks = clk.summary()
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -792,6 +876,7 @@ def run_gpu(args):
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "precision": precision,
             "planning": plan,
             "small_configs": smalls,
             "final": {"T_max": st["T_max"], "u_max": st["u_max"], "status": st["status"]},
@@ -831,7 +916,20 @@ def main():
     ap.add_argument("--sur-epochs", type=int, default=50)
     ap.add_argument("--sur-tol", type=float, default=1.0)
     ap.add_argument("--sur-coverage", type=float, default=0.95)
+    ap.add_argument("--no-precision", action="store_true", help="skip the 32^3 long-run error leg")
+    ap.add_argument("--oracle-trajectory", default=None, help=argparse.SUPPRESS)  # child of the precision leg
+    ap.add_argument("--oracle-every", type=int, default=1000, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-dt", type=float, default=0.0, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)  # child of the cpu_baseline leg
+    ap.add_argument("--cpu-parallel", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_trajectory:
+        oracle_trajectory_child(args.workload, args.steps, args.oracle_every, args.oracle_dt, args.oracle_trajectory)
+        return 0
+    if args.cpu_sample:
+        print(json.dumps(cpu_oracle_sample(make_problem(args.workload), args.cpu_steps, seconds=args.cpu_seconds,
+                                           parallel=args.cpu_parallel)))
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

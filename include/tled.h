@@ -46,7 +46,7 @@
 extern "C" {
 #endif
 
-#define TLED_VERSION 4
+#define TLED_VERSION 5
 
 /* status codes */
 #define TLED_OK 0
@@ -154,6 +154,16 @@ typedef struct tled_params {
     double kappa_hgT;   /* H8 thermal hourglass coefficient (default 0.1) */
     uint32_t flags;     /* TLED_EXPANSION | TLED_TEMP_DEP | TLED_COMPENSATED */
     int32_t tile_elems; /* elements per tile, 0 = default (H8 512, T4 1024) */
+    int32_t n_sub;      /* mechanical subcycling: n_sub >= 1 mechanical substeps per thermal step (0 = 1).
+                           A step (tled_step, n_steps of a batch scenario) is then a mechanical substep
+                           of length dt_thermal / n_sub; every substep advances u (Eq. 27) and the Prony
+                           state; the last of each n_sub also advances T (Eq. 20), Omega and the CEM43
+                           dose by the thermal step, explicit in T at the thermal step's start, with the
+                           sources at that start time and the thermal loads of the current displacement.
+                           dt (if > 0) is the THERMAL step; dt = 0 takes dt_safety x min(n_sub dt_mech,
+                           dt_thermal); an automatic mass scale makes dt / n_sub the safe mechanical step.
+                           tled_get_dt and tled_scenario_dt report the substep. */
+    int32_t pad;
 } tled_params;
 
 typedef struct tled_stats {
@@ -351,11 +361,16 @@ int tled_autotune(tled_ctx *ctx, void *dev_workspace, int64_t bytes, int32_t tri
 #define TLED_MODE_GRID 4
 int tled_get_mode(tled_ctx *ctx, int32_t *mode);
 
-/* Self-test of the bounded device waits (after init): runs a one-CTA kernel whose wait
- * can never complete -- which = 0 an mbarrier wait (as the tile kernel's copies use),
- * 1 a grid-barrier wait (as the grid-resident mode uses) -- and returns what a step
- * would report: TLED_E_TIMEOUT after about a second.  The status is cleared again
- * afterwards, so the context stays usable.  Nothing faults or hangs. */
+/* Self-test of the bounded device waits (after init): runs a kernel whose wait can
+ * never complete and returns what a step would report: TLED_E_TIMEOUT after about a
+ * second or two.  which = 0: a one-CTA kernel's mbarrier wait (as the tile kernel's
+ * copies use); 1: a one-CTA kernel's grid-barrier wait (as the grid-resident mode
+ * uses); 2: the step's own tile kernel with the node staging of tile 0 left out, so
+ * that the CTA holding it waits in vain, skips its element pass, waits (bounded) for
+ * its other copies and leaves while the other CTAs finish their tiles (streamed mode
+ * only, else E_STATE; the nodal state is then that of a partial step -- set it again,
+ * e.g. with tled_set_state or tled_load_state, before stepping on).  The status is
+ * cleared again afterwards, so the context stays usable.  Nothing faults or hangs. */
 int tled_selftest_wait(tled_ctx *ctx, int32_t which);
 
 /* Scalar diagnostics, reduced on the device in FP64 in a fixed order
@@ -367,11 +382,12 @@ int tled_get_stats(tled_ctx *ctx, tled_stats *s);
 
 /* Allocation-free diagnostics (the paper has no counterpart: this is a
  * service for callers that cannot allocate device memory when they want the
- * numbers -- code running during CUDA graph capture, where cudaMalloc is not
- * allowed; real-time loops in which an allocation would synchronise the
- * device; processes whose device memory is fully held by another caching
- * allocator).  Enqueues on the context stream the same FP64 reduction as
- * tled_get_stats and writes six doubles to the DEVICE buffer `out`:
+ * numbers -- real-time loops in which an allocation would synchronise the
+ * device or take an unbounded time, and processes whose device memory is fully
+ * held by another framework's caching allocator).  Enqueues on the context
+ * stream the same FP64 reduction as tled_get_stats and writes six doubles to
+ * the DEVICE buffer `out` (device or managed memory of the context's device;
+ * anything else is refused with E_ARG):
  *   out[0] kinetic energy sum_i 1/2 m_i |v_i|^2          (J)
  *   out[1] heat content sum_i C_i (T_i - T0)              (J)
  *   out[2] max_i (T_i - T0), out[3] min_i (T_i - T0)       (K)
@@ -382,11 +398,14 @@ int tled_get_stats(tled_ctx *ctx, tled_stats *s);
  * doubles, 18,944 bytes, that every GPU loading the library keeps until the
  * process exits).  Allocates nothing (no cudaMalloc, no allocating library
  * call) and does not synchronise.  The first call on a device looks up that
- * array's device address; make that first call before any stream capture.
- * All calls in the process share the array: each call overwrites the partial
- * sums it reads, so nothing needs clearing, but calls whose kernels overlap
- * on the GPU (different streams, or different contexts on one device) race
- * on it and must be ordered by the caller. */
+ * array's device address (with the device current) and keeps it for the
+ * process; make that first call before any stream capture.  After a
+ * cudaDeviceReset of the device the kept address belongs to the ended context:
+ * do not call this entry point in that process again.  All calls in the
+ * process share the array: each call overwrites the partial sums it reads, so
+ * nothing needs clearing, but calls whose kernels overlap on the GPU
+ * (different streams, or different contexts on one device) race on it and
+ * must be ordered by the caller. */
 int tled_get_stats_noalloc(tled_ctx *ctx, int32_t n_blocks, double *out);
 
 /* Checkpoint: serialise the exact device state (bitwise) with a header and

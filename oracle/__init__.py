@@ -84,6 +84,7 @@ def lib():
         L.ora_incidence.argtypes = [C.POINTER(_Model), _i64p, _i64p]
         L.ora_step_parallel.argtypes = [C.POINTER(_Model), C.POINTER(_State), _i64p, _i64p, _dp, _dp, _dp]
         L.ora_threads.restype = C.c_int
+        L.ora_step_subcycled.argtypes = [C.POINTER(_Model), C.POINTER(_State), C.c_int, _dp, _dp]
         _lib = L
     return _lib
 
@@ -153,8 +154,9 @@ class OracleModel:
         for f in ("c_heat", "beta_c", "beta_k", "T_ref", "wbcb", "Qm", "T0", "Ta", "lnA", "Ea", "gamma",
                   "mass_scale", "kappa_hg", "kappa_hgT", "ramp_time", "aniso_alpha", "aniso_k"):
             setattr(m, f, float(getattr(prob, f)))
-        if prob.mass_scale < 0:  # R17: scaled so that the fixed dt is the safe mechanical step
-            m.mass_scale = mass_scale_for(prob, prob.dt, prob.dt_safety)
+        self.n_sub = max(1, int(getattr(prob, "n_sub", 1)))
+        if prob.mass_scale < 0:  # R17: scaled so that the fixed (sub)step is the safe mechanical step
+            m.mass_scale = mass_scale_for(prob, prob.dt / self.n_sub, prob.dt_safety)
         self.mass_scale = m.mass_scale
         m.expansion = int(bool(prob.expansion))
         m.temp_dep = int(bool(prob.temp_dep))
@@ -168,8 +170,12 @@ class OracleModel:
         rc = L.ora_setup(C.byref(m))
         if rc != 0:
             raise ValueError(f"oracle: non-positive reference Jacobian in element {-rc - 1}")
-        if dt is None:
-            dt = prob.dt if prob.dt > 0 else self.stable_dt(prob.dt_safety)
+        if dt is None:  # with subcycling dt is the thermal step, n_sub mechanical substeps long
+            if prob.dt > 0:
+                dt = prob.dt
+            else:
+                self.stable_dt(prob.dt_safety)
+                dt = prob.dt_safety * min(self.n_sub * self.dt_mech, self.dt_th)
         m.dt = float(dt)
         self.dt = float(dt)
         self._f = np.zeros((nn, 3))
@@ -201,6 +207,16 @@ class OracleModel:
         for _ in range(n):
             cs = s._c()
             L.ora_step(C.byref(self._m), C.byref(cs), _p(self._f), _p(self._fT))
+            s.t, s.step = cs.t, cs.step
+        return s
+
+    def step_thermal(self, s: OracleState, n=1):
+        """n thermal steps of self.dt, each of prob.n_sub mechanical substeps
+        (ora_step_subcycled)."""
+        L = lib()
+        for _ in range(n):
+            cs = s._c()
+            L.ora_step_subcycled(C.byref(self._m), C.byref(cs), self.n_sub, _p(self._f), _p(self._fT))
             s.t, s.step = cs.t, cs.step
         return s
 

@@ -832,3 +832,52 @@ int ora_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* mechanical subcycling: n_sub mechanical substeps per thermal step   */
+/* ------------------------------------------------------------------ */
+int ora_step_subcycled(const ora_model *m, ora_state *s, int n_sub, double *f, double *fT) {
+    const int npe = m->npe;
+    /* the mechanical substep: the Prony recurrence and Eq. (27) with dt / n_sub */
+    ora_model mm = *m;
+    mm.dt = m->dt / n_sub;
+    /* the thermal step starts here: the temperature is held at T(t_th) during the
+     * substeps and advances once, explicit in T(t_th), with the sources at t_th */
+    const double t_th = s->t;
+    double fe[24], fTe[8];
+    for (int j = 0; j < n_sub; j++) {
+        memset(f, 0, 3 * m->nn * sizeof(double));
+        memset(fT, 0, m->nn * sizeof(double));
+        for (int64_t e = 0; e < m->ne; e++) {
+            double *vs = m->n_prony ? s->visc + e * m->n_prony * 6 : NULL;
+            ora_element(&mm, e, s->u, s->T, vs, vs, fe, fTe);
+            const int32_t *cn = m->conn + e * npe;
+            for (int a = 0; a < npe; a++) {
+                for (int i = 0; i < 3; i++) f[3 * (int64_t)cn[a] + i] += fe[3 * a + i];
+                fT[cn[a]] += fTe[a];
+            }
+        }
+        const int thermal = j == n_sub - 1; /* the last substep also advances T and the damage */
+        ora_state st = *s;
+        st.t = t_th;
+        for (int64_t i = 0; i < m->nn; i++) {
+            double un[3], Tn, On, u_th[3], T_th, O_th;
+            node_update(&mm, s, i, f + 3 * i, fT[i], un, &Tn, &On); /* u over the substep */
+            if (thermal) {
+                /* T and Omega over the whole thermal step, with this substep's thermal loads
+                 * (current displacement, T(t_th)) and the sources at t_th */
+                node_update(m, &st, i, f + 3 * i, fT[i], u_th, &T_th, &O_th);
+                if (s->cem) s->cem[i] += m->dt * cem43_rate(s->T[i]);
+                s->T[i] = T_th;
+                s->Omega[i] = O_th;
+            }
+            for (int d = 0; d < 3; d++) {
+                s->u_prev[3 * i + d] = s->u[3 * i + d];
+                s->u[3 * i + d] = un[d];
+            }
+        }
+        s->t += mm.dt;
+        s->step += 1;
+    }
+    return 0;
+}

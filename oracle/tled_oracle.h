@@ -142,6 +142,16 @@ int ora_step_parallel(const ora_model *m, ora_state *s, const int64_t *offsets, 
 
 /* Threads ora_step_parallel uses (1 without OpenMP). */
 int ora_threads(void);
+
+/* One thermal step of m->dt with mechanical subcycling: n_sub substeps of
+ * m->dt / n_sub, each an element pass (Prony recurrence with the substep) and
+ * the central-difference update of Eq. (27) over the substep; the temperature
+ * is held at T(t) during the substeps, and the last one also advances T, Omega
+ * and the CEM43 dose over m->dt (Eq. 20, explicit in T(t)) with its own
+ * thermal loads (the current displacement) and the sources at the thermal
+ * step's start t.  s->t advances by the substep each substep; n_sub = 1 is
+ * ora_step.  Work arrays as for ora_step.  Returns 0. */
+int ora_step_subcycled(const ora_model *m, ora_state *s, int n_sub, double *f, double *fT);
 #ifdef __cplusplus
 }
 #endif

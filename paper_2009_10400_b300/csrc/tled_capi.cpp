@@ -64,6 +64,7 @@ struct Scenario {
     // derived at init (the stable-step bounds once per set-up: dt_valid)
     double dt = 0, dt_mech = 0, dt_th = 0;
     double mass_scale = 1.0;  // mechanical mass multiplier in use (prm.mass_scale, or the automatic choice)
+    double dt_thermal = 0;    // the thermal step (dt with n_sub = 1; n_sub dt with mechanical subcycling)
     bool dt_valid = false;
     int64_t node_off = 0, elem_off = 0, probe_off = 0;
     int src_off = 0;
@@ -79,6 +80,7 @@ tled_params default_params() {
     p.kappa_hgT = 0.1;
     p.flags = TLED_EXPANSION | TLED_COMPENSATED;
     p.tile_elems = 0;
+    p.n_sub = 1;
     return p;
 }
 
@@ -465,6 +467,9 @@ ScenDev scen_dev(const Scenario &s) {
     d.Qm = (float)s.mat.Qm;
     d.src_off = s.src_off;
     d.n_src = (int)s.src.size();
+    d.n_sub = s.prm.n_sub;
+    d.dt_th = s.prm.n_sub == 1 ? dt : s.dt_thermal;
+    d.dtf_th = (float)d.dt_th;
     return d;
 }
 
@@ -636,7 +641,7 @@ int resolve_bounds(tled_ctx *c, Scenario &s) {
         if (s.prm.dt > s.prm.dt_safety * s.dt_th)
             return fail(c, TLED_E_ARG, "dt " + std::to_string(s.prm.dt) + " exceeds the thermal stable step " +
                                            std::to_string(s.prm.dt_safety * s.dt_th));
-        const double r = s.prm.dt / (s.prm.dt_safety * s.dt_mech);
+        const double r = s.prm.dt / s.prm.n_sub / (s.prm.dt_safety * s.dt_mech);  // the mechanical step
         s.mass_scale = std::max(1.0, r * r);
         s.dt_mech *= std::sqrt(s.mass_scale);
     }
@@ -807,6 +812,8 @@ int tled_set_params(tled_ctx *c, const tled_params *p) {
         return fail(c, TLED_E_ARG, "invalid solver parameters");
     if (q.mass_scale < 0 ? !(q.dt > 0) : !(q.mass_scale >= 1.0))
         return fail(c, TLED_E_ARG, "mass_scale must be >= 1, or < 0 (automatic) with a fixed dt > 0");
+    if (q.n_sub == 0) q.n_sub = 1;
+    if (q.n_sub < 1 || q.n_sub > 1000000) return fail(c, TLED_E_ARG, "n_sub must be 1..1000000 (0 = 1)");
     invalidate(c);
     single(c).prm = q;
     single(c).dt_valid = false;
@@ -897,7 +904,11 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     int src_off = 0;
     for (auto &s : c->sc) {
         if ((rc = resolve_bounds(c, s))) return rc;
-        s.dt = s.prm.dt > 0 ? s.prm.dt : s.prm.dt_safety * std::min(s.dt_mech, s.dt_th);
+        // the step is the mechanical (sub)step; the thermal step is n_sub of them
+        const int ns_ = s.prm.n_sub;
+        const double dt_thermal = s.prm.dt > 0 ? s.prm.dt : s.prm.dt_safety * std::min(ns_ * s.dt_mech, s.dt_th);
+        s.dt = ns_ == 1 ? dt_thermal : dt_thermal / ns_;
+        s.dt_thermal = dt_thermal;
         s.src_off = src_off;
         src_off += c->batch ? (int)s.src.size() : kSingleSources;
     }
@@ -1000,6 +1011,10 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     if ((rc = upload_scenarios(c))) return rc;
     if ((rc = write_state(c, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
     if ((rc = upload_clock(c, 0, 0.0))) return rc;
+    {  // the active prefixes on the device from the start (every launch reads them)
+        const int ranks = active_ranks(c, 0);
+        if (ranks > 0 && (rc = set_active(c, ranks))) return rc;
+    }
     // --- kernel arguments
     const Scenario &s0 = c->sc[0];
     const tled_material &m = s0.mat;
@@ -1125,6 +1140,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
         h = fnv1a(&s.mat, sizeof(tled_material), h);
         h = fnv1a(&s.prm, sizeof(tled_params), h);
         h = fnv1a(&s.dt, 8, h);
+        h = fnv1a(&s.prm.n_sub, 4, h);
     }
     c->setup_hash = h;
     return TLED_OK;
@@ -1472,6 +1488,13 @@ int tled_get_stats_noalloc(tled_ctx *c, int32_t n_blocks, double *out) {
         return fail(c, TLED_E_ARG, "n_blocks must be 1.." + std::to_string(tled::kNoAllocMaxBlocks) +
                                        " (size of the static scratch array), got " + std::to_string(n_blocks));
     CUDA_TRY(c, cudaSetDevice(c->device));
+    cudaPointerAttributes pa{};  // a query: allocates nothing
+    if (cudaPointerGetAttributes(&pa, out) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, TLED_E_ARG, "out is not a device pointer");
+    }
+    if (!((pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) && pa.device == c->device))
+        return fail(c, TLED_E_ARG, "out must be device (or managed) memory of the context's device");
     double *scratch = nullptr;
     CUDA_TRY(c, tled::noalloc_scratch(c->device, &scratch));
     CUDA_TRY(c, tled::launch_stats_blocks(c->A, c->nn, n_blocks, scratch, out, c->stream));
@@ -1589,13 +1612,24 @@ int tled_autotune(tled_ctx *c, void *dev_workspace, int64_t bytes, int32_t trial
 int tled_selftest_wait(tled_ctx *c, int32_t which) {
     if (!c) return TLED_E_ARG;
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
-    if (which != 0 && which != 1) return fail(c, TLED_E_ARG, "which must be 0 (mbarrier) or 1 (grid barrier)");
+    if (which < 0 || which > 2)
+        return fail(c, TLED_E_ARG, "which must be 0 (mbarrier), 1 (grid barrier) or 2 (tile kernel)");
+    if (which == 2 && (c->resident || c->coop))
+        return fail(c, TLED_E_STATE, "the tile-kernel self-test needs the streamed step mode (TLED_STREAMED)");
     CUDA_TRY(c, cudaSetDevice(c->device));
     if (int rc = check_status(c)) return rc;  // start from a clean status
     tled::StepArgs a = c->A;
     a.gbar = dptr<unsigned>(c, c->L.gbar);
     CUDA_TRY(c, cudaMemsetAsync(a.gbar, 0, 4, c->stream));
-    CUDA_TRY(c, tled::launch_wait_selftest(a, which, c->stream));
+    if (which == 2) {  // the step's own tile kernel, with tile 0's node staging left out
+        const int ranks = active_ranks(c, c->step);
+        if (ranks == 0) return fail(c, TLED_E_STATE, "every scenario has finished");
+        if (int rc = set_active(c, ranks)) return rc;  // the active-tile count the kernel reads
+        a.stage_skip = 1;
+        CUDA_TRY(c, tled::launch_tile_step(a, c->tile_ctas, c->npe, 0, c->stream));
+    } else {
+        CUDA_TRY(c, tled::launch_wait_selftest(a, which, c->stream));
+    }
     const int rc = check_status(c);  // the timed-out wait's status, as a step would report it
     // clear it again: the context stays usable
     const unsigned st[4] = {0u, 0xffffffffu, 0xffffffffu, 0u};

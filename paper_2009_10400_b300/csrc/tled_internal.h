@@ -83,13 +83,15 @@ struct ResDesc {
 
 // Constant per-scenario parameters (device table).
 struct ScenDev {
-    double dt;
+    double dt;             // the step: the mechanical (sub)step
+    double dt_th;          // the thermal step, n_sub dt
     float dtf, inv_dt;
+    float dtf_th;          // (float) dt_th
     float damp_a, damp_b;  // v+ = damp_a v - damp_b f / m: (1 - g dt/2)/(1 + g dt/2), dt/(1 + g dt/2)
     float pr_a[4], pr_b[4];  // Prony: dt phi/(dt + tau), tau/(dt + tau)
     float Qm;              // metabolic heat W/m^3
     int src_off, n_src;    // sources [src_off, src_off + n_src) of the global table
-    int pad;
+    int n_sub;             // mechanical substeps per thermal step (1: every step is a coupled step)
 };
 
 // A single problem's scenario table and source rows, passed by value to a one-block
@@ -171,6 +173,9 @@ struct StepArgs {
     int cs_rec, cs_pat, cs_sh, cs_xu, cs_X, cs_lo, cs_vo, cs_nc, cs_slot, cs_total;
     int64_t n_partials;     // partial sums per buffer (the grid-resident mode double-buffers them)
     unsigned int *gbar;
+    // self-test of the tile kernel's own bounded wait: 1 + the tile whose node staging the
+    // kernel leaves out (so that the wait for it runs out); 0 = none (every normal launch)
+    int stage_skip;
 };
 
 // kernel launchers (tled_kernels.cu); npe 4 or 8, or 0 for a batch mixing both element types

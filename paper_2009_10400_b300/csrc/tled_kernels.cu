@@ -64,9 +64,14 @@ __device__ __forceinline__ void add_ff(float &hi, float &lo, float d) {
 
 // Per-scenario values of one step: time, step size, damping and Prony
 // coefficients, and the heat sources' centres c(t) = c0 + v t and powers.
+// With mechanical subcycling (n_sub > 1) a step is a mechanical substep: every
+// substep advances u by dt; the last of each group of n_sub (thermal = 1)
+// also advances T, Omega and the dose by the thermal step dt_th = n_sub dt,
+// with the sources at the group's start time t_th (explicit in T(t_th)).
 struct ScenStep {
-    double t, dt;
-    float dtf, inv_dt, damp_a, damp_b, Qm;
+    double t, dt, dt_th;
+    float dtf, inv_dt, damp_a, damp_b, Qm, dtf_th;
+    int thermal;
     float pr_a[4], pr_b[4];
     int n;
     int sph;  // 1 if a source is a uniform sphere
@@ -79,11 +84,17 @@ struct ScenStep {
 // a group; thread `lane` handles source `lane`, lane 0 the scalars (no barrier inside).
 __device__ __forceinline__ void prepare_scen(const StepArgs &A, int s, int k, ScenStep &P, int lane, int nlanes) {
     const ScenDev &D = A.scn[s];
-    const double t = A.scn_time[s] + (double)(A.scn_step[s] + k) * D.dt;  // t0 + n dt, no accumulation
+    const int64_t n = A.scn_step[s] + k;
+    const double t = A.scn_time[s] + (double)n * D.dt;  // t0 + n dt, no accumulation
+    // the thermal step this (sub)step belongs to starts at t_th; sources are evaluated there
+    const double t_th = D.n_sub > 1 ? A.scn_time[s] + (double)(n - n % D.n_sub) * D.dt : t;
     if (lane == 0) {
         P.t = t;
         P.dt = D.dt;
         P.dtf = D.dtf;
+        P.dt_th = D.dt_th;
+        P.dtf_th = D.dtf_th;
+        P.thermal = D.n_sub <= 1 || n % D.n_sub == D.n_sub - 1;
         P.inv_dt = D.inv_dt;
         P.damp_a = D.damp_a;
         P.damp_b = D.damp_b;
@@ -98,13 +109,13 @@ __device__ __forceinline__ void prepare_scen(const StepArgs &A, int s, int k, Sc
     }
     for (int q = lane; q < D.n_src; q += nlanes) {
         const double *p = A.src + kSrcRow * (int64_t)(D.src_off + q);
-        P.cx[q] = (float)(p[0] + p[3] * t);
-        P.cy[q] = (float)(p[1] + p[4] * t);
-        P.cz[q] = (float)(p[2] + p[5] * t);
+        P.cx[q] = (float)(p[0] + p[3] * t_th);
+        P.cy[q] = (float)(p[1] + p[4] * t_th);
+        P.cz[q] = (float)(p[2] + p[5] * t_th);
         const bool sphere = p[10] == 1.0;
         P.inv2s2[q] = sphere ? 0.f : (float)(0.5 / (p[6] * p[6]));
         P.r2[q] = sphere ? (float)(p[6] * p[6]) : INFINITY;
-        P.P[q] = (t >= p[8] && t < p[9]) ? (float)p[7] : 0.f;
+        P.P[q] = (t_th >= p[8] && t_th < p[9]) ? (float)p[7] : 0.f;
     }
 }
 
@@ -168,11 +179,11 @@ __device__ __forceinline__ void node_advance(const StepArgs &A, const ScenStep &
     const unsigned mask = __float_as_uint(nc.z);
     const bool comp = (A.flags & TLED_COMPENSATED) != 0;
     const float dt = S.dtf;
-    if (A.cem && dose) {  // CEM43 dose (Sapareto-Dewey) at T(t): dt R^(43 - T) / 60 minutes, R = 0.5 at or
-                  // above 43 C, 0.25 below; FP64 (single problems)
+    if (A.cem && dose && S.thermal) {  // CEM43 dose (Sapareto-Dewey) at T(t): dt R^(43 - T) / 60 minutes,
+                  // R = 0.5 at or above 43 C, 0.25 below; FP64 (single problems)
         const double T = A.T0 + ((double)xu.w + (double)lo.w);
         const double x = T - 43.0;  // R^(43 - T) = 2^(x) or 4^(x)
-        A.cem[g] += S.dt * exp2(T >= 43.0 ? x : 2.0 * x) / 60.0;
+        A.cem[g] += S.dt_th * exp2(T >= 43.0 ? x : 2.0 * x) / 60.0;
     }
     // current position for the heat source (state at t)
     const float px = X.x + (xu.x + lo.x), py = X.y + (xu.y + lo.y), pz = X.z + (xu.z + lo.z);
@@ -221,15 +232,16 @@ __device__ __forceinline__ void node_advance(const StepArgs &A, const ScenStep &
             Q += S.P[s] * __expf(-(dx * dx + dy * dy + dz * dz) * S.inv2s2[s]);
         }
     }
-    if (!(mask & TLED_FIX_T)) {
-        const float dth = dt * iC * (-f.w + X.w * Q - nc.w * (theta - A.theta_a));
+    const float dtt = S.dtf_th;
+    if (!(mask & TLED_FIX_T) && S.thermal) {
+        const float dth = dtt * iC * (-f.w + X.w * Q - nc.w * (theta - A.theta_a));
         if (comp)
             add_ff(th, tl, dth);
         else
             th += dth;
     }
     // Arrhenius damage integral, explicit in T(t); exp(ln A - Ea/(R T)) avoids A > FLT_MAX
-    const float Om = vo.w + dt * __expf(A.lnA - __fdividef(A.Ea_R, theta + A.T0_K));
+    const float Om = S.thermal ? vo.w + dtt * __expf(A.lnA - __fdividef(A.Ea_R, theta + A.T0_K)) : vo.w;
     if (!(isfinite(th) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) {
         atomicOr(A.status, kStatusNaN);
         atomicMin(A.status + 2, (unsigned)g);
@@ -792,7 +804,7 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);  // [0] element buffer, [2] nodes, [3] node state
     const int G = gridDim.x;
 
-    const int n_tiles = *A.n_active;  // tiles of unfinished scenarios form a prefix
+    const int n_tiles = min(*A.n_active, A.n_tiles);  // tiles of unfinished scenarios form a prefix
     TileInfo T{};
     int scn = 0;
     if ((int)blockIdx.x < n_tiles) {
@@ -805,7 +817,7 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
         s_abort = 0;
         if ((int)blockIdx.x < n_tiles) {
             stage_elem(A, blockIdx.x, smem, &bar[0]);
-            stage_nodes<NPE>(A, T, smem, &bar[2]);
+            if (A.stage_skip != 1 + (int)blockIdx.x) stage_nodes<NPE>(A, T, smem, &bar[2]);
         }
     }
     __syncthreads();  // barrier init visible to all
@@ -835,15 +847,18 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
             cur_scn = scn;
         }
         // ---- 1. structure record, interior nodes and shared-node lists (bulk copies); then the
-        //         shared nodes' (u, theta, X0) by 16-byte asynchronous copies (mostly L2 hits)
-        bool ok = mbar_wait(&bar[2], i & 1);
-        for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
-            const int64_t g = s_shg[l - T.n_int];
-            cp_async16(&s_xu[l], &A.xu[g]);
-            if constexpr (!BRICK) cp_async16(&s_X[l], &A.X0[g]);  // bricks: only interior X0 is read
+        //         shared nodes' (u, theta, X0) by 16-byte asynchronous copies (mostly L2 hits).
+        //         A thread reads the shared-node list only once it has seen that copy complete.
+        const bool ok2 = mbar_wait(&bar[2], i & 1);
+        if (ok2) {
+            for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
+                const int64_t g = s_shg[l - T.n_int];
+                cp_async16(&s_xu[l], &A.xu[g]);
+                if constexpr (!BRICK) cp_async16(&s_X[l], &A.X0[g]);  // bricks: only interior X0 is read
+            }
         }
-        ok = mbar_wait(&bar[0], i & 1) && ok;
-        if (!ok) {
+        const bool ok0 = mbar_wait(&bar[0], i & 1);
+        if (!(ok0 && ok2)) {
             atomicOr(A.status, kStatusTimeout);
             s_abort = 1;
         }
@@ -859,7 +874,13 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
         }
         cp_async_wait_all();
         __syncthreads();
-        if (s_abort) return;
+        if (s_abort) {  // the status says why; no copy of this CTA may still be in flight when it leaves
+            if (threadIdx.x == 0) {
+                mbar_wait(&bar[0], i & 1);
+                mbar_wait(&bar[2], i & 1);
+            }
+            return;
+        }
         if (threadIdx.x == 0) {
             fence_proxy_async();
             if (ns_smem) {
@@ -879,11 +900,15 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
         }
         __syncthreads();
         // ---- 4. fixed-order gather into nodes, nodal update; shared nodes: partial sum
+        bool ok3 = true;
         if (ns_smem) {
-            if (!mbar_wait(&bar[3], ph_s)) atomicOr(A.status, kStatusTimeout);
-            ph_s ^= 1;
+            ok3 = mbar_wait(&bar[3], ph_s);
+            if (!ok3) {
+                atomicOr(A.status, kStatusTimeout);
+                s_abort = 1;
+            }
         }
-        for (int l = threadIdx.x; l < T.nl; l += kBlock) {
+        for (int l = threadIdx.x; l < T.nl && ok3; l += kBlock) {
             const float4 acc = gather_node(slot, s_code, s_row, l);
             if (l < T.n_int) {
                 const int64_t g = (int64_t)T.ib + l;
@@ -899,6 +924,11 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
             }
         }
         __syncthreads();
+        if (s_abort) {  // a node-state copy timed out: wait (bounded) for it, then leave
+            if (threadIdx.x == 0) mbar_wait(&bar[3], ph_s);
+            return;
+        }
+        ph_s ^= (uint32_t)ns_smem;
         // ---- 5. stage the next tile's element record (into the consumed slot buffer),
         //         structure record, interior nodes and shared-node lists
         if (threadIdx.x == 0 && has_next) {
@@ -918,7 +948,7 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
 // previous chunk's (once per launch for a single problem).
 __global__ void __launch_bounds__(256) shared_step_kernel(const StepArgs A, const int k) {
     __shared__ ScenStep S;
-    const int64_t n_sh = A.n_active[1];  // shared nodes of unfinished scenarios form a prefix
+    const int64_t n_sh = min((int64_t)A.n_active[1], A.n_shared);  // shared nodes of unfinished scenarios: a prefix
     const bool multi = A.n_scn > 1;      // a batch: nodes carry their scenario
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int cur = -1;

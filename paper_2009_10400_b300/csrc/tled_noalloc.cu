@@ -2,10 +2,9 @@
 // (tled_get_stats_noalloc in include/tled.h).
 //
 // Some callers cannot allocate device memory at the moment they want the
-// diagnostics: code that runs while a CUDA graph is being captured (cudaMalloc
-// is not permitted during capture), real-time loops where an allocation would
-// synchronise the device, and processes whose device memory is fully reserved
-// by another framework's caching allocator.  For them the reduction's block
+// diagnostics: real-time loops in which an allocation would synchronise the
+// device or take an unbounded time, and processes whose device memory is fully
+// reserved by another framework's caching allocator.  For them the reduction's block
 // partial sums live in this file-scope array instead of the caller's
 // workspace.  It is kNoAllocMaxBlocks x 8 doubles (18,944 bytes) and stays
 // resident on every GPU that loads the library until the process exits.
@@ -25,7 +24,9 @@ double *g_dev_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on `device`.  The host-side name of the
 // array is only a stand-in, so the address is looked up once per device (with
-// that device current) and cached.  The caller must have made `device`
+// that device current) and cached for the process.  A cudaDeviceReset of the
+// device ends the context that address belongs to, so the cached address is
+// stale afterwards (the header says so).  The caller must have made `device`
 // current.  Returns cudaSuccess or the lookup's error.
 cudaError_t noalloc_scratch(int device, double **ptr) {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;

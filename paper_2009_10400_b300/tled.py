@@ -51,7 +51,7 @@ class Source(C.Structure):
 class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("dt_safety", C.c_double), ("gamma", C.c_double), ("mass_scale", C.c_double),
                 ("kappa_hg", C.c_double), ("kappa_hgT", C.c_double), ("flags", C.c_uint32),
-                ("tile_elems", C.c_int32)]
+                ("tile_elems", C.c_int32), ("n_sub", C.c_int32), ("pad", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -299,8 +299,8 @@ class Solver:
         self._check(lib().tled_set_probes(self.h, xyz.shape[0], _p(xyz)))
 
     def set_params(self, dt=0.0, dt_safety=0.8, gamma=0.0, mass_scale=1.0, kappa_hg=0.1, kappa_hgT=0.1,
-                   flags=EXPANSION | COMPENSATED, tile_elems=0):
-        p = Params(dt, dt_safety, gamma, mass_scale, kappa_hg, kappa_hgT, flags, tile_elems)
+                   flags=EXPANSION | COMPENSATED, tile_elems=0, n_sub=1):
+        p = Params(dt, dt_safety, gamma, mass_scale, kappa_hg, kappa_hgT, flags, tile_elems, n_sub, 0)
         self._check(lib().tled_set_params(self.h, C.byref(p)))
 
     def workspace_size(self) -> int:
@@ -339,7 +339,7 @@ class Solver:
             flags = default_flags(prob)
         s.set_params(dt=float(prob.dt if dt is None else dt), dt_safety=prob.dt_safety, gamma=prob.gamma,
                      mass_scale=prob.mass_scale, kappa_hg=prob.kappa_hg, kappa_hgT=prob.kappa_hgT, flags=flags,
-                     tile_elems=tile_elems)
+                     tile_elems=tile_elems, n_sub=prob.n_sub)
         if probes is not None:
             s.set_probes(probes)
         return s

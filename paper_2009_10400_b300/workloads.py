@@ -75,7 +75,8 @@ class Problem:
                                   # mechanical step (R17 mass scaling, needs a fixed dt)
     kappa_hg: float = 0.1
     kappa_hgT: float = 0.1
-    dt: float = 0.0               # 0 = use the stable step
+    dt: float = 0.0               # 0 = use the stable step (with n_sub > 1: the thermal step)
+    n_sub: int = 1                # mechanical substeps per thermal step (subcycling)
     dt_safety: float = 0.8
     sources: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 11)))
     mask: Optional[np.ndarray] = None     # (nn,) uint8
@@ -265,8 +266,8 @@ def block_h8(n=128, seed=3, n_steps=5000, h=1e-3, noise=0.1, n_sources=4):
     mat = _material(conn.shape[0], rng, noise=noise)
     src = [source(rng.uniform(L / 4, 3 * L / 4, 3), rng.uniform(2e6, 8e6)) for _ in range(n_sources)]
     mask = np.where(np.isclose(X[:, 2], 0.0), MASK_U, 0).astype(np.uint8)
-    return Problem(name=f"block_h8_{n}", npe=8, X=X, conn=conn, **mat, sources=src, mask=mask,
-                   n_steps=n_steps)
+    name = f"block_h8_{n}" if h == 1e-3 else f"block_h8_{n}_h{h * 1e3:g}mm"
+    return Problem(name=name, npe=8, X=X, conn=conn, **mat, sources=src, mask=mask, n_steps=n_steps)
 
 
 def ellipsoid_t4(seed=2, spacing=3.7e-3, semi_axes=(0.075, 0.05, 0.04), n_steps=10000,

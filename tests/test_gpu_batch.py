@@ -43,7 +43,8 @@ def test_batch_h8_each_scenario_matches_oracle():
     tled = _tled()
     scen = _scenarios_h8()
     n_steps = [300, 120, 210]
-    dts = [None, 2.0e-4, None]
+    # the oracle's own stable step (R16) where no step is given
+    dts = [oracle.OracleModel(p).dt if dt is None else dt for p, dt in zip(scen, [None, 2.0e-4, None])]
     b = tled.Batch()
     for p, n, dt in zip(scen, n_steps, dts):
         b.add(p, n, dt=dt)
@@ -56,7 +57,8 @@ def test_batch_h8_each_scenario_matches_oracle():
         info = b.scenario(i)
         assert info["steps"] == n and info["nodes"] == p.nn
         sl = slice(info["node_off"], info["node_off"] + info["nodes"])
-        ref = _oracle_final(p, n, b.scenario_dt(i))
+        assert b.scenario_dt(i) == dts[i]
+        ref = _oracle_final(p, n, dts[i])
         c = compare(u[sl], T[sl], d[sl], ref.u, ref.T, ref.Omega)
         assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E and c["d_abs"] <= TOL_DAMAGE, (i, c)
 
@@ -73,9 +75,10 @@ def test_batch_mixed_h8_t4_matches_oracle():
     n_steps = [160, 240, 90, 200]
     for p in scen[2:]:  # the planning workloads' fixed dt with mass scaling and damping
         p.dt, p.gamma, p.mass_scale = 0.01, 5.0, -1.0  # R17, derived by the library and the oracle each
+    dts = [p.dt if p.dt > 0 else oracle.OracleModel(p).dt for p in scen]  # the oracle's stable step (R16)
     b = tled.Batch()
-    for p, n in zip(scen, n_steps):
-        b.add(p, n, dt=p.dt)
+    for p, n, dt in zip(scen, n_steps, dts):
+        b.add(p, n, dt=dt)
     b.init()
     assert b.plan_info()["npe"] == 0
     assert b.run() == max(n_steps)
@@ -84,16 +87,17 @@ def test_batch_mixed_h8_t4_matches_oracle():
     for i, (p, n) in enumerate(zip(scen, n_steps)):
         info = b.scenario(i)
         sl = slice(info["node_off"], info["node_off"] + info["nodes"])
-        ref = _oracle_final(p, n, b.scenario_dt(i))
+        ref = _oracle_final(p, n, dts[i])
         c = compare(u[sl], T[sl], d[sl], ref.u, ref.T, ref.Omega)
         assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E and c["d_abs"] <= TOL_DAMAGE, (i, c)
 
 def test_batch_t4_matches_single_runs():
     tled = _tled()
     probs = [W.cube_t4(n=4, seed=40), W.cube_t4(n=5, seed=41)]
+    dts = [oracle.OracleModel(p).dt for p in probs]
     b = tled.Batch()
-    for p in probs:
-        b.add(p, 150)
+    for p, dt in zip(probs, dts):
+        b.add(p, 150, dt=dt)
     b.init()
     b.run()
     b.sync()
@@ -101,7 +105,7 @@ def test_batch_t4_matches_single_runs():
     for i, p in enumerate(probs):
         info = b.scenario(i)
         sl = slice(info["node_off"], info["node_off"] + info["nodes"])
-        ref = _oracle_final(p, 150, b.scenario_dt(i))
+        ref = _oracle_final(p, 150, dts[i])
         assert np.linalg.norm(T[sl] - ref.T) / np.linalg.norm(ref.T - 37) <= TOL_E
 
 
@@ -147,8 +151,8 @@ def test_probes_match_oracle_off_centroid(kind):
     rng = np.random.default_rng(23)
     lo, hi = p.X.min(0), p.X.max(0)
     pts = lo + (hi - lo) * rng.uniform(0.1, 0.9, (500, 3))
-    s = tled.Solver.from_problem(p, probes=pts)
-    m = oracle.OracleModel(p, dt=s.get_dt()[0])
+    m = oracle.OracleModel(p)
+    s = tled.Solver.from_problem(p, probes=pts, dt=m.dt)
     st = W.random_state(p, 24, theta_scale=20.0)
     st["Omega"] = rng.uniform(0.0, 3.0, p.nn)
     s.set_state(st["u"], st["v"], st["T"], st["Omega"], st["visc"])
@@ -158,7 +162,7 @@ def test_probes_match_oracle_off_centroid(kind):
     np.testing.assert_allclose(pr[0], T_o, rtol=0, atol=2e-6 * np.ptp(st["T"]))
     np.testing.assert_allclose(pr[1], d_o, rtol=0, atol=2e-6)
     # a trajectory: both sides step 300 times from rest
-    s2 = tled.Solver.from_problem(p, probes=pts)
+    s2 = tled.Solver.from_problem(p, probes=pts, dt=m.dt)
     o = m.init_state()
     m.step(o, 300)
     s2.step(300)
@@ -173,14 +177,14 @@ def test_probes_match_oracle_off_centroid(kind):
 def test_autotune_then_parity():
     tled = _tled()
     p = W.block_h8(n=12, h=4e-3)
-    s = tled.Solver.from_problem(p)
+    m = oracle.OracleModel(p)
+    s = tled.Solver.from_problem(p, dt=m.dt)
     ch = s.autotune(trial_steps=10)
     assert ch["tile_elems"] in (256, 192, 128) and ch["ctas"] >= 1 and not ch["cached"]
     s2 = tled.Solver.from_problem(p)
     assert s2.autotune(trial_steps=10)["cached"]
     # the cached choice includes the step mode (streamed, resident or grid-resident)
     assert (s2.resident, s2.grid_resident) == (s.resident, s.grid_resident)
-    m = oracle.OracleModel(p, dt=s.get_dt()[0])
     o = m.init_state()
     m.step(o, 200)
     s.step(200)

@@ -23,4 +23,30 @@ def test_bounded_waits_report_timeout_and_the_context_recovers():
     ref.sync()
     for a, b in ((s.displacement(), ref.displacement()), (s.temperature(), ref.temperature())):
         assert np.array_equal(a, b)
-    assert s.selftest_wait(2) == tled.E_ARG
+    assert s.selftest_wait(3) == tled.E_ARG
+    assert s.selftest_wait(2) == tled.E_STATE  # the resident mode has no tile kernel launch
+
+
+def test_tile_kernel_timeout_path_leaves_cleanly():
+    """The streamed step's tile kernel with one tile's node staging left out: the
+    CTA that holds the tile sees its bounded mbarrier wait run out, reads none of
+    the missing lists, skips its element pass and leaves after waiting (bounded)
+    for its own copies; the library reports E_TIMEOUT and clears it, and after
+    the state is set again the context steps bitwise like a fresh one."""
+    from paper_2009_10400_b300 import tled
+    prob = W.cube_h8(n=10)
+    flags = tled.default_flags(prob) | tled.STREAMED
+    s = tled.Solver.from_problem(prob, flags=flags)
+    assert not s.resident and not s.grid_resident
+    assert s.plan_info()["n_tiles"] > 1
+    assert s.selftest_wait(2) == tled.E_TIMEOUT
+    z3, z = np.zeros((prob.nn, 3)), np.zeros(prob.nn)
+    s.set_state(z3, z3, np.full(prob.nn, prob.T0), z, None)
+    s.step(40)
+    s.sync()
+    ref = tled.Solver.from_problem(prob, flags=flags)
+    ref.step(40)
+    ref.sync()
+    for a, b in ((s.displacement(), ref.displacement()), (s.temperature(), ref.temperature()),
+                 (s.damage(), ref.damage())):
+        assert np.array_equal(a, b)

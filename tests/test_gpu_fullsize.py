@@ -104,7 +104,8 @@ def test_planning_batch_256_single_step_sampled():
         p, st = scen[i], states[i]
         info = b.scenario(i)
         off = info["node_off"]
-        m = oracle.OracleModel(p, dt=b.scenario_dt(i))
+        m = oracle.OracleModel(p)  # the scenario's fixed dt (0.01 s) and the oracle's own R17 mass scale
+        assert b.scenario_dt(i) == m.dt
         os_ = m.state_from(**st, t=0.05, step=5)
         nodes = np.sort(rng.choice(p.nn, min(256, p.nn), replace=False))
         ou, oT, oO = m.step_nodes(os_, nodes)

@@ -343,7 +343,9 @@ def test_energy_balance_on_gpu():
         s.step(49)
     E = np.array(E)
     assert np.ptp(E) / E[0] < 1e-2
-    ref = p9_energy_history(oracle.OracleModel(p, dt=s.get_dt()[0]), p, u0, 30, 50)
+    m = oracle.OracleModel(p)
+    assert s.get_dt()[0] == pytest.approx(m.dt, rel=1e-12)  # both derive the stable step (R16) on their own
+    ref = p9_energy_history(m, p, u0, 30, 50)
     np.testing.assert_allclose(E, ref, rtol=1e-4)
 
 def test_inversion_is_reported():
@@ -361,3 +363,28 @@ def test_inversion_is_reported():
     with pytest.raises(tled.TledError) as ei:
         s.sync()
     assert ei.value.code == tled.E_INVERTED
+
+
+@pytest.mark.parametrize("n_sub", [3, 8])
+def test_subcycled_trajectory_matches_oracle(n_sub):
+    """Mechanical subcycling (study f4): n_sub mechanical substeps per thermal
+    step of 4 x the stable step, coupled heating with thermal expansion and
+    Prony viscosity, against the oracle's own subcycled step
+    (ora_step_subcycled); compared after every 20 thermal steps."""
+    tled = _tled()
+    p = W.cube_h8(n=6, jitter=0.15, seed=61)
+    p.sources = np.array([W.source((0.02, 0.025, 0.03), 9e6, sigma=6e-3, vel=(0.01, 0.0, -0.005))])
+    m1 = oracle.OracleModel(p)  # the stable (mechanical) step
+    p.n_sub, p.dt = n_sub, 0.9 * n_sub * m1.dt
+    m = oracle.OracleModel(p)
+    g = tled.Solver.from_problem(p)
+    assert g.get_dt()[0] == pytest.approx(p.dt / n_sub, rel=1e-15)
+    s = m.init_state()
+    for _ in range(5):
+        m.step_thermal(s, 20)
+        g.step(20 * n_sub)
+        g.sync()
+        c = compare(g.displacement(), g.temperature(), g.damage(), s.u, s.T, s.Omega, p.T0)
+        assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E and c["d_abs"] <= TOL_DAMAGE, c
+    print(f"subcycled n_sub={n_sub}", c)
+    assert s.T.max() - p.T0 > 0.05 and np.abs(s.u).max() > 1e-9

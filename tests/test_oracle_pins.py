@@ -751,3 +751,76 @@ def test_mass_scale_for_fixed_step():
     m = oracle.OracleModel(p, dt=dt)
     m.stable_dt(0.8)
     np.testing.assert_allclose(0.8 * m.dt_mech, dt, rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# mechanical subcycling (study f4): reductions to the plain step
+# ---------------------------------------------------------------------------
+def test_subcycling_with_one_substep_is_the_plain_step():
+    p = W.cube_h8(n=4, jitter=0.2, seed=12)
+    p.sources = np.array([W.source((0.02, 0.025, 0.03), 8e6, sigma=6e-3, vel=(0.01, 0, 0))])
+    m = oracle.OracleModel(p)
+    st = W.random_state(p, 5, u_scale=1e-3)
+    a, b = m.state_from(**st), m.state_from(**st)
+    m.step(a, 25)
+    m.step_thermal(b, 25)
+    for f in ("u", "u_prev", "T", "Omega", "visc", "cem"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+
+
+def test_subcycling_thermal_part_is_the_plain_thermal_step():
+    """Displacements held at zero (every component prescribed, no expansion): the
+    subcycled temperature, damage and dose after N thermal steps are exactly
+    those of N plain steps of the thermal step (the substeps change nothing the
+    heat equation sees, and T advances once per thermal step, explicitly)."""
+    p = W.cube_h8(n=4, jitter=0.2, seed=13)
+    p.mask[:] = W.MASK_U
+    p.expansion = False
+    p.sources = np.array([W.source((0.02, 0.025, 0.03), 8e6, sigma=6e-3, vel=(0.01, -0.02, 0))])
+    p.dt, p.n_sub = 2e-3, 7
+    sub = oracle.OracleModel(p)
+    p1 = W.cube_h8(n=4, jitter=0.2, seed=13)
+    p1.mask[:] = W.MASK_U
+    p1.expansion = False
+    p1.sources = p.sources
+    p1.dt = 2e-3
+    plain = oracle.OracleModel(p1)
+    a, b = sub.init_state(), plain.init_state()
+    a.T[:] = b.T[:] = 37.0 + np.linspace(0, 8, p.nn)
+    sub.step_thermal(a, 30)
+    plain.step(b, 30)
+    for f in ("T", "Omega", "cem"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    np.testing.assert_array_equal(a.u, 0.0)
+    assert a.step == 30 * 7 and a.t == pytest.approx(30 * 2e-3, rel=1e-12)
+    assert a.T.max() > 37.5
+
+
+def test_subcycling_mechanical_part_is_the_plain_substep():
+    """No heat (no sources or perfusion, uniform T = T0): N thermal steps of n_sub
+    substeps move the body exactly as N n_sub plain steps of the substep
+    (Prony recurrence, damping and Eq. 27 over the substep; the prescribed
+    displacement ramp at each substep's end)."""
+    def problem(**kw):
+        p = W.cube_h8(n=3, jitter=0.15, seed=14)
+        p.sources = np.zeros((0, 11))
+        p.wbcb, p.gamma = 0.0, 3.0
+        top = p.X[:, 2] > 0.042  # the top layer of nodes (jittered around z = 5 cm)
+        p.mask[top] = W.MASK_U
+        p.ubar = np.zeros((p.nn, 3))
+        p.ubar[top, 2] = 2e-3
+        p.ramp_time = 0.02
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    n_sub, dts = 5, 2.5e-3
+    sub = oracle.OracleModel(problem(dt=dts, n_sub=n_sub))
+    plain = oracle.OracleModel(problem(dt=dts / n_sub))
+    a, b = sub.init_state(), plain.init_state()
+    sub.step_thermal(a, 12)
+    plain.step(b, 12 * n_sub)
+    for f in ("u", "u_prev", "visc"):
+        np.testing.assert_array_equal(getattr(a, f), getattr(b, f), err_msg=f)
+    assert a.t == b.t
+    assert np.abs(a.u).max() > 1e-3  # the ramp has moved the top face and the body follows

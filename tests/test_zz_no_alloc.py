@@ -1,9 +1,9 @@
 """The allocation-free diagnostics entry point (tled_get_stats_noalloc).
 
 It exists for callers that cannot allocate device memory when they need the
-numbers (inside CUDA graph capture, in real-time loops, or with all device
-memory held by another allocator): its scratch is a static device array, so
-it must agree with the workspace-based tled_get_stats.  This file is named to
+numbers (real-time loops, or all device memory held by another allocator):
+its scratch is a static device array, so it must agree with the
+workspace-based tled_get_stats.  This file is named to
 be collected last; it also passes when run alone in a fresh process.
 """
 import ctypes as C
@@ -50,3 +50,9 @@ def test_noalloc_stats_match_workspace_stats_twice():
     s.stats_noalloc(out, n_blocks=7)
     s.sync()
     _close(out.cpu().numpy(), expect)
+    # an output in host memory (pageable or pinned), passed straight through the C ABI,
+    # is refused by the host-side pointer check before anything is enqueued
+    for host in (torch.zeros(6, dtype=torch.float64), torch.zeros(6, dtype=torch.float64).pin_memory()):
+        rc = tled.lib().tled_get_stats_noalloc(s.h, 0, C.c_void_p(host.data_ptr()))
+        assert rc == tled.E_ARG, rc
+    s.sync()  # nothing was launched: the stream and the status are clean
