@@ -647,14 +647,14 @@ def run_surrogate_inference(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     P = args.sur_grid ** 3
-    sur = surrogate.Surrogate(n_out=2 * P, width=512, depth=6, members=args.sur_members, max_batch=4096)
+    sur = surrogate.Surrogate(n_out=2 * P, width=512, depth=6, members=args.sur_members, max_batch=4096,
+                              per_power=False)
     rng = np.random.default_rng(0)
-    for net in sur.members:
-        net.set_params(surrogate.he_init(sur.dims, rng))
+    for k in range(args.sur_members):  # seeded He-normal weights (throughput does not depend on them)
+        sur.engine.set_member_params(k, np.concatenate(
+            [np.concatenate([rng.normal(0.0, np.sqrt(2.0 / K), N * K), np.zeros(N)])
+             for K, N in zip(sur.dims[:-1], sur.dims[1:])]))
     dev = "cuda:0"
-    sur._scale = torch.ones(2 * P, device=dev)
-    sur._shift = torch.zeros(2 * P, device=dev)
-    sur._offset = torch.zeros(2 * P, device=dev)
     Xd = torch.tensor(W.sample_scenarios(4096, seed=7), dtype=torch.float32, device=dev)
     for _ in range(max(args.warmup, 3)):
         sur.predict_device(Xd, P, args.sur_tol)

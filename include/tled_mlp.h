@@ -76,7 +76,7 @@ int tled_mlp_train_step_rows(tled_mlp *m, const float *x, const float *t, const 
  *   mean [B][n_out]  ensemble mean of z
  *   std  [B][n_out]  population standard deviation of z (two-pass)
  *   spread [B]       max of std over outputs [0, n_spread)
- *   fallback [B]     1 where spread > tol, else 0 (uint8)
+ *   fallback [B]     1 where spread > tol, else 0 (uint8; a negative tol flags every row)
  * Any of the four outputs may be NULL.  n_out must be a multiple of 4 and y,
  * mean and std 16-byte aligned (rows are read and written as float4).  Used to accept a surrogate answer or
  * send the scenario back to the solver.  Errors: E_ARG, E_CUDA. */
@@ -90,6 +90,73 @@ int tled_mlp_sync(tled_mlp *m);
  * members of an ensemble side by side); ordering against the previous stream is the
  * caller's.  Errors: E_ARG for a NULL network. */
 int tled_mlp_set_stream(tled_mlp *m, void *cuda_stream);
+
+/* ---- the surrogate: an ensemble of these networks with its data handling ----
+ * (The paper has no learned component; this is the learned extension named in
+ * the header comment above.)  tled_sur holds n_members networks [n_in, width x
+ * (depth - 1), n_out] (tled_mlp_create's limits apply), each with its own CUDA
+ * stream so that the members train and infer side by side; all results are
+ * ordered on the stream given at creation.  Workspace as for the networks
+ * (caller-provided, nothing allocated on the device by the library).
+ * max_rows: largest training set; max_epochs: most epochs of one tled_sur_train. */
+typedef struct tled_sur tled_sur;
+/* Input features (computed by a library kernel before the first layer): every raw
+ * input mapped to v in [-1, 1] (tled_sur_set_inputs), then for every input column j
+ * whose bit is set in enc_cols and every octave f < n_freq the pair sin(pi 2^f v_j),
+ * cos(pi 2^f v_j) -- e.g. the source position, on which the answer depends through a
+ * peak that moves with it; n_freq = 0: the raw inputs only.  n_in <= 32, n_freq <= 12. */
+int tled_sur_create(tled_sur **out, int device, void *cuda_stream, int32_t n_members, int32_t n_in, int32_t width,
+                    int32_t depth, int32_t n_out, int32_t n_T, int32_t max_batch, int64_t max_rows,
+                    int32_t max_epochs, int32_t n_freq, uint32_t enc_cols);
+int tled_sur_destroy(tled_sur *s);
+const char *tled_sur_last_error(const tled_sur *s);
+int tled_sur_workspace_size(tled_sur *s, int64_t *bytes);
+/* place the networks and buffers in the workspace (256-byte aligned) */
+int tled_sur_init(tled_sur *s, void *dev_workspace, int64_t bytes);
+/* inputs mapped to [-1, 1] over [lo, hi] (host float32 [n_in] each; identity until set) */
+int tled_sur_set_inputs(tled_sur *s, const float *lo, const float *hi);
+/* Output transform.  power_col >= 0: the first n_T outputs are temperatures T (C) and
+ * are learned as the rise per unit source power, (T - T_ref) / (x[power_col] /
+ * power_ref) -- the bioheat problem is linear in the source power when c and k do
+ * not depend on T -- and mapped back per row at inference.  Every output is then
+ * standardised: norm 0, per output (mean and standard deviation of its column);
+ * norm 1, mean per output but one scale per group of outputs (the temperatures
+ * [0, n_T), the rest), so that the training loss weighs errors of the same
+ * physical size alike.  Errors: E_ARG. */
+int tled_sur_set_outputs(tled_sur *s, int32_t power_col, float power_ref, float T_ref, int32_t norm);
+/* Train every member from a seeded He-normal initialisation with Adam (beta 0.9,
+ * 0.999, eps 1e-8) at learning rate lr on the mean squared error of the
+ * standardised targets: x [n][n_in] raw inputs and y [n][n_out] outputs in physical
+ * units, both device float32; `epochs` passes, each over a permutation of the rows
+ * (member k's from the splitmix64 stream seeded by `seed`) in mini-batches of
+ * `batch` (a multiple of 128; the last partial batch is dropped).  Each member
+ * replays a CUDA graph of one epoch on its own stream.  loss_history: host float32
+ * [n_members][epochs] of mean training losses, or NULL.  Synchronises.
+ * Errors: E_ARG, E_STATE, E_CUDA. */
+int tled_sur_train(tled_sur *s, const float *x, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
+                   uint64_t seed, float *loss_history);
+/* Ensemble answer for B <= max_batch scenario rows x [B][n_in] (device float32),
+ * enqueued: mean and std [B][n_out] in physical units (population std over the
+ * members), spread [B] = max of std over outputs [0, n_spread), fallback_mask [B]
+ * = 1 where spread > spread_tol_K (those scenarios go to the solver); any output
+ * may be NULL.  Errors: E_ARG, E_STATE. */
+int tled_sur_predict(tled_sur *s, const float *x, int32_t B, int32_t n_spread, float spread_tol_K, float *mean,
+                     float *std, float *spread, uint8_t *fallback_mask);
+/* Calibrate the spread threshold against solver answers y [n][n_out] (device) for
+ * the scenarios x [n][n_in]: the largest threshold tau <= tol_K such that among the
+ * scenarios with spread <= tau at least a `coverage` fraction have max over outputs
+ * [0, n_spread) of |mean - y| <= tol_K; *tau = -1 if none qualifies; *accepted =
+ * the fraction of the n scenarios with spread <= tau.  Synchronises. */
+int tled_sur_calibrate(tled_sur *s, const float *x, const float *y, int64_t n, int32_t n_spread, float tol_K,
+                       float coverage, float *tau, float *accepted);
+/* The threshold rule of tled_sur_calibrate on host arrays spread [n] and err [n]
+ * (no GPU needed): the longest prefix of the scenarios sorted by spread whose
+ * fraction with err <= tol_K is at least `coverage`, capped at tol_K. */
+int tled_sur_spread_threshold(int64_t n, const float *spread, const float *err, float tol_K, float coverage,
+                              float *tau, float *accepted);
+/* member k's network (parameters, gradients, single-member inference) */
+int tled_sur_member(tled_sur *s, int32_t k, tled_mlp **member);
+int tled_sur_sync(tled_sur *s);
 
 #ifdef __cplusplus
 }

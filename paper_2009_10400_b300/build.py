@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libtled.so")
-SOURCES = ["tled_host.cpp", "tled_capi.cpp", "tled_kernels.cu", "tled_noalloc.cu", "mlp_capi.cpp", "mlp_kernels.cu"]
+SOURCES = ["tled_host.cpp", "tled_capi.cpp", "tled_kernels.cu", "tled_noalloc.cu", "mlp_capi.cpp", "mlp_kernels.cu",
+           "sur_capi.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O3", *ARCH, "-lineinfo", "--expt-relaxed-constexpr"]

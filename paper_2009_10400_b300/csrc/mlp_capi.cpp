@@ -337,7 +337,7 @@ int tled_mlp_ensemble(int device, void *stream, int32_t n_members, const float *
                       float *mean, float *std, float *spread, uint8_t *fallback) {
     if (n_out % 4 || ((uintptr_t)mean & 15) || ((uintptr_t)std & 15)) return TLED_E_ARG;  // float4 rows
     if (n_members < 1 || n_members > kMaxMembers || !y || B < 0 || n_out < 1 || n_spread < 0 || n_spread > n_out ||
-        !(tol >= 0) || n_row_scaled < 0 || n_row_scaled > n_out || (row_src && row_stride < 1) ||
+        std::isnan(tol) || n_row_scaled < 0 || n_row_scaled > n_out || (row_src && row_stride < 1) ||
         !std::isfinite(row_mult))
         return TLED_E_ARG;
     EnsembleArgs e{};
@@ -432,3 +432,41 @@ int tled_mlp_sync(tled_mlp *m) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// internal entries for the surrogate engine (sur_capi.cpp)
+// ---------------------------------------------------------------------------
+int tmlp_train_step_graphable(tled_mlp *m, cudaStream_t stream, const float *x, const float *t, const int32_t *rows,
+                              int B, float lr, float *loss, int64_t *t_dev, float *bc_dev) {
+    if (!m || !x || !t || !t_dev || !bc_dev) return fail(m, TLED_E_ARG, "NULL argument");
+    if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
+    if (int rc = check_batch(m, B)) return rc;
+    cudaStream_t keep = m->stream;
+    m->stream = stream;
+    int rc = forward(m, x, rows, B, P<float>(m, m->y));
+    if (!rc) rc = backward(m, t, rows, B, loss);
+    if (!rc) {
+        cudaError_t e = launch_adam_tick(t_dev, bc_dev, stream);
+        for (int l = 0; l < m->L && e == cudaSuccess; l++) {
+            const Layer &ly = m->layer[l];
+            const int64_t n = (int64_t)ly.N * ly.K + ly.N;
+            e = launch_adam(P<float>(m, m->p_w) + ly.poff, P<float>(m, m->p_m) + ly.poff, P<float>(m, m->p_v) + ly.poff,
+                            P<float>(m, m->p_g) + ly.poff, n, lr, 0.9f, 0.999f, 1e-8f, 1.f, 1.f, ly.N, ly.K, ly.Kp,
+                            P<__nv_bfloat16>(m, ly.wb), P<__nv_bfloat16>(m, ly.wt), stream, bc_dev);
+        }
+        if (e != cudaSuccess) rc = fail(m, TLED_E_CUDA, std::string("adam: ") + cudaGetErrorString(e));
+    }
+    m->stream = keep;
+    return rc;
+}
+
+int tmlp_forward_on(tled_mlp *m, cudaStream_t stream, const float *x, int B, float *y) {
+    if (!m || !x || !y) return fail(m, TLED_E_ARG, "NULL argument");
+    if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
+    if (int rc = check_batch(m, B)) return rc;
+    cudaStream_t keep = m->stream;
+    m->stream = stream;
+    const int rc = forward(m, x, nullptr, B, y);
+    m->stream = keep;
+    return rc;
+}

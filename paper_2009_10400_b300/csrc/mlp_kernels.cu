@@ -366,9 +366,14 @@ __global__ void bias_grad_kernel(const __nv_bfloat16 *__restrict__ dzt, int B, i
 // Adam on FP32 master parameters; refresh the bf16 weights W [N][ld] and W^T [ld][N]
 __global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float *__restrict__ v,
                             const float *__restrict__ grad, int64_t n, float lr, float b1, float b2, float eps,
-                            float bc1, float bc2, int N, int K, int ld, __nv_bfloat16 *wb, __nv_bfloat16 *wt) {
+                            float bc1, float bc2, const float *__restrict__ bc, int N, int K, int ld,
+                            __nv_bfloat16 *wb, __nv_bfloat16 *wt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (bc) {  // the bias corrections of the device step counter (graph-captured training)
+        bc1 = bc[0];
+        bc2 = bc[1];
+    }
     const float gr = grad[i];
     const float mi = b1 * m[i] + (1.f - b1) * gr;
     const float vi = b2 * v[i] + (1.f - b2) * gr * gr;
@@ -517,8 +522,143 @@ cudaError_t launch_bias_grad(const __nv_bfloat16 *dzt, int B, int N, float *db, 
 
 cudaError_t launch_adam(float *w, float *m, float *v, const float *grad, int64_t n, float lr, float b1, float b2,
                         float eps, float bc1, float bc2, int N, int K, int ld, __nv_bfloat16 *wb, __nv_bfloat16 *wt,
-                        cudaStream_t s) {
-    adam_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w, m, v, grad, n, lr, b1, b2, eps, bc1, bc2, N, K, ld, wb, wt);
+                        cudaStream_t s, const float *bc) {
+    adam_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w, m, v, grad, n, lr, b1, b2, eps, bc1, bc2, bc, N, K, ld, wb,
+                                                       wt);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// device step counter of Adam, and the surrogate's data kernels
+// ---------------------------------------------------------------------------
+// t += 1; bc = (1 - 0.9^t, 1 - 0.999^t), in FP64 like the host path
+__global__ void adam_tick_kernel(int64_t *t, float *bc) {
+    const int64_t n = ++*t;
+    bc[0] = (float)(1.0 - pow(0.9, (double)n));
+    bc[1] = (float)(1.0 - pow(0.999, (double)n));
+}
+cudaError_t launch_adam_tick(int64_t *t, float *bc, cudaStream_t s) {
+    adam_tick_kernel<<<1, 1, 0, s>>>(t, bc);
+    return cudaGetLastError();
+}
+
+// z[i][j] = (y[i][j] - T_ref) / (x[i][power_col] inv_Pref) for j < n_T, else y[i][j]
+__global__ void sur_transform_kernel(const float *__restrict__ x, int ld_x, const float *__restrict__ y, int64_t n,
+                                     int n_out, int n_T, int power_col, float T_ref, float inv_Pref, float *z) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * n_out;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n_out;
+        const int j = (int)(i % n_out);
+        const float v = y[i];
+        z[i] = (j < n_T && power_col >= 0) ? (v - T_ref) / (x[r * ld_x + power_col] * inv_Pref) : v;
+    }
+}
+// column means and centred sums of squares over n rows (FP64, rows in order), one thread per column
+__global__ void column_stats_kernel(const float *__restrict__ z, int64_t n, int n_out, double *mean, double *m2) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_out) return;
+    double s = 0.0;
+    for (int64_t r = 0; r < n; r++) s += (double)z[r * n_out + j];
+    const double mu = s / (double)n;
+    double q = 0.0;
+    for (int64_t r = 0; r < n; r++) {
+        const double d = (double)z[r * n_out + j] - mu;
+        q += d * d;
+    }
+    mean[j] = mu;
+    m2[j] = q;
+}
+__global__ void standardize_kernel(float *z, int64_t n, int n_out, const float *__restrict__ shift,
+                                   const float *__restrict__ scale) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n * n_out;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(i % n_out);
+        z[i] = (z[i] - shift[j]) / scale[j];
+    }
+}
+// err[r] = max over j < n_cmp of |a[r][j] - b[r][j]|; one block per row
+__global__ void row_max_abs_diff_kernel(const float *__restrict__ a, const float *__restrict__ b, int n_out, int n_cmp,
+                                        float *err) {
+    const int64_t r = blockIdx.x;
+    float m = 0.f;
+    for (int j = threadIdx.x; j < n_cmp; j += blockDim.x) m = fmaxf(m, fabsf(a[r * n_out + j] - b[r * n_out + j]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float q = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) q = fmaxf(q, red[w]);
+        err[r] = q;
+    }
+}
+// out = mean of losses[0..k) (FP64 sum in order)
+__global__ void mean_losses_kernel(const float *losses, int k, float *out) {
+    double s = 0.0;
+    for (int i = 0; i < k; i++) s += losses[i];
+    *out = (float)(s / k);
+}
+
+// Input features of the surrogate: v = (x - shift) * scale for every raw column, then
+// for every column j in enc_cols and octave f < n_freq the pair sin(pi 2^f v_j),
+// cos(pi 2^f v_j); rows [n, n_rows) (padding) are zero.  feat [n_rows][n_feat].
+__global__ void sur_encode_kernel(const float *__restrict__ x, int ld_x, int64_t n, int64_t n_rows, int n_in,
+                                  const float *__restrict__ shift, const float *__restrict__ scale, int n_freq,
+                                  unsigned enc_cols, int n_feat, float *feat) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows * n_feat;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / n_feat;
+        const int c = (int)(i % n_feat);
+        float out = 0.f;
+        if (r < n) {
+            if (c < n_in) {
+                out = (x[r * ld_x + c] - shift[c]) * scale[c];
+            } else {
+                int k = (c - n_in) >> 1;  // which (column, octave) pair
+                const bool cosine = ((c - n_in) & 1) != 0;
+                int j = 0;
+                for (; j < n_in; j++)
+                    if (enc_cols & (1u << j)) {
+                        if (k < n_freq) break;
+                        k -= n_freq;
+                    }
+                const float v = (x[r * ld_x + j] - shift[j]) * scale[j];
+                float sv, cv;
+                sincospif(ldexpf(v, k), &sv, &cv);
+                out = cosine ? cv : sv;
+            }
+        }
+        feat[i] = out;
+    }
+}
+cudaError_t launch_sur_encode(const float *x, int ld_x, int64_t n, int64_t n_rows, int n_in, const float *shift,
+                              const float *scale, int n_freq, unsigned enc_cols, int n_feat, float *feat,
+                              cudaStream_t s) {
+    sur_encode_kernel<<<592, 256, 0, s>>>(x, ld_x, n, n_rows, n_in, shift, scale, n_freq, enc_cols, n_feat, feat);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sur_transform(const float *x, int ld_x, const float *y, int64_t n, int n_out, int n_T,
+                                 int power_col, float T_ref, float inv_Pref, float *z, cudaStream_t s) {
+    sur_transform_kernel<<<1184, 256, 0, s>>>(x, ld_x, y, n, n_out, n_T, power_col, T_ref, inv_Pref, z);
+    return cudaGetLastError();
+}
+cudaError_t launch_column_stats(const float *z, int64_t n, int n_out, double *mean, double *m2, cudaStream_t s) {
+    column_stats_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(z, n, n_out, mean, m2);
+    return cudaGetLastError();
+}
+cudaError_t launch_standardize(float *z, int64_t n, int n_out, const float *shift, const float *scale,
+                               cudaStream_t s) {
+    standardize_kernel<<<1184, 256, 0, s>>>(z, n, n_out, shift, scale);
+    return cudaGetLastError();
+}
+cudaError_t launch_row_max_abs_diff(const float *a, const float *b, int64_t n, int n_out, int n_cmp, float *err,
+                                    cudaStream_t s) {
+    if (n > 0) row_max_abs_diff_kernel<<<(unsigned)n, 256, 0, s>>>(a, b, n_out, n_cmp, err);
+    return cudaGetLastError();
+}
+cudaError_t launch_mean_losses(const float *losses, int k, float *out, cudaStream_t s) {
+    mean_losses_kernel<<<1, 1, 0, s>>>(losses, k, out);
     return cudaGetLastError();
 }
 

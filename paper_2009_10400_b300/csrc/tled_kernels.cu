@@ -305,6 +305,42 @@ __device__ __forceinline__ void wht8x2(float2 *x) {
 // WHT index -> VTK corner (an involution)
 __device__ __forceinline__ constexpr int wht_corner(int i) { return i == 2 ? 3 : i == 3 ? 2 : i == 6 ? 7 : i == 7 ? 6 : i; }
 
+// Corner values of an H8 element (local corner ids cl) transformed against the
+// shape-function sign vectors by Walsh-Hadamard butterflies: (u_x, u_y) and (u_z,
+// theta) in pairs and, with WITH_X, (X, Y) in a pair and Z alone.  Mode i of the
+// transform: 0 the corner sum, 1/2/4 minus the xi/eta/zeta sums, 3/6/5 the xi eta /
+// eta zeta / xi zeta hourglass sums, 7 minus the xi eta zeta sum.
+template <bool WITH_X>
+__device__ __forceinline__ void h8_modes(const int *cl, const float4 *__restrict__ s_xu,
+                                         const float4 *__restrict__ s_X, float *wx, float *wy, float *wz, float *wt,
+                                         float *px, float *py, float *pz) {
+    float2 uxy[8], uzt[8], pxy[8];
+    float qz[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int a = cl[wht_corner(i)];
+        const float4 q = s_xu[a];
+        uxy[i] = make_float2(q.x, q.y);
+        uzt[i] = make_float2(q.z, q.w);
+        if constexpr (WITH_X) {
+            const float4 x = s_X[a];
+            pxy[i] = make_float2(x.x, x.y);
+            qz[i] = x.z;
+        }
+    }
+    wht8x2(uxy); wht8x2(uzt);
+    if constexpr (WITH_X) {
+        wht8x2(pxy); wht8(qz);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        wx[i] = uxy[i].x; wy[i] = uxy[i].y; wz[i] = uzt[i].x; wt[i] = uzt[i].y;
+        if constexpr (WITH_X) {
+            px[i] = pxy[i].x; py[i] = pxy[i].y; pz[i] = qz[i];
+        }
+    }
+}
+
 // NPR: Prony terms (a compile-time count, so that only the terms in use take registers)
 template <int NPR>
 struct ElemIn {
@@ -375,51 +411,25 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
     const float V = E.V, mu = E.mu, kap = E.kap, k1 = E.k1, k2 = E.k2, kc = E.kc, al = E.al;
     const float ax = E.ax, ay = E.ay, az = E.az;
 
-    // ---- corner values and the sums against the shape-function sign vectors
+    // ---- corner values and the sums against the shape-function sign vectors: here the
+    //      constant and linear modes; the H8 hourglass modes are transformed again where
+    //      they are used (from the same shared-memory values, so bitwise the same), which
+    //      keeps them out of the registers the stress evaluation needs
     float G[3][3], gt[3], the;
-    float hu[4][3], ht[4], cX[4][3];  // H8 hourglass projections
+    float hu[4][3], ht[4];  // H8 hourglass modes of u and theta (bricks: kept from this transform)
     if constexpr (NPE == 8) {
-        // (u_x, u_y), (u_z, theta) and (X, Y) transformed in pairs, Z alone
-        float2 uxy[8], uzt[8], pxy[8];
-        float pz[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            const int a = cl[wht_corner(i)];
-            const float4 q = s_xu[a];
-            uxy[i] = make_float2(q.x, q.y);
-            uzt[i] = make_float2(q.z, q.w);
-            if constexpr (!BRICK) {
-                const float4 x = s_X[a];
-                pxy[i] = make_float2(x.x, x.y);
-                pz[i] = x.z;
-            }
-        }
-        wht8x2(uxy); wht8x2(uzt);
-        if constexpr (!BRICK) {
-            wht8x2(pxy); wht8(pz);
-        }
-        float wx[8], wy[8], wz[8], wt[8], px[8], py[8];
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            wx[i] = uxy[i].x; wy[i] = uxy[i].y; wz[i] = uzt[i].x; wt[i] = uzt[i].y;
-            if constexpr (!BRICK) {
-                px[i] = pxy[i].x; py[i] = pxy[i].y;
-            }
-        }
+        float wx[8], wy[8], wz[8], wt[8];
+        h8_modes<false>(cl, s_xu, s_X, wx, wy, wz, wt, nullptr, nullptr, nullptr);
         G[0][0] = -wx[1]; G[0][1] = -wx[2]; G[0][2] = -wx[4];
         G[1][0] = -wy[1]; G[1][1] = -wy[2]; G[1][2] = -wy[4];
         G[2][0] = -wz[1]; G[2][1] = -wz[2]; G[2][2] = -wz[4];
         gt[0] = -wt[1]; gt[1] = -wt[2]; gt[2] = -wt[4];
         the = 0.125f * wt[0];
-        // hourglass vectors xi eta, eta zeta, xi zeta, xi eta zeta
-        hu[0][0] = wx[3]; hu[1][0] = wx[6]; hu[2][0] = wx[5]; hu[3][0] = -wx[7];
-        hu[0][1] = wy[3]; hu[1][1] = wy[6]; hu[2][1] = wy[5]; hu[3][1] = -wy[7];
-        hu[0][2] = wz[3]; hu[1][2] = wz[6]; hu[2][2] = wz[5]; hu[3][2] = -wz[7];
-        ht[0] = wt[3]; ht[1] = wt[6]; ht[2] = wt[5]; ht[3] = -wt[7];
-        if constexpr (!BRICK) {
-            cX[0][0] = px[3]; cX[1][0] = px[6]; cX[2][0] = px[5]; cX[3][0] = -px[7];
-            cX[0][1] = py[3]; cX[1][1] = py[6]; cX[2][1] = py[5]; cX[3][1] = -py[7];
-            cX[0][2] = pz[3]; cX[1][2] = pz[6]; cX[2][2] = pz[5]; cX[3][2] = -pz[7];
+        if constexpr (BRICK) {
+            hu[0][0] = wx[3]; hu[1][0] = wx[6]; hu[2][0] = wx[5]; hu[3][0] = -wx[7];
+            hu[0][1] = wy[3]; hu[1][1] = wy[6]; hu[2][1] = wy[5]; hu[3][1] = -wy[7];
+            hu[0][2] = wz[3]; hu[1][2] = wz[6]; hu[2][2] = wz[5]; hu[3][2] = -wz[7];
+            ht[0] = wt[3]; ht[1] = wt[6]; ht[2] = wt[5]; ht[3] = -wt[7];
         }
     } else {
         float ux[4], uy[4], uz[4], th[4];
@@ -643,6 +653,22 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
         const float khg = A.khg * (kap + (4.f / 3.f) * mu) * V * jn2 * (1.f / 64.f);
         const float khgT = A.khgT * kT * V * jn2 * (1.f / 64.f);
         float qa[4][3], qT[4];
+        // general hexahedra: the hourglass modes of u, theta and X, transformed again from
+        // shared memory (the empty asm keeps the compiler from carrying the first transform's
+        // values across the stress evaluation, where the registers are scarcest)
+        float cX[4][3];
+        if constexpr (!BRICK) {
+            asm volatile("" ::: "memory");
+            float wx[8], wy[8], wz[8], wt[8], px[8], py[8], pz[8];
+            h8_modes<true>(cl, s_xu, s_X, wx, wy, wz, wt, px, py, pz);
+            hu[0][0] = wx[3]; hu[1][0] = wx[6]; hu[2][0] = wx[5]; hu[3][0] = -wx[7];
+            hu[0][1] = wy[3]; hu[1][1] = wy[6]; hu[2][1] = wy[5]; hu[3][1] = -wy[7];
+            hu[0][2] = wz[3]; hu[1][2] = wz[6]; hu[2][2] = wz[5]; hu[3][2] = -wz[7];
+            ht[0] = wt[3]; ht[1] = wt[6]; ht[2] = wt[5]; ht[3] = -wt[7];
+            cX[0][0] = px[3]; cX[1][0] = px[6]; cX[2][0] = px[5]; cX[3][0] = -px[7];
+            cX[0][1] = py[3]; cX[1][1] = py[6]; cX[2][1] = py[5]; cX[3][1] = -py[7];
+            cX[0][2] = pz[3]; cX[1][2] = pz[6]; cX[2][2] = pz[5]; cX[3][2] = -pz[7];
+        }
         if constexpr (BRICK) {  // c_al = 0: gamma_a,al = h_a,al and q_al = sum_b h_b,al u_b
 #pragma unroll
             for (int l = 0; l < 4; l++) {

@@ -32,6 +32,24 @@ _SIGS = {
     "tled_mlp_ensemble": ([C.c_int, C.c_void_p, C.c_int32, C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_void_p,
                            C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_void_p, C.c_int32, C.c_float,
                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "tled_sur_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                         C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_uint32], C.c_int),
+    "tled_sur_destroy": ([C.c_void_p], C.c_int),
+    "tled_sur_last_error": ([C.c_void_p], C.c_char_p),
+    "tled_sur_workspace_size": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "tled_sur_init": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
+    "tled_sur_set_inputs": ([C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+    "tled_sur_set_outputs": ([C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_int32], C.c_int),
+    "tled_sur_train": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
+                        C.POINTER(C.c_float)], C.c_int),
+    "tled_sur_predict": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_void_p,
+                          C.c_void_p, C.c_void_p], C.c_int),
+    "tled_sur_calibrate": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_float,
+                            C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+    "tled_sur_spread_threshold": ([C.c_int64, C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_float, C.c_float,
+                                   C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+    "tled_sur_member": ([C.c_void_p, C.c_int32, C.POINTER(C.c_void_p)], C.c_int),
+    "tled_sur_sync": ([C.c_void_p], C.c_int),
 }
 _ready = False
 
@@ -177,3 +195,109 @@ def ensemble(ys, out_scale=None, out_shift=None, n_spread=0, tol=0.0, device=0, 
     if rc:
         raise TledError(rc, "tled_mlp_ensemble: invalid arguments or CUDA error")
     return mean, std, spread, fb
+
+
+def spread_threshold(spread, err, tol, coverage=1.0):
+    """The library's calibration rule (tled_sur_spread_threshold) on host
+    arrays: returns (tau, accepted fraction); tau = -1 if nothing qualifies."""
+    sp = np.ascontiguousarray(spread, np.float32)
+    er = np.ascontiguousarray(err, np.float32)
+    tau, frac = C.c_float(), C.c_float()
+    fp = C.POINTER(C.c_float)
+    rc = lib().tled_sur_spread_threshold(sp.size, sp.ctypes.data_as(fp), er.ctypes.data_as(fp), float(tol),
+                                         float(coverage), C.byref(tau), C.byref(frac))
+    if rc:
+        raise TledError(rc, "tled_sur_spread_threshold: invalid arguments")
+    return float(tau.value), float(frac.value)
+
+
+class SurrogateEngine:
+    """ctypes handle of a tled_sur (an ensemble of MLPs with its data handling);
+    tensors are PyTorch CUDA float32 (inputs, outputs) on the engine's device."""
+
+    def __init__(self, dims, members, n_T, max_batch, max_rows, max_epochs, device=0, stream=None, n_freq=0,
+                 enc_cols=()):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("the surrogate needs a CUDA device; there is no CPU fallback")
+        self._torch = torch
+        self.dims, self.members, self.max_batch, self.device = list(dims), int(members), int(max_batch), device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        h = C.c_void_p()
+        mask = sum(1 << int(j) for j in enc_cols)
+        rc = lib().tled_sur_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream), self.members, dims[0],
+                                   dims[1], len(dims) - 1, dims[-1], int(n_T), self.max_batch, int(max_rows),
+                                   int(max_epochs), int(n_freq), mask)
+        self.n_feat = dims[0] + 2 * int(n_freq) * len(set(enc_cols))
+        if rc:
+            raise TledError(rc, "tled_sur_create: invalid sizes (widths and outputs multiples of 128, batch of 128)")
+        self.h = h
+        n = C.c_int64()
+        self._check(lib().tled_sur_workspace_size(h, C.byref(n)))
+        self.ws = torch.empty(n.value + 256, dtype=torch.uint8, device=f"cuda:{device}")
+        self._check(lib().tled_sur_init(h, C.c_void_p((self.ws.data_ptr() + 255) & ~255), n.value))
+
+    def _check(self, rc):
+        if rc:
+            raise TledError(rc, lib().tled_sur_last_error(self.h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().tled_sur_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_inputs(self, lo, hi):
+        fp = C.POINTER(C.c_float)
+        lo = np.ascontiguousarray(lo, np.float32)
+        hi = np.ascontiguousarray(hi, np.float32)
+        self._check(lib().tled_sur_set_inputs(self.h, lo.ctypes.data_as(fp), hi.ctypes.data_as(fp)))
+
+    def set_outputs(self, power_col, power_ref, T_ref, norm):
+        self._check(lib().tled_sur_set_outputs(self.h, int(power_col), float(power_ref), float(T_ref), int(norm)))
+
+    def train(self, x, y, epochs, batch, lr, seed):
+        hist = np.zeros((self.members, epochs), np.float32)
+        self._check(lib().tled_sur_train(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0],
+                                         int(epochs), int(batch), float(lr), int(seed),
+                                         hist.ctypes.data_as(C.POINTER(C.c_float))))
+        return hist
+
+    def predict(self, x, n_spread, tol, mean=None, std=None, spread=None, fallback=None):
+        vp = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+        self._check(lib().tled_sur_predict(self.h, C.c_void_p(x.data_ptr()), x.shape[0], int(n_spread), float(tol),
+                                           vp(mean), vp(std), vp(spread), vp(fallback)))
+
+    def calibrate(self, x, y, n_spread, tol, coverage):
+        tau, frac = C.c_float(), C.c_float()
+        self._check(lib().tled_sur_calibrate(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0],
+                                             int(n_spread), float(tol), float(coverage), C.byref(tau),
+                                             C.byref(frac)))
+        return float(tau.value), float(frac.value)
+
+    def member_params(self, k):
+        m = C.c_void_p()
+        self._check(lib().tled_sur_member(self.h, int(k), C.byref(m)))  # dims[0] = n_feat inputs
+        n = C.c_int64()
+        lib().tled_mlp_num_params(m, C.byref(n))
+        p = np.empty(n.value, np.float32)
+        if lib().tled_mlp_get_params(m, p.ctypes.data_as(C.POINTER(C.c_float))):
+            raise TledError(-4, lib().tled_mlp_last_error(m).decode())
+        return p
+
+    def set_member_params(self, k, p):
+        m = C.c_void_p()
+        self._check(lib().tled_sur_member(self.h, int(k), C.byref(m)))
+        p = np.ascontiguousarray(p, np.float32)
+        if lib().tled_mlp_set_params(m, p.ctypes.data_as(C.POINTER(C.c_float))):
+            raise TledError(-4, lib().tled_mlp_last_error(m).decode())
+
+    def sync(self):
+        self._check(lib().tled_sur_sync(self.h))

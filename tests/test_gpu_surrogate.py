@@ -62,6 +62,13 @@ def test_surrogate_learns_and_falls_back():
     out, fb, info = sur.solve(Q[te], P, tol=tol, n=n, dt=dt)
     assert 0 < fb.sum() < len(fb)
     np.testing.assert_allclose(out[fb], Y[te][fb], rtol=0, atol=1e-9)
+    # at the stated tolerance of 1 K (the fallback rule as written: spread > 1 K goes to
+    # the solver): the fraction answered by the surrogate and the worst answered error
+    out1, fb1, info1 = sur.solve(Q[te], P, tol=1.0, n=n, dt=dt)
+    err1 = np.abs(out1[:, :P] - T[te]).max(1)
+    np.testing.assert_allclose(out1[fb1], Y[te][fb1], rtol=0, atol=1e-9)
+    print(f"at 1 K: surrogate answers {np.mean(~fb1):.2f} of the cases, worst answered error "
+          f"{err1[~fb1].max() if (~fb1).any() else 0.0:.3f} K, {len(fb1) / info1['seconds']:.1f} solves/s")
     # calibration against solver answers: with coverage 1, every calibration case
     # whose spread is at or below the threshold meets the tolerance
     tol_c = float(np.median(err))

@@ -174,16 +174,18 @@ def test_batch_planning_keeps_scenarios_apart():
 
 
 def test_surrogate_spread_threshold_rule():
-    """Calibration picks the longest prefix (by spread) whose errors meet the
-    tolerance at the requested coverage, never above the tolerance itself."""
+    """Calibration (the library's host rule, tled_sur_spread_threshold) picks
+    the longest prefix (by spread) whose errors meet the tolerance at the
+    requested coverage, never above the tolerance itself."""
     from paper_2009_10400_b300.surrogate import spread_threshold
+    f32 = lambda v: float(np.float32(v))  # the rule works on float32 arrays
     spread = [0.1, 0.2, 0.3, 0.4, 0.5, 0.6]
     err = [0.5, 0.8, 1.5, 0.9, 2.0, 0.7]
-    assert spread_threshold(spread, err, tol=1.0, coverage=1.0) == (0.2, 2 / 6)
-    assert spread_threshold(spread, err, tol=1.0, coverage=0.75) == (0.4, 4 / 6)
+    assert spread_threshold(spread, err, tol=1.0, coverage=1.0) == (f32(0.2), f32(2 / 6))
+    assert spread_threshold(spread, err, tol=1.0, coverage=0.75) == (f32(0.4), f32(4 / 6))
     assert spread_threshold(spread, [2.0] + err[1:], tol=1.0, coverage=1.0) == (-1.0, 0.0)
     tau, frac = spread_threshold([0.5, 2.0, 3.0], [0.1, 0.1, 0.1], tol=1.0)
-    assert tau == 1.0 and frac == 1 / 3
+    assert tau == 1.0 and frac == f32(1 / 3)
 
 
 def test_cem43_is_refused_in_a_batch():

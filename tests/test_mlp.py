@@ -197,3 +197,67 @@ def test_input_scaling_and_row_gather():
     a.sync()
     b.sync()
     np.testing.assert_array_equal(a.get_params(), b.get_params())
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("norm", [0, 1])
+def test_surrogate_engine_transform_standardisation_and_training(norm):
+    """The surrogate engine (tled_sur): temperatures learned as rise per unit
+    source power and standardised (per output, or one scale per output group),
+    checked through networks whose outputs are known -- all zero (answer: the
+    column means mapped back) and all one (answer: mean + scale); then seeded
+    training is reproducible and fits its data."""
+    import torch
+
+    from paper_2009_10400_b300.mlp import SurrogateEngine
+    rng = np.random.default_rng(11)
+    n, n_in, n_out, n_T = 512, 12, 256, 128
+    dims = [n_in, 128, 128, n_out]
+    X = rng.uniform(0.0, 1.0, (n, n_in))
+    X[:, 0] = rng.uniform(1e6, 1e7, n)  # source power, W/m^3
+    feat = X.copy()
+    feat[:, 0] = (X[:, 0] - 5.5e6) / 4.5e6
+    w1 = rng.normal(size=(n_in, n_out)) / 2  # a smooth function of the inputs, learnable
+    base = np.tanh(feat @ w1) * np.linspace(0.1, 3.0, n_out) + np.linspace(-1, 1, n_out)
+    Y = base.copy()
+    Y[:, :n_T] = 37.0 + (X[:, :1] / 5e6) * (2.0 + np.abs(base[:, :n_T]))  # temperatures, linear in power
+    eng = SurrogateEngine(dims, 3, n_T, max_batch=512, max_rows=1024, max_epochs=8)
+    eng.set_inputs(np.zeros(n_in), np.concatenate([[1e7], np.ones(n_in - 1)]))
+    eng.set_outputs(0, 5e6, 37.0, norm)
+    xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(Y, dtype=torch.float32, device="cuda")
+    hist = eng.train(xd, yd, epochs=8, batch=128, lr=2e-3, seed=3)
+    assert hist.shape == (3, 8) and np.all(hist[:, -1] < 0.8 * hist[:, 0]), hist
+    # the transform and its statistics, in FP64 here
+    Z = Y.copy()
+    Z[:, :n_T] = (Y[:, :n_T] - 37.0) / (X[:, :1] / 5e6)
+    mu, sd = Z.mean(0), Z.std(0)
+    if norm == 1:
+        sd = np.concatenate([np.full(n_T, np.sqrt(np.mean(sd[:n_T] ** 2))),
+                             np.full(n_out - n_T, np.sqrt(np.mean(sd[n_T:] ** 2)))])
+    row = np.concatenate([X[:, :1] / 5e6 * np.ones((1, n_T)), np.ones((n, n_out - n_T))], 1)
+    off = np.concatenate([np.full(n_T, 37.0), np.zeros(n_out - n_T)])
+    n_par = sum(k * m + m for k, m in zip(dims[:-1], dims[1:]))
+    mean = torch.empty(n, n_out, device="cuda")
+    std = torch.empty(n, n_out, device="cuda")
+    spread = torch.empty(n, device="cuda")
+    fb = torch.empty(n, dtype=torch.uint8, device="cuda")
+    for level in (0.0, 1.0):  # every member answers `level` (standardised) for every output
+        p = np.zeros(n_par, np.float32)
+        p[-n_out:] = level  # last layer bias
+        for k in range(3):
+            eng.set_member_params(k, p)
+        eng.predict(xd, n_T, 0.5, mean, std, spread, fb)
+        eng.sync()
+        expect = (mu + level * sd) * row + off
+        np.testing.assert_allclose(mean.cpu().numpy(), expect, rtol=2e-5, atol=2e-5 * np.abs(expect).max())
+        # identical members: the spread is rounding of the ensemble mean only
+        rnd = 1e-6 * np.abs(expect).max()
+        assert float(std.abs().max()) <= rnd and float(spread.max()) <= rnd and int(fb.sum()) == 0
+    # seeded training is reproducible (graph-replayed epochs, members side by side)
+    eng.train(xd, yd, epochs=8, batch=128, lr=2e-3, seed=3)
+    p_a = [eng.member_params(k) for k in range(3)]
+    eng.train(xd, yd, epochs=8, batch=128, lr=2e-3, seed=3)
+    for k in range(3):
+        np.testing.assert_array_equal(eng.member_params(k), p_a[k])
+    assert not np.array_equal(p_a[0], p_a[1])  # the members start and shuffle differently
