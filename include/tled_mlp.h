@@ -107,7 +107,17 @@ typedef struct tled_sur tled_sur;
  * peak that moves with it; n_freq = 0: the raw inputs only.  n_in <= 32, n_freq <= 12. */
 int tled_sur_create(tled_sur **out, int device, void *cuda_stream, int32_t n_members, int32_t n_in, int32_t width,
                     int32_t depth, int32_t n_out, int32_t n_T, int32_t max_batch, int64_t max_rows,
-                    int32_t max_epochs, int32_t n_freq, uint32_t enc_cols);
+                    int32_t max_epochs, int32_t n_freq, uint32_t enc_cols, int32_t max_sym);
+/* Symmetries of the scenario family, used to augment the training data (e.g. the
+ * reflections of a cube that leave the problem unchanged, with the probe lattice
+ * reflected with them): n_sym <= max_sym maps g, each taking an input row x to x'
+ * with x'_j = in_a[g][j] x[in_src[g][j]] + in_b[g][j] and an output row y to y' with
+ * y'_o = y[out_perm[g][o]] (host arrays [n_sym][n_in] and [n_sym][n_out], copied; the
+ * identity should be one of them).  tled_sur_train then trains on the n x n_sym rows
+ * of the augmented set (row g n + i: map g applied to data row i); max_rows bounds
+ * that count.  n_sym = 0: no augmentation.  Errors: E_ARG, E_STATE. */
+int tled_sur_set_symmetries(tled_sur *s, int32_t n_sym, const int32_t *in_src, const float *in_a, const float *in_b,
+                            const int32_t *out_perm);
 int tled_sur_destroy(tled_sur *s);
 const char *tled_sur_last_error(const tled_sur *s);
 int tled_sur_workspace_size(tled_sur *s, int64_t *bytes);
@@ -125,16 +135,19 @@ int tled_sur_set_inputs(tled_sur *s, const float *lo, const float *hi);
  * physical size alike.  Errors: E_ARG. */
 int tled_sur_set_outputs(tled_sur *s, int32_t power_col, float power_ref, float T_ref, int32_t norm);
 /* Train every member from a seeded He-normal initialisation with Adam (beta 0.9,
- * 0.999, eps 1e-8) at learning rate lr on the mean squared error of the
- * standardised targets: x [n][n_in] raw inputs and y [n][n_out] outputs in physical
- * units, both device float32; `epochs` passes, each over a permutation of the rows
- * (member k's from the splitmix64 stream seeded by `seed`) in mini-batches of
- * `batch` (a multiple of 128; the last partial batch is dropped).  Each member
- * replays a CUDA graph of one epoch on its own stream.  loss_history: host float32
+ * 0.999, eps 1e-8) on the mean squared error of the standardised targets: x
+ * [n][n_in] raw inputs and y [n][n_out] outputs in physical units, both device
+ * float32; `epochs` passes, each over a permutation of the rows (member k's from the
+ * splitmix64 stream seeded by `seed`) in mini-batches of `batch` (a multiple of 128;
+ * the last partial batch is dropped).  Learning rate: lr, decaying by a cosine to
+ * lr_end over the whole run (lr_end = lr: constant).  bootstrap != 0: member k
+ * trains on n rows drawn with replacement (once; every epoch permutes them), so the
+ * members' spread also reflects the sampling of the data.  Each member replays a
+ * CUDA graph of one epoch on its own stream.  loss_history: host float32
  * [n_members][epochs] of mean training losses, or NULL.  Synchronises.
  * Errors: E_ARG, E_STATE, E_CUDA. */
 int tled_sur_train(tled_sur *s, const float *x, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
-                   uint64_t seed, float *loss_history);
+                   float lr_end, int32_t bootstrap, uint64_t seed, float *loss_history);
 /* Ensemble answer for B <= max_batch scenario rows x [B][n_in] (device float32),
  * enqueued: mean and std [B][n_out] in physical units (population std over the
  * members), spread [B] = max of std over outputs [0, n_spread), fallback_mask [B]

@@ -437,7 +437,8 @@ int tled_mlp_sync(tled_mlp *m) {
 // internal entries for the surrogate engine (sur_capi.cpp)
 // ---------------------------------------------------------------------------
 int tmlp_train_step_graphable(tled_mlp *m, cudaStream_t stream, const float *x, const float *t, const int32_t *rows,
-                              int B, float lr, float *loss, int64_t *t_dev, float *bc_dev) {
+                              int B, float lr, float lr_end, int64_t n_decay, float *loss, int64_t *t_dev,
+                              float *bc_dev) {
     if (!m || !x || !t || !t_dev || !bc_dev) return fail(m, TLED_E_ARG, "NULL argument");
     if (!m->inited) return fail(m, TLED_E_STATE, "call tled_mlp_init first");
     if (int rc = check_batch(m, B)) return rc;
@@ -446,7 +447,7 @@ int tmlp_train_step_graphable(tled_mlp *m, cudaStream_t stream, const float *x, 
     int rc = forward(m, x, rows, B, P<float>(m, m->y));
     if (!rc) rc = backward(m, t, rows, B, loss);
     if (!rc) {
-        cudaError_t e = launch_adam_tick(t_dev, bc_dev, stream);
+        cudaError_t e = launch_adam_tick(t_dev, bc_dev, lr, lr_end, n_decay, stream);
         for (int l = 0; l < m->L && e == cudaSuccess; l++) {
             const Layer &ly = m->layer[l];
             const int64_t n = (int64_t)ly.N * ly.K + ly.N;

@@ -52,12 +52,15 @@ cudaError_t launch_bias_grad(const __nv_bfloat16 *dzt, int B, int N, float *db, 
 cudaError_t launch_adam(float *w, float *m, float *v, const float *grad, int64_t n, float lr, float b1, float b2,
                         float eps, float bc1, float bc2, int N, int K, int ld, __nv_bfloat16 *wb, __nv_bfloat16 *wt,
                         cudaStream_t s, const float *bc = nullptr);
-cudaError_t launch_adam_tick(int64_t *t, float *bc, cudaStream_t s);
+cudaError_t launch_adam_tick(int64_t *t, float *bc, float lr, float lr_end, int64_t n_decay, cudaStream_t s);
 // surrogate data: temperature rise per unit source power, column statistics, standardisation,
 // per-row maximum error, mean of per-step losses
 cudaError_t launch_sur_encode(const float *x, int ld_x, int64_t n, int64_t n_rows, int n_in, const float *shift,
                               const float *scale, int n_freq, unsigned enc_cols, int n_feat, float *feat,
                               cudaStream_t s);
+cudaError_t launch_sur_augment(const float *x, const float *y, int64_t n, int n_in, int n_out, int n_sym,
+                               const int32_t *src, const float *a, const float *b, const int32_t *perm, float *xa,
+                               float *ya, cudaStream_t s);
 cudaError_t launch_sur_transform(const float *x, int ld_x, const float *y, int64_t n, int n_out, int n_T,
                                  int power_col, float T_ref, float inv_Pref, float *z, cudaStream_t s);
 cudaError_t launch_column_stats(const float *z, int64_t n, int n_out, double *mean, double *m2, cudaStream_t s);
@@ -72,9 +75,12 @@ cudaError_t launch_gather_grad(const float *G, const float *db, int N, int K, in
 
 // Internal entry of the MLP (mlp_capi.cpp) for the surrogate engine: one Adam step
 // on rows of a device-resident data set, enqueued on `stream`, with Adam's step
-// counter on the device (t_dev, bc_dev: advanced by the step itself), so that a
-// sequence of steps can be captured in a CUDA graph.
+// counter on the device (t_dev, bc_dev [3]: advanced by the step itself, the
+// learning rate decaying from lr to lr_end over n_decay steps by a cosine, or
+// constant for n_decay <= 0), so that a sequence of steps can be captured in a
+// CUDA graph.
 struct tled_mlp;
 int tmlp_train_step_graphable(tled_mlp *m, cudaStream_t stream, const float *x, const float *t, const int32_t *rows,
-                              int B, float lr, float *loss, int64_t *t_dev, float *bc_dev);
+                              int B, float lr, float lr_end, int64_t n_decay, float *loss, int64_t *t_dev,
+                              float *bc_dev);
 int tmlp_forward_on(tled_mlp *m, cudaStream_t stream, const float *x, int B, float *y);

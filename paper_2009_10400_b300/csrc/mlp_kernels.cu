@@ -370,9 +370,10 @@ __global__ void adam_kernel(float *__restrict__ w, float *__restrict__ m, float 
                             __nv_bfloat16 *wb, __nv_bfloat16 *wt) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (bc) {  // the bias corrections of the device step counter (graph-captured training)
+    if (bc) {  // the device step counter's bias corrections and learning rate (graph-captured training)
         bc1 = bc[0];
         bc2 = bc[1];
+        lr = bc[2];
     }
     const float gr = grad[i];
     const float mi = b1 * m[i] + (1.f - b1) * gr;
@@ -531,14 +532,22 @@ cudaError_t launch_adam(float *w, float *m, float *v, const float *grad, int64_t
 // ---------------------------------------------------------------------------
 // device step counter of Adam, and the surrogate's data kernels
 // ---------------------------------------------------------------------------
-// t += 1; bc = (1 - 0.9^t, 1 - 0.999^t), in FP64 like the host path
-__global__ void adam_tick_kernel(int64_t *t, float *bc) {
+// t += 1; bc = (1 - 0.9^t, 1 - 0.999^t, lr_t) in FP64 like the host path, with the learning
+// rate lr_t = lr_end + (lr - lr_end) (1 + cos(pi min(t - 1, n_decay) / n_decay)) / 2 over
+// n_decay steps (cosine decay; n_decay <= 0: constant lr)
+__global__ void adam_tick_kernel(int64_t *t, float *bc, float lr, float lr_end, int64_t n_decay) {
     const int64_t n = ++*t;
     bc[0] = (float)(1.0 - pow(0.9, (double)n));
     bc[1] = (float)(1.0 - pow(0.999, (double)n));
+    if (n_decay > 0) {
+        const double x = (double)min(n - 1, n_decay) / (double)n_decay;
+        bc[2] = (float)(lr_end + (lr - lr_end) * 0.5 * (1.0 + cospi(x)));
+    } else {
+        bc[2] = lr;
+    }
 }
-cudaError_t launch_adam_tick(int64_t *t, float *bc, cudaStream_t s) {
-    adam_tick_kernel<<<1, 1, 0, s>>>(t, bc);
+cudaError_t launch_adam_tick(int64_t *t, float *bc, float lr, float lr_end, int64_t n_decay, cudaStream_t s) {
+    adam_tick_kernel<<<1, 1, 0, s>>>(t, bc, lr, lr_end, n_decay);
     return cudaGetLastError();
 }
 
@@ -635,6 +644,40 @@ cudaError_t launch_sur_encode(const float *x, int ld_x, int64_t n, int64_t n_row
                               const float *scale, int n_freq, unsigned enc_cols, int n_feat, float *feat,
                               cudaStream_t s) {
     sur_encode_kernel<<<592, 256, 0, s>>>(x, ld_x, n, n_rows, n_in, shift, scale, n_freq, enc_cols, n_feat, feat);
+    return cudaGetLastError();
+}
+
+// Augmented rows under n_sym symmetries: row g n + i of the augmented set is symmetry g
+// applied to data row i: x'[j] = a[g][j] x[i][src[g][j]] + b[g][j], y'[o] = y[i][perm[g][o]].
+__global__ void sur_augment_x_kernel(const float *__restrict__ x, int64_t n, int n_in, int n_sym,
+                                     const int32_t *__restrict__ src, const float *__restrict__ a,
+                                     const float *__restrict__ b, float *xa) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n_sym * n * n_in;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(q % n_in);
+        const int64_t r = q / n_in;
+        const int g = (int)(r / n);
+        const int64_t i = r % n;
+        const int k = g * n_in + j;
+        xa[q] = a[k] * x[i * n_in + src[k]] + b[k];
+    }
+}
+__global__ void sur_augment_y_kernel(const float *__restrict__ y, int64_t n, int n_out, int n_sym,
+                                     const int32_t *__restrict__ perm, float *ya) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n_sym * n * n_out;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(q % n_out);
+        const int64_t r = q / n_out;
+        const int g = (int)(r / n);
+        const int64_t i = r % n;
+        ya[q] = y[i * n_out + perm[(int64_t)g * n_out + o]];
+    }
+}
+cudaError_t launch_sur_augment(const float *x, const float *y, int64_t n, int n_in, int n_out, int n_sym,
+                               const int32_t *src, const float *a, const float *b, const int32_t *perm, float *xa,
+                               float *ya, cudaStream_t s) {
+    sur_augment_x_kernel<<<592, 256, 0, s>>>(x, n, n_in, n_sym, src, a, b, xa);
+    sur_augment_y_kernel<<<2368, 256, 0, s>>>(y, n, n_out, n_sym, perm, ya);
     return cudaGetLastError();
 }
 

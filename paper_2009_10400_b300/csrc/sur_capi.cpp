@@ -52,6 +52,10 @@ struct tled_sur {
     std::string err;
     int n_members = 0, n_in = 0, n_out = 0, n_T = 0, max_batch = 0, max_epochs = 0;
     int n_freq = 0, n_feat = 0;  // input encoding: octaves, features per row
+    // symmetries of the scenario family (training data augmentation), host copies
+    int n_sym = 0;
+    std::vector<int32_t> sym_src, sym_perm;
+    std::vector<float> sym_a, sym_b;
     unsigned enc_cols = 0;       // raw input columns that get sin / cos features
     int64_t max_rows = 0;
     std::vector<int32_t> dims;
@@ -62,7 +66,8 @@ struct tled_sur {
     int graph_steps = 0, graph_batch = 0;
     int64_t graph_rows = 0;
     const float *graph_x = nullptr;
-    float graph_lr = 0.f;
+    float graph_lr = 0.f, graph_lr_end = 0.f;
+    int64_t graph_decay = 0;
     // outputs: temperature rise per unit power for the first n_T outputs (power_col >= 0)
     int power_col = -1, norm = 0;
     float P_ref = 1.f, T_ref = 0.f;
@@ -73,7 +78,9 @@ struct tled_sur {
     std::vector<size_t> o_net;
     size_t o_targets = 0, o_scale = 0, o_shift = 0, o_offset = 0, o_rows = 0, o_perms = 0, o_steploss = 0, o_hist = 0, o_t = 0,
            o_bc = 0, o_ys = 0, o_feat = 0, o_feat_train = 0, o_in_shift = 0, o_in_scale = 0, o_err = 0, o_mean = 0,
-           o_m2 = 0, o_spread = 0, o_cmean = 0, total = 0;
+           o_m2 = 0, o_spread = 0, o_cmean = 0, o_xaug = 0, o_sym_src = 0, o_sym_a = 0, o_sym_b = 0, o_sym_perm = 0,
+           total = 0;
+    int max_sym = 0;  // symmetries the workspace holds
     int max_steps = 0;
 };
 
@@ -188,12 +195,13 @@ extern "C" {
 
 int tled_sur_create(tled_sur **out, int device, void *stream, int32_t n_members, int32_t n_in, int32_t width,
                     int32_t depth, int32_t n_out, int32_t n_T, int32_t max_batch, int64_t max_rows,
-                    int32_t max_epochs, int32_t n_freq, uint32_t enc_cols) {
+                    int32_t max_epochs, int32_t n_freq, uint32_t enc_cols, int32_t max_sym) {
     if (!out) return TLED_E_ARG;
     *out = nullptr;
     if (n_members < 1 || n_members > tmlp::kMaxMembers || n_in < 1 || n_in > 32 || width < 128 || width % 128 ||
         depth < 2 || n_out < 128 || n_out % 128 || n_T < 0 || n_T > n_out || max_batch < 128 || max_batch % 128 ||
-        max_rows < max_batch || max_epochs < 1 || n_freq < 0 || n_freq > 12 || (n_in < 32 && (enc_cols >> n_in)))
+        max_rows < max_batch || max_epochs < 1 || n_freq < 0 || n_freq > 12 || (n_in < 32 && (enc_cols >> n_in)) ||
+        max_sym < 0 || max_sym > 64)
         return TLED_E_ARG;
     tled_sur *s = new tled_sur;
     s->device = device;
@@ -205,6 +213,7 @@ int tled_sur_create(tled_sur **out, int device, void *stream, int32_t n_members,
     s->max_batch = max_batch;
     s->max_rows = max_rows;
     s->max_epochs = max_epochs;
+    s->max_sym = max_sym;
     s->n_freq = n_freq;
     s->enc_cols = n_freq > 0 ? enc_cols : 0u;
     s->n_feat = n_in + 2 * n_freq * __builtin_popcount(s->enc_cols);
@@ -281,7 +290,7 @@ int tled_sur_workspace_size(tled_sur *s, int64_t *bytes) {
     s->o_steploss = take(4 * nm * (size_t)s->max_steps);
     s->o_hist = take(4 * nm * (size_t)s->max_epochs);
     s->o_t = take(8 * nm);
-    s->o_bc = take(8 * nm);
+    s->o_bc = take(16 * nm);  // per member: bias corrections and the step's learning rate
     s->o_ys = take(4 * nm * (size_t)s->max_batch * no);
     s->o_feat = take(4 * (size_t)s->max_batch * s->n_feat);
     s->o_feat_train = take(4 * (size_t)s->max_rows * s->n_feat);
@@ -292,6 +301,11 @@ int tled_sur_workspace_size(tled_sur *s, int64_t *bytes) {
     s->o_cmean = take(4 * (size_t)s->max_batch * no);
     s->o_mean = take(8 * no);
     s->o_m2 = take(8 * no);
+    s->o_xaug = take(4 * (size_t)s->max_rows * s->n_in);  // raw inputs of the (augmented) training set
+    s->o_sym_src = take(4 * (size_t)s->max_sym * s->n_in);
+    s->o_sym_a = take(4 * (size_t)s->max_sym * s->n_in);
+    s->o_sym_b = take(4 * (size_t)s->max_sym * s->n_in);
+    s->o_sym_perm = take(4 * (size_t)s->max_sym * no);
     s->total = off;
     *bytes = (int64_t)off;
     return TLED_OK;
@@ -320,6 +334,12 @@ int tled_sur_init(tled_sur *s, void *dev_workspace, int64_t bytes) {
     SCUDA(s, cudaMemcpy(s->ws + s->o_offset, zero.data(), 4 * (size_t)s->n_out, cudaMemcpyHostToDevice));
     s->inited = true;
     s->trained = false;
+    if (s->n_sym > 0) {
+        const int ns = s->n_sym;
+        std::vector<int32_t> src(s->sym_src), perm(s->sym_perm);
+        std::vector<float> a(s->sym_a), b(s->sym_b);
+        if (int rc = tled_sur_set_symmetries(s, ns, src.data(), a.data(), b.data(), perm.data())) return rc;
+    }
     if (!s->in_lo.empty()) return tled_sur_set_inputs(s, s->in_lo.data(), s->in_hi.data());
     return TLED_OK;
 }
@@ -342,6 +362,32 @@ int tled_sur_set_inputs(tled_sur *s, const float *lo, const float *hi) {
     return TLED_OK;
 }
 
+int tled_sur_set_symmetries(tled_sur *s, int32_t n_sym, const int32_t *in_src, const float *in_a, const float *in_b,
+                            const int32_t *out_perm) {
+    if (int rc = check(s)) return rc;
+    if (n_sym < 0 || n_sym > s->max_sym) return fail(s, TLED_E_ARG, "0 <= n_sym <= max_sym");
+    if (n_sym > 0 && (!in_src || !in_a || !in_b || !out_perm)) return fail(s, TLED_E_ARG, "NULL symmetry table");
+    const size_t ni = (size_t)n_sym * s->n_in, no = (size_t)n_sym * s->n_out;
+    for (size_t q = 0; q < ni; q++)
+        if (in_src[q] < 0 || in_src[q] >= s->n_in || !std::isfinite(in_a[q]) || !std::isfinite(in_b[q]))
+            return fail(s, TLED_E_ARG, "symmetry input map: source column out of range or a non-finite factor");
+    for (size_t q = 0; q < no; q++)
+        if (out_perm[q] < 0 || out_perm[q] >= s->n_out) return fail(s, TLED_E_ARG, "symmetry output index out of range");
+    s->n_sym = n_sym;
+    s->sym_src.assign(in_src, in_src + ni);
+    s->sym_a.assign(in_a, in_a + ni);
+    s->sym_b.assign(in_b, in_b + ni);
+    s->sym_perm.assign(out_perm, out_perm + no);
+    if (n_sym == 0) return TLED_OK;
+    SCUDA(s, cudaSetDevice(s->device));
+    SCUDA(s, cudaMemcpy(s->ws + s->o_sym_src, in_src, 4 * ni, cudaMemcpyHostToDevice));
+    SCUDA(s, cudaMemcpy(s->ws + s->o_sym_a, in_a, 4 * ni, cudaMemcpyHostToDevice));
+    SCUDA(s, cudaMemcpy(s->ws + s->o_sym_b, in_b, 4 * ni, cudaMemcpyHostToDevice));
+    SCUDA(s, cudaMemcpy(s->ws + s->o_sym_perm, out_perm, 4 * no, cudaMemcpyHostToDevice));
+    s->trained = false;
+    return TLED_OK;
+}
+
 int tled_sur_set_outputs(tled_sur *s, int32_t power_col, float power_ref, float T_ref, int32_t norm) {
     if (!s) return TLED_E_ARG;
     if (power_col >= s->n_in || (power_col >= 0 && !(power_ref > 0)) || (norm != 0 && norm != 1))
@@ -355,17 +401,32 @@ int tled_sur_set_outputs(tled_sur *s, int32_t power_col, float power_ref, float 
 }
 
 int tled_sur_train(tled_sur *s, const float *x, const float *y, int64_t n, int32_t epochs, int32_t batch, float lr,
-                   uint64_t seed, float *loss_history) {
+                   float lr_end, int32_t bootstrap, uint64_t seed, float *loss_history) {
     if (int rc = check(s)) return rc;
     if (!x || !y) return fail(s, TLED_E_ARG, "NULL data");
     if (batch < 128 || batch % 128 || batch > s->max_batch) return fail(s, TLED_E_ARG, "batch: a multiple of 128 <= max_batch");
-    if (n < batch || n > s->max_rows) return fail(s, TLED_E_ARG, "rows: batch <= n <= max_rows");
+    const int64_t n_data = n;
+    if (s->n_sym > 0) n = n_data * s->n_sym;  // the augmented set
+    if (n < batch || n > s->max_rows)
+        return fail(s, TLED_E_ARG, "rows: batch <= n (x n_sym with symmetries) <= max_rows");
     if (epochs < 1 || epochs > s->max_epochs) return fail(s, TLED_E_ARG, "epochs: 1..max_epochs");
     if (!(lr > 0) || !std::isfinite(lr)) return fail(s, TLED_E_ARG, "learning rate must be positive");
+    if (!(lr_end >= 0) || lr_end > lr) return fail(s, TLED_E_ARG, "0 <= lr_end <= lr");
     SCUDA(s, cudaSetDevice(s->device));
     const int no = s->n_out;
-    // --- targets: temperature rise per unit power, then standardised
+    // --- the training set (augmented by the symmetries, if set), then the targets:
+    //     temperature rise per unit power, then standardised
     float *z = P<float>(s, s->o_targets);
+    float *xr = P<float>(s, s->o_xaug);
+    if (s->n_sym > 0) {
+        SCUDA(s, tmlp::launch_sur_augment(x, y, n_data, s->n_in, no, s->n_sym, P<int32_t>(s, s->o_sym_src),
+                                          P<float>(s, s->o_sym_a), P<float>(s, s->o_sym_b),
+                                          P<int32_t>(s, s->o_sym_perm), xr, z, s->stream));
+        y = z;  // transformed in place below (elementwise)
+    } else {
+        SCUDA(s, cudaMemcpyAsync(xr, x, 4 * (size_t)n * s->n_in, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    x = xr;
     SCUDA(s, tmlp::launch_sur_transform(x, s->n_in, y, n, no, s->n_T, s->power_col, s->T_ref, 1.f / s->P_ref, z,
                                         s->stream));
     SCUDA(s, tmlp::launch_column_stats(z, n, no, P<double>(s, s->o_mean), P<double>(s, s->o_m2), s->stream));
@@ -407,8 +468,11 @@ int tled_sur_train(tled_sur *s, const float *x, const float *y, int64_t n, int32
     SCUDA(s, cudaStreamSynchronize(s->stream));  // host copies consumed; data ready for the members' streams
     // --- members: seeded He initialisation; one epoch of Adam steps captured per member
     const int steps = (int)(n / batch);
+    // cosine decay from lr to lr_end over the whole run (lr_end == lr: constant)
+    const int64_t n_decay = lr_end < lr ? (int64_t)steps * epochs : 0;
     const bool same_graph = s->graph_steps == steps && s->graph_batch == batch && s->graph_x == x &&
-                            s->graph_rows == n && s->graph_lr == lr;
+                            s->graph_rows == n && s->graph_lr == lr && s->graph_lr_end == lr_end &&
+                            s->graph_decay == n_decay;
     if (!same_graph) drop_graphs(s);
     SplitMix master{seed};
     std::vector<SplitMix> rng;
@@ -418,21 +482,22 @@ int tled_sur_train(tled_sur *s, const float *x, const float *y, int64_t n, int32
         int32_t *rows = P<int32_t>(s, s->o_rows) + (size_t)k * s->max_rows;
         float *sl = P<float>(s, s->o_steploss) + (size_t)k * s->max_steps;
         int64_t *tk = P<int64_t>(s, s->o_t) + k;
-        float *bck = P<float>(s, s->o_bc) + 2 * k;
+        float *bck = P<float>(s, s->o_bc) + 4 * k;
         if (!s->graph[k]) {
             // first use of every kernel outside capture (module loading, attributes): one step
             // on the first rows, undone by the initialisation below
             for (int64_t i = 0; i < n; i++) perm[i] = (int32_t)i;
             SCUDA(s, cudaMemcpyAsync(rows, perm.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, s->ms[k]));
             SCUDA(s, cudaMemsetAsync(tk, 0, 8, s->ms[k]));
-            SMLP(s, k, tmlp_train_step_graphable(s->net[k], s->ms[k], xf, z, rows, batch, lr, sl, tk, bck));
+            SMLP(s, k, tmlp_train_step_graphable(s->net[k], s->ms[k], xf, z, rows, batch, lr, lr_end, n_decay, sl, tk,
+                                                 bck));
             SCUDA(s, cudaStreamSynchronize(s->ms[k]));
             cudaGraph_t g = nullptr;
             SCUDA(s, cudaStreamBeginCapture(s->ms[k], cudaStreamCaptureModeThreadLocal));
             int rc = TLED_OK;
             for (int j = 0; j < steps && rc == TLED_OK; j++)
-                rc = tmlp_train_step_graphable(s->net[k], s->ms[k], xf, z, rows + (size_t)j * batch, batch, lr, sl + j,
-                                               tk, bck);
+                rc = tmlp_train_step_graphable(s->net[k], s->ms[k], xf, z, rows + (size_t)j * batch, batch, lr, lr_end,
+                                               n_decay, sl + j, tk, bck);
             const cudaError_t e = cudaStreamEndCapture(s->ms[k], &g);
             if (rc) {
                 if (g) cudaGraphDestroy(g);
@@ -453,14 +518,19 @@ int tled_sur_train(tled_sur *s, const float *x, const float *y, int64_t n, int32
     s->graph_x = x;
     s->graph_rows = n;
     s->graph_lr = lr;
+    s->graph_lr_end = lr_end;
+    s->graph_decay = n_decay;
     // --- every member's permutations of all epochs (Fisher-Yates), uploaded once; then the
     //     epochs: each member copies its epoch's rows on the device and replays its epoch
     //     graph, the members side by side on their streams
-    std::vector<int32_t> perms((size_t)epochs * n);
+    //     (bootstrap: member k's rows are n draws with replacement, made once, and every epoch
+    //     permutes that multiset, so the members see different samples of the data)
+    std::vector<int32_t> perms((size_t)epochs * n), base(n);
     for (int k = 0; k < s->n_members; k++) {
+        for (int64_t i = 0; i < n; i++) base[i] = bootstrap ? (int32_t)rng[k].below((uint64_t)n) : (int32_t)i;
         for (int e = 0; e < epochs; e++) {
             int32_t *pe = perms.data() + (size_t)e * n;
-            for (int64_t i = 0; i < n; i++) pe[i] = (int32_t)i;
+            std::copy(base.begin(), base.end(), pe);
             for (int64_t i = n - 1; i > 0; i--) std::swap(pe[i], pe[rng[k].below((uint64_t)i + 1)]);
         }
         int32_t *dst = P<int32_t>(s, s->o_perms) + (size_t)k * s->max_epochs * s->max_rows;

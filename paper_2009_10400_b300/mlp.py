@@ -33,15 +33,18 @@ _SIGS = {
                            C.c_void_p, C.c_void_p, C.c_int32, C.c_float, C.c_int32, C.c_void_p, C.c_int32, C.c_float,
                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "tled_sur_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                         C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_uint32], C.c_int),
+                         C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32, C.c_uint32, C.c_int32],
+                        C.c_int),
+    "tled_sur_set_symmetries": ([C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float),
+                                 C.POINTER(C.c_float), C.POINTER(C.c_int32)], C.c_int),
     "tled_sur_destroy": ([C.c_void_p], C.c_int),
     "tled_sur_last_error": ([C.c_void_p], C.c_char_p),
     "tled_sur_workspace_size": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_sur_init": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
     "tled_sur_set_inputs": ([C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
     "tled_sur_set_outputs": ([C.c_void_p, C.c_int32, C.c_float, C.c_float, C.c_int32], C.c_int),
-    "tled_sur_train": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_uint64,
-                        C.POINTER(C.c_float)], C.c_int),
+    "tled_sur_train": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32, C.c_float, C.c_float,
+                        C.c_int32, C.c_uint64, C.POINTER(C.c_float)], C.c_int),
     "tled_sur_predict": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_float, C.c_void_p, C.c_void_p,
                           C.c_void_p, C.c_void_p], C.c_int),
     "tled_sur_calibrate": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_float, C.c_float,
@@ -216,7 +219,7 @@ class SurrogateEngine:
     tensors are PyTorch CUDA float32 (inputs, outputs) on the engine's device."""
 
     def __init__(self, dims, members, n_T, max_batch, max_rows, max_epochs, device=0, stream=None, n_freq=0,
-                 enc_cols=()):
+                 enc_cols=(), max_sym=0):
         import torch
 
         if not torch.cuda.is_available():
@@ -228,7 +231,7 @@ class SurrogateEngine:
         mask = sum(1 << int(j) for j in enc_cols)
         rc = lib().tled_sur_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream), self.members, dims[0],
                                    dims[1], len(dims) - 1, dims[-1], int(n_T), self.max_batch, int(max_rows),
-                                   int(max_epochs), int(n_freq), mask)
+                                   int(max_epochs), int(n_freq), mask, int(max_sym))
         self.n_feat = dims[0] + 2 * int(n_freq) * len(set(enc_cols))
         if rc:
             raise TledError(rc, "tled_sur_create: invalid sizes (widths and outputs multiples of 128, batch of 128)")
@@ -260,14 +263,24 @@ class SurrogateEngine:
         hi = np.ascontiguousarray(hi, np.float32)
         self._check(lib().tled_sur_set_inputs(self.h, lo.ctypes.data_as(fp), hi.ctypes.data_as(fp)))
 
+    def set_symmetries(self, src, a, b, perm):
+        """src, a, b [n_sym][n_in] (x'_j = a x[src] + b), perm [n_sym][n_out] (y'_o = y[perm])."""
+        src = np.ascontiguousarray(src, np.int32)
+        a = np.ascontiguousarray(a, np.float32)
+        b = np.ascontiguousarray(b, np.float32)
+        perm = np.ascontiguousarray(perm, np.int32)
+        ip, fp = C.POINTER(C.c_int32), C.POINTER(C.c_float)
+        self._check(lib().tled_sur_set_symmetries(self.h, src.shape[0], src.ctypes.data_as(ip), a.ctypes.data_as(fp),
+                                                  b.ctypes.data_as(fp), perm.ctypes.data_as(ip)))
+
     def set_outputs(self, power_col, power_ref, T_ref, norm):
         self._check(lib().tled_sur_set_outputs(self.h, int(power_col), float(power_ref), float(T_ref), int(norm)))
 
-    def train(self, x, y, epochs, batch, lr, seed):
+    def train(self, x, y, epochs, batch, lr, seed, lr_end=None, bootstrap=False):
         hist = np.zeros((self.members, epochs), np.float32)
         self._check(lib().tled_sur_train(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.shape[0],
-                                         int(epochs), int(batch), float(lr), int(seed),
-                                         hist.ctypes.data_as(C.POINTER(C.c_float))))
+                                         int(epochs), int(batch), float(lr), float(lr if lr_end is None else lr_end),
+                                         int(bool(bootstrap)), int(seed), hist.ctypes.data_as(C.POINTER(C.c_float))))
         return hist
 
     def predict(self, x, n_spread, tol, mean=None, std=None, spread=None, fallback=None):

@@ -50,6 +50,46 @@ def solve_scenarios(Q, n=16, dt=0.01, chunk=512, device=0):
     return T, D, dict(seconds=time.perf_counter() - t0, launch_steps=steps)
 
 
+def cube_symmetries(n=16, side=0.05, n_in=12):
+    """The 16 reflections of the scenario cube that leave its heating problem
+    unchanged -- x, y, z mirrored and x <-> y swapped (the faces are adiabatic
+    and the source is a Gaussian; the one mechanical boundary, the held bottom,
+    moves nodes by ~1e-5 of an element, so temperatures follow the reflection)
+    -- as the surrogate engine's tables: the source position mapped (inputs 1-3),
+    the other inputs unchanged, and the n^3 element-centroid probes (x fastest;
+    temperatures then damage) permuted with the reflection.  Returns (src, a, b,
+    perm) with [16][n_in] and [16][2 n^3] entries."""
+    import itertools
+
+    ijk = np.stack(np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij"), -1).reshape(-1, 3)
+    ijk = ijk[:, ::-1]  # rows in x-fastest probe order: (i, j, k) of probe i + n (j + n k)
+    src, a, b, perm = [], [], [], []
+    for fx, fy, fz, sw in itertools.product((0, 1), repeat=4):
+        s_ = np.arange(n_in)
+        a_ = np.ones(n_in)
+        b_ = np.zeros(n_in)
+        for col, f in ((1, fx), (2, fy), (3, fz)):
+            if f:
+                a_[col], b_[col] = -1.0, side
+        if sw:  # x' and y' read the (mirrored) y and x
+            s_[1], s_[2] = 2, 1
+            a_[1], a_[2] = a_[2], a_[1]
+            b_[1], b_[2] = b_[2], b_[1]
+        # the map is g = (swap) after (mirrors); the mapped scenario's field is T'(x) = T(g^-1 x),
+        # so probe p of the mapped row reads probe g^-1(p) = (mirrors) after (swap) of the data row
+        q = ijk.copy()
+        if sw: q[:, [0, 1]] = q[:, [1, 0]]
+        if fx: q[:, 0] = n - 1 - q[:, 0]
+        if fy: q[:, 1] = n - 1 - q[:, 1]
+        if fz: q[:, 2] = n - 1 - q[:, 2]
+        p = q[:, 0] + n * (q[:, 1] + n * q[:, 2])
+        src.append(s_)
+        a.append(a_)
+        b.append(b_)
+        perm.append(np.concatenate([p, n ** 3 + p]))
+    return np.array(src), np.array(a), np.array(b), np.array(perm)
+
+
 P_REF = 5e6  # W/m^3: the temperature outputs are learned per unit of power / P_REF
 T_REF = 37.0  # C: initial and arterial temperature of the scenarios
 
@@ -69,31 +109,35 @@ class Surrogate:
     errors alike."""
 
     def __init__(self, n_out, width=512, depth=6, members=5, max_batch=4096, device=0, n_in=12, n_T=None,
-                 per_power=True, norm=1, max_rows=20480, max_epochs=64, n_freq=4):
+                 per_power=True, norm=1, max_rows=20480, max_epochs=64, n_freq=0, symmetric=False, grid=16):
         self.n_T = n_out // 2 if n_T is None else n_T
         self.n_members = members
         self.max_batch = max_batch
         self.device = device
-        # sin / cos features of the source position (inputs 1-3) at n_freq octaves
+        # optional sin / cos features of the source position (inputs 1-3) at n_freq octaves
         self.engine = SurrogateEngine([n_in] + [width] * (depth - 1) + [n_out], members, self.n_T, max_batch,
-                                      max_rows, max_epochs, device=device, n_freq=n_freq, enc_cols=(1, 2, 3))
+                                      max_rows, max_epochs, device=device, n_freq=n_freq, enc_cols=(1, 2, 3),
+                                      max_sym=16 if symmetric else 0)
         self.dims = [self.engine.n_feat] + [width] * (depth - 1) + [n_out]
         lo, hi = W.surrogate_ranges()
         self.engine.set_inputs(lo, hi)
         self.engine.set_outputs(0 if per_power else -1, P_REF, T_REF, norm)
+        if symmetric:  # the training set augmented by the 16 reflections of the cube
+            self.engine.set_symmetries(*cube_symmetries(grid, n_in=n_in))
         self.tau = None
 
     def _dev(self):
         return f"cuda:{self.device}"
 
-    def fit(self, Q, Y, epochs=50, batch=256, lr=1e-3, seed=0):
+    def fit(self, Q, Y, epochs=50, batch=256, lr=1e-3, seed=0, lr_end=None, bootstrap=False):
         """Train every member (Adam on the standardised targets, seeded
-        initialisation and per-epoch permutations); returns the mean training
-        loss per epoch of each member."""
+        initialisation and per-epoch permutations; lr decaying by a cosine to
+        lr_end when given; bootstrap resampling per member); returns the mean
+        training loss per epoch of each member."""
         import torch
         X = torch.tensor(np.atleast_2d(Q), dtype=torch.float32, device=self._dev())
         Yd = torch.tensor(np.asarray(Y), dtype=torch.float32, device=self._dev())
-        hist = self.engine.train(X, Yd, epochs, batch, lr, seed)
+        hist = self.engine.train(X, Yd, epochs, batch, lr, seed, lr_end=lr_end, bootstrap=bootstrap)
         return [list(map(float, h)) for h in hist]
 
     def predict_device(self, Xd, n_spread, tol, want_std=True):
