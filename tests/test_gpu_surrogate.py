@@ -87,29 +87,39 @@ def test_surrogate_learns_and_falls_back():
 def test_surrogate_answers_at_one_kelvin():
     """The learned part at the stated accuracy: trained on the solver's data
     augmented by the cube's 16 reflections, with the spread threshold
-    calibrated against the solver on half of the held-out scenarios (every
-    calibration case at or below it within 1 K), the surrogate answers a
-    non-zero fraction of the other half, every answer within 1 K of the
-    solver, and the rest comes back from the solver exactly."""
+    calibrated against the solver on 512 held-out scenarios (every calibration
+    case at or below it within 0.8 K: the bench's policy, a margin below the
+    stated 1 K), the surrogate answers a non-zero fraction of 256 further
+    scenarios, every answer within 1 K of the solver, and the rest comes back
+    from the solver exactly."""
     from paper_2009_10400_b300 import surrogate
     n, dt = 8, 0.05
     P = n ** 3
-    Q = W.sample_scenarios(1280, seed=12, duration=(5.0, 30.0))
+    n_tr, n_cal, n_ev = 2048, 512, 256
+    Q = W.sample_scenarios(n_tr + n_cal + n_ev, seed=12, duration=(5.0, 30.0))
     T, D, tm = surrogate.solve_scenarios(Q, n=n, dt=dt)
     Y = np.concatenate([T, D], 1)
-    tr, cal, ev = slice(0, 1024), slice(1024, 1152), slice(1152, 1280)
-    sur = surrogate.Surrogate(n_out=2 * P, width=256, depth=4, members=3, max_batch=4096, symmetric=True, grid=n,
-                              max_rows=16 * 1024)
+    tr, cal, ev = slice(0, n_tr), slice(n_tr, n_tr + n_cal), slice(n_tr + n_cal, n_tr + n_cal + n_ev)
+    sur = surrogate.Surrogate(n_out=2 * P, width=256, depth=4, members=4, max_batch=4096, symmetric=True, grid=n,
+                              max_rows=16 * n_tr)
     sur.fit(Q[tr], Y[tr], epochs=20, batch=128, lr=2e-3, seed=1)
-    tau, frac = sur.calibrate(Q[cal], Y[cal], P, tol=1.0, coverage=1.0)
+    mean, std = sur.predict(Q[ev])
+    err_ev = np.abs(mean[:, :P] - T[ev]).max(1)
+    sp_ev = std[:, :P].max(1)
+    for m in (1.0, 0.8, 0.6):  # the trade-off, for the record
+        tau_m, f_m = sur.calibrate(Q[cal], Y[cal], P, tol=m, coverage=1.0)
+        acc = sp_ev <= tau_m
+        print(f"calibrated at {m:.1f} K: threshold {tau_m:.3f} K, answers {acc.mean():.3f} of the evaluation "
+              f"cases, worst answered {err_ev[acc].max() if acc.any() else 0.0:.3f} K")
+    tau, frac = sur.calibrate(Q[cal], Y[cal], P, tol=0.8, coverage=1.0)
     out, fb, info = sur.solve(Q[ev], P, tol=1.0, n=n, dt=dt)
     err = np.abs(out[:, :P] - T[ev]).max(1)
-    rate = (ev.stop - ev.start) / info["seconds"]
+    rate = n_ev / info["seconds"]
     solver_rate = len(Q) / tm["seconds"]
     print(f"at 1 K: threshold {tau:.3f} K (calibration accepts {frac:.2f}); the surrogate answers "
           f"{np.mean(~fb):.2f} of the evaluation cases, worst answered error "
           f"{err[~fb].max() if (~fb).any() else 0.0:.3f} K; {rate:.1f} solves/s with fallback, "
-          f"batched solver {solver_rate:.1f} solves/s")
+          f"batched solver {solver_rate:.1f} solves/s; median worst-probe error {np.median(err_ev):.3f} K")
     np.testing.assert_allclose(out[fb], Y[ev][fb], rtol=0, atol=1e-9)  # fallbacks: the solver's answers
     assert (~fb).any(), (tau, frac)
     assert np.all(err[~fb] <= 1.0), err[~fb].max()

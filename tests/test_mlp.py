@@ -261,3 +261,49 @@ def test_surrogate_engine_transform_standardisation_and_training(norm):
     for k in range(3):
         np.testing.assert_array_equal(eng.member_params(k), p_a[k])
     assert not np.array_equal(p_a[0], p_a[1])  # the members start and shuffle differently
+
+
+@pytest.mark.gpu
+def test_surrogate_engine_symmetry_augmentation():
+    """Training-set augmentation: with the identity and a map that mirrors input 1
+    (x' = 1 - x) and reverses the outputs, the engine trains on both copies of
+    every row; networks answering zero then return the column means of the
+    augmented, transformed targets (computed here in FP64)."""
+    import torch
+
+    from paper_2009_10400_b300.mlp import SurrogateEngine
+    rng = np.random.default_rng(12)
+    n, n_in, n_out, n_T = 256, 4, 128, 64
+    dims = [n_in, 128, n_out]
+    X = rng.uniform(0.0, 1.0, (n, n_in))
+    X[:, 0] = rng.uniform(1e6, 1e7, n)
+    Y = rng.normal(size=(n, n_out)) * 3.0
+    Y[:, :n_T] += 37.0
+    src = np.tile(np.arange(n_in), (2, 1))
+    a, b = np.ones((2, n_in)), np.zeros((2, n_in))
+    a[1, 1], b[1, 1] = -1.0, 1.0
+    perm = np.stack([np.arange(n_out), np.arange(n_out)[::-1]])
+    eng = SurrogateEngine(dims, 2, n_T, max_batch=256, max_rows=2 * n, max_epochs=2, max_sym=2)
+    eng.set_symmetries(src, a, b, perm)
+    eng.set_outputs(0, 5e6, 37.0, 0)
+    xd = torch.tensor(X, dtype=torch.float32, device="cuda")
+    yd = torch.tensor(Y, dtype=torch.float32, device="cuda")
+    eng.train(xd, yd, epochs=1, batch=128, lr=1e-3, seed=1)
+    Xa = np.concatenate([X, X * a[1] + b[1]])
+    Ya = np.concatenate([Y, Y[:, perm[1]]])
+    Za = Ya.copy()
+    Za[:, :n_T] = (Ya[:, :n_T] - 37.0) / (Xa[:, :1] / 5e6)
+    mu = Za.mean(0)
+    n_par = sum(k * m + m for k, m in zip(dims[:-1], dims[1:]))
+    for k in range(2):
+        eng.set_member_params(k, np.zeros(n_par, np.float32))
+    mean = torch.empty(n, n_out, device="cuda")
+    eng.predict(xd, n_T, 1.0, mean)
+    eng.sync()
+    row = np.concatenate([X[:, :1] / 5e6 * np.ones((1, n_T)), np.ones((n, n_out - n_T))], 1)
+    expect = mu * row + np.concatenate([np.full(n_T, 37.0), np.zeros(n_out - n_T)])
+    np.testing.assert_allclose(mean.cpu().numpy(), expect, rtol=2e-5, atol=2e-5 * np.abs(expect).max())
+    # rows beyond max_rows after augmentation are refused
+    big = torch.zeros(2 * n + 128, n_in, device="cuda")
+    with pytest.raises(Exception):
+        eng.train(big, torch.zeros(2 * n + 128, n_out, device="cuda"), epochs=1, batch=128, lr=1e-3, seed=1)
