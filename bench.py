@@ -47,6 +47,8 @@ def make_problem(workload):
         return W.block_h8(n=128)
     if workload == "ellipsoid_t4":
         return W.ellipsoid_t4()
+    if workload == "cube_h8_8":
+        return W.cube_h8(n=8)
     if workload.startswith("block_h8_"):  # block_h8_N (h = 1 mm) or block_h8_N_hXmm
         parts = workload.split("_")
         h = float(parts[3][1:-2]) * 1e-3 if len(parts) > 3 else 1e-3
@@ -278,10 +280,10 @@ def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1, warmup_seconds=10
             "cpu_model": cpu_model(), "nproc": os.cpu_count()}
 
 
-def cpu_sample_subprocess(args, parallel):
-    """cpu_oracle_sample of the bench's workload in a fresh Python process."""
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", args.workload,
-           "--cpu-steps", str(args.cpu_steps), "--cpu-seconds", str(args.cpu_seconds)]
+def cpu_sample_subprocess(args, parallel, workload=None, max_steps=None, seconds=None):
+    """cpu_oracle_sample of a workload (default: the bench's) in a fresh Python process."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload or args.workload,
+           "--cpu-steps", str(max_steps or args.cpu_steps), "--cpu-seconds", str(seconds or args.cpu_seconds)]
     if parallel:
         cmd.append("--cpu-parallel")
     r = subprocess.run(cmd, capture_output=True, text=True, check=True)
@@ -420,10 +422,11 @@ def run_reference(args):
     return 0
 
 
-def small_configs(device, stream, steps=2000):
+def small_configs(device, stream, steps=2000, args=None):
     """The L2-resident workloads (8^3 H8 cube; ~120k-tet ellipsoid): steps/s,
     element-steps/s and the floor bytes per second they stream from L2 (no HBM
-    fraction is claimed for them)."""
+    fraction is claimed for them), beside the FP64 oracle on all host cores
+    (a bounded sample in a child process)."""
     import torch
 
     from paper_2009_10400_b300 import tled
@@ -442,11 +445,41 @@ def small_configs(device, stream, steps=2000):
         sec = ev0.elapsed_time(ev1) * 1e-3
         s.sync()
         s.close()
-        out.append({"workload": prob.name, "elements": prob.ne, "nodes": prob.nn, "steps": steps,
-                    "steps_per_s": steps / sec, "element_steps_per_s": prob.ne * steps / sec,
-                    "floor_bytes_per_step": algorithmic_bytes(prob, len(prob.prony_g)),
-                    "l2_gbs": algorithmic_bytes(prob, len(prob.prony_g)) * steps / sec / 1e9})
+        row = {"workload": prob.name, "elements": prob.ne, "nodes": prob.nn, "steps": steps,
+               "steps_per_s": steps / sec, "element_steps_per_s": prob.ne * steps / sec,
+               "floor_bytes_per_step": algorithmic_bytes(prob, len(prob.prony_g)),
+               "l2_gbs": algorithmic_bytes(prob, len(prob.prony_g)) * steps / sec / 1e9}
+        if args is not None and not args.no_cpu_baseline:
+            name = "cube_h8_8" if prob.npe == 8 else "ellipsoid_t4"
+            row["cpu_oracle"] = cpu_sample_subprocess(args, True, workload=name, max_steps=steps, seconds=6.0)
+        out.append(row)
     return out
+
+
+def cpu_planning_sample(n_scen, n_sub, max_steps=200):
+    """The batched planning workload's CPU reference: the FP64 oracle on all host
+    cores over a stratified subset of the scenarios, each run for at most
+    max_steps steps and its time extrapolated to the scenario's step count."""
+    import oracle
+    from paper_2009_10400_b300 import workloads as W
+
+    scen = W.planning_scenarios(n_scen)
+    sub = list(range(0, len(scen), max(1, len(scen) // n_sub)))[:n_sub]
+    total, el_steps = 0.0, 0
+    for i in sub:
+        p = scen[i]
+        m = oracle.OracleModel(p)
+        s = m.init_state()
+        m.step_parallel(s, 2)  # first touch
+        k = min(max_steps, p.n_steps)
+        t0 = time.perf_counter()
+        m.step_parallel(s, k)
+        total += (time.perf_counter() - t0) * p.n_steps / k
+        el_steps += p.ne * p.n_steps
+    return {"solves_per_s": len(sub) / total, "element_steps_per_s": el_steps / total, "cores": oracle.threads(),
+            "sample": f"{len(sub)} of the {n_scen} scenarios (stratified), each {max_steps} steps timed and its time "
+                      f"extrapolated to its step count, FP64 C oracle, OpenMP on {oracle.threads()} host cores",
+            "kind": "oracle", "extrapolated": True}
 
 
 def planning_bench(args, device, stream):
@@ -850,7 +883,7 @@ def run_gpu(args):
     s.close()
     del s
     torch.cuda.empty_cache()
-    smalls = None if args.no_planning else small_configs(local, stream)
+    smalls = None if args.no_planning else small_configs(local, stream, args=args if rank == 0 and ws == 1 else None)
     precision = None
     if not args.no_precision and rank == 0 and prob.name.startswith("block_h8"):
         precision = precision_leg(args, local, stream)
@@ -858,6 +891,10 @@ def run_gpu(args):
     if not args.no_planning and prob.name.startswith("block_h8"):
         plan = planning_bench(args, local, stream)
         plan["scenario_solves_per_s"] = ws * plan["batched_solves_per_s"]
+        if not args.no_cpu_baseline and rank == 0 and ws == 1:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-planning",
+                                "--plan-scenarios", str(args.plan_scenarios)], capture_output=True, text=True, check=True)
+            plan["cpu_oracle"] = json.loads(r.stdout.strip().splitlines()[-1])
 
     out = None
     if rank == 0:
@@ -940,10 +977,14 @@ def main():
     ap.add_argument("--oracle-every", type=int, default=1000, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-dt", type=float, default=0.0, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)  # child of the cpu_baseline leg
+    ap.add_argument("--cpu-planning", action="store_true", help=argparse.SUPPRESS)  # child: planning CPU reference
     ap.add_argument("--cpu-parallel", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_trajectory:
         oracle_trajectory_child(args.workload, args.steps, args.oracle_every, args.oracle_dt, args.oracle_trajectory)
+        return 0
+    if args.cpu_planning:
+        print(json.dumps(cpu_planning_sample(args.plan_scenarios, 8)))
         return 0
     if args.cpu_sample:
         print(json.dumps(cpu_oracle_sample(make_problem(args.workload), args.cpu_steps, seconds=args.cpu_seconds,
