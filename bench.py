@@ -262,13 +262,14 @@ def cpu_oracle_sample(prob, max_steps, seconds=12.0, warmup=1, warmup_seconds=10
     step = m.step_parallel if parallel else m.step
     cores = oracle.threads() if parallel else 1
     t0 = time.perf_counter()
-    n_warm = 0
+    n_warm, one = 0, float("inf")
     while n_warm < max(1, warmup):
+        t1 = time.perf_counter()
         step(s, 1)
+        one = min(one, time.perf_counter() - t1)  # the first step also starts the thread pool
         n_warm += 1
         if time.perf_counter() - t0 > warmup_seconds:
             break
-    one = (time.perf_counter() - t0) / n_warm
     steps = int(max(1, min(max_steps, seconds // max(one, 1e-9))))
     t0 = time.perf_counter()
     step(s, steps)
@@ -988,7 +989,7 @@ def main():
         return 0
     if args.cpu_sample:
         print(json.dumps(cpu_oracle_sample(make_problem(args.workload), args.cpu_steps, seconds=args.cpu_seconds,
-                                           parallel=args.cpu_parallel)))
+                                           warmup=3, parallel=args.cpu_parallel)))
         return 0
     if args.warmup < 3:
         args.warmup = 3
