@@ -1185,24 +1185,36 @@ int tled_scenario_dt(tled_ctx *c, int32_t idx, double *dt) {
 }
 
 static int capture_graph(tled_ctx *c, int K, cudaGraphExec_t *out);
-// The step graph of K steps (cached per K).  Should the grid-resident launch be refused
-// (a cooperative launch needs every CTA placed at once), the context falls back to the
-// streamed kernels, which compute the same numbers.
+// the step graphs of 1, 2, 4, ..., kGraphChunk steps
+static int capture_graphs(tled_ctx *c) {
+    for (int k = 1; k <= kGraphChunk; k *= 2) {
+        cudaGraphExec_t g;
+        if (int rc = capture_graph(c, k, &g)) return rc;
+    }
+    return TLED_OK;
+}
+// The step graph of K steps, K a power of two up to kGraphChunk.  The first request captures
+// (and uploads) all of them, so that every later call, of any step count, replays cached
+// graphs only: n steps run as the graphs of n's binary digits.  Should the grid-resident
+// launch be refused (a cooperative launch needs every CTA placed at once), the context falls
+// back to the streamed kernels, which compute the same numbers.
 static int get_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     auto it = c->graphs.find(K);
-    if (it != c->graphs.end()) {
-        *out = it->second;
-        return TLED_OK;
+    if (it == c->graphs.end()) {
+        int rc = capture_graphs(c);
+        if (rc && c->coop) {
+            cudaGetLastError();  // clear the refused launch's error
+            drop_graphs(c);
+            c->coop = false;
+            c->coop_ok = false;
+            rc = capture_graphs(c);
+        }
+        if (rc) return rc;
+        it = c->graphs.find(K);
+        if (it == c->graphs.end()) return fail(c, TLED_E_STATE, "no step graph for this chunk size");
     }
-    int rc = capture_graph(c, K, out);
-    if (rc && c->coop) {
-        cudaGetLastError();  // clear the refused launch's error
-        drop_graphs(c);
-        c->coop = false;
-        c->coop_ok = false;
-        rc = capture_graph(c, K, out);
-    }
-    return rc;
+    *out = it->second;
+    return TLED_OK;
 }
 static int capture_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     auto it = c->graphs.find(K);
@@ -1234,6 +1246,11 @@ static int capture_graph(tled_ctx *c, int K, cudaGraphExec_t *out) {
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    e = cudaGraphUpload(exec, c->stream);  // the first replay then starts at once
+    if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return cuda_fail(c, e, "cudaGraphUpload");
+    }
     c->graphs[K] = exec;
     *out = exec;
     return TLED_OK;
@@ -1250,7 +1267,8 @@ static int run_steps(tled_ctx *c, int64_t n, int64_t *done) {
         int64_t seg = std::min<int64_t>(n - ran, end == INT64_MAX ? INT64_MAX : end - c->step);
         if (int rc = set_active(c, ranks)) return rc;
         while (seg > 0) {
-            const int K = (int)std::min<int64_t>(seg, kGraphChunk);
+            int K = kGraphChunk;  // the largest cached chunk that fits
+            while (K > seg) K >>= 1;
             cudaGraphExec_t g;
             if (int rc = get_graph(c, K, &g)) return rc;
             CUDA_TRY(c, cudaGraphLaunch(g, c->stream));
