@@ -57,10 +57,15 @@ def make_problem(workload):
 
 
 def probe_lattice(prob, n):
-    """n^3 probe points on a lattice spanning the inner 80 % of the mesh's box."""
-    lo, hi = prob.X.min(0), prob.X.max(0)
-    g = [np.linspace(lo[j] + 0.1 * (hi[j] - lo[j]), hi[j] - 0.1 * (hi[j] - lo[j]), n) for j in range(3)]
-    return np.stack(np.meshgrid(*g, indexing="ij"), -1).reshape(-1, 3)
+    """n^3 probe points: on a block, a lattice spanning the inner 80 % of its box; on
+    any other mesh (whose box holds points outside it), the centroids of n^3
+    elements spread evenly over the element order."""
+    if prob.name.startswith("block_h8"):
+        lo, hi = prob.X.min(0), prob.X.max(0)
+        g = [np.linspace(lo[j] + 0.1 * (hi[j] - lo[j]), hi[j] - 0.1 * (hi[j] - lo[j]), n) for j in range(3)]
+        return np.stack(np.meshgrid(*g, indexing="ij"), -1).reshape(-1, 3)
+    idx = np.linspace(0, prob.ne - 1, min(n ** 3, prob.ne)).astype(np.int64)
+    return prob.X[prob.conn[idx]].mean(1)
 
 
 def algorithmic_bytes(prob, n_prony):
