@@ -941,7 +941,9 @@ def run_gpu(args):
                                    % args.roofline_steps,
                          "tile_kernel_ms": k_tile / args.roofline_steps,
                          "shared_kernel_ms": k_sh / args.roofline_steps,
-                         "tile_share": k_tile / (k_tile + k_sh), "peak_source": src},
+                         "tile_share": k_tile / (k_tile + k_sh), "peak_source": src,
+                         **({} if workload_config(prob)["l2"].startswith("inputs larger") else
+                            {"note": "L2-resident working set: no HBM fraction is claimed for it"})},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(src_host.numel() * 8),
                     "d2h_bytes_per_step": int(P_host[0].numel() * 8), "steps": n_e2e,
                     "note": "every step: tled_set_heat_sources from pinned host, tled_step(1), tled_get_probes "
