@@ -582,7 +582,8 @@ def run_surrogate(args):
     sur = surrogate.Surrogate(n_out=2 * P, width=512, depth=6, members=args.sur_members, max_batch=4096,
                               symmetric=True, grid=n, max_rows=n_sym * n_train, max_epochs=max(64, args.sur_epochs))
     t0 = time.perf_counter()
-    hist = sur.fit(Q[tr], Y[tr], epochs=args.sur_epochs, batch=256, lr=1e-3, seed=0)
+    hist = sur.fit(Q[tr], Y[tr], epochs=args.sur_epochs, batch=256, lr=1e-3, seed=0,
+                   lr_end=args.sur_lr_end if args.sur_lr_end > 0 else None)
     torch.cuda.synchronize()
     fit_s = time.perf_counter() - t0
     n_train_steps = args.sur_members * args.sur_epochs * (n_sym * n_train // 256)
@@ -684,7 +685,9 @@ def run_surrogate(args):
                        "effective_solves_per_s": (ev.stop - ev.start) / info["seconds"]},
         "speedup_vs_solver": (Bq / inf_s) / solver_rate,
         "training": f"{args.sur_epochs} epochs over the training scenarios augmented by the cube's {n_sym} "
-                    f"reflections ({n_sym * n_train} rows), batch 256, Adam lr 1e-3, each member from its own "
+                    f"reflections ({n_sym * n_train} rows), batch 256, Adam lr 1e-3"
+                    + (f" decayed along a cosine to {args.sur_lr_end:g}" if args.sur_lr_end > 0 else "")
+                    + ", each member from its own "
                     "seeded initialisation and permutations, members side by side (one CUDA graph per epoch)",
     }
     print(json.dumps(line))
@@ -990,6 +993,7 @@ def main():
     ap.add_argument("--sur-chunk", type=int, default=512)
     ap.add_argument("--sur-members", type=int, default=5)
     ap.add_argument("--sur-epochs", type=int, default=50)
+    ap.add_argument("--sur-lr-end", type=float, default=1e-5, help="cosine learning-rate decay target (0: constant)")
     ap.add_argument("--sur-tol", type=float, default=1.0)
     ap.add_argument("--sur-coverage", type=float, default=1.0)
     ap.add_argument("--sur-cal-margin", type=float, default=0.8)

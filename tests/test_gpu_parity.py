@@ -231,6 +231,28 @@ def test_deterministic_bitwise():
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("streamed", [True, False])
+def test_any_split_of_the_steps_is_bitwise_the_same(streamed):
+    """A call of n steps replays the cached graphs of n's binary digits (and of
+    32-step chunks): 69 steps in one call, one step at a time, and as 5 + 64 give
+    bitwise the same state, in the streamed and in the resident mode."""
+    tled = _tled()
+    prob = W.block_h8(n=12, h=4e-3)
+    flags = tled.default_flags(prob) | (tled.STREAMED if streamed else 0)
+    outs = []
+    for split in ([69], [1] * 69, [5, 64]):
+        s = tled.Solver.from_problem(prob, flags=flags, tile_elems=64)
+        assert (s.resident or s.grid_resident) == (not streamed)
+        for n in split:
+            s.step(n)
+        s.sync()
+        outs.append((s.displacement(), s.temperature(), s.damage()))
+    assert np.abs(outs[0][0]).max() > 0
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+
+
 def test_brick_kernel_matches_general_h8():
     """An axis-aligned H8 block (vanishing reference hourglass projections,
     diagonal J0^-1) takes the brick kernel, which drops those terms and the

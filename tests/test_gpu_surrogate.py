@@ -102,7 +102,7 @@ def test_surrogate_answers_at_one_kelvin():
     tr, cal, ev = slice(0, n_tr), slice(n_tr, n_tr + n_cal), slice(n_tr + n_cal, n_tr + n_cal + n_ev)
     sur = surrogate.Surrogate(n_out=2 * P, width=256, depth=4, members=4, max_batch=4096, symmetric=True, grid=n,
                               max_rows=16 * n_tr)
-    sur.fit(Q[tr], Y[tr], epochs=20, batch=128, lr=2e-3, seed=1)
+    sur.fit(Q[tr], Y[tr], epochs=20, batch=128, lr=2e-3, seed=1, lr_end=1e-5)
     mean, std = sur.predict(Q[ev])
     err_ev = np.abs(mean[:, :P] - T[ev]).max(1)
     sp_ev = std[:, :P].max(1)
