@@ -90,6 +90,8 @@ struct tled_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    bool l2_set = false;         // this context raised the persisting-L2 set-aside (restored on destroy)
+    size_t l2_prev = 0;          // ... from this value
     std::string err;
     bool batch = false;
     std::vector<Scenario> sc;
@@ -190,6 +192,10 @@ Layout make_layout(const tled_ctx *c) {
     bool any_ubar = false;
     for (auto &s : c->sc) any_ubar |= !s.ubar.empty();
     L.xu = take(16 * nn);
+    // the partial sums directly after (u, theta): with the shared nodes' entries, which sit at
+    // the end of xu, they form one range for the L2 persistence window (tled_init)
+    // small problems (grid-resident candidates) get a second buffer of partial sums
+    L.partials = take(16 * (size_t)p.n_partials * (p.n_tiles <= kCoopTilesMax ? 2 : 1));
     L.lo = take(16 * nn);
     L.vel = take(16 * nn);
     L.X0 = take(16 * nn);
@@ -200,8 +206,6 @@ Layout make_layout(const tled_ctx *c) {
     L.tile_info = take(4 * p.tile_info.size());
     L.tile_shared = take(4 * p.tile_shared.size());
     L.pattern = take(2 * p.patterns.size());
-    // small problems (grid-resident candidates) get a second buffer of partial sums
-    L.partials = take(16 * (size_t)p.n_partials * (p.n_tiles <= kCoopTilesMax ? 2 : 1));
     L.sh_rowptr = take(4 * p.sh_rowptr.size());
     L.part_pos = take(4 * p.part_pos.size());
     L.scn = take(sizeof(ScenDev) * ns);
@@ -672,6 +676,47 @@ const char *tled_status_string(int code) {
     }
 }
 
+// Persisting-L2 window of the streamed step: the shared nodes' (u, theta) and the partial sums,
+// which the tile kernel writes and the shared-node kernel reads back within the step, and which
+// the tiles around a shared node read several times (the rest of the step streams ~15x more
+// bytes through L2 and would evict them).  The set-aside is this process's CUDA context limit;
+// the previous value comes back when the context is destroyed.
+void release_l2(tled_ctx *c) {
+    if (!c->l2_set) return;
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, c->l2_prev);
+    c->l2_set = false;
+}
+void setup_l2(tled_ctx *c, tled::StepArgs &A) {
+    A.l2_base = nullptr;
+    A.l2_bytes = 0;
+    A.l2_hit = 0.f;
+    const Plan &p = c->plan;
+    if (p.n_shared <= 0) return;
+    int max_set = 0, max_win = 0;
+    if (cudaDeviceGetAttribute(&max_set, cudaDevAttrMaxPersistingL2CacheSize, c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, c->device) != cudaSuccess ||
+        max_set <= 0 || max_win <= 0)
+        return;
+    char *lo = c->ws + c->L.xu + 16 * (size_t)p.n_interior;
+    char *hi = c->ws + c->L.partials + 16 * (size_t)p.n_partials;
+    const size_t win = std::min<size_t>((size_t)(hi - lo), (size_t)max_win);
+    const size_t set = std::min<size_t>(win, (size_t)max_set);
+    size_t prev = 0;
+    if (cudaDeviceGetLimit(&prev, cudaLimitPersistingL2CacheSize) != cudaSuccess) return;
+    if (set > prev) {
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, set) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        if (!c->l2_set) c->l2_prev = prev;
+        c->l2_set = true;
+    }
+    A.l2_base = lo;
+    A.l2_bytes = win;
+    A.l2_hit = (float)std::min(1.0, (double)std::max(set, prev) / (double)win);
+}
+
 static int create_ctx(tled_ctx **out, int device, void *cuda_stream, bool batch) {
     if (!out) return TLED_E_ARG;
     *out = nullptr;
@@ -713,6 +758,7 @@ int tled_destroy(tled_ctx *c) {
         cudaSetDevice(c->device);
         drop_graphs(c);
         if (c->cap) cudaStreamDestroy(c->cap);
+        release_l2(c);
     }
     delete c;
     return TLED_OK;
@@ -1078,6 +1124,7 @@ int tled_init(tled_ctx *c, void *dev_workspace, int64_t bytes) {
     A.wide = npe == 4 && p.n_tiles > tled::kTileCtasPerSm * n_sm;
     tled::tile_smem_layout(A, npe);
     CUDA_TRY(c, tled::tile_kernel_setup(A, npe));
+    setup_l2(c, A);
     c->tile_ctas = tled::tile_grid(A, npe, n_sm);
     c->shared_blocks = tled::shared_grid(A, n_sm);
     if (c->grid_override > 0) c->tile_ctas = std::min(c->tile_ctas, c->grid_override);

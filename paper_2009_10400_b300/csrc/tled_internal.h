@@ -173,6 +173,10 @@ struct StepArgs {
     int cs_rec, cs_pat, cs_sh, cs_xu, cs_X, cs_lo, cs_vo, cs_nc, cs_slot, cs_total;
     int64_t n_partials;     // partial sums per buffer (the grid-resident mode double-buffers them)
     unsigned int *gbar;
+    // persisting-L2 access window of the streamed step kernels (l2_bytes 0: none)
+    void *l2_base;
+    size_t l2_bytes;
+    float l2_hit;
     // self-test of the tile kernel's own bounded wait: 1 + the tile whose node staging the
     // kernel leaves out (so that the wait for it runs out); 0 = none (every normal launch)
     int stage_skip;

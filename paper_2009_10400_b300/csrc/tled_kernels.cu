@@ -1813,10 +1813,31 @@ int tile_grid(const StepArgs &a, int npe, int n_sm) {
     return std::max(1, std::min(a.n_tiles, per_sm * n_sm));
 }
 
+// a streamed step kernel's launch, with the persisting-L2 window when the context set one
+static cudaError_t launch_step_kernel(void (*kern)(const StepArgs, const int), int grid, int block, size_t smem,
+                                     cudaStream_t s, const StepArgs &a, int k) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    if (a.l2_bytes > 0) {
+        at[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        at[0].val.accessPolicyWindow.base_ptr = a.l2_base;
+        at[0].val.accessPolicyWindow.num_bytes = a.l2_bytes;
+        at[0].val.accessPolicyWindow.hitRatio = a.l2_hit;
+        at[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        at[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, a, k);
+}
+
 cudaError_t launch_tile_step(const StepArgs &a, int n_ctas, int npe, int k, cudaStream_t s) {
     if (a.n_tiles <= 0) return cudaSuccess;
-    tile_kernel(a, npe)<<<n_ctas, kBlock, (size_t)a.sm_total, s>>>(a, k);
-    return cudaGetLastError();
+    return launch_step_kernel(tile_kernel(a, npe), n_ctas, kBlock, (size_t)a.sm_total, s, a, k);
 }
 
 int shared_grid(const StepArgs &a, int n_sm) {
@@ -1828,8 +1849,7 @@ int shared_grid(const StepArgs &a, int n_sm) {
 
 cudaError_t launch_shared_step(const StepArgs &a, int n_blocks, int k, cudaStream_t s) {
     if (a.n_shared <= 0) return cudaSuccess;
-    shared_step_kernel<<<n_blocks, 256, 0, s>>>(a, k);
-    return cudaGetLastError();
+    return launch_step_kernel(shared_step_kernel, n_blocks, 256, 0, s, a, k);
 }
 
 cudaError_t launch_isotherm(const StepArgs &a, int64_t nn, double theta_iso, double *partials, double *out,
