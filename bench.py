@@ -820,6 +820,7 @@ def run_gpu(args):
         ("; H8 brick instance: every element an axis-aligned brick, reference hourglass projections exactly zero"
          if s.brick else "; general H8 instance (TLED_GENERAL_H8)" if args.general_h8 else "")
     info = s.plan_info()
+    l2_window = s.l2_window()
     dt = s.get_dt()[0]
     n_prony = len(prob.prony_g)
 
@@ -929,7 +930,7 @@ def run_gpu(args):
             "plan": {"dt_s": dt, "tiles": info["n_tiles"], "shared_nodes": info["n_shared"],
                      "layout_bytes_per_step": layout_bytes(prob, n_prony, brick),
                      "accumulation": "float-float compensated u and T", "parallelism": f"replicas x{ws}",
-                     "kernels": kernel_desc},
+                     "kernels": kernel_desc, "l2_persisting": l2_window},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
                          "kernel": "tile_step_kernel + shared_step_kernel (one step)",

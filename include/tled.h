@@ -304,6 +304,17 @@ int tled_step_timed(tled_ctx *ctx, int64_t n, double *ms);
  * init).  info has 8 entries. */
 int tled_plan_info(tled_ctx *ctx, int64_t *info);
 
+/* L2 residency of the streamed step (after init): the streamed step kernels are
+ * launched with an access-policy window over the shared nodes' (u, theta) and
+ * the partial sums, which the tile kernel writes and the shared-node kernel reads
+ * back within the step, marked persisting; init raises the CUDA context's
+ * persisting set-aside (cudaLimitPersistingL2CacheSize, a limit of the calling
+ * process's context) to the window's size, capped by the device's maximum, and
+ * tled_destroy puts the previous value back.  out[0] window bytes (0: none, e.g.
+ * no shared nodes), out[1] set-aside bytes, out[2] the window's hit ratio times
+ * 1e6.  An implementation choice of this library, not part of the paper. */
+int tled_l2_window(tled_ctx *ctx, int64_t *out);
+
 /* ---- probes (temperature and damage at points, e.g. a 16^3 lattice) ----
  * Set-up call of a single-scenario context: n points xyz [n][3] (host
  * float64, reference coordinates).  Each point is located in the mesh when

@@ -1518,6 +1518,18 @@ int tled_plan_info(tled_ctx *c, int64_t *info) {
     return TLED_OK;
 }
 
+int tled_l2_window(tled_ctx *c, int64_t *out) {
+    if (!c || !out) return fail(c, TLED_E_ARG, "NULL out");
+    if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");
+    size_t set = 0;
+    CUDA_TRY(c, cudaSetDevice(c->device));
+    CUDA_TRY(c, cudaDeviceGetLimit(&set, cudaLimitPersistingL2CacheSize));
+    out[0] = (int64_t)c->A.l2_bytes;
+    out[1] = (int64_t)set;
+    out[2] = (int64_t)std::llround(1e6 * (double)c->A.l2_hit);
+    return TLED_OK;
+}
+
 int tled_get_stats(tled_ctx *c, tled_stats *s) {
     if (!c || !s) return fail(c, TLED_E_ARG, "NULL stats");
     if (!c->inited) return fail(c, TLED_E_STATE, "call tled_init first");

@@ -100,6 +100,7 @@ _SIGS = {
     "tled_step_timed": ([C.c_void_p, C.c_int64, _dp], C.c_int),
     "tled_get_stats_noalloc": ([C.c_void_p, C.c_int32, C.c_void_p], C.c_int),
     "tled_plan_info": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
+    "tled_l2_window": ([C.c_void_p, C.POINTER(C.c_int64)], C.c_int),
     "tled_set_probes": ([C.c_void_p, C.c_int64, _dp], C.c_int),
     "tled_get_probes": ([C.c_void_p, C.c_void_p, C.c_int], C.c_int),
     "tled_batch_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_void_p], C.c_int),
@@ -371,6 +372,12 @@ class Solver:
 
     def plan_info(self) -> dict:
         return plan_info(self.h, self._check)
+
+    def l2_window(self) -> dict:
+        """The streamed step's persisting-L2 window: bytes, the context's set-aside, hit ratio."""
+        out = (C.c_int64 * 3)()
+        self._check(lib().tled_l2_window(self.h, out))
+        return {"window_bytes": int(out[0]), "set_aside_bytes": int(out[1]), "hit_ratio": out[2] / 1e6}
 
     def selftest_wait(self, which: int) -> int:
         """Run the bounded-wait self-test (0: mbarrier, 1: grid barrier); returns the

@@ -410,3 +410,25 @@ def test_subcycled_trajectory_matches_oracle(n_sub):
         assert c["e_u"] <= TOL_E and c["e_theta"] <= TOL_E and c["d_abs"] <= TOL_DAMAGE, c
     print(f"subcycled n_sub={n_sub}", c)
     assert s.T.max() - p.T0 > 0.05 and np.abs(s.u).max() > 1e-9
+
+
+def test_l2_window_is_set_and_the_limit_restored():
+    """The streamed step's persisting-L2 window covers the shared nodes' (u, theta)
+    and the partial sums; the context's persisting set-aside is raised for it
+    and put back when the library context is destroyed."""
+    from cuda.bindings import runtime as rt
+    tled = _tled()
+    lim = rt.cudaLimit.cudaLimitPersistingL2CacheSize
+    err, before = rt.cudaDeviceGetLimit(lim)
+    assert err == rt.cudaError_t.cudaSuccess
+    prob = W.block_h8(n=12, h=4e-3)
+    s = tled.Solver.from_problem(prob, flags=tled.default_flags(prob) | tled.STREAMED, tile_elems=64)
+    info, w = s.plan_info(), s.l2_window()
+    assert info["n_shared"] > 0
+    assert w["window_bytes"] >= 16 * (info["n_shared"] + info["n_partials"])
+    assert w["set_aside_bytes"] > 0 and 0.0 < w["hit_ratio"] <= 1.0
+    s.step(10)
+    s.sync()
+    s.close()
+    err, after = rt.cudaDeviceGetLimit(lim)
+    assert err == rt.cudaError_t.cudaSuccess and after == before
