@@ -1109,7 +1109,7 @@ __global__ void __launch_bounds__(kResBlock, 1) resident_step_kernel(const StepA
         __syncthreads();
         for (int j0 = 0; j0 < D.n_t; j0 += kResLanes) {
             const int j = j0 + lane;
-            const bool on = j < D.n_t;  // this lane has a tile in this round
+            const bool on = j < D.n_t;  // this lane has a tile in this pass
             char *blk = smem + A.rs_tiles + (on ? j : j0) * A.rs_tile;
             const int *ti = reinterpret_cast<const int *>(blk + A.rt_info);
             const int ne_t = on ? ti[0] : 0, q0 = on ? ti[1] : 0, n_int = on ? ti[2] : 0, nl = on ? ti[3] : 0;
