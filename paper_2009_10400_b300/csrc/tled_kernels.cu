@@ -755,21 +755,46 @@ __device__ __forceinline__ void stage_elem(const StepArgs &A, int t, char *buf, 
     bulk_g2s(buf, A.elem_rec + (int64_t)t * A.rec_bytes, rb, bar);
     if (vb) bulk_g2s(buf + rb, A.visc + (int64_t)t * (vb / 4), vb, bar);
 }
-// structure record, interior (u, theta, X0) and shared-node lists (global index, partial
-// position; the lists start on 16-byte boundaries, the copy is rounded up to 4 entries) of tile T
+// structure record and interior (u, theta, X0) of tile T; the record is left out when the
+// buffer already holds it (have_pat: the previous tile named the same record, the norm in
+// block and voxel meshes, whose tiles share a few records)
 template <int NPE>
-__device__ __forceinline__ void stage_nodes(const StepArgs &A, const TileInfo &T, char *smem, uint64_t *bar) {
-    const uint32_t cb = (uint32_t)pattern_u16(NPE ? NPE : T.npe) * 2;
-    const uint32_t sb = 4u * (uint32_t)((T.nl - T.n_int + 3) & ~3);
-    mbar_expect_tx(bar, cb + 32u * T.n_int + 2u * sb);
-    bulk_g2s(smem + A.sm_pat, A.pattern + (int64_t)T.pat * A.pat_stride, cb, bar);
+__device__ __forceinline__ void stage_nodes(const StepArgs &A, const TileInfo &T, char *smem, uint64_t *bar,
+                                            bool have_pat = false) {
+    const uint32_t cb = have_pat ? 0u : (uint32_t)pattern_u16(NPE ? NPE : T.npe) * 2;
+    mbar_expect_tx(bar, cb + 32u * T.n_int);
+    if (cb) bulk_g2s(smem + A.sm_pat, A.pattern + (int64_t)T.pat * A.pat_stride, cb, bar);
     if (T.n_int > 0) {
         bulk_g2s(smem + A.sm_xu, A.xu + T.ib, 16u * T.n_int, bar);
         bulk_g2s(smem + A.sm_X, A.X0 + T.ib, 16u * T.n_int, bar);
     }
+}
+// shared-node lists of tile T (global index, partial position; they start on 16-byte
+// boundaries, the copy is rounded up to 4 entries) into list buffer b: two buffers, so that
+// the next tile's lists arrive while this tile still reads its own
+template <int NPE>
+__device__ __forceinline__ int *list_buf(const StepArgs &A, char *smem, int b) {
+    return reinterpret_cast<int *>(smem + A.sm_sh) + b * 2 * max_local(NPE);
+}
+template <int NPE>
+__device__ __forceinline__ void stage_lists(const StepArgs &A, const TileInfo &T, char *smem, int b, uint64_t *bar) {
+    const uint32_t sb = 4u * (uint32_t)((T.nl - T.n_int + 3) & ~3);
+    mbar_expect_tx(bar, 2u * sb);  // 0 bytes: the arrival alone completes the phase
     if (sb) {
-        bulk_g2s(smem + A.sm_sh, A.tile_shared + T.sh_off, sb, bar);
-        bulk_g2s(smem + A.sm_sh + 4 * max_local(NPE), A.part_pos + T.sh_off, sb, bar);
+        int *lb = list_buf<NPE>(A, smem, b);
+        bulk_g2s(lb, A.tile_shared + T.sh_off, sb, bar);
+        bulk_g2s(lb + max_local(NPE), A.part_pos + T.sh_off, sb, bar);
+    }
+}
+// the shared nodes' (u, theta) (and, for general elements, X0) of tile T by 16-byte
+// asynchronous copies (mostly L2 hits), from list buffer lb; completion by cp_async_wait_all
+template <int NPE, bool BRICK>
+__device__ __forceinline__ void gather_shared(const StepArgs &A, const TileInfo &T, const int *lb, float4 *s_xu,
+                                              float4 *s_X) {
+    for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
+        const int64_t g = lb[l - T.n_int];
+        cp_async16(&s_xu[l], &A.xu[g]);
+        if constexpr (!BRICK) cp_async16(&s_X[l], &A.X0[g]);  // bricks: only interior X0 is read
     }
 }
 // warm L2 with tile t's streams
@@ -822,12 +847,11 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
     __shared__ ScenStep S;
     __shared__ int s_abort;
     const uint16_t *s_pat = reinterpret_cast<const uint16_t *>(smem + A.sm_pat);  // structure record
-    const int *s_shg = reinterpret_cast<const int *>(smem + A.sm_sh);  // shared node -> global index
-    const int *s_ppos = s_shg + max_local(NPE);                        // shared node -> partial position
     float4 *s_xu = reinterpret_cast<float4 *>(smem + A.sm_xu);
     float4 *s_X = reinterpret_cast<float4 *>(smem + A.sm_X);
     float4 *ns = reinterpret_cast<float4 *>(smem + A.sm_ns);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);  // [0] element buffer, [2] nodes, [3] node state
+    // [0] element buffer, [1] shared-node lists, [2] structure record and interior nodes, [3] node state
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + A.sm_bar);
     const int G = gridDim.x;
 
     const int n_tiles = min(*A.n_active, A.n_tiles);  // tiles of unfinished scenarios form a prefix
@@ -844,9 +868,16 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
         if ((int)blockIdx.x < n_tiles) {
             stage_elem(A, blockIdx.x, smem, &bar[0]);
             if (A.stage_skip != 1 + (int)blockIdx.x) stage_nodes<NPE>(A, T, smem, &bar[2]);
+            stage_lists<NPE>(A, T, smem, 0, &bar[1]);
         }
     }
     __syncthreads();  // barrier init visible to all
+    // the first tile's shared nodes; a thread reads a list only once it has seen its copy complete
+    bool ok1 = true;
+    if ((int)blockIdx.x < n_tiles) {
+        ok1 = mbar_wait(&bar[1], 0);
+        if (ok1) gather_shared<NPE, BRICK>(A, T, list_buf<NPE>(A, smem, 0), s_xu, s_X);
+    }
     uint32_t ph_s = 0;
     int i = 0, cur_scn = -1;
     for (int t = blockIdx.x; t < n_tiles; t += G, i++) {
@@ -872,19 +903,13 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
             prepare_scen(A, scn, k, S, threadIdx.x, kBlock);
             cur_scn = scn;
         }
-        // ---- 1. structure record, interior nodes and shared-node lists (bulk copies); then the
-        //         shared nodes' (u, theta, X0) by 16-byte asynchronous copies (mostly L2 hits).
-        //         A thread reads the shared-node list only once it has seen that copy complete.
+        const int *s_shg = list_buf<NPE>(A, smem, i & 1);  // shared node -> global index
+        const int *s_ppos = s_shg + max_local(NPE);        // shared node -> partial position
+        // ---- 1. structure record and interior nodes, element record (bulk copies); the shared
+        //         nodes' gathers were issued with those copies (or before the loop)
         const bool ok2 = mbar_wait(&bar[2], i & 1);
-        if (ok2) {
-            for (int l = T.n_int + threadIdx.x; l < T.nl; l += kBlock) {
-                const int64_t g = s_shg[l - T.n_int];
-                cp_async16(&s_xu[l], &A.xu[g]);
-                if constexpr (!BRICK) cp_async16(&s_X[l], &A.X0[g]);  // bricks: only interior X0 is read
-            }
-        }
         const bool ok0 = mbar_wait(&bar[0], i & 1);
-        if (!(ok0 && ok2)) {
+        if (!(ok0 && ok2 && ok1)) {
             atomicOr(A.status, kStatusTimeout);
             s_abort = 1;
         }
@@ -904,11 +929,13 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
             if (threadIdx.x == 0) {
                 mbar_wait(&bar[0], i & 1);
                 mbar_wait(&bar[2], i & 1);
+                mbar_wait(&bar[1], i & 1);
             }
             return;
         }
         if (threadIdx.x == 0) {
             fence_proxy_async();
+            if (has_next) stage_lists<NPE>(A, Tn, smem, (i + 1) & 1, &bar[1]);  // the other buffer is free
             if (ns_smem) {
                 mbar_expect_tx(&bar[3], 48u * T.n_int);
                 bulk_g2s(ns, A.lo + T.ib, 16u * T.n_int, &bar[3]);
@@ -950,17 +977,24 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
             }
         }
         __syncthreads();
-        if (s_abort) {  // a node-state copy timed out: wait (bounded) for it, then leave
-            if (threadIdx.x == 0) mbar_wait(&bar[3], ph_s);
+        if (s_abort) {  // a node-state copy timed out: wait (bounded) for it and the next lists, then leave
+            if (threadIdx.x == 0) {
+                mbar_wait(&bar[3], ph_s);
+                if (has_next) mbar_wait(&bar[1], (i + 1) & 1);
+            }
             return;
         }
         ph_s ^= (uint32_t)ns_smem;
-        // ---- 5. stage the next tile's element record (into the consumed slot buffer),
-        //         structure record, interior nodes and shared-node lists
-        if (threadIdx.x == 0 && has_next) {
-            fence_proxy_async();
-            stage_elem(A, t + G, smem, &bar[0]);
-            stage_nodes<NPE>(A, Tn, smem, &bar[2]);
+        // ---- 5. stage the next tile's element record (into the consumed slot buffer), structure
+        //         record and interior nodes, and gather its shared nodes at the same time
+        if (has_next) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async();
+                stage_elem(A, t + G, smem, &bar[0]);
+                stage_nodes<NPE>(A, Tn, smem, &bar[2], Tn.pat == T.pat);
+            }
+            ok1 = mbar_wait(&bar[1], (i + 1) & 1);
+            if (ok1) gather_shared<NPE, BRICK>(A, Tn, list_buf<NPE>(A, smem, (i + 1) & 1), s_xu, s_X);
         }
         T = Tn;
         scn = scn_n;
@@ -1612,8 +1646,8 @@ void tile_smem_layout(StepArgs &a, int npe) {
     off = align128(off + kNsMax * 48);
     a.sm_pat = off;
     off = align128(off + pattern_u16(npe) * 2);
-    a.sm_sh = off;
-    off = align128(off + 2 * max_local(npe) * 4);
+    a.sm_sh = off;  // two list buffers of (global index, partial position)
+    off = align128(off + 4 * max_local(npe) * 4);
     a.sm_xu = off;
     off = align128(off + max_local(npe) * 16);
     a.sm_X = off;
