@@ -309,7 +309,8 @@ int tled_plan_info(tled_ctx *ctx, int64_t *info);
  * the partial sums, which the tile kernel writes and the shared-node kernel reads
  * back within the step, marked persisting; init raises the CUDA context's
  * persisting set-aside (cudaLimitPersistingL2CacheSize, a limit of the calling
- * process's context) to the window's size, capped by the device's maximum, and
+ * process's context) to the window's size, capped by the device's maximum and by
+ * 40 % of L2 (the hit ratio then covers the capped share of the window), and
  * tled_destroy puts the previous value back.  out[0] window bytes (0: none, e.g.
  * no shared nodes), out[1] set-aside bytes, out[2] the window's hit ratio times
  * 1e6.  An implementation choice of this library, not part of the paper. */

@@ -731,9 +731,6 @@ __device__ __forceinline__ void element_step(const StepArgs &A, const ScenStep &
 // ---------------------------------------------------------------------------
 // tile kernel (persistent: CTA b handles tiles b, b + gridDim.x, ...)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
 
 struct TileInfo {
     int e0, ne_t, ib, n_int, nl, sh_off, pat, npe;  // pat: structure record id
@@ -795,28 +792,6 @@ __device__ __forceinline__ void gather_shared(const StepArgs &A, const TileInfo 
         const int64_t g = lb[l - T.n_int];
         cp_async16(&s_xu[l], &A.xu[g]);
         if constexpr (!BRICK) cp_async16(&s_X[l], &A.X0[g]);  // bricks: only interior X0 is read
-    }
-}
-// warm L2 with tile t's streams
-template <int NPE>
-__device__ void prefetch_tile(const StepArgs &A, int t, const TileInfo &T) {
-    const int npe = NPE ? NPE : T.npe;
-    prefetch_l2(A.elem_rec + (int64_t)t * A.rec_bytes, rec_len(A));
-    const uint32_t vb = visc_tile_bytes(A);
-    if (vb) prefetch_l2(A.visc + (int64_t)t * (vb / 4), vb);
-    prefetch_l2(A.pattern + (int64_t)T.pat * A.pat_stride, (uint32_t)pattern_u16(npe) * 2);
-    if (T.n_int > 0) {
-        const uint32_t nb = 16u * T.n_int;
-        prefetch_l2(A.xu + T.ib, nb);
-        prefetch_l2(A.X0 + T.ib, nb);
-        prefetch_l2(A.lo + T.ib, nb);
-        prefetch_l2(A.vel + T.ib, nb);
-        prefetch_l2(A.nodec + T.ib, nb);
-    }
-    const uint32_t sb = 4u * (uint32_t)((T.nl - T.n_int + 3) & ~3);
-    if (sb) {
-        prefetch_l2(A.tile_shared + T.sh_off, sb);
-        prefetch_l2(A.part_pos + T.sh_off, sb);
     }
 }
 
@@ -881,8 +856,9 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
     uint32_t ph_s = 0;
     int i = 0, cur_scn = -1;
     for (int t = blockIdx.x; t < n_tiles; t += G, i++) {
-        // the records of the next tile (and, for the L2 prefetch, of the one after), loaded
-        // here so that their latency hides behind this tile
+        // the records of the next tile, loaded here so that their latency hides behind this
+        // tile (an L2 prefetch of the tile after next was measured slower: 151.4 against 147.2
+        // us per 128^3 step, the general H8 instance 195.5 against 185.3)
         const bool has_next = t + G < n_tiles;
         TileInfo Tn = T;
         int scn_n = scn;
@@ -890,9 +866,6 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
             Tn = tile_info(A, t + G);
             scn_n = __ldg(A.tile_scn + t + G);
         }
-        const bool has_pf = threadIdx.x == 0 && t + 2 * G < n_tiles;
-        TileInfo Tp = T;
-        if (has_pf) Tp = tile_info(A, t + 2 * G);
         const int npe = NPE ? NPE : T.npe;
         const uint16_t *s_code = s_pat + kTile * npe;  // gather slot offsets
         const uint16_t *s_row = s_code + kTile * npe;   // and their row offsets
@@ -942,7 +915,6 @@ __global__ void __launch_bounds__(kBlock, CPS) tile_step_kernel(const StepArgs A
                 bulk_g2s(ns + T.n_int, A.vel + T.ib, 16u * T.n_int, &bar[3]);
                 bulk_g2s(ns + 2 * T.n_int, A.nodec + T.ib, 16u * T.n_int, &bar[3]);
             }
-            if (has_pf) prefetch_tile<NPE>(A, t + 2 * G, Tp);
         }
         // ---- 3. element pass
         if (active) {
