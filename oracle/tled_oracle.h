@@ -12,6 +12,12 @@
  *
  * Every function below names the equation it follows.  Where the paper is
  * silent or garbled, the reading taken is stated at the point of use.
+ *
+ * Parity unpinned (no value of the paper or closed form fixes them; they are
+ * held only by the invariants the tests check and by oracle-vs-GPU): the H8
+ * hourglass coefficient (reading of the cited stabilisation, no formula in the
+ * paper), the perfusion-unit, source-shape and mass-scaling readings, and whole
+ * multi-thousand-step trajectories.
  */
 #ifndef TLED_ORACLE_H
 #define TLED_ORACLE_H
