@@ -679,7 +679,7 @@ const char *tled_status_string(int code) {
 
 // Persisting-L2 window of the streamed step: the shared nodes' (u, theta) and the partial sums,
 // which the tile kernel writes and the shared-node kernel reads back within the step, and which
-// the tiles around a shared node read several times (the rest of the step streams ~15x more
+// the tiles around a shared node read several times (the rest of the step streams ~10x more
 // bytes through L2 and would evict them).  The set-aside is this process's CUDA context limit;
 // the previous value comes back when the context is destroyed.
 void release_l2(tled_ctx *c) {
