@@ -91,6 +91,14 @@ def test_planning_batch_256_single_step_sampled():
         b.add(p, p.n_steps)
     b.init()
     b.autotune(trial_steps=10)
+    # the persisting-L2 window of this batch is larger than the 40 % of L2 the library sets
+    # aside at most: the hit ratio covers only the capped share
+    from cuda.bindings import runtime as rt
+    err, l2 = rt.cudaDeviceGetAttribute(rt.cudaDeviceAttr.cudaDevAttrL2CacheSize, 0)
+    assert err == rt.cudaError_t.cudaSuccess
+    w = b.l2_window()
+    assert w["window_bytes"] > 0.4 * l2
+    assert 0.0 < w["hit_ratio"] <= 0.4 * l2 / w["window_bytes"] + 1e-6
     states = [W.random_state(p, 100 + i, u_scale=1e-4, n_prony=len(p.prony_g)) for i, p in enumerate(scen)]
     cat = {k: np.concatenate([st[k] for st in states]) for k in ("u", "v", "T", "Omega", "visc")}
     b.set_state(cat["u"], cat["v"], cat["T"], cat["Omega"], cat["visc"], t=0.05, step=5)
