@@ -218,3 +218,33 @@ def test_binding_constants_match_the_header():
         assert getattr(tled, py) == val(c), (py, c)
     assert val("TLED_MODE_RESIDENT") == 1 and val("TLED_MODE_BRICK") == 2
 
+
+
+def test_bench_graph_launch_count():
+    """A call of n steps replays the cached graphs of 32 steps and of the binary
+    digits of the rest: the bench's launch count follows that decomposition."""
+    import bench
+    assert bench.graph_chunks(0) == 0
+    assert bench.graph_chunks(1) == 1
+    assert bench.graph_chunks(20) == 2     # 16 + 4
+    assert bench.graph_chunks(32) == 1
+    assert bench.graph_chunks(69) == 4     # 32 + 32 + 4 + 1
+    assert bench.graph_chunks(500) == 15 + 2  # 15 x 32, then 20 = 16 + 4
+    for n in range(1, 200):
+        full, rest = divmod(n, 32)
+        assert bench.graph_chunks(n) == full + bin(rest).count("1")
+
+
+def test_bench_probe_points_lie_in_the_mesh():
+    """On a block the bench probes a lattice inside the box; on any other mesh it
+    probes element centroids (a lattice over the box would leave the mesh)."""
+    import bench
+    blk = W.block_h8(n=8)
+    q = bench.probe_lattice(blk, 4)
+    lo, hi = blk.X.min(0), blk.X.max(0)
+    assert q.shape == (64, 3) and np.all(q > lo) and np.all(q < hi)
+    cube = W.cube_t4(n=4)
+    q = bench.probe_lattice(cube, 4)
+    assert q.shape == (min(64, cube.ne), 3)
+    cen = cube.X[cube.conn].mean(1)
+    assert all(np.min(np.abs(cen - p).sum(1)) < 1e-12 for p in q)
