@@ -817,7 +817,9 @@ def run_gpu(args):
     flags = tled.default_flags(prob) | (tled.GENERAL_H8 if args.general_h8 else 0)
     s = tled.Solver.from_problem(prob, device=local, stream=stream, probes=probes, flags=flags)
     brick = s.brick
-    kernel_desc = ("resident (one CTA, K steps per launch)" if s.resident else "streamed (tile + shared-node kernels)") + \
+    kernel_desc = ("resident (one CTA, K steps per launch)" if s.resident else
+                   "grid-resident (one cooperative launch of K steps, one CTA per tile)" if s.grid_resident else
+                   "streamed (tile + shared-node kernels)") + \
         ("; H8 brick instance: every element an axis-aligned brick, reference hourglass projections exactly zero"
          if s.brick else "; general H8 instance (TLED_GENERAL_H8)" if args.general_h8 else "")
     info = s.plan_info()
